@@ -1,0 +1,358 @@
+"""Benchmark of one full FMM velocity evaluation (Fig. 1 stages 1-10) on GB300.
+
+Default workload: N = 2^20 uniform particles in [0, 1)^2, gamma ~ N(0, 1)/N, sigma = 0.5/sqrt(N), depth 7,
+p = 17, precision form (FP32 near field, FP32/FP64 sweep), CUDA-graph replay. One step = one evaluation on
+inputs resident in HBM; L2 is flushed (a 256 MiB write) before every timed step, outside the timed events.
+
+Prints ONE JSON line (rank 0). Extra keys: roofline of the dominant kernel (near-field P2P), cpu_baseline
+(the FP64 oracle on the host cores), e2e (the host-buffer entry point with copies inside the timed region),
+exposed sweep time, FP64-form throughput, accuracy of the precision form, clocks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload uniform_1m|patches_16m]
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mparticles/s per FMM eval @ rel-err ≤1e-6 (FP32 form vs FP64); exposed sweep ms"
+P2P_FLOPS_PER_PAIR = 22  # §3 of the paper
+SMS, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_GHZ / 1000.0  # 80.5 TFLOP/s at the maximum SM clock
+
+
+def workload(name: str):
+    import fmm_inputs as fi
+
+    if name == "uniform_1m":
+        return fi.uniform_1m(), "N=2^20 uniform in [0,1)^2, gamma~N(0,1)/N, sigma=0.5/sqrt(N), depth 7, p=17"
+    if name == "patches_16m":
+        return fi.patches_16m(), ("N=2^24 from 8 Gaussian patches (std 0.05, circulations +-1), sigma=0.5/sqrt(N), "
+                                  "uniform depth 9, p=20")
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for r in csv.reader(fh):
+                if len(r) >= 9:
+                    rows.append([c.strip() for c in r])
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def timed_steps(fn, steps: int, flush, stream, stage_times=None):
+    """Per-step device time (ms) with CUDA events on the launching stream; L2 flushed before each step."""
+    import torch
+
+    ms, p2p = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        if stage_times is not None:
+            t = stage_times()
+            if len(t) >= 2:
+                p2p.append(t[1])
+    return ms, p2p
+
+
+def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
+    import numpy as np
+    import torch
+
+    from paper_1008_2410_gb300 import api
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+
+        dist = dist_
+    w, desc = workload(args.workload)
+    n = w.n
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    f = api.FMM(w.depth, w.p, w.sigma, precision=args.precision, domain=w.domain, graph=True)
+    f.set_timing(True)
+    u = torch.empty_like(x)
+    v = torch.empty_like(x)
+    step = lambda: f.velocity(x, y, g, u, v)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = f.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, p2p_ms = timed_steps(step, args.steps, flush, stream, f.stage_times)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = f.kernel_launches() - launches0
+    clk = clocks.stop()
+    total = sum(ms)
+    if dist:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    ms_per_step = total / args.steps
+    value = world * n / (ms_per_step / 1e3) / 1e6
+
+    out = {"metric": METRIC, "value": value, "unit": "Mparticles/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64 (precision form)" if args.precision == "mixed" else "f64",
+           "data": "synthetic (seeded; the paper uses no dataset)",
+           "config": {"workload": f"{args.workload}: {desc}", "precision": args.precision,
+                      "l2": "flushed before every timed step (256 MiB write, outside the timed events)",
+                      "graph": True, "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+           "gpu_launches": int(launches), "clocks": clk}
+    if rank != 0 and world > 1:
+        return None
+    if args.quick:
+        return out
+
+    # exposed sweep: full evaluation minus the near-field-only evaluation (same launch configuration)
+    ms_near, _ = timed_steps(lambda: f.velocity_near(x, y, g, u, v), args.steps, flush, stream)
+    ms_far, _ = timed_steps(lambda: f.velocity_far(x, y, g, u, v), args.steps, flush, stream)
+    t_full = statistics.median(ms)
+    t_near = statistics.median(ms_near)
+    t_far = statistics.median(ms_far)
+    f.set_graph(False)
+    f.velocity(x, y, g, u, v)
+    st = f.stage_times()  # [bin, near, up, m2l, l2l, combine, total, overlapped]
+    f.set_graph(True)
+    sweep_alone = max(t_far - st[0] - st[5], 1e-6) if st else None
+    exposed = max(t_full - t_near, 0.0)
+    out["exposed_sweep_ms"] = exposed
+    out["sweep"] = {"full_ms": t_full, "near_only_ms": t_near, "far_only_ms": t_far,
+                    "sweep_alone_ms": sweep_alone,
+                    "hidden_fraction": None if not sweep_alone else max(0.0, 1.0 - exposed / sweep_alone),
+                    "stage_ms_eager": dict(zip(["binning", "near", "up", "m2l", "l2l", "l2p_sum", "total",
+                                                 "fork_to_join"], st))}
+
+    # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
+    f.set_count_pairs(True)
+    f.velocity(x, y, g, u, v)
+    pairs = f.pair_count()
+    f.set_count_pairs(False)
+    p2p_avg = statistics.mean(p2p_ms) if p2p_ms else None
+    achieved = P2P_FLOPS_PER_PAIR * pairs / (p2p_avg / 1e3) / 1e12 if p2p_avg else None
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "p2p_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            import hashlib
+
+            rec = json.load(open(tr_path))
+            src = open(os.path.join(ROOT, "paper_1008_2410_gb300", "csrc", "p2p.cu"), "rb").read()
+            if rec.get("p2p_cu_sha1") == hashlib.sha1(src).hexdigest() and rec.get("workload") == args.workload:
+                traffic = rec.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    out["roofline"] = {"bound": "alu", "kernel": "k_p2p32 (near field, stage 9)" if args.precision == "mixed"
+                       else "k_p2p64 (near field, stage 9)",
+                       "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": traffic,
+                       "pairs_per_launch": pairs, "avg_launch_ms": p2p_avg,
+                       "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+
+    # accuracy of the precision form against the plain FP64 form (same tree, same p) and FP64 throughput
+    if args.precision == "mixed":
+        f64 = api.FMM(w.depth, w.p, w.sigma, precision="fp64", domain=w.domain, graph=True)
+        u64, v64 = f64.velocity(x, y, g)
+        f64.velocity(x, y, g, u64, v64)
+        ms64, _ = timed_steps(lambda: f64.velocity(x, y, g, u64, v64), max(2, min(5, args.steps)), flush, stream)
+        f.velocity(x, y, g, u, v)
+        torch.cuda.synchronize()
+        num = torch.sqrt(((u - u64) ** 2).sum() + ((v - v64) ** 2).sum())
+        den = torch.sqrt((u64**2).sum() + (v64**2).sum())
+        out["rel_err_vs_fp64_form"] = float(num / den)
+        out["fp64_form"] = {"value": n / (statistics.median(ms64) / 1e3) / 1e6, "unit": "Mparticles/s",
+                            "ms_per_step": statistics.median(ms64)}
+        f64.close()
+
+    # end to end through the host-buffer entry point: H2D of x, y, gamma and D2H of u, v inside the timed region
+    xh, yh, gh = (torch.from_numpy(a).pin_memory() for a in (w.x, w.y, w.gamma))
+    uh = torch.empty(n, dtype=torch.float64).pin_memory()
+    vh = torch.empty(n, dtype=torch.float64).pin_memory()
+    f.velocity_host(xh, yh, gh, uh, vh)
+    ke = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        f.velocity_host(xh, yh, gh, uh, vh)
+    te = (time.perf_counter() - t0) / ke
+    out["e2e"] = {"value": n / te / 1e6, "unit": "Mparticles/s", "h2d_bytes_per_step": 3 * 8 * n,
+                  "d2h_bytes_per_step": 2 * 8 * n, "ms_per_step": te * 1e3}
+
+    # the paper's overlap bound (§4) with P = resident warps of this GPU
+    from paper_1008_2410_gb300 import model
+
+    P = SMS * 64
+    out["model"] = {"B_actual": n / 4**w.depth, "B_min_for_overlap": model.min_leaf_occupancy_for_overlap(w.p, n, P),
+                    "P_warps": P, "B_opt": model.b_opt(w.p)}
+
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, u.cpu().numpy(), v.cpu().numpy())
+    f.close()
+    return out
+
+
+def cpu_baseline(w, u_gpu, v_gpu) -> dict:
+    """The FP64 oracle as it stands, on all host cores: one full FMM evaluation of the same workload (or, above
+    2^21 particles, its far field plus near field at 4096 sampled targets), plus accuracy figures of the GPU
+    result against it and against the direct sum at 256 sampled targets."""
+    import numpy as np
+
+    import fmm_inputs as fi
+    import oracle
+
+    oracle.build()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    full = w.n <= (1 << 21)
+    t = None if full else fi.sample_targets(w.n, 4096)
+    t0 = time.perf_counter()
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, targets=t)
+    dt = time.perf_counter() - t0
+    count = w.n if full else 4096
+    ug, vg = (u_gpu, v_gpu) if full else (u_gpu[t], v_gpu[t])
+    err_fmm = float(np.sqrt(np.sum((ug - uo) ** 2 + (vg - vo) ** 2) / np.sum(uo**2 + vo**2)))
+    ts = fi.sample_targets(w.n, 256, seed_index=8)
+    ud, vd = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=ts)
+    err_dir = float(np.sqrt(np.sum((u_gpu[ts] - ud) ** 2 + (v_gpu[ts] - vd) ** 2) / np.sum(ud**2 + vd**2)))
+    return {"value": count / dt / 1e6, "unit": "Mparticles/s", "cores": cores, "kind": "oracle",
+            "sample": ("full evaluation, all targets" if full else
+                       "far field of all particles + near field at 4096 sampled targets; rate = targets/s"),
+            "seconds": dt, "gpu_rel_err_vs_oracle_fmm": err_fmm, "gpu_rel_err_vs_direct_sum_256": err_dir}
+
+
+def run_reference(args, rank: int, world: int) -> dict | None:
+    """The oracle timed on the host cores on this arm's workload and metric; each step is one full oracle FMM
+    evaluation (above 2^21 particles: the far field plus the near field at 4096 sampled targets)."""
+    if rank != 0:
+        return None
+    import fmm_inputs as fi
+    import oracle
+
+    oracle.build()
+    w, desc = workload(args.workload)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    full = w.n <= (1 << 21)
+    t = None if full else fi.sample_targets(w.n, 4096)
+    count = w.n if full else 4096
+    steps = max(1, args.steps)
+    warm = max(0, min(args.warmup, 1))
+    for _ in range(warm):
+        oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, targets=t)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, targets=t)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / steps
+    value = count / (ms / 1e3) / 1e6
+    sample = "full evaluation, all targets" if full else "far field + near field at 4096 sampled targets"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mparticles/s", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; the paper uses no dataset)",
+            "config": {"workload": f"{args.workload}: {desc}", "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "Mparticles/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Mparticles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="uniform_1m", choices=["uniform_1m", "patches_16m"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="main timing only")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+    if out is not None and rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

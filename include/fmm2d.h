@@ -1,0 +1,167 @@
+/*
+ * fmm2d.h -- C ABI of the GB300 (sm_103a) library for one Fast Multipole velocity evaluation of 2D
+ * Gaussian vortex blobs (M. G. Knepley, "Removing the Barrier to Scalability in Parallel FMM").
+ *
+ * What one evaluation computes:
+ *   u_i = sum_{j != i} gamma_j K_sigma(z_i - z_j)                                   (Eq. 7)
+ *   K_sigma(z) = (-v, u) (1 - exp(-|z|^2 / 2 sigma^2)) / (2 pi |z|^2), z = (u, v)    (Eq. 6)
+ * with the paper's FMM split (§2, last paragraph): the exact K_sigma between particles whose finest-level
+ * leaves are equal or adjacent (stage 9 of Fig. 1), and the point-vortex kernel through p-term multipole
+ * and local expansions (§3 coefficients, stages 4-8) for every other pair. Fig. 1's stages map to:
+ *   1 root square (given, or the bounding-box rule below)  2 particle binning into leaves
+ *   3 interaction lists (implicit on the uniform tree)     4 P2M  5 M2M  6 M2L  7 L2L  8 L2P
+ *   9 near-field direct sum (P2P)                          10 sum of near and far parts
+ * Stage 9 runs on the caller's stream while stages 4-7 run concurrently on a second, high-priority stream
+ * (Fig. 1: no dependency between {4,5,6,7} and {9}); stage 8 is fused into stage 10 after the join.
+ *
+ * Conventions for every call:
+ *   - Array arguments of fmm_velocity*, fmm_velocity_adjoint and fmm_velocity_batched are DEVICE pointers
+ *     (cudaMalloc / torch CUDA tensors) of FP64 values, one value per particle, in the caller's order.
+ *     fmm_velocity_host takes HOST pointers instead. The caller owns all arrays; the library never frees or
+ *     keeps them past the call. Outputs are written in the caller's particle order.
+ *   - The handle owns its scratch memory (grown on demand, freed by fmm_destroy), two CUDA streams' worth
+ *     of events, and an optional CUDA graph of the whole evaluation.
+ *   - Calls are asynchronous on the handle's stream (fmm_set_stream; default: the legacy default stream).
+ *     Errors found on the host are returned at once. Errors found on the device (a point outside an explicit
+ *     root square, a non-finite coordinate, an internal bounds check) are returned by fmm_sync or by the next
+ *     call on the handle, as FMM_EINVAL or FMM_EINTERNAL.
+ *   - n == 0 is a no-op that returns FMM_OK.
+ *   - One handle must not be used by two host threads at once.
+ *
+ * Root square and leaves (the paper is silent; these are this library's rules, shared with its tests):
+ *   - default square: centre of the particles' bounding box, side = extent * (1 + 2^-20) (at least 1e-300);
+ *   - leaf column ix = floor((x - x0) * (2^L / S)) in IEEE double, clamped to [0, 2^L - 1] (likewise iy);
+ *     a point on a leaf edge belongs to the upper leaf, x = x0 + S to the last leaf.
+ */
+#ifndef FMM2D_H
+#define FMM2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_ctx *fmm_handle;
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_EINVAL = 1,    /* bad argument, or (device) a point outside the explicit square / non-finite */
+    FMM_ENOMEM = 2,    /* device or pinned-host allocation failed */
+    FMM_ECUDA = 3,     /* a CUDA runtime call failed; fmm_last_error has the CUDA message */
+    FMM_ETIMEOUT = 4,  /* a bounded device-side wait (bulk-copy barrier) ran out */
+    FMM_EINTERNAL = 5  /* a device-side bounds check failed */
+} fmm_status;
+
+typedef enum {
+    FMM_FP64 = 0,  /* plain form: every stage in FP64 */
+    FMM_MIXED = 1  /* precision form: FP32 near field (leaf-relative split coordinates, small-r series,
+                      compensated sums), FP32 P2M/L2P and fine-level M2M/M2L/L2L, FP64 on coarse levels */
+} fmm_precision;
+
+/* Creates a handle. tree_depth L in [0, 12] (4^L leaves; L <= 1 means every pair is near field),
+ * p in [1, 32] expansion terms (§3's t), sigma > 0 the blob core (Eq. 2). *out is set on success. */
+fmm_status fmm_create(int tree_depth, int p, double sigma, fmm_handle *out);
+
+/* Frees the handle and everything it owns. NULL is accepted. Synchronises the handle's streams first. */
+fmm_status fmm_destroy(fmm_handle h);
+
+/* Fixes the root square [x0, x0 + side] x [y0, y0 + side] (side > 0). Points outside it make the
+ * evaluation report FMM_EINVAL. fmm_clear_domain returns to the bounding-box rule. */
+fmm_status fmm_set_domain(fmm_handle h, double x0, double y0, double side);
+fmm_status fmm_clear_domain(fmm_handle h);
+
+/* Chooses the plain FP64 form or the precision form (see fmm_precision). Default FMM_FP64. */
+fmm_status fmm_set_precision(fmm_handle h, fmm_precision mode);
+
+/* In the precision form, levels 2..coarse_level of M2M, M2L and L2L run in FP64 and finer levels in FP32.
+ * Default 4; -1 runs every level in FP32. Ignored by FMM_FP64. */
+fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level);
+
+/* Changes depth, p or sigma of an existing handle (same ranges as fmm_create). */
+fmm_status fmm_set_params(fmm_handle h, int tree_depth, int p, double sigma);
+
+/* Sets the stream every call is ordered on (a cudaStream_t; NULL = legacy default stream). */
+fmm_status fmm_set_stream(fmm_handle h, void *cuda_stream);
+
+/* Enables (1) or disables (0, default) capturing the evaluation into a CUDA graph that later calls with the
+ * same sizes, pointers and parameters replay with one launch. */
+fmm_status fmm_set_graph(fmm_handle h, int enable);
+
+/* Near-field tile shape: targets per thread-block work item and threads per block (0 = automatic).
+ * Set by fmm_autotune; exposed for experiments. */
+fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread);
+
+/* Velocity of n particles (x, y, gamma device FP64 arrays) written to u, v (device FP64). Fig. 1 stages
+ * 1-10 as described at the top of this file. */
+fmm_status fmm_velocity(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                        double *u, double *v);
+
+/* Same result from HOST arrays (pageable or pinned): copies the inputs into handle-owned device memory,
+ * evaluates, copies u, v back and synchronises the stream before returning. */
+fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                             double *u, double *v);
+
+/* The two halves of the FMM split on their own (same conventions as fmm_velocity):
+ *   fmm_velocity_near -- stage 9 only: sum over particles in the same or adjacent leaves, exact K_sigma;
+ *   fmm_velocity_far  -- stages 4-8 only: the expansions' point-vortex field of all other particles.
+ * fmm_velocity == near + far, up to rounding. */
+fmm_status fmm_velocity_near(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                             double *u, double *v);
+fmm_status fmm_velocity_far(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                            double *u, double *v);
+
+/* Adjoint (reverse-mode derivative) of fmm_velocity for a loss L with dL/du = gu, dL/dv = gv (device FP64):
+ * writes dL/dgamma, dL/dx, dL/dy (device FP64; any output may be NULL to skip it). The far field's
+ * transpose is evaluated exactly (the truncated far-field operator of this tree is antisymmetric), so finite
+ * differences of fmm_velocity agree to rounding as long as no particle changes leaf. Always FP64. */
+fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                                const double *gu, const double *gv, double *dgamma, double *dx, double *dy);
+
+/* nsys independent systems in one evaluation (one launch per stage across all systems). offsets (HOST,
+ * nsys + 1 entries, non-decreasing, offsets[0] = 0) delimit each system's particles in the device arrays.
+ * depths (HOST, nsys entries, each in [0, 12]) and sigmas (HOST, nsys entries > 0) may be NULL to use the
+ * handle's depth / sigma for every system. domains (HOST, 3 * nsys: x0, y0, side) may be NULL for the
+ * bounding-box rule per system. p and the precision form are the handle's. */
+fmm_status fmm_velocity_batched(fmm_handle h, int nsys, const int64_t *offsets, const int *depths,
+                                const double *sigmas, const double *domains, const double *x, const double *y,
+                                const double *gamma, double *u, double *v);
+
+/* Waits for all work of the handle and returns the first device-side error since the last check. */
+fmm_status fmm_sync(fmm_handle h);
+
+/* Per-stage device times (ms) of the last evaluation when timing is on (fmm_set_timing(h, 1); not with
+ * graphs): out[0] binning, [1] near field, [2] up sweep (P2M+M2M), [3] M2L, [4] L2L, [5] L2P+sum,
+ * [6] whole evaluation, [7] near field and sweep overlapped (from the fork to the join). Returns the number
+ * of values written (at most cap). */
+fmm_status fmm_set_timing(fmm_handle h, int enable);
+int fmm_stage_times(fmm_handle h, float *out, int cap);
+
+/* Number of ordered near-field pairs (i != j) of the last evaluation's tree (computed on the device when
+ * counting is on: fmm_set_count_pairs(h, 1)). */
+fmm_status fmm_set_count_pairs(fmm_handle h, int enable);
+int64_t fmm_last_pair_count(fmm_handle h);
+
+/* Number of kernels the library launched since the handle was created (graph replays count each kernel
+ * node once per replay). */
+int64_t fmm_kernel_launches(fmm_handle h);
+
+/* Picks depth and near-field tile for the handle's p, sigma and precision by timing fmm_velocity on the given
+ * particles (device arrays, left unchanged; u, v are scratch outputs). Tries depths depth_lo..depth_hi.
+ * The choice is stored in the handle and, when the environment variable FMM2D_TUNE_CACHE names a file,
+ * cached there keyed by (n, p, precision). */
+fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                        double *u, double *v, int depth_lo, int depth_hi);
+fmm_status fmm_get_params(fmm_handle h, int *tree_depth, int *p, double *sigma, int *p2p_threads,
+                          int *p2p_targets_per_thread);
+
+/* Human-readable text of a status, and the last error message recorded on the handle. */
+const char *fmm_status_string(fmm_status s);
+const char *fmm_last_error(fmm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM2D_H */

@@ -76,6 +76,8 @@ def _load():
         lib.oracle_fmm.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int, _D,
                                    ctypes.c_int64, _I64, _D, _D, _I64]
         lib.oracle_fmm.restype = ctypes.c_int
+        lib.oracle_fmm_parts.argtypes = lib.oracle_fmm.argtypes + [ctypes.c_int]
+        lib.oracle_fmm_parts.restype = ctypes.c_int
         lib.oracle_split_direct.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D,
                                             ctypes.c_int64, _I64, _D, _D]
         lib.oracle_split_direct.restype = ctypes.c_int
@@ -205,15 +207,17 @@ def interaction_list_sizes(level: int) -> np.ndarray:
     return out.reshape(1 << level, 1 << level)
 
 
-def fmm(x, y, gamma, sigma: float, depth: int, p: int, domain=None, targets=None):
-    """Serial FMM (Fig. 1). Returns (u, v, near_pairs) at ``targets`` (all particles if None)."""
+def fmm(x, y, gamma, sigma: float, depth: int, p: int, domain=None, targets=None, parts: str = "both"):
+    """Serial FMM (Fig. 1). Returns (u, v, near_pairs) at ``targets`` (all particles if None).
+    parts = "near" (stage 9 only), "far" (stages 4-8 only) or "both"."""
     x, y, g = _f64(x), _f64(y), _f64(gamma)
     n = x.size
     nt, t = _targets(n, targets)
     u, v = np.zeros(nt), np.zeros(nt)
     npairs = ctypes.c_int64(0)
-    rc = _load().oracle_fmm(n, _ptr(x), _ptr(y), _ptr(g), float(sigma), int(depth), int(p), _ptr(_dom(domain)),
-                            nt, _ptr(t, _I64), _ptr(u), _ptr(v), ctypes.byref(npairs))
+    code = {"near": 1, "far": 2, "both": 3}[parts]
+    rc = _load().oracle_fmm_parts(n, _ptr(x), _ptr(y), _ptr(g), float(sigma), int(depth), int(p),
+                                  _ptr(_dom(domain)), nt, _ptr(t, _I64), _ptr(u), _ptr(v), ctypes.byref(npairs), code)
     if rc == -1:
         raise ValueError("point outside the root square")
     if rc != 0:

@@ -476,8 +476,10 @@ static void free_needed(unsigned char **need, int L)
 /* One FMM velocity evaluation (Fig. 1 stages 1-10) at the targets tidx (all particles if NULL; then nt = n).
  * dom = {x0, y0, S} or NULL for the default square. *npairs (if not NULL) receives the number of ordered
  * near-field pairs evaluated (i != j). Returns 0, -1 for a point outside an explicit square, -2 on OOM. */
-int oracle_fmm(int64_t n, const double *x, const double *y, const double *g, double sigma, int L, int p,
-               const double *dom, int64_t nt, const int64_t *tidx, double *u, double *v, int64_t *npairs)
+/* parts: 1 = stage 9 (near field) only, 2 = stages 4-8 (far field) only, 3 = both (the FMM). */
+int oracle_fmm_parts(int64_t n, const double *x, const double *y, const double *g, double sigma, int L, int p,
+                     const double *dom, int64_t nt, const int64_t *tidx, double *u, double *v, int64_t *npairs,
+                     int parts)
 {
     if (npairs)
         *npairs = 0;
@@ -494,7 +496,8 @@ int oracle_fmm(int64_t n, const double *x, const double *y, const double *g, dou
     for (int64_t j = 0; j < n; ++j)
         qim[j] = -g[j] / (2.0 * ORACLE_PI); /* q_j = -i gamma_j / (2 pi) */
     unsigned char **need = mark_needed(&t, nt, tidx);
-    upward_downward(&t, x, y, qre, qim, need);
+    if (parts & 2)
+        upward_downward(&t, x, y, qre, qim, need);
     int nside = 1 << L;
     int64_t pairs = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : pairs)
@@ -503,7 +506,7 @@ int oracle_fmm(int64_t n, const double *x, const double *y, const double *g, dou
         int bx = t.ix[i], by = t.iy[i];
         /* stage 9: near field over the leaf and its neighbours, exact K_sigma */
         double su = 0.0, sv = 0.0;
-        for (int ny = by - 1; ny <= by + 1; ++ny)
+        for (int ny = by - 1; ny <= by + 1 && (parts & 1); ++ny)
             for (int nx = bx - 1; nx <= bx + 1; ++nx) {
                 if (nx < 0 || ny < 0 || nx >= nside || ny >= nside)
                     continue;
@@ -521,7 +524,7 @@ int oracle_fmm(int64_t n, const double *x, const double *y, const double *g, dou
             }
         /* stage 8: far field from the leaf's local expansion */
         double w[2] = {0.0, 0.0};
-        if (L >= 2) {
+        if (L >= 2 && (parts & 2)) {
             cplx c = box_centre(&t, L, bx, by);
             oracle_l2p(p, (double *)(t.loc[L] + ((int64_t)by * nside + bx) * p), x[i] - creal(c), y[i] - cimag(c), w);
         }
@@ -536,6 +539,12 @@ int oracle_fmm(int64_t n, const double *x, const double *y, const double *g, dou
     free(qim);
     tree_free(&t);
     return 0;
+}
+
+int oracle_fmm(int64_t n, const double *x, const double *y, const double *g, double sigma, int L, int p,
+               const double *dom, int64_t nt, const int64_t *tidx, double *u, double *v, int64_t *npairs)
+{
+    return oracle_fmm_parts(n, x, y, g, sigma, L, p, dom, nt, tidx, u, v, npairs, 3);
 }
 
 /* The exact sum the FMM approximates (§2, last paragraph): K_sigma between particles whose leaves are

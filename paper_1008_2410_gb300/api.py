@@ -1,0 +1,221 @@
+"""Python face of the C ABI: an ``FMM`` handle class over torch tensors and ``FMMVelocity``, an
+``autograd.Function`` whose backward is the library's hand-written adjoint.
+
+PyTorch supplies device memory and the current stream only; each method passes raw pointers to the CUDA
+library and every stage of the evaluation runs there. Device tensors must be contiguous float64 on the
+handle's GPU; ``velocity_host`` takes CPU tensors (pinned or pageable) and copies inside the library.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import FMM_FP64, FMM_MIXED, check
+
+
+def _dev(t: torch.Tensor, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _host(t: torch.Tensor, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CPU tensor")
+    return t.data_ptr()
+
+
+class FMM:
+    """One FMM configuration: tree depth L (4^L leaves), p expansion terms, blob core sigma.
+
+    precision: "fp64" (plain form) or "mixed" (precision form). domain: (x0, y0, side) or None for the
+    bounding-box rule. graph: capture and replay the evaluation as a CUDA graph.
+    """
+
+    def __init__(self, depth: int, p: int, sigma: float, precision: str = "fp64", domain=None,
+                 graph: bool = False, coarse_level: int | None = None):
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        st = self._lib.fmm_create(int(depth), int(p), float(sigma), ctypes.byref(h))
+        if st != _lib.FMM_OK:
+            raise _lib.FMMError(st, self._lib.fmm_status_string(st).decode())
+        self.h = h
+        self.set_precision(precision)
+        if domain is not None:
+            self.set_domain(*domain)
+        if graph:
+            self.set_graph(True)
+        if coarse_level is not None:
+            check(self._lib.fmm_set_coarse_level(self.h, int(coarse_level)), self.h)
+
+    # -- configuration
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self._lib.fmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: str) -> None:
+        mode = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
+        check(self._lib.fmm_set_precision(self.h, mode), self.h)
+        self.precision = precision
+
+    def set_domain(self, x0: float, y0: float, side: float) -> None:
+        check(self._lib.fmm_set_domain(self.h, float(x0), float(y0), float(side)), self.h)
+
+    def clear_domain(self) -> None:
+        check(self._lib.fmm_clear_domain(self.h), self.h)
+
+    def set_params(self, depth: int, p: int, sigma: float) -> None:
+        check(self._lib.fmm_set_params(self.h, int(depth), int(p), float(sigma)), self.h)
+
+    def set_graph(self, enable: bool) -> None:
+        check(self._lib.fmm_set_graph(self.h, int(bool(enable))), self.h)
+
+    def set_p2p_tile(self, threads: int, targets_per_thread: int) -> None:
+        check(self._lib.fmm_set_p2p_tile(self.h, int(threads), int(targets_per_thread)), self.h)
+
+    def set_timing(self, enable: bool) -> None:
+        check(self._lib.fmm_set_timing(self.h, int(bool(enable))), self.h)
+
+    def set_count_pairs(self, enable: bool) -> None:
+        check(self._lib.fmm_set_count_pairs(self.h, int(bool(enable))), self.h)
+
+    def params(self) -> dict:
+        d, p, th, kt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        s = ctypes.c_double()
+        check(self._lib.fmm_get_params(self.h, ctypes.byref(d), ctypes.byref(p), ctypes.byref(s), ctypes.byref(th),
+                                       ctypes.byref(kt)), self.h)
+        return {"depth": d.value, "p": p.value, "sigma": s.value, "p2p_threads": th.value,
+                "p2p_targets_per_thread": kt.value}
+
+    def _stream(self) -> None:
+        s = torch.cuda.current_stream()
+        check(self._lib.fmm_set_stream(self.h, ctypes.c_void_p(s.cuda_stream)), self.h)
+
+    # -- evaluations
+    def _call(self, fn, x, y, gamma, u, v):
+        n = x.numel()
+        if u is None:
+            u = torch.empty_like(x)
+        if v is None:
+            v = torch.empty_like(x)
+        for t, nm in ((y, "y"), (gamma, "gamma"), (u, "u"), (v, "v")):
+            if t.numel() != n:
+                raise ValueError(f"{nm} has {t.numel()} elements, expected {n}")
+        self._stream()
+        check(fn(self.h, n, _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"), _dev(u, "u"), _dev(v, "v")), self.h)
+        return u, v
+
+    def velocity(self, x, y, gamma, u=None, v=None):
+        """(u, v) at every particle: the full FMM evaluation (Fig. 1, stages 1-10)."""
+        return self._call(self._lib.fmm_velocity, x, y, gamma, u, v)
+
+    def velocity_near(self, x, y, gamma, u=None, v=None):
+        """Stage 9 alone: K_sigma over particles in the same or adjacent leaves."""
+        return self._call(self._lib.fmm_velocity_near, x, y, gamma, u, v)
+
+    def velocity_far(self, x, y, gamma, u=None, v=None):
+        """Stages 4-8 alone: the expansions' point-vortex field of all non-adjacent leaves."""
+        return self._call(self._lib.fmm_velocity_far, x, y, gamma, u, v)
+
+    def velocity_host(self, x, y, gamma, u=None, v=None):
+        """Same as velocity() for CPU tensors: copies in and out inside the library, synchronous."""
+        n = x.numel()
+        u = torch.empty_like(x) if u is None else u
+        v = torch.empty_like(x) if v is None else v
+        self._stream()
+        check(self._lib.fmm_velocity_host(self.h, n, _host(x, "x"), _host(y, "y"), _host(gamma, "gamma"),
+                                          _host(u, "u"), _host(v, "v")), self.h)
+        return u, v
+
+    def adjoint(self, x, y, gamma, gu, gv, need=(True, True, True)):
+        """Gradient of sum(gu * u + gv * v) w.r.t. (gamma, x, y); entries of ``need`` that are False give None."""
+        n = x.numel()
+        outs = [torch.empty_like(x) if k else None for k in need]
+        self._stream()
+        ptr = [o.data_ptr() if o is not None else None for o in outs]
+        check(self._lib.fmm_velocity_adjoint(self.h, n, _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"),
+                                             _dev(gu, "gu"), _dev(gv, "gv"), ptr[0], ptr[1], ptr[2]), self.h)
+        return tuple(outs)
+
+    def velocity_batched(self, offsets, x, y, gamma, depths=None, sigmas=None, domains=None, u=None, v=None):
+        """Independent systems in one evaluation; offsets (nsys + 1, host ints) delimit them in x, y, gamma."""
+        import numpy as np
+
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        nsys = off.size - 1
+        dep = None if depths is None else np.ascontiguousarray(np.asarray(depths, dtype=np.int32))
+        sig = None if sigmas is None else np.ascontiguousarray(np.asarray(sigmas, dtype=np.float64))
+        dom = None if domains is None else np.ascontiguousarray(np.asarray(domains, dtype=np.float64).reshape(-1))
+        u = torch.empty_like(x) if u is None else u
+        v = torch.empty_like(x) if v is None else v
+        self._stream()
+        check(self._lib.fmm_velocity_batched(
+            self.h, nsys, off.ctypes.data, None if dep is None else dep.ctypes.data,
+            None if sig is None else sig.ctypes.data, None if dom is None else dom.ctypes.data,
+            _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"), _dev(u, "u"), _dev(v, "v")), self.h)
+        return u, v
+
+    def autotune(self, x, y, gamma, depth_lo: int, depth_hi: int) -> dict:
+        u = torch.empty_like(x)
+        v = torch.empty_like(x)
+        self._stream()
+        check(self._lib.fmm_autotune(self.h, x.numel(), _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"),
+                                     _dev(u, "u"), _dev(v, "v"), int(depth_lo), int(depth_hi)), self.h)
+        return self.params()
+
+    # -- diagnostics
+    def sync(self) -> None:
+        check(self._lib.fmm_sync(self.h), self.h)
+
+    def stage_times(self) -> list[float]:
+        buf = (ctypes.c_float * 8)()
+        k = self._lib.fmm_stage_times(self.h, buf, 8)
+        return [buf[i] for i in range(k)]
+
+    def pair_count(self) -> int:
+        return int(self._lib.fmm_last_pair_count(self.h))
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.fmm_kernel_launches(self.h))
+
+
+class FMMVelocity(torch.autograd.Function):
+    """(u, v) = FMM(x, y, gamma) with the library's adjoint as backward (FP64 form for the gradient)."""
+
+    @staticmethod
+    def forward(ctx, x, y, gamma, fmm: FMM):
+        u, v = fmm.velocity(x.contiguous(), y.contiguous(), gamma.contiguous())
+        ctx.save_for_backward(x, y, gamma)
+        ctx.fmm = fmm
+        return u, v
+
+    @staticmethod
+    def backward(ctx, gu, gv):
+        x, y, gamma = ctx.saved_tensors
+        fmm = ctx.fmm
+        gu = torch.zeros_like(x) if gu is None else gu.contiguous()
+        gv = torch.zeros_like(x) if gv is None else gv.contiguous()
+        need = (ctx.needs_input_grad[2], ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        prec = fmm.precision
+        if prec != "fp64":
+            fmm.set_precision("fp64")
+        try:
+            dg, dx, dy = fmm.adjoint(x.contiguous(), y.contiguous(), gamma.contiguous(), gu, gv, need=need)
+        finally:
+            if prec != "fp64":
+                fmm.set_precision(prec)
+        return dx, dy, dg, None
+
+
+def fmm_velocity(x, y, gamma, fmm: FMM):
+    """Differentiable FMM velocity: returns (u, v)."""
+    return FMMVelocity.apply(x, y, gamma, fmm)

@@ -1,0 +1,404 @@
+// binning.cu -- Fig. 1 stages 1-2: root square, leaf keys, counting sort into leaf order, gather of the
+// particle data into the layout the near-field and expansion kernels read.
+//
+// The root square and leaf rule are this library's reading of the paper (which leaves them open): an
+// explicit square, or the particles' bounding box centred with side extent * (1 + 2^-20); the leaf column
+// is floor((x - x0) * (2^L / S)) in IEEE double without FMA contraction, clamped to [0, 2^L - 1].
+// Within a leaf, particles keep the caller's order, so every run gives bit-identical results.
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+// Order-preserving map of doubles onto unsigned integers (for atomicMin / atomicMax).
+__device__ inline unsigned long long ord_of(double d)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ inline double double_of(unsigned long long u)
+{
+    unsigned long long b = (u & 0x8000000000000000ull) ? (u & ~0x8000000000000000ull) : ~u;
+    return __longlong_as_double((long long)b);
+}
+
+// ------------------------------------------------------------------ stage 1: bounding box
+
+__global__ void k_bbox(const SysDev *__restrict__ sys, int nsys, int n, const double *__restrict__ x,
+                       const double *__restrict__ y, unsigned long long *minmax)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = i < n;
+    int k = valid ? (nsys == 1 ? 0 : find_sys_by_particle(sys, nsys, i)) : -1;
+    bool use = valid && !sys[k].explicit_domain && isfinite(x[i]) && isfinite(y[i]);
+    unsigned long long xmn = use ? ord_of(x[i]) : ~0ull, xmx = use ? ord_of(x[i]) : 0ull;
+    unsigned long long ymn = use ? ord_of(y[i]) : ~0ull, ymx = use ? ord_of(y[i]) : 0ull;
+    int k0 = __shfl_sync(0xffffffffu, k, 0);
+    if (__all_sync(0xffffffffu, k == k0 || k < 0)) {
+        for (int o = 16; o > 0; o >>= 1) {
+            xmn = min(xmn, __shfl_xor_sync(0xffffffffu, xmn, o));
+            xmx = max(xmx, __shfl_xor_sync(0xffffffffu, xmx, o));
+            ymn = min(ymn, __shfl_xor_sync(0xffffffffu, ymn, o));
+            ymx = max(ymx, __shfl_xor_sync(0xffffffffu, ymx, o));
+        }
+        if ((threadIdx.x & 31) == 0 && k0 >= 0 && xmx != 0ull) {
+            atomicMin(&minmax[4 * k0 + 0], xmn);
+            atomicMax(&minmax[4 * k0 + 1], xmx);
+            atomicMin(&minmax[4 * k0 + 2], ymn);
+            atomicMax(&minmax[4 * k0 + 3], ymx);
+        }
+    } else if (use) {
+        atomicMin(&minmax[4 * k + 0], xmn);
+        atomicMax(&minmax[4 * k + 1], xmx);
+        atomicMin(&minmax[4 * k + 2], ymn);
+        atomicMax(&minmax[4 * k + 3], ymx);
+    }
+}
+
+// Root square of every system without an explicit one: centre of the box, side = extent * (1 + 2^-20),
+// at least 1e-300. Explicit IEEE operations keep the result identical to a plain C evaluation.
+__global__ void k_domain_finalize(SysDev *sys, int nsys, const unsigned long long *minmax)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsys || sys[k].explicit_domain)
+        return;
+    if (sys[k].np == 0 || minmax[4 * k + 1] == 0ull) {
+        sys[k].x0 = 0.0;
+        sys[k].y0 = 0.0;
+        sys[k].S = 1.0;
+        return;
+    }
+    double xmin = double_of(minmax[4 * k + 0]), xmax = double_of(minmax[4 * k + 1]);
+    double ymin = double_of(minmax[4 * k + 2]), ymax = double_of(minmax[4 * k + 3]);
+    double ex = __dsub_rn(xmax, xmin), ey = __dsub_rn(ymax, ymin);
+    double ext = ex > ey ? ex : ey;
+    double side = __dmul_rn(ext, 1.0 + 0x1p-20);
+    if (side < 1e-300)
+        side = 1e-300;
+    double cx = __dmul_rn(0.5, __dadd_rn(xmin, xmax)), cy = __dmul_rn(0.5, __dadd_rn(ymin, ymax));
+    double half = __dmul_rn(0.5, side);
+    sys[k].x0 = __dsub_rn(cx, half);
+    sys[k].y0 = __dsub_rn(cy, half);
+    sys[k].S = side;
+}
+
+__global__ void k_minmax_init(unsigned long long *minmax, int nsys)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nsys) {
+        minmax[4 * k + 0] = ~0ull;
+        minmax[4 * k + 1] = 0ull;
+        minmax[4 * k + 2] = ~0ull;
+        minmax[4 * k + 3] = 0ull;
+    }
+}
+
+int launch_bbox(const Work &w, const double *x, const double *y, cudaStream_t s)
+{
+    k_minmax_init<<<(w.nsys + 127) / 128, 128, 0, s>>>(w.minmax, w.nsys);
+    k_bbox<<<(w.n + 255) / 256, 256, 0, s>>>(w.sys, w.nsys, w.n, x, y, w.minmax);
+    return 2;
+}
+
+int launch_domain_finalize(const Work &w, cudaStream_t s)
+{
+    k_domain_finalize<<<(w.nsys + 127) / 128, 128, 0, s>>>(w.sys, w.nsys, w.minmax);
+    return 1;
+}
+
+// ------------------------------------------------------------------ stage 2: leaf keys and histogram
+
+__global__ void k_keys(const SysDev *__restrict__ sys, int nsys, int n, const double *__restrict__ x,
+                       const double *__restrict__ y, int *__restrict__ key, int *__restrict__ cnt,
+                       unsigned int *status)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int k = nsys == 1 ? 0 : find_sys_by_particle(sys, nsys, i);
+    const SysDev &d = sys[k];
+    double xi = x[i], yi = y[i];
+    int L = d.depth, nside = 1 << L;
+    bool bad = !isfinite(xi) || !isfinite(yi);
+    if (d.explicit_domain) {
+        double xe = __dadd_rn(d.x0, d.S), ye = __dadd_rn(d.y0, d.S);
+        bad = bad || !(xi >= d.x0) || !(xi <= xe) || !(yi >= d.y0) || !(yi <= ye);
+    }
+    if (bad)
+        atomicOr(status, FMM_DEV_OUTSIDE);
+    double scale = ldexp(1.0, L) / d.S;
+    double tx = floor(__dmul_rn(__dsub_rn(xi, d.x0), scale));
+    double ty = floor(__dmul_rn(__dsub_rn(yi, d.y0), scale));
+    int ix = tx < 0.0 ? 0 : (tx > (double)(nside - 1) ? nside - 1 : (int)tx);
+    int iy = ty < 0.0 ? 0 : (ty > (double)(nside - 1) ? nside - 1 : (int)ty);
+    if (!(tx == tx)) ix = 0;  // NaN (already flagged)
+    if (!(ty == ty)) iy = 0;
+    int kk = (int)(d.leaf0 + (int64_t)iy * nside + ix);
+    key[i] = kk;
+    atomicAdd(&cnt[kk], 1);
+}
+
+int launch_keys(const Work &w, const double *x, const double *y, cudaStream_t s)
+{
+    k_keys<<<(w.n + 255) / 256, 256, 0, s>>>(w.sys, w.nsys, w.n, x, y, w.key, w.cnt, w.status);
+    return 1;
+}
+
+// ------------------------------------------------------------------ exclusive scan cnt -> start
+
+#define SCAN_BLOCK 1024
+
+__global__ void k_scan_block(const int *__restrict__ in, int nin, int *__restrict__ out, int *__restrict__ bsum)
+{
+    __shared__ int sh[SCAN_BLOCK / 32];
+    int base = blockIdx.x * SCAN_BLOCK;
+    int t = threadIdx.x;  // 256 threads, 4 values each
+    int v[4], s = 0;
+    for (int j = 0; j < 4; ++j) {
+        int idx = base + t * 4 + j;
+        v[j] = idx < nin ? in[idx] : 0;
+        s += v[j];
+    }
+    int lane = t & 31, wid = t >> 5;
+    int inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += u;
+    }
+    if (lane == 31)
+        sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int ws = lane < 8 ? sh[lane] : 0;
+        int wi = ws;
+        for (int o = 1; o < 8; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o)
+                wi += u;
+        }
+        if (lane < 8)
+            sh[lane] = wi - ws;
+        if (lane == 7)
+            bsum[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    int ex = sh[wid] + inc - s;
+    for (int j = 0; j < 4; ++j) {
+        int idx = base + t * 4 + j;
+        if (idx < nin)
+            out[idx] = ex;
+        ex += v[j];
+    }
+}
+
+__global__ void k_scan_top(int *bsum, int nb, int *total_out)
+{
+    __shared__ int sh[32];
+    __shared__ int carry_sh;
+    int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0)
+        carry_sh = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        int idx = base + t;
+        int v = idx < nb ? bsum[idx] : 0;
+        int inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o)
+                inc += u;
+        }
+        if (lane == 31)
+            sh[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int ws = sh[lane], wi = ws;
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o)
+                    wi += u;
+            }
+            sh[lane] = wi - ws;
+        }
+        __syncthreads();
+        int carry = carry_sh;
+        int ex = carry + sh[wid] + inc - v;
+        if (idx < nb)
+            bsum[idx] = ex;
+        __syncthreads();
+        if (t == 1023)
+            carry_sh = ex + v;
+        __syncthreads();
+    }
+    if (t == 0)
+        *total_out = carry_sh;
+}
+
+__global__ void k_scan_add(int *out, int nin, const int *__restrict__ bsum)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < nin)
+        out[idx] += bsum[idx / SCAN_BLOCK];
+}
+
+int launch_scan(const Work &w, cudaStream_t s)
+{
+    int nb = (w.nleaf + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    k_scan_block<<<nb, 256, 0, s>>>(w.cnt, w.nleaf, w.start, w.scan_tmp);
+    k_scan_top<<<1, 1024, 0, s>>>(w.scan_tmp, nb, w.start + w.nleaf);
+    k_scan_add<<<(w.nleaf + 255) / 256, 256, 0, s>>>(w.start, w.nleaf, w.scan_tmp);
+    return 3;
+}
+
+// ------------------------------------------------------------------ counting-sort scatter and in-leaf order
+
+__global__ void k_scatter(int n, const int *__restrict__ key, const int *__restrict__ start, int *cnt, int *tmp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int k = key[i];
+    int pos = start[k] + atomicSub(&cnt[k], 1) - 1;  // cnt returns to 0 for the next evaluation
+    tmp[pos] = i;
+}
+
+// One block per leaf: ranks the leaf's caller indices (all distinct) so the leaf keeps the caller's order.
+#define SORT_TILE 2048
+__global__ void k_leaf_sort(int nleaf, const int *__restrict__ start, const int *__restrict__ tmp, int *perm,
+                            int *sleaf)
+{
+    __shared__ int tile[SORT_TILE];
+    int leaf = blockIdx.x;
+    if (leaf >= nleaf)
+        return;
+    int s0 = start[leaf], c = start[leaf + 1] - s0;
+    if (c <= 0)
+        return;
+    if (c == 1) {
+        if (threadIdx.x == 0) {
+            perm[s0] = tmp[s0];
+            sleaf[s0] = leaf;
+        }
+        return;
+    }
+    for (int e0 = 0; e0 < c; e0 += blockDim.x) {
+        int e = e0 + threadIdx.x;
+        int v = e < c ? tmp[s0 + e] : 0;
+        int rank = 0;
+        for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
+            int m = min(SORT_TILE, c - f0);
+            __syncthreads();
+            for (int j = threadIdx.x; j < m; j += blockDim.x)
+                tile[j] = tmp[s0 + f0 + j];
+            __syncthreads();
+            if (e < c)
+                for (int j = 0; j < m; ++j)
+                    rank += tile[j] < v;
+        }
+        if (e < c) {
+            perm[s0 + rank] = v;
+            sleaf[s0 + e] = leaf;
+        }
+    }
+}
+
+int launch_scatter_sort(const Work &w, cudaStream_t s)
+{
+    k_scatter<<<(w.n + 255) / 256, 256, 0, s>>>(w.n, w.key, w.start, w.cnt, w.tmp);
+    k_leaf_sort<<<w.nleaf, 128, 0, s>>>(w.nleaf, w.start, w.tmp, w.perm, w.sleaf);
+    return 2;
+}
+
+// ------------------------------------------------------------------ gather into leaf order
+
+__global__ void k_gather64(int n, const int *__restrict__ perm, const double *__restrict__ x,
+                           const double *__restrict__ y, const double *__restrict__ g, double *sx, double *sy,
+                           double *sg, const double *__restrict__ gu, const double *__restrict__ gv, double *sgu,
+                           double *sgv)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n)
+        return;
+    int i = perm[pos];
+    sx[pos] = x[i];
+    sy[pos] = y[i];
+    sg[pos] = g[i];
+    if (gu) {
+        sgu[pos] = gu[i];
+        sgv[pos] = gv[i];
+    }
+}
+
+// Precision form: coordinates relative to the leaf centre in leaf units, split as hi + lo floats so the
+// pair differences keep FP64-level resolution: zeta = (x - x0) * 2^L / S - (ix + 1/2), hi = fl32(zeta),
+// lo = fl32(zeta - hi).
+__global__ void k_gather32(int n, const SysDev *__restrict__ sys, int nsys, const int *__restrict__ perm,
+                           const int *__restrict__ sleaf, const double *__restrict__ x, const double *__restrict__ y,
+                           const double *__restrict__ g, float4 *pos4, float *g32)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n)
+        return;
+    int i = perm[pos];
+    int k = nsys == 1 ? 0 : find_sys_by_particle(sys, nsys, pos);
+    const SysDev &d = sys[k];
+    int L = d.depth;
+    int local = (int)(sleaf[pos] - d.leaf0);
+    int ix = local & ((1 << L) - 1), iy = local >> L;
+    double scale = ldexp(1.0, L) / d.S;
+    double zx = __dsub_rn(__dmul_rn(__dsub_rn(x[i], d.x0), scale), (double)ix + 0.5);
+    double zy = __dsub_rn(__dmul_rn(__dsub_rn(y[i], d.y0), scale), (double)iy + 0.5);
+    float hx = (float)zx, hy = (float)zy;
+    float lx = (float)(zx - (double)hx), ly = (float)(zy - (double)hy);
+    pos4[pos] = make_float4(hx, hy, lx, ly);
+    g32[pos] = (float)g[i];
+}
+
+int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
+                  const double *gv, cudaStream_t s)
+{
+    int nb = (w.n + 255) / 256;
+    if (w.mixed && !gu) {
+        k_gather32<<<nb, 256, 0, s>>>(w.n, w.sys, w.nsys, w.perm, w.sleaf, x, y, g, w.pos4, w.g32);
+        return 1;
+    }
+    k_gather64<<<nb, 256, 0, s>>>(w.n, w.perm, x, y, g, w.sx, w.sy, w.sg, gu, gv, w.sgu, w.sgv);
+    return 1;
+}
+
+// ------------------------------------------------------------------ ordered near-field pair count
+
+__global__ void k_pair_count(const SysDev *__restrict__ sys, int nsys, int nleaf, const int *__restrict__ start,
+                             unsigned long long *out)
+{
+    int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c = 0;
+    if (leaf < nleaf) {
+        int k = nsys == 1 ? 0 : find_sys_by_leaf(sys, nsys, leaf);
+        const SysDev &d = sys[k];
+        int L = d.depth, ns = 1 << L, local = (int)(leaf - d.leaf0);
+        int ix = local & (ns - 1), iy = local >> L;
+        long long own = start[leaf + 1] - start[leaf], nb = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int jx = ix + dx, jy = iy + dy;
+                if (jx < 0 || jy < 0 || jx >= ns || jy >= ns)
+                    continue;
+                int j = (int)(d.leaf0 + (int64_t)jy * ns + jx);
+                nb += start[j + 1] - start[j];
+            }
+        c = (unsigned long long)(own * nb - own);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c)
+        atomicAdd(out, c);
+}
+
+int launch_pair_count(const Work &w, cudaStream_t s)
+{
+    k_pair_count<<<(w.nleaf + 255) / 256, 256, 0, s>>>(w.sys, w.nsys, w.nleaf, w.start, w.pair_count);
+    return 1;
+}
+
+}  // namespace fmm

@@ -1,0 +1,1115 @@
+// capi.cu -- the C ABI declared in include/fmm2d.h: handle, workspace, the two-stream stage DAG of Fig. 1,
+// CUDA-graph capture and replay, device status, timing, and the autotuner.
+//
+// Schedule of one evaluation (Fig. 1; {4,5,6,7} has no dependency on {9}):
+//   caller stream : [1-2] bbox, keys, scan, scatter, in-leaf order, gather --fork-->  [9] P2P  --join--> [8+10]
+//   side stream   :                                                          [4] P2M [5] M2M [6] M2L [7] L2L
+// The side stream has the highest priority, so whenever near-field blocks retire the block scheduler issues
+// the (small, latency-bound) coarse-level sweep kernels first; the near-field work fills the rest of the GPU.
+#include <algorithm>
+#include <cerrno>
+#include <cmath>
+#include <new>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fmm2d.h"
+#include "fmm_internal.cuh"
+
+using namespace fmm;
+
+namespace {
+
+enum Mode { MODE_FULL = 0, MODE_NEAR = 1, MODE_FAR = 2 };
+
+struct SysHost {
+    int64_t p0, np;
+    int depth;
+    double sigma;
+    int explicit_domain;
+    double dom[3];
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct fmm_ctx {
+    int depth = 0, p = 0;
+    double sigma = 0.0;
+    int has_domain = 0;
+    double dom[3] = {0, 0, 1};
+    int mixed = 0;
+    int coarse = 4;
+    cudaStream_t stream = nullptr;  // caller's stream
+    cudaStream_t exec = nullptr;    // internal stream used for graph capture / replay
+    cudaStream_t side = nullptr;    // high-priority stream of the multipole sweep
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_status = nullptr, ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_t[8] = {};
+    int timing = 0, count_pairs = 0, use_graph = 0;
+    int p2p_threads = 64, p2p_kt = 1;
+    int device = 0;
+    // workspace
+    void *ws = nullptr;
+    size_t ws_cap = 0;
+    Work w{};
+    // tables (depend on p only)
+    void *tab = nullptr;
+    Tables t{};
+    int tab_p = -1;
+    // host-visible status
+    unsigned int *h_status = nullptr;
+    unsigned long long *h_pairs = nullptr;
+    int status_pending = 0;
+    int pairs_valid = 0;
+    // system table cache
+    std::vector<SysHost> sys_cfg;
+    std::vector<SysDev> sys_dev;
+    std::vector<int> sys_list;
+    LevelInfo lv{};
+    uint64_t cfg_version = 1;
+    uint64_t uploaded_version = 0;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    int g_nodes = 0;
+    uint64_t layout_version = 1;
+    size_t layout_sig[6] = {};
+    struct GKey {
+        int mode, n, nsys, mixed, coarse, threads, kt, count_pairs, p, timing;
+        uint64_t layout;
+        const void *ptr[5];
+        uint64_t version;
+        void *ws;
+    } gkey{};
+    // host-buffer staging
+    double *d_io = nullptr;
+    size_t d_io_cap = 0;
+    int64_t launches = 0;
+    int last_timed = 0;
+    std::string err;
+};
+
+static fmm_status set_err(fmm_handle h, fmm_status s, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return s;
+}
+
+#define CU(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return set_err(h, e_ == cudaErrorMemoryAllocation ? FMM_ENOMEM : FMM_ECUDA, "%s: %s (%s:%d)", \
+                           #call, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+    } while (0)
+
+static fmm_status device_status_to_fmm(unsigned int st)
+{
+    if (st & FMM_DEV_BOUNDS)
+        return FMM_EINTERNAL;
+    if (st & FMM_DEV_TIMEOUT)
+        return FMM_ETIMEOUT;
+    if (st & FMM_DEV_OUTSIDE)
+        return FMM_EINVAL;
+    return FMM_OK;
+}
+
+// Reports (once) a device-side error of an earlier evaluation, without blocking.
+static fmm_status poll_status(fmm_handle h, bool block)
+{
+    if (!h->status_pending)
+        return FMM_OK;
+    if (block) {
+        CU(cudaEventSynchronize(h->ev_status));
+    } else {
+        cudaError_t q = cudaEventQuery(h->ev_status);
+        if (q == cudaErrorNotReady)
+            return FMM_OK;
+        if (q != cudaSuccess)
+            return set_err(h, FMM_ECUDA, "evaluation failed: %s", cudaGetErrorString(q));
+    }
+    h->status_pending = 0;
+    unsigned int st = *h->h_status;
+    if (st) {
+        *h->h_status = 0;
+        CU(cudaMemsetAsync(h->w.status, 0, sizeof(unsigned int), h->stream));
+        fmm_status s = device_status_to_fmm(st);
+        const char *what = s == FMM_EINVAL     ? "a particle lies outside the root square or is not finite"
+                           : s == FMM_ETIMEOUT ? "a bounded wait for a shared-memory copy ran out"
+                                               : "a device bounds check failed";
+        return set_err(h, s, "device reported: %s (status 0x%x)", what, st);
+    }
+    return FMM_OK;
+}
+
+// ------------------------------------------------------------------ tables
+
+static fmm_status ensure_tables(fmm_handle h)
+{
+    if (h->tab_p == h->p)
+        return FMM_OK;
+    const int P = FMM_PMAX, RS = 2 * FMM_PMAX + 2;
+    size_t n_mat = 4 * P * P, n_rho = FMM_NOFF * RS, n_bin = P * P;
+    std::vector<double2> m2m(n_mat), l2l(n_mat), rho(n_rho);
+    std::vector<double> bin(n_bin);
+    build_tables_host(h->p, m2m.data(), l2l.data(), rho.data(), bin.data());
+    std::vector<float2> m2m32(n_mat), l2l32(n_mat), rho32(n_rho);
+    std::vector<float> bin32(n_bin);
+    for (size_t i = 0; i < n_mat; ++i) {
+        m2m32[i] = make_float2((float)m2m[i].x, (float)m2m[i].y);
+        l2l32[i] = make_float2((float)l2l[i].x, (float)l2l[i].y);
+    }
+    for (size_t i = 0; i < n_rho; ++i)
+        rho32[i] = make_float2((float)rho[i].x, (float)rho[i].y);
+    for (size_t i = 0; i < n_bin; ++i)
+        bin32[i] = (float)bin[i];
+    size_t off[8], total = 0;
+    size_t sz[8] = {n_mat * 16, n_mat * 16, n_mat * 8, n_mat * 8, n_rho * 16, n_rho * 8, n_bin * 8, n_bin * 4};
+    for (int i = 0; i < 8; ++i) {
+        off[i] = total;
+        total += align256(sz[i]);
+    }
+    if (!h->tab) {
+        CU(cudaMalloc(&h->tab, total));
+    }
+    char *b = (char *)h->tab;
+    h->t.m2m64 = (double2 *)(b + off[0]);
+    h->t.l2l64 = (double2 *)(b + off[1]);
+    h->t.m2m32 = (float2 *)(b + off[2]);
+    h->t.l2l32 = (float2 *)(b + off[3]);
+    h->t.rho64 = (double2 *)(b + off[4]);
+    h->t.rho32 = (float2 *)(b + off[5]);
+    h->t.binom64 = (double *)(b + off[6]);
+    h->t.binom32 = (float *)(b + off[7]);
+    CU(cudaMemcpy(h->t.m2m64, m2m.data(), sz[0], cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->t.l2l64, l2l.data(), sz[1], cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->t.m2m32, m2m32.data(), sz[2], cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->t.l2l32, l2l32.data(), sz[3], cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->t.rho64, rho.data(), sz[4], cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->t.rho32, rho32.data(), sz[5], cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->t.binom64, bin.data(), sz[6], cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->t.binom32, bin32.data(), sz[7], cudaMemcpyHostToDevice));
+    h->tab_p = h->p;
+    return FMM_OK;
+}
+
+// ------------------------------------------------------------------ system table and workspace
+
+// Builds device descriptors, leaf / box offsets and per-level system lists for the configured systems.
+static void build_system_layout(fmm_handle h, int64_t *nleaf_out, int64_t *nbox_out)
+{
+    int nsys = (int)h->sys_cfg.size();
+    h->sys_dev.assign(nsys, SysDev{});
+    int64_t leaf = 0, box = 0;
+    int maxd = 0;
+    for (int k = 0; k < nsys; ++k) {
+        const SysHost &c = h->sys_cfg[k];
+        SysDev &d = h->sys_dev[k];
+        d.p0 = c.p0;
+        d.np = c.np;
+        d.depth = c.depth;
+        d.sigma = c.sigma;
+        d.explicit_domain = c.explicit_domain;
+        d.x0 = c.dom[0];
+        d.y0 = c.dom[1];
+        d.S = c.dom[2];
+        d.leaf0 = leaf;
+        leaf += (int64_t)1 << (2 * c.depth);
+        for (int l = 0; l <= FMM_MAXL; ++l)
+            d.box0[l] = -1;
+        if (c.depth > maxd)
+            maxd = c.depth;
+    }
+    // boxes grouped by level, then by system, so one level of all systems is one contiguous range
+    for (int l = 2; l <= maxd; ++l)
+        for (int k = 0; k < nsys; ++k)
+            if (h->sys_cfg[k].depth >= l) {
+                h->sys_dev[k].box0[l] = box;
+                box += (int64_t)1 << (2 * l);
+            }
+    LevelInfo lv{};
+    lv.maxdepth = maxd;
+    h->sys_list.clear();
+    for (int l = 0; l <= FMM_MAXL + 1; ++l) {
+        lv.first_at[l] = (int)h->sys_list.size();
+        int cnt = 0;
+        for (int k = 0; k < nsys; ++k)
+            if (l <= FMM_MAXL && h->sys_cfg[k].depth >= l) {
+                h->sys_list.push_back(k);
+                ++cnt;
+            }
+        lv.nsys_at[l] = cnt;
+    }
+    int64_t acc = 0;
+    for (int l = 0; l <= FMM_MAXL + 1; ++l)
+        lv.m2l_item0[l] = 0;
+    for (int l = 2; l <= maxd; ++l) {
+        lv.m2l_item0[l] = acc;
+        acc += (int64_t)lv.nsys_at[l] << (2 * l);
+    }
+    lv.m2l_item0[maxd + 1 <= FMM_MAXL + 1 ? maxd + 1 : FMM_MAXL + 1] = acc;
+    lv.mindepth2 = 0;
+    for (int k = 0; k < nsys; ++k) {
+        int dk = h->sys_cfg[k].depth;
+        if (dk >= 2 && (lv.mindepth2 == 0 || dk < lv.mindepth2))
+            lv.mindepth2 = dk;
+    }
+    h->lv = lv;
+    *nleaf_out = leaf;
+    *nbox_out = box;
+}
+
+struct Layout {
+    size_t off[40];
+    size_t total;
+};
+
+static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
+{
+    int64_t nleaf, nbox;
+    build_system_layout(h, &nleaf, &nbox);
+    if (n >= ((int64_t)1 << 31) - 64 || nleaf >= ((int64_t)1 << 31) - 2)
+        return set_err(h, FMM_EINVAL, "too many particles (%lld) or leaves (%lld) for 32-bit indices",
+                       (long long)n, (long long)nleaf);
+    int nsys = (int)h->sys_cfg.size();
+    int p = h->p;
+    bool mixed = h->mixed && !adjoint;
+    bool f64 = !mixed || adjoint;
+    size_t np = (size_t)n + 8;
+    size_t sizes[40];
+    int i = 0;
+    sizes[i++] = np * 4;                                      // 0 key
+    sizes[i++] = (size_t)nleaf * 4 + 16;                      // 1 cnt
+    sizes[i++] = (size_t)(nleaf + 1) * 4 + 16;                // 2 start
+    sizes[i++] = (size_t)((nleaf + 1023) / 1024 + 2) * 4;     // 3 scan_tmp
+    sizes[i++] = np * 4;                                      // 4 tmp
+    sizes[i++] = np * 4;                                      // 5 perm
+    sizes[i++] = np * 4;                                      // 6 sleaf
+    sizes[i++] = f64 ? np * 8 : 0;                            // 7 sx
+    sizes[i++] = f64 ? np * 8 : 0;                            // 8 sy
+    sizes[i++] = f64 ? np * 8 : 0;                            // 9 sg
+    sizes[i++] = mixed ? np * 16 : 0;                         // 10 pos4
+    sizes[i++] = mixed ? np * 4 : 0;                          // 11 g32
+    sizes[i++] = mixed ? 0 : np * 16;                         // 12 near64
+    sizes[i++] = mixed ? np * 8 : 0;                          // 13 near32
+    sizes[i++] = (size_t)nbox * 4 + 16;                       // 14 bcount
+    sizes[i++] = (size_t)nbox * p * 16;                       // 15 M64
+    sizes[i++] = (size_t)nbox * p * 16;                       // 16 L64
+    sizes[i++] = mixed ? (size_t)nbox * p * 8 : 0;            // 17 M32
+    sizes[i++] = mixed ? (size_t)nbox * p * 8 : 0;            // 18 L32
+    sizes[i++] = adjoint ? np * 8 : 0;                        // 19 sgu
+    sizes[i++] = adjoint ? np * 8 : 0;                        // 20 sgv
+    sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 21 AM64
+    sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 22 AL64
+    sizes[i++] = 0;                                           // 23 (unused)
+    sizes[i++] = (size_t)nsys * 32;                           // 24 minmax
+    sizes[i++] = 64;                                          // 25 status + pair count
+    sizes[i++] = (size_t)nsys * sizeof(SysDev);               // 26 sys
+    sizes[i++] = (h->sys_list.size() + 1) * 4;                // 27 sys_list
+    sizes[i++] = adjoint ? np * 24 : 0;                       // 28 adj_far
+    int count = i;
+    Layout lay;
+    size_t total = 0;
+    for (int j = 0; j < count; ++j) {
+        lay.off[j] = total;
+        total += align256(sizes[j]);
+    }
+    if (total > h->ws_cap) {
+        if (h->ws) {
+            CU(cudaDeviceSynchronize());
+            CU(cudaFree(h->ws));
+            h->ws = nullptr;
+            h->ws_cap = 0;
+        }
+        size_t cap = total + total / 8;
+        CU(cudaMalloc(&h->ws, cap));
+        h->ws_cap = cap;
+        CU(cudaMemset(h->ws, 0, cap));
+        h->uploaded_version = 0;
+    }
+    size_t sig[6] = {(size_t)n, (size_t)nleaf, (size_t)nbox, (size_t)p, (size_t)(mixed ? 1 : 0) + 2 * (size_t)adjoint,
+                     (size_t)h->ws};
+    if (memcmp(sig, h->layout_sig, sizeof sig) != 0) {
+        memcpy(h->layout_sig, sig, sizeof sig);
+        h->layout_version++;
+    }
+    char *b = (char *)h->ws;
+    Work &w = h->w;
+    w = Work{};
+    w.n = (int)n;
+    w.nleaf = (int)nleaf;
+    w.nbox = nbox;
+    w.p = p;
+    w.mixed = mixed ? 1 : 0;
+    w.coarse_level = h->coarse;
+    w.nsys = nsys;
+    w.maxdepth = h->lv.maxdepth;
+    w.key = (int *)(b + lay.off[0]);
+    w.cnt = (int *)(b + lay.off[1]);
+    w.start = (int *)(b + lay.off[2]);
+    w.scan_tmp = (int *)(b + lay.off[3]);
+    w.tmp = (int *)(b + lay.off[4]);
+    w.perm = (int *)(b + lay.off[5]);
+    w.sleaf = (int *)(b + lay.off[6]);
+    w.sx = sizes[7] ? (double *)(b + lay.off[7]) : nullptr;
+    w.sy = sizes[8] ? (double *)(b + lay.off[8]) : nullptr;
+    w.sg = sizes[9] ? (double *)(b + lay.off[9]) : nullptr;
+    w.pos4 = sizes[10] ? (float4 *)(b + lay.off[10]) : nullptr;
+    w.g32 = sizes[11] ? (float *)(b + lay.off[11]) : nullptr;
+    w.near64 = sizes[12] ? (double2 *)(b + lay.off[12]) : nullptr;
+    w.near32 = sizes[13] ? (float2 *)(b + lay.off[13]) : nullptr;
+    w.bcount = (int *)(b + lay.off[14]);
+    w.M64 = (double2 *)(b + lay.off[15]);
+    w.L64 = (double2 *)(b + lay.off[16]);
+    w.M32 = sizes[17] ? (float2 *)(b + lay.off[17]) : nullptr;
+    w.L32 = sizes[18] ? (float2 *)(b + lay.off[18]) : nullptr;
+    w.sgu = sizes[19] ? (double *)(b + lay.off[19]) : nullptr;
+    w.sgv = sizes[20] ? (double *)(b + lay.off[20]) : nullptr;
+    w.AM64 = sizes[21] ? (double2 *)(b + lay.off[21]) : nullptr;
+    w.AL64 = sizes[22] ? (double2 *)(b + lay.off[22]) : nullptr;
+    w.minmax = (unsigned long long *)(b + lay.off[24]);
+    w.status = (unsigned int *)(b + lay.off[25]);
+    w.pair_count = (unsigned long long *)(b + lay.off[25] + 32);
+    w.sys = (SysDev *)(b + lay.off[26]);
+    w.sys_list = (int *)(b + lay.off[27]);
+    w.adj_far = sizes[28] ? (double *)(b + lay.off[28]) : nullptr;
+    w.lv = h->lv;
+    return FMM_OK;
+}
+
+static fmm_status upload_systems(fmm_handle h)
+{
+    if (h->uploaded_version == h->cfg_version && h->w.sys)
+        return FMM_OK;
+    // the previous evaluation may still read the table: order the upload on the stream
+    CU(cudaMemcpyAsync(h->w.sys, h->sys_dev.data(), h->sys_dev.size() * sizeof(SysDev), cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaMemcpyAsync(h->w.sys_list, h->sys_list.data(), h->sys_list.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->uploaded_version = h->cfg_version;
+    return FMM_OK;
+}
+
+static void set_single_system(fmm_handle h, int64_t n)
+{
+    SysHost c{};
+    c.p0 = 0;
+    c.np = n;
+    c.depth = h->depth;
+    c.sigma = h->sigma;
+    c.explicit_domain = h->has_domain;
+    c.dom[0] = h->dom[0];
+    c.dom[1] = h->dom[1];
+    c.dom[2] = h->dom[2];
+    if (h->sys_cfg.size() != 1 || memcmp(&h->sys_cfg[0], &c, sizeof c) != 0) {
+        h->sys_cfg.assign(1, c);
+        h->cfg_version++;
+    }
+}
+
+// ------------------------------------------------------------------ the stage DAG
+
+// Timing events: inside a stream capture they must be external event-record nodes to carry timestamps.
+static cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    return cudaEventRecordWithFlags(ev, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                                : cudaEventRecordDefault);
+}
+
+static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const double *x, const double *y,
+                                  const double *g, double *u, double *v)
+{
+    Work &w = h->w;
+    bool far = mode != MODE_NEAR && w.lv.maxdepth >= 2;
+    bool near = mode != MODE_FAR;
+    bool timed = h->timing != 0;  // in a graph the event records become event-record nodes
+    int64_t nl = 0;
+    if (timed)
+        CU(record_timing(h->ev_t[0], s));
+    CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
+    bool any_bbox = false;
+    for (auto &c : h->sys_cfg)
+        any_bbox |= !c.explicit_domain;
+    if (any_bbox)
+        nl += launch_bbox(w, x, y, s);
+    nl += launch_domain_finalize(w, s);
+    nl += launch_keys(w, x, y, s);
+    nl += launch_scan(w, s);
+    nl += launch_scatter_sort(w, s);
+    nl += launch_gather(w, x, y, g, nullptr, nullptr, s);
+    if (timed)
+        CU(record_timing(h->ev_t[1], s));
+    if (far) {
+        CU(cudaEventRecord(h->ev_fork, s));
+        CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        nl += launch_p2m(w, h->t, 0, h->side);
+        for (int l = w.lv.maxdepth - 1; l >= 2; --l)
+            nl += launch_m2m(w, h->t, l, 0, h->side, 1);
+        if (timed)
+            CU(record_timing(h->ev_t[2], h->side));
+        nl += launch_m2l(w, h->t, 0, h->side, 1);
+        if (timed)
+            CU(record_timing(h->ev_t[3], h->side));
+        for (int l = 2; l < w.lv.maxdepth; ++l)
+            nl += launch_l2l(w, h->t, l, 0, h->side, 1);
+        if (timed)
+            CU(record_timing(h->ev_t[4], h->side));
+        CU(cudaEventRecord(h->ev_join, h->side));
+    }
+    if (near)
+        nl += launch_p2p(w, h->p2p_threads, h->p2p_kt, s);
+    if (timed)
+        CU(record_timing(h->ev_t[5], s));
+    if (far)
+        CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+    if (timed)
+        CU(record_timing(h->ev_t[6], s));
+    nl += launch_combine(w, near ? 1 : 0, far ? 1 : 0, u, v, s);
+    if (h->count_pairs) {
+        CU(cudaMemsetAsync(w.pair_count, 0, sizeof(unsigned long long), s));
+        nl += launch_pair_count(w, s);
+        CU(cudaMemcpyAsync(h->h_pairs, w.pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    }
+    CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    if (timed)
+        CU(record_timing(h->ev_t[7], s));
+    CU(cudaGetLastError());
+    h->launches += nl;
+    h->last_timed = timed;
+    return FMM_OK;
+}
+
+static int count_kernel_nodes(cudaGraph_t g)
+{
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess)
+        return 0;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+            ++k;
+    }
+    return k;
+}
+
+static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x, const double *y,
+                              const double *g, double *u, double *v)
+{
+    fmm_status st;
+    if ((st = ensure_tables(h)) != FMM_OK)
+        return st;
+    if ((st = ensure_workspace(h, n, 0)) != FMM_OK)
+        return st;
+    if ((st = upload_systems(h)) != FMM_OK)
+        return st;
+    if (h->count_pairs)
+        h->pairs_valid = 1;
+    if (!h->use_graph) {
+        if ((st = enqueue_forward(h, h->stream, mode, x, y, g, u, v)) != FMM_OK)
+            return st;
+        CU(cudaEventRecord(h->ev_status, h->stream));
+        h->status_pending = 1;
+        return FMM_OK;
+    }
+    fmm_ctx::GKey key{};
+    key.mode = mode;
+    key.n = (int)n;
+    key.nsys = (int)h->sys_cfg.size();
+    key.mixed = h->w.mixed;
+    key.coarse = h->coarse;
+    key.threads = h->p2p_threads;
+    key.kt = h->p2p_kt;
+    key.count_pairs = h->count_pairs;
+    key.p = h->p;
+    key.timing = h->timing;
+    key.layout = h->layout_version;
+    key.ptr[0] = x;
+    key.ptr[1] = y;
+    key.ptr[2] = g;
+    key.ptr[3] = u;
+    key.ptr[4] = v;
+    key.version = h->cfg_version;
+    key.ws = h->ws;
+    if (!h->gexec || memcmp(&key, &h->gkey, sizeof key) != 0) {
+        if (h->gexec) {
+            CU(cudaGraphExecDestroy(h->gexec));
+            h->gexec = nullptr;
+        }
+        CU(cudaStreamBeginCapture(h->exec, cudaStreamCaptureModeThreadLocal));
+        int64_t before = h->launches;
+        st = enqueue_forward(h, h->exec, mode, x, y, g, u, v);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->exec, &graph);
+        h->launches = before;
+        if (st != FMM_OK) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess)
+            return set_err(h, FMM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        h->g_nodes = count_kernel_nodes(graph);
+        e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            h->gexec = nullptr;
+            return set_err(h, FMM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        }
+        h->gkey = key;
+    }
+    CU(cudaEventRecord(h->ev_in, h->stream));
+    CU(cudaStreamWaitEvent(h->exec, h->ev_in, 0));
+    CU(cudaGraphLaunch(h->gexec, h->exec));
+    CU(cudaEventRecord(h->ev_out, h->exec));
+    CU(cudaStreamWaitEvent(h->stream, h->ev_out, 0));
+    h->launches += h->g_nodes;
+    CU(cudaEventRecord(h->ev_status, h->stream));
+    h->status_pending = 1;
+    return FMM_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+fmm_status fmm_create(int tree_depth, int p, double sigma, fmm_handle *out)
+{
+    if (!out)
+        return FMM_EINVAL;
+    *out = nullptr;
+    if (tree_depth < 0 || tree_depth > FMM_MAXL || p < 1 || p > FMM_PMAX || !(sigma > 0.0) || !(sigma < 1e300))
+        return FMM_EINVAL;
+    fmm_handle h = new (std::nothrow) fmm_ctx();
+    if (!h)
+        return FMM_ENOMEM;
+    h->depth = tree_depth;
+    h->p = p;
+    h->sigma = sigma;
+    cudaError_t e = cudaGetDevice(&h->device);
+    int lo = 0, hi = 0;
+    if (e == cudaSuccess)
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&h->exec, cudaStreamNonBlocking);
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_join, &h->ev_status, &h->ev_in, &h->ev_out};
+    for (auto ev : evs)
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i)
+        e = cudaEventCreate(&h->ev_t[i]);
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&h->h_status, 64);
+    if (e == cudaSuccess) {
+        h->h_pairs = (unsigned long long *)((char *)h->h_status + 32);
+        *h->h_status = 0;
+        *h->h_pairs = 0;
+    }
+    if (e != cudaSuccess) {
+        fmm_destroy(h);
+        return e == cudaErrorMemoryAllocation ? FMM_ENOMEM : FMM_ECUDA;
+    }
+    *out = h;
+    return FMM_OK;
+}
+
+fmm_status fmm_destroy(fmm_handle h)
+{
+    if (!h)
+        return FMM_OK;
+    if (h->stream || h->side)
+        cudaDeviceSynchronize();
+    if (h->gexec)
+        cudaGraphExecDestroy(h->gexec);
+    cudaEvent_t evs[] = {h->ev_fork, h->ev_join, h->ev_status, h->ev_in, h->ev_out};
+    for (auto ev : evs)
+        if (ev)
+            cudaEventDestroy(ev);
+    for (int i = 0; i < 8; ++i)
+        if (h->ev_t[i])
+            cudaEventDestroy(h->ev_t[i]);
+    if (h->side)
+        cudaStreamDestroy(h->side);
+    if (h->exec)
+        cudaStreamDestroy(h->exec);
+    if (h->ws)
+        cudaFree(h->ws);
+    if (h->tab)
+        cudaFree(h->tab);
+    if (h->d_io)
+        cudaFree(h->d_io);
+    if (h->h_status)
+        cudaFreeHost(h->h_status);
+    delete h;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_domain(fmm_handle h, double x0, double y0, double side)
+{
+    if (!h)
+        return FMM_EINVAL;
+    if (!(side > 0.0) || !std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(side))
+        return set_err(h, FMM_EINVAL, "invalid root square");
+    h->has_domain = 1;
+    h->dom[0] = x0;
+    h->dom[1] = y0;
+    h->dom[2] = side;
+    return FMM_OK;
+}
+
+fmm_status fmm_clear_domain(fmm_handle h)
+{
+    if (!h)
+        return FMM_EINVAL;
+    h->has_domain = 0;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_precision(fmm_handle h, fmm_precision mode)
+{
+    if (!h || (mode != FMM_FP64 && mode != FMM_MIXED))
+        return FMM_EINVAL;
+    h->mixed = mode == FMM_MIXED;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level)
+{
+    if (!h || coarse_level < -1 || coarse_level > FMM_MAXL)
+        return FMM_EINVAL;
+    h->coarse = coarse_level;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_params(fmm_handle h, int tree_depth, int p, double sigma)
+{
+    if (!h || tree_depth < 0 || tree_depth > FMM_MAXL || p < 1 || p > FMM_PMAX || !(sigma > 0.0))
+        return FMM_EINVAL;
+    h->depth = tree_depth;
+    h->p = p;
+    h->sigma = sigma;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_stream(fmm_handle h, void *cuda_stream)
+{
+    if (!h)
+        return FMM_EINVAL;
+    h->stream = (cudaStream_t)cuda_stream;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_graph(fmm_handle h, int enable)
+{
+    if (!h)
+        return FMM_EINVAL;
+    h->use_graph = enable ? 1 : 0;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread)
+{
+    if (!h)
+        return FMM_EINVAL;
+    if (threads == 0)
+        threads = 64;
+    if (targets_per_thread == 0)
+        targets_per_thread = 1;
+    if (threads < 32 || threads > 128 || (threads & 31) ||
+        (targets_per_thread != 1 && targets_per_thread != 2 && targets_per_thread != 4))
+        return set_err(h, FMM_EINVAL, "tile: threads in {32, 64, 96, 128}, targets per thread in {1, 2, 4}");
+    h->p2p_threads = threads;
+    h->p2p_kt = targets_per_thread;
+    return FMM_OK;
+}
+
+static fmm_status check_common(fmm_handle h, int64_t n, const void *x, const void *y, const void *g, const void *u,
+                               const void *v)
+{
+    if (!h)
+        return FMM_EINVAL;
+    if (n < 0)
+        return set_err(h, FMM_EINVAL, "n < 0");
+    if (n > 0 && (!x || !y || !g || !u || !v))
+        return set_err(h, FMM_EINVAL, "NULL array");
+    return FMM_OK;
+}
+
+static fmm_status velocity_mode(fmm_handle h, int mode, int64_t n, const double *x, const double *y,
+                                const double *g, double *u, double *v)
+{
+    fmm_status st = check_common(h, n, x, y, g, u, v);
+    if (st != FMM_OK)
+        return st;
+    if ((st = poll_status(h, false)) != FMM_OK)
+        return st;
+    if (n == 0)
+        return FMM_OK;
+    set_single_system(h, n);
+    return run_forward(h, mode, n, x, y, g, u, v);
+}
+
+fmm_status fmm_velocity(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma, double *u,
+                        double *v)
+{
+    return velocity_mode(h, MODE_FULL, n, x, y, gamma, u, v);
+}
+
+fmm_status fmm_velocity_near(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                             double *u, double *v)
+{
+    return velocity_mode(h, MODE_NEAR, n, x, y, gamma, u, v);
+}
+
+fmm_status fmm_velocity_far(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                            double *u, double *v)
+{
+    return velocity_mode(h, MODE_FAR, n, x, y, gamma, u, v);
+}
+
+fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                             double *u, double *v)
+{
+    fmm_status st = check_common(h, n, x, y, gamma, u, v);
+    if (st != FMM_OK)
+        return st;
+    if ((st = poll_status(h, false)) != FMM_OK)
+        return st;
+    if (n == 0)
+        return FMM_OK;
+    size_t need = (size_t)n * 5 * sizeof(double);
+    if (need > h->d_io_cap) {
+        if (h->d_io) {
+            CU(cudaDeviceSynchronize());
+            CU(cudaFree(h->d_io));
+            h->d_io = nullptr;
+            h->d_io_cap = 0;
+        }
+        CU(cudaMalloc(&h->d_io, need));
+        h->d_io_cap = need;
+    }
+    double *dx = h->d_io, *dy = dx + n, *dg = dy + n, *du = dg + n, *dv = du + n;
+    size_t bytes = (size_t)n * sizeof(double);
+    CU(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(dy, y, bytes, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(dg, gamma, bytes, cudaMemcpyHostToDevice, h->stream));
+    set_single_system(h, n);
+    if ((st = run_forward(h, MODE_FULL, n, dx, dy, dg, du, dv)) != FMM_OK)
+        return st;
+    CU(cudaMemcpyAsync(u, du, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(v, dv, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return poll_status(h, true);
+}
+
+fmm_status fmm_velocity_batched(fmm_handle h, int nsys, const int64_t *offsets, const int *depths,
+                                const double *sigmas, const double *domains, const double *x, const double *y,
+                                const double *gamma, double *u, double *v)
+{
+    if (!h)
+        return FMM_EINVAL;
+    if (nsys < 1 || nsys > FMM_MAXSYS || !offsets)
+        return set_err(h, FMM_EINVAL, "nsys must be in [1, %d] and offsets given", FMM_MAXSYS);
+    if (offsets[0] != 0)
+        return set_err(h, FMM_EINVAL, "offsets[0] must be 0");
+    for (int k = 0; k < nsys; ++k) {
+        if (offsets[k + 1] < offsets[k])
+            return set_err(h, FMM_EINVAL, "offsets must be non-decreasing");
+        if (depths && (depths[k] < 0 || depths[k] > FMM_MAXL))
+            return set_err(h, FMM_EINVAL, "depth of system %d out of range", k);
+        if (sigmas && !(sigmas[k] > 0.0))
+            return set_err(h, FMM_EINVAL, "sigma of system %d must be > 0", k);
+        if (domains && !(domains[3 * k + 2] > 0.0))
+            return set_err(h, FMM_EINVAL, "side of system %d must be > 0", k);
+    }
+    int64_t n = offsets[nsys];
+    fmm_status st = check_common(h, n, x, y, gamma, u, v);
+    if (st != FMM_OK)
+        return st;
+    if ((st = poll_status(h, false)) != FMM_OK)
+        return st;
+    if (n == 0)
+        return FMM_OK;
+    std::vector<SysHost> cfg(nsys);
+    for (int k = 0; k < nsys; ++k) {
+        SysHost &c = cfg[k];
+        memset(&c, 0, sizeof c);
+        c.p0 = offsets[k];
+        c.np = offsets[k + 1] - offsets[k];
+        c.depth = depths ? depths[k] : h->depth;
+        c.sigma = sigmas ? sigmas[k] : h->sigma;
+        c.explicit_domain = domains ? 1 : 0;
+        if (domains) {
+            c.dom[0] = domains[3 * k];
+            c.dom[1] = domains[3 * k + 1];
+            c.dom[2] = domains[3 * k + 2];
+        }
+    }
+    if (h->sys_cfg.size() != cfg.size() || memcmp(h->sys_cfg.data(), cfg.data(), cfg.size() * sizeof(SysHost))) {
+        h->sys_cfg = cfg;
+        h->cfg_version++;
+    }
+    return run_forward(h, MODE_FULL, n, x, y, gamma, u, v);
+}
+
+fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                                const double *gu, const double *gv, double *dgamma, double *dx, double *dy)
+{
+    fmm_status st = check_common(h, n, x, y, gamma, gu, gv);
+    if (st != FMM_OK)
+        return st;
+    if ((st = poll_status(h, false)) != FMM_OK)
+        return st;
+    if (n == 0)
+        return FMM_OK;
+    set_single_system(h, n);
+    if ((st = ensure_tables(h)) != FMM_OK)
+        return st;
+    if ((st = ensure_workspace(h, n, 1)) != FMM_OK)
+        return st;
+    if ((st = upload_systems(h)) != FMM_OK)
+        return st;
+    Work &w = h->w;
+    cudaStream_t s = h->stream;
+    int64_t nl = 0;
+    bool far = w.lv.maxdepth >= 2;
+    CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
+    if (!h->has_domain)
+        nl += launch_bbox(w, x, y, s);
+    nl += launch_domain_finalize(w, s);
+    nl += launch_keys(w, x, y, s);
+    nl += launch_scan(w, s);
+    nl += launch_scatter_sort(w, s);
+    nl += launch_gather(w, x, y, gamma, gu, gv, s);
+    if (far) {
+        CU(cudaEventRecord(h->ev_fork, s));
+        CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        for (int adj = 0; adj < 2; ++adj) {
+            nl += launch_p2m(w, h->t, adj, h->side);
+            for (int l = w.lv.maxdepth - 1; l >= 2; --l)
+                nl += launch_m2m(w, h->t, l, adj, h->side, 1);
+            nl += launch_m2l(w, h->t, adj, h->side, 1);
+            for (int l = 2; l < w.lv.maxdepth; ++l)
+                nl += launch_l2l(w, h->t, l, adj, h->side, 1);
+        }
+        nl += launch_adjoint_far(w, h->side);
+        CU(cudaEventRecord(h->ev_join, h->side));
+    }
+    // near field written to the outputs first; the far part is added after the join
+    nl += launch_adjoint_p2p(w, dgamma, dx, dy, s);
+    if (far) {
+        CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+        nl += launch_adjoint_combine(w, dgamma, dx, dy, s);
+    }
+    CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(h->ev_status, s));
+    CU(cudaGetLastError());
+    h->status_pending = 1;
+    h->launches += nl;
+    return FMM_OK;
+}
+
+fmm_status fmm_sync(fmm_handle h)
+{
+    if (!h)
+        return FMM_EINVAL;
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaStreamSynchronize(h->side));
+    CU(cudaStreamSynchronize(h->exec));
+    return poll_status(h, true);
+}
+
+fmm_status fmm_set_timing(fmm_handle h, int enable)
+{
+    if (!h)
+        return FMM_EINVAL;
+    h->timing = enable ? 1 : 0;
+    return FMM_OK;
+}
+
+int fmm_stage_times(fmm_handle h, float *out, int cap)
+{
+    if (!h || !out || cap <= 0 || !h->last_timed)
+        return 0;
+    if (cudaEventSynchronize(h->ev_t[7]) != cudaSuccess)
+        return 0;
+    float v[8];
+    auto el = [&](int a, int b) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev_t[a], h->ev_t[b]);
+        return ms;
+    };
+    bool far = h->w.lv.maxdepth >= 2;
+    v[0] = el(0, 1);
+    v[1] = el(1, 5);
+    v[2] = far ? el(1, 2) : 0.f;
+    v[3] = far ? el(2, 3) : 0.f;
+    v[4] = far ? el(3, 4) : 0.f;
+    v[5] = el(6, 7);
+    v[6] = el(0, 7);
+    v[7] = el(1, 6);
+    int m = cap < 8 ? cap : 8;
+    for (int i = 0; i < m; ++i)
+        out[i] = v[i];
+    return m;
+}
+
+fmm_status fmm_set_count_pairs(fmm_handle h, int enable)
+{
+    if (!h)
+        return FMM_EINVAL;
+    h->count_pairs = enable ? 1 : 0;
+    return FMM_OK;
+}
+
+int64_t fmm_last_pair_count(fmm_handle h)
+{
+    if (!h || !h->pairs_valid)
+        return -1;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return -1;
+    return (int64_t)*h->h_pairs;
+}
+
+int64_t fmm_kernel_launches(fmm_handle h) { return h ? h->launches : -1; }
+
+fmm_status fmm_get_params(fmm_handle h, int *tree_depth, int *p, double *sigma, int *p2p_threads,
+                          int *p2p_targets_per_thread)
+{
+    if (!h)
+        return FMM_EINVAL;
+    if (tree_depth)
+        *tree_depth = h->depth;
+    if (p)
+        *p = h->p;
+    if (sigma)
+        *sigma = h->sigma;
+    if (p2p_threads)
+        *p2p_threads = h->p2p_threads;
+    if (p2p_targets_per_thread)
+        *p2p_targets_per_thread = h->p2p_kt;
+    return FMM_OK;
+}
+
+// Times fmm_velocity (median of 5 after 2 warm-up runs) for each candidate depth and tile and keeps the best.
+fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma, double *u,
+                        double *v, int depth_lo, int depth_hi)
+{
+    fmm_status st = check_common(h, n, x, y, gamma, u, v);
+    if (st != FMM_OK)
+        return st;
+    if (depth_lo < 0 || depth_hi > FMM_MAXL || depth_lo > depth_hi)
+        return set_err(h, FMM_EINVAL, "bad depth range");
+    const char *cache = getenv("FMM2D_TUNE_CACHE");
+    char keybuf[160];
+    snprintf(keybuf, sizeof keybuf, "n=%lld p=%d mixed=%d sigma=%.17g lo=%d hi=%d", (long long)n, h->p, h->mixed,
+             h->sigma, depth_lo, depth_hi);
+    if (cache) {
+        FILE *f = fopen(cache, "r");
+        if (f) {
+            char line[256];
+            while (fgets(line, sizeof line, f)) {
+                int d, th, kt;
+                char *bar = strchr(line, '|');
+                if (!bar)
+                    continue;
+                *bar = 0;
+                if (strcmp(line, keybuf) == 0 && sscanf(bar + 1, "%d %d %d", &d, &th, &kt) == 3) {
+                    fclose(f);
+                    h->depth = d;
+                    return fmm_set_p2p_tile(h, th, kt);
+                }
+            }
+            fclose(f);
+        }
+    }
+    int tiles[][2] = {{64, 1}, {64, 2}, {128, 1}, {128, 2}, {32, 2}};
+    int ntile = h->mixed ? 5 : 1;
+    int save_graph = h->use_graph, save_timing = h->timing;
+    h->use_graph = 0;
+    h->timing = 0;
+    float best = 1e30f;
+    int bd = h->depth, bth = h->p2p_threads, bkt = h->p2p_kt;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    for (int d = depth_lo; d <= depth_hi; ++d) {
+        for (int ti = 0; ti < ntile; ++ti) {
+            h->depth = d;
+            h->p2p_threads = tiles[ti][0];
+            h->p2p_kt = tiles[ti][1];
+            float ts[5];
+            bool ok = true;
+            for (int r = 0; r < 7 && ok; ++r) {
+                CU(cudaEventRecord(e0, h->stream));
+                ok = fmm_velocity(h, n, x, y, gamma, u, v) == FMM_OK;
+                CU(cudaEventRecord(e1, h->stream));
+                CU(cudaEventSynchronize(e1));
+                if (r >= 2)
+                    cudaEventElapsedTime(&ts[r - 2], e0, e1);
+            }
+            if (!ok)
+                continue;
+            std::sort(ts, ts + 5);
+            if (ts[2] < best) {
+                best = ts[2];
+                bd = d;
+                bth = tiles[ti][0];
+                bkt = tiles[ti][1];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->use_graph = save_graph;
+    h->timing = save_timing;
+    h->depth = bd;
+    h->p2p_threads = bth;
+    h->p2p_kt = bkt;
+    if (cache) {
+        FILE *f = fopen(cache, "a");
+        if (f) {
+            fprintf(f, "%s|%d %d %d\n", keybuf, bd, bth, bkt);
+            fclose(f);
+        }
+    }
+    if (best >= 1e30f)
+        return set_err(h, FMM_ECUDA, "no candidate ran");
+    return FMM_OK;
+}
+
+const char *fmm_status_string(fmm_status s)
+{
+    switch (s) {
+    case FMM_OK: return "ok";
+    case FMM_EINVAL: return "invalid argument or particle outside the root square";
+    case FMM_ENOMEM: return "out of memory";
+    case FMM_ECUDA: return "CUDA error";
+    case FMM_ETIMEOUT: return "device wait timed out";
+    case FMM_EINTERNAL: return "device bounds check failed";
+    }
+    return "unknown status";
+}
+
+const char *fmm_last_error(fmm_handle h) { return h ? h->err.c_str() : "no handle"; }
+
+}  // extern "C"

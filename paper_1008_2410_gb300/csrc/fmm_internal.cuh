@@ -1,0 +1,148 @@
+// fmm_internal.cuh -- data layout and kernel entry points shared by the library's translation units.
+//
+// Layout in HBM (one workspace allocation per handle, carved into 256-byte aligned arrays):
+//   particles in the caller's order : key[n] (global leaf of each particle)
+//   particles in leaf order         : perm[n] (sorted position -> caller index), sleaf[n] (global leaf),
+//                                     FP64 form: sx, sy, sg (absolute coordinates, circulation),
+//                                     precision form: pos4[n] = (xh, yh, xl, yl) leaf-relative split
+//                                     coordinates in leaf units, g32[n]
+//   leaves                          : cnt[nleaf] (histogram), start[nleaf + 1] (first sorted position)
+//   boxes (levels 2..L of every system, row-major per level): bcount[nbox] (particles in the box),
+//                                     multipoles and locals, p complex coefficients per box, FP64 and/or FP32
+// Expansions are stored radius-scaled so every translation matrix is level independent:
+//   multipole  a~_m = sum_j q'_j zeta_j^m, zeta = (z - c) / w_l, q' = -i gamma (the 1/2pi is applied at the end)
+//   local      b^_l = w_l^(l+1) b_l, so that the far field at z is (1 / (2 pi w_L)) sum_l b^_l zeta^l.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FMM_MAXL 12
+#define FMM_PMAX 32
+#define FMM_MAXSYS 4096
+#define FMM_NOFF 49  // M2L offsets (dx, dy) in [-3, 3]^2, indexed (dy + 3) * 7 + (dx + 3)
+
+// device status bits (OR-ed into the status word)
+#define FMM_DEV_OUTSIDE 1u
+#define FMM_DEV_BOUNDS 2u
+#define FMM_DEV_TIMEOUT 4u
+
+namespace fmm {
+
+// Per-system descriptor, device resident (one per system of a batch; a plain evaluation is a batch of one).
+struct SysDev {
+    int64_t p0, np;                 // particle range [p0, p0 + np) in caller and in sorted order
+    int64_t leaf0;                  // first global leaf of this system
+    int64_t box0[FMM_MAXL + 1];     // first global box of level l (2 <= l <= depth), else -1
+    double x0, y0, S;               // root square (explicit, or written by the bounding-box kernel)
+    double sigma;
+    int depth;
+    int explicit_domain;
+    int pad[2];
+};
+
+// Per-level work lists for the tree sweeps, computed on the host and passed by value. The systems that have
+// level l (depth >= l) are sys_list[first_at[l] .. first_at[l] + nsys_at[l]) (device array, ascending).
+struct LevelInfo {
+    int nsys_at[FMM_MAXL + 2];
+    int first_at[FMM_MAXL + 2];
+    int64_t m2l_item0[FMM_MAXL + 2];  // prefix over levels 2..maxdepth of (systems at l) * 4^l boxes
+    int maxdepth;
+    int mindepth2;                     // smallest depth >= 2 among the systems (0 if none)
+};
+
+// Read-only tables that depend on p only.
+struct Tables {
+    double2 *m2m64, *l2l64;   // [4][PMAX][PMAX]  (child position c = cy * 2 + cx; row n / k, column m / l)
+    float2 *m2m32, *l2l32;
+    double2 *rho64;           // [FMM_NOFF][2 PMAX + 2]  (1/delta)^k
+    float2 *rho32;
+    double *binom64;          // [PMAX][PMAX]  C(m + l, m)
+    float *binom32;
+};
+
+struct Work {
+    int n;
+    int nleaf;
+    int64_t nbox;
+    int p;
+    int mixed;
+    int coarse_level;         // levels <= this run in FP64 in the precision form
+    int nsys;
+    int maxdepth;
+    // arrays
+    int *key, *cnt, *start, *scan_tmp, *tmp, *perm, *sleaf;
+    double *sx, *sy, *sg;
+    float4 *pos4;
+    float *g32;
+    double2 *near64;
+    float2 *near32;
+    int *bcount;
+    double2 *M64, *L64;
+    float2 *M32, *L32;
+    // adjoint extras
+    double *sgu, *sgv;
+    double2 *AM64, *AL64;     // expansions of the adjoint charges G = gu + i gv
+    double2 *wprime;          // derivative of the forward far field at each sorted particle
+    unsigned long long *minmax;  // [4 * nsys] bounding-box reduction
+    unsigned int *status;
+    unsigned long long *pair_count;
+    double *adj_far;          // [3 n] far-field part of (dgamma, dx, dy) in leaf order
+    SysDev *sys;
+    int *sys_list;
+    LevelInfo lv;
+};
+
+// Level precision in the precision form: FP64 for l <= coarse_level.
+__host__ __device__ inline bool level_fp64(const Work &w, int l) { return !w.mixed || l <= w.coarse_level; }
+
+// System of a particle / leaf: the last system whose first particle / leaf is <= the index (systems are
+// contiguous and ordered; empty systems share their first index with the next system).
+__device__ inline int find_sys_by_particle(const SysDev *sys, int nsys, int64_t i)
+{
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sys[mid].p0 <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ inline int find_sys_by_leaf(const SysDev *sys, int nsys, int64_t leaf)
+{
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sys[mid].leaf0 <= leaf)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---- launchers (each returns the number of kernels launched) ----
+int launch_bbox(const Work &w, const double *x, const double *y, cudaStream_t s);
+int launch_domain_finalize(const Work &w, cudaStream_t s);
+int launch_keys(const Work &w, const double *x, const double *y, cudaStream_t s);
+int launch_scan(const Work &w, cudaStream_t s);  // cnt -> start
+int launch_scatter_sort(const Work &w, cudaStream_t s);
+int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
+                  const double *gv, cudaStream_t s);
+int launch_pair_count(const Work &w, cudaStream_t s);
+int launch_p2m(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t s);
+int launch_m2m(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
+int launch_m2l(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t s, int prio);
+int launch_l2l(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
+int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);
+int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
+int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far
+int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);  // adds it
+int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);
+
+void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom);
+
+}  // namespace fmm

@@ -1,0 +1,585 @@
+// sweep.cu -- Fig. 1 stages 4-8 and 10: P2M, M2M, M2L, L2L, and the fused L2P + sum + unsort.
+//
+// Expansions (§3: a t-term multipole with coefficients sum_p Gamma_p (x_p - x_c)^m, times -i/2pi) are kept
+// radius-scaled: a~_m = sum_j q'_j zeta_j^m with zeta = (z - c)/w_l and q' = -i gamma; locals
+// b^_l = w_l^(l+1) b_l. In these units every translation matrix is the same on every level:
+//   M2M  a~'_n = sum_{m<=n} C(n, m) delta^(n-m) 2^-m a~_m,          delta = (c_child - c_parent)/w_parent
+//   M2L  b^_l  = sum_m (-1)^(m+1) C(m+l, m) rho^(m+l+1) a~_m,       rho = w / (c_source - c_target)
+//   L2L  b^'_k = sum_{l>=k} C(l, k) delta^(l-k) 2^-(l+1) b^_l,     delta = (c_child - c_parent)/w_child
+// and the far field at z is w = u - i v = (1 / (2 pi w_L)) sum_l b^_l zeta^l. M2L is evaluated in the
+// factored form b^_l = rho^(l+1) sum_m C(m+l, m) [(-1)^(m+1) rho^m a~_m]: a real p x p contraction between
+// two diagonal complex scalings, 2p^2 + 12p flops per translation instead of 8p^2.
+#include <type_traits>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+template <typename R>
+struct cx {
+    R re, im;
+};
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b)
+{
+    return {a.re + b.re, a.im + b.im};
+}
+
+template <typename R>
+struct store_of;
+template <>
+struct store_of<double> {
+    typedef double2 T;
+};
+template <>
+struct store_of<float> {
+    typedef float2 T;
+};
+
+template <typename R, typename S>
+__device__ __forceinline__ cx<R> ldc(const S *p, int64_t i)
+{
+    S v = p[i];
+    return {(R)v.x, (R)v.y};
+}
+template <typename R>
+__device__ __forceinline__ void stc(double2 *p, int64_t i, cx<R> v)
+{
+    p[i] = make_double2((double)v.re, (double)v.im);
+}
+template <typename R>
+__device__ __forceinline__ void stc(float2 *p, int64_t i, cx<R> v)
+{
+    p[i] = make_float2((float)v.re, (float)v.im);
+}
+
+__device__ __forceinline__ int sys_at_level(const Work &w, int l, int sidx)
+{
+    return w.sys_list[w.lv.first_at[l] + sidx];
+}
+
+// ------------------------------------------------------------------ stage 4: P2M (one warp per leaf)
+
+// Compute type R; coefficients written to the leaf level's array (FP64 or FP32). PM >= p terms are
+// accumulated (the first p are the p-term expansion; the rest are discarded).
+template <int PM, typename R>
+__global__ void __launch_bounds__(64) k_p2m(Work w, int adj)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R> *sh = reinterpret_cast<cx<R> *>(smem_raw) + (threadIdx.x >> 5) * 32 * (PM + 1);
+    int lane = threadIdx.x & 31;
+    int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (leaf >= w.nleaf)
+        return;
+    int k = w.nsys == 1 ? 0 : find_sys_by_leaf(w.sys, w.nsys, leaf);
+    const SysDev &d = w.sys[k];
+    int L = d.depth;
+    if (L < 2)
+        return;
+    int local = (int)(leaf - d.leaf0);
+    int64_t box = d.box0[L] + local;
+    int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
+    if (lane == 0)
+        w.bcount[box] = c;
+    if (c == 0)
+        return;
+    int ix = local & ((1 << L) - 1), iy = local >> L;
+    double scale = ldexp(1.0, L) / d.S;
+    cx<R> a[PM];
+#pragma unroll
+    for (int m = 0; m < PM; ++m)
+        a[m] = {(R)0, (R)0};
+    for (int j = s0 + lane; j < s0 + c; j += 32) {
+        cx<R> z, q;
+        if (w.mixed) {
+            float4 pp = w.pos4[j];
+            z = {(R)pp.x + (R)pp.z, (R)pp.y + (R)pp.w};
+            q = {(R)0, -(R)w.g32[j]};
+        } else {
+            z = {(R)((w.sx[j] - d.x0) * scale - (ix + 0.5)), (R)((w.sy[j] - d.y0) * scale - (iy + 0.5))};
+            if (adj)
+                q = {(R)w.sgu[j], (R)w.sgv[j]};
+            else
+                q = {(R)0, -(R)w.sg[j]};
+        }
+        cx<R> pw = q;
+#pragma unroll
+        for (int m = 0; m < PM; ++m) {
+            a[m] = cadd(a[m], pw);
+            pw = cmul(pw, z);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < PM; ++m)
+        sh[lane * (PM + 1) + m] = a[m];
+    __syncwarp();
+    if (lane < w.p) {
+        cx<R> s = {(R)0, (R)0};
+        for (int r = 0; r < 32; ++r)
+            s = cadd(s, sh[r * (PM + 1) + lane]);
+        int64_t idx = box * w.p + lane;
+        if (level_fp64(w, L))
+            stc(adj ? w.AM64 : w.M64, idx, s);
+        else
+            stc(w.M32, idx, s);
+    }
+}
+
+template <int PM>
+static void p2m_dispatch(const Work &w, int adj, cudaStream_t s)
+{
+    int blocks = (int)(((int64_t)w.nleaf * 32 + 63) / 64);
+    // FP32 accumulation only when every system's leaf level is an FP32 level; the FP64 kernel writes either.
+    if (w.mixed && w.lv.mindepth2 > w.coarse_level) {
+        size_t sm = 2 * 32 * (PM + 1) * sizeof(cx<float>);
+        k_p2m<PM, float><<<blocks, 64, sm, s>>>(w, adj);
+    } else {
+        size_t sm = 2 * 32 * (PM + 1) * sizeof(cx<double>);
+        k_p2m<PM, double><<<blocks, 64, sm, s>>>(w, adj);
+    }
+}
+
+int launch_p2m(const Work &w, const Tables &t, int adj, cudaStream_t s)
+{
+    (void)t;
+    if (w.p <= 8)
+        p2m_dispatch<8>(w, adj, s);
+    else if (w.p <= 16)
+        p2m_dispatch<16>(w, adj, s);
+    else if (w.p <= 24)
+        p2m_dispatch<24>(w, adj, s);
+    else
+        p2m_dispatch<32>(w, adj, s);
+    return 1;
+}
+
+// ------------------------------------------------------------------ stage 5: M2M (thread per parent coefficient)
+
+template <typename RA, typename SC, typename SP>
+__global__ void k_m2m(Work w, const double2 *__restrict__ tab64, const float2 *__restrict__ tab32, int l,
+                      const SC *__restrict__ child, SP *parent)
+{
+    int p = w.p;
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nb = (int64_t)1 << (2 * l);
+    int64_t total = (int64_t)w.lv.nsys_at[l + 1] * nb * p;
+    if (g >= total)
+        return;
+    int n = (int)(g % p);
+    int64_t rest = g / p;
+    int b = (int)(rest & (nb - 1));
+    int sidx = (int)(rest >> (2 * l));
+    const SysDev &d = w.sys[sys_at_level(w, l + 1, sidx)];
+    int ns = 1 << l, bx = b & (ns - 1), by = b >> l;
+    int64_t pbox = d.box0[l] + b;
+    cx<RA> acc = {(RA)0, (RA)0};
+    int count = 0;
+    for (int c = 0; c < 4; ++c) {
+        int cx_ = c & 1, cy_ = c >> 1;
+        int64_t cbox = d.box0[l + 1] + (int64_t)(2 * by + cy_) * (2 * ns) + (2 * bx + cx_);
+        int cc = w.bcount[cbox];
+        count += cc;
+        if (cc == 0)
+            continue;
+        for (int m = 0; m <= n; ++m) {
+            cx<RA> T;
+            if constexpr (std::is_same<RA, double>::value) {
+                double2 t = tab64[(c * FMM_PMAX + n) * FMM_PMAX + m];
+                T = {(RA)t.x, (RA)t.y};
+            } else {
+                float2 t = tab32[(c * FMM_PMAX + n) * FMM_PMAX + m];
+                T = {(RA)t.x, (RA)t.y};
+            }
+            acc = cadd(acc, cmul(T, ldc<RA>(child, cbox * p + m)));
+        }
+    }
+    if (n == 0)
+        w.bcount[pbox] = count;
+    if (count)
+        stc(parent, pbox * p + n, acc);
+}
+
+int launch_m2m(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, int prio)
+{
+    (void)prio;
+    int64_t total = (int64_t)w.lv.nsys_at[l + 1] * ((int64_t)1 << (2 * l)) * w.p;
+    if (total == 0)
+        return 0;
+    int blocks = (int)((total + 127) / 128);
+    bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
+    double2 *M64 = adj ? w.AM64 : w.M64;
+    if (pd && cd)
+        k_m2m<double, double2, double2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, M64, M64);
+    else if (pd)
+        k_m2m<double, float2, double2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, w.M32, M64);
+    else
+        k_m2m<float, float2, float2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, w.M32, w.M32);
+    return 1;
+}
+
+// ------------------------------------------------------------------ stage 6: M2L (warp per target box, all levels)
+
+template <typename R, typename S>
+__device__ void m2l_box(const Work &w, const typename store_of<R>::T *__restrict__ rho, const R *__restrict__ binom,
+                        const S *__restrict__ M, S *Loc, const SysDev &d, int l, int b, cx<R> *alpha)
+{
+    int lane = threadIdx.x & 31, p = w.p;
+    int ns = 1 << l, bx = b & (ns - 1), by = b >> l;
+    int px = bx >> 1, py = by >> 1, np_ = ns >> 1;
+    cx<R> acc = {(R)0, (R)0};
+    const int RS = 2 * FMM_PMAX + 2;
+    for (int qy = py - 1; qy <= py + 1; ++qy) {
+        if (qy < 0 || qy >= np_)
+            continue;
+        for (int qx = px - 1; qx <= px + 1; ++qx) {
+            if (qx < 0 || qx >= np_)
+                continue;
+            for (int c = 0; c < 4; ++c) {
+                int jx = 2 * qx + (c & 1), jy = 2 * qy + (c >> 1);
+                int ddx = jx - bx, ddy = jy - by;
+                if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1)
+                    continue;
+                int64_t sb = d.box0[l] + (int64_t)jy * ns + jx;
+                if (w.bcount[sb] == 0)
+                    continue;
+                int o = (ddy + 3) * 7 + (ddx + 3);
+                const typename store_of<R>::T *rp = rho + o * RS;
+                if (lane < p) {
+                    cx<R> a = ldc<R>(M, sb * p + lane);
+                    auto r = rp[lane];
+                    cx<R> t = cmul(cx<R>{(R)r.x, (R)r.y}, a);
+                    if (!(lane & 1)) {  // (-1)^(m+1)
+                        t.re = -t.re;
+                        t.im = -t.im;
+                    }
+                    alpha[lane] = t;
+                }
+                __syncwarp();
+                if (lane < p) {
+                    cx<R> beta = {(R)0, (R)0};
+                    for (int m = 0; m < p; ++m) {
+                        R cb = binom[m * FMM_PMAX + lane];
+                        cx<R> am = alpha[m];
+                        beta.re += cb * am.re;
+                        beta.im += cb * am.im;
+                    }
+                    auto r1 = rp[lane + 1];
+                    acc = cadd(acc, cmul(cx<R>{(R)r1.x, (R)r1.y}, beta));
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (lane < p)
+        stc(Loc, (d.box0[l] + b) * (int64_t)p + lane, acc);
+}
+
+__global__ void __launch_bounds__(128) k_m2l(Work w, Tables t, int adj)
+{
+    __shared__ __align__(16) double2 alpha_sh[4][32];
+    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int l = 2;
+    while (l < w.lv.maxdepth && gw >= w.lv.m2l_item0[l + 1])
+        ++l;
+    if (l > w.lv.maxdepth || gw >= w.lv.m2l_item0[l + 1])
+        return;
+    int64_t g = gw - w.lv.m2l_item0[l];
+    int b = (int)(g & (((int64_t)1 << (2 * l)) - 1));
+    int sidx = (int)(g >> (2 * l));
+    const SysDev &d = w.sys[sys_at_level(w, l, sidx)];
+    if (w.bcount[d.box0[l] + b] == 0)
+        return;
+    int wi = threadIdx.x >> 5;
+    if (level_fp64(w, l)) {
+        double2 *M = adj ? w.AM64 : w.M64, *Lc = adj ? w.AL64 : w.L64;
+        m2l_box<double, double2>(w, t.rho64, t.binom64, M, Lc, d, l, b,
+                                 reinterpret_cast<cx<double> *>(alpha_sh[wi]));
+    } else {
+        m2l_box<float, float2>(w, t.rho32, t.binom32, w.M32, w.L32, d, l, b,
+                               reinterpret_cast<cx<float> *>(alpha_sh[wi]));
+    }
+}
+
+int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio)
+{
+    (void)prio;
+    int64_t warps = w.lv.m2l_item0[w.lv.maxdepth + 1];
+    if (w.lv.maxdepth < 2 || warps == 0)
+        return 0;
+    int64_t blocks = (warps * 32 + 127) / 128;
+    k_m2l<<<(unsigned)blocks, 128, 0, s>>>(w, t, adj);
+    return 1;
+}
+
+// ------------------------------------------------------------------ stage 7: L2L (thread per child coefficient)
+
+template <typename RA, typename SPa, typename SCh>
+__global__ void k_l2l(Work w, const double2 *__restrict__ tab64, const float2 *__restrict__ tab32, int l,
+                      const SPa *__restrict__ parent, SCh *child)
+{
+    int p = w.p;
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nb = (int64_t)1 << (2 * (l + 1));
+    int64_t total = (int64_t)w.lv.nsys_at[l + 1] * nb * p;
+    if (g >= total)
+        return;
+    int kk = (int)(g % p);
+    int64_t rest = g / p;
+    int b = (int)(rest & (nb - 1));
+    int sidx = (int)(rest >> (2 * (l + 1)));
+    const SysDev &d = w.sys[sys_at_level(w, l + 1, sidx)];
+    int64_t cbox = d.box0[l + 1] + b;
+    if (w.bcount[cbox] == 0)
+        return;
+    int ns = 1 << (l + 1), bx = b & (ns - 1), by = b >> (l + 1);
+    int c = (by & 1) * 2 + (bx & 1);
+    int64_t pbox = d.box0[l] + (int64_t)(by >> 1) * (ns >> 1) + (bx >> 1);
+    cx<RA> acc = ldc<RA>(child, cbox * p + kk);
+    for (int j = kk; j < p; ++j) {
+        cx<RA> T;
+        if constexpr (std::is_same<RA, double>::value) {
+            double2 t = tab64[(c * FMM_PMAX + kk) * FMM_PMAX + j];
+            T = {(RA)t.x, (RA)t.y};
+        } else {
+            float2 t = tab32[(c * FMM_PMAX + kk) * FMM_PMAX + j];
+            T = {(RA)t.x, (RA)t.y};
+        }
+        acc = cadd(acc, cmul(T, ldc<RA>(parent, pbox * p + j)));
+    }
+    stc(child, cbox * p + kk, acc);
+}
+
+int launch_l2l(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, int prio)
+{
+    (void)prio;
+    int64_t total = (int64_t)w.lv.nsys_at[l + 1] * ((int64_t)1 << (2 * (l + 1))) * w.p;
+    if (total == 0)
+        return 0;
+    int blocks = (int)((total + 127) / 128);
+    bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
+    double2 *L64 = adj ? w.AL64 : w.L64;
+    if (pd && cd)
+        k_l2l<double, double2, double2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, L64);
+    else if (pd)
+        k_l2l<double, double2, float2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, w.L32);
+    else
+        k_l2l<float, float2, float2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, w.L32, w.L32);
+    return 1;
+}
+
+// ------------------------------------------------------------------ stages 8 + 10: L2P, sum, unsort
+
+template <typename R, typename S>
+__device__ __forceinline__ cx<R> horner(const S *__restrict__ b, int64_t base, int p, cx<R> z)
+{
+    cx<R> acc = ldc<R>(b, base + p - 1);
+    for (int l = p - 2; l >= 0; --l)
+        acc = cadd(cmul(acc, z), ldc<R>(b, base + l));
+    return acc;
+}
+
+__global__ void k_combine(Work w, int use_near, int use_far, double *__restrict__ u, double *__restrict__ v)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= w.n)
+        return;
+    int k = w.nsys == 1 ? 0 : find_sys_by_particle(w.sys, w.nsys, pos);
+    const SysDev &d = w.sys[k];
+    int L = d.depth;
+    double fu = 0.0, fv = 0.0;
+    if (use_far && L >= 2) {
+        int local = (int)(w.sleaf[pos] - d.leaf0);
+        int64_t base = (d.box0[L] + local) * (int64_t)w.p;
+        double f = 1.0 / (2.0 * 3.14159265358979323846 * ldexp(d.S, -L));
+        if (level_fp64(w, L)) {
+            cx<double> z;
+            if (w.mixed) {
+                float4 pp = w.pos4[pos];
+                z = {(double)pp.x + (double)pp.z, (double)pp.y + (double)pp.w};
+            } else {
+                int ix = local & ((1 << L) - 1), iy = local >> L;
+                double scale = ldexp(1.0, L) / d.S;
+                z = {(w.sx[pos] - d.x0) * scale - (ix + 0.5), (w.sy[pos] - d.y0) * scale - (iy + 0.5)};
+            }
+            cx<double> s = horner<double>(w.L64, base, w.p, z);
+            fu = s.re * f;
+            fv = -s.im * f;
+        } else {
+            float4 pp = w.pos4[pos];
+            cx<float> z = {pp.x + pp.z, pp.y + pp.w};
+            cx<float> s = horner<float>(w.L32, base, w.p, z);
+            fu = (double)s.re * f;
+            fv = -(double)s.im * f;
+        }
+    }
+    double nu = 0.0, nv = 0.0;
+    if (use_near) {
+        if (w.mixed) {
+            float2 t = w.near32[pos];
+            nu = t.x;
+            nv = t.y;
+        } else {
+            double2 t = w.near64[pos];
+            nu = t.x;
+            nv = t.y;
+        }
+    }
+    int i = w.perm[pos];
+    u[i] = nu + fu;
+    v[i] = nv + fv;
+}
+
+int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s)
+{
+    k_combine<<<(w.n + 255) / 256, 256, 0, s>>>(w, use_near, use_far, u, v);
+    return 1;
+}
+
+// ------------------------------------------------------------------ adjoint: far-field part (FP64)
+
+// With G = gu + i gv, q = -i gamma / 2pi, w the forward far field and phi(z) = sum_i G_i / (z - z_i) the far
+// field of the adjoint charges (same tree, same truncation), the transpose of the far-field operator is
+// (T^T G)_j = -phi(z_j) because the truncated operator is antisymmetric. Hence
+//   dL/dgamma_j = -Im phi(z_j) / 2pi,  dL/dx_j = Re(G_j w'(z_j)) - Re(q_j phi'(z_j)),
+//   dL/dy_j = -Im(G_j w'(z_j)) + Im(q_j phi'(z_j)).
+__global__ void k_adjoint_far(Work w)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= w.n)
+        return;
+    int k = w.nsys == 1 ? 0 : find_sys_by_particle(w.sys, w.nsys, pos);
+    const SysDev &d = w.sys[k];
+    int L = d.depth;
+    double dg = 0.0, dx = 0.0, dy = 0.0;
+    if (L >= 2) {
+        int local = (int)(w.sleaf[pos] - d.leaf0);
+        int64_t base = (d.box0[L] + local) * (int64_t)w.p;
+        int ix = local & ((1 << L) - 1), iy = local >> L;
+        double scale = ldexp(1.0, L) / d.S, wl = ldexp(d.S, -L);
+        cx<double> z = {(w.sx[pos] - d.x0) * scale - (ix + 0.5), (w.sy[pos] - d.y0) * scale - (iy + 0.5)};
+        // forward derivative w' and adjoint phi, phi' by Horner on the polynomial and its derivative
+        cx<double> bw = {0, 0}, bwd = {0, 0}, ph = {0, 0}, phd = {0, 0};
+        for (int l = w.p - 1; l >= 0; --l) {
+            cx<double> bl = ldc<double>(w.L64, base + l), Bl = ldc<double>(w.AL64, base + l);
+            bwd = cadd(cmul(bwd, z), bw);
+            bw = cadd(cmul(bw, z), bl);
+            phd = cadd(cmul(phd, z), ph);
+            ph = cadd(cmul(ph, z), Bl);
+        }
+        const double twopi = 2.0 * 3.14159265358979323846;
+        cx<double> wp = {bwd.re / (twopi * wl * wl), bwd.im / (twopi * wl * wl)};
+        cx<double> phi = {ph.re / wl, ph.im / wl};
+        cx<double> phip = {phd.re / (wl * wl), phd.im / (wl * wl)};
+        cx<double> G = {w.sgu[pos], w.sgv[pos]};
+        cx<double> q = {0.0, -w.sg[pos] / twopi};
+        cx<double> Gw = cmul(G, wp), qp = cmul(q, phip);
+        dg = -phi.im / twopi;
+        dx = Gw.re - qp.re;
+        dy = -Gw.im + qp.im;
+    }
+    w.adj_far[pos] = dg;
+    w.adj_far[(int64_t)w.n + pos] = dx;
+    w.adj_far[2 * (int64_t)w.n + pos] = dy;
+}
+
+int launch_adjoint_far(const Work &w, cudaStream_t s)
+{
+    k_adjoint_far<<<(w.n + 255) / 256, 256, 0, s>>>(w);
+    return 1;
+}
+
+__global__ void k_adjoint_add(Work w, double *__restrict__ dg, double *__restrict__ dx, double *__restrict__ dy)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= w.n)
+        return;
+    int i = w.perm[pos];
+    int64_t n = w.n;
+    if (dg)
+        dg[i] += w.adj_far[pos];
+    if (dx)
+        dx[i] += w.adj_far[n + pos];
+    if (dy)
+        dy[i] += w.adj_far[2 * n + pos];
+}
+
+int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s)
+{
+    k_adjoint_add<<<(w.n + 255) / 256, 256, 0, s>>>(w, dg, dx, dy);
+    return 1;
+}
+
+// ------------------------------------------------------------------ tables
+
+static double binom_host(int n, int k)
+{
+    if (k < 0 || k > n)
+        return 0.0;
+    double c = 1.0;
+    for (int i = 1; i <= k; ++i)
+        c = c * (double)(n - k + i) / (double)i;
+    return c;
+}
+
+// m2m[c][n][m] = C(n, m) delta_c^(n-m) 2^-m, delta_c = ((cx - 1/2) + i (cy - 1/2)) / 2;
+// l2l[c][k][l] = C(l, k) delta_c^(l-k) 2^-(l+1), delta_c = (cx - 1/2) + i (cy - 1/2);
+// rho[o][k] = (1/delta_o)^k, delta_o = dx + i dy; binom[m][l] = C(m + l, m).
+void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom)
+{
+    (void)p;
+    const int P = FMM_PMAX;
+    for (int c = 0; c < 4; ++c) {
+        double ddx = (c & 1) - 0.5, ddy = (c >> 1) - 0.5;
+        double pre[2 * FMM_PMAX][2], prl[2 * FMM_PMAX][2];
+        pre[0][0] = 1.0;
+        pre[0][1] = 0.0;
+        prl[0][0] = 1.0;
+        prl[0][1] = 0.0;
+        for (int k = 1; k < P; ++k) {
+            double ar = 0.5 * ddx, ai = 0.5 * ddy;  // M2M delta
+            pre[k][0] = pre[k - 1][0] * ar - pre[k - 1][1] * ai;
+            pre[k][1] = pre[k - 1][0] * ai + pre[k - 1][1] * ar;
+            prl[k][0] = prl[k - 1][0] * ddx - prl[k - 1][1] * ddy;  // L2L delta
+            prl[k][1] = prl[k - 1][0] * ddy + prl[k - 1][1] * ddx;
+        }
+        for (int n = 0; n < P; ++n)
+            for (int m = 0; m < P; ++m) {
+                double2 t = make_double2(0.0, 0.0), s = make_double2(0.0, 0.0);
+                if (m <= n) {
+                    double f = binom_host(n, m) * ldexp(1.0, -m);
+                    t = make_double2(f * pre[n - m][0], f * pre[n - m][1]);
+                }
+                m2m[(c * P + n) * P + m] = t;
+                // l2l: row k = n, column l = m (l >= k)
+                if (m >= n) {
+                    double f = binom_host(m, n) * ldexp(1.0, -(m + 1));
+                    s = make_double2(f * prl[m - n][0], f * prl[m - n][1]);
+                }
+                l2l[(c * P + n) * P + m] = s;
+            }
+    }
+    const int RS = 2 * FMM_PMAX + 2;
+    for (int oy = -3; oy <= 3; ++oy)
+        for (int ox = -3; ox <= 3; ++ox) {
+            int o = (oy + 3) * 7 + (ox + 3);
+            double den = (double)(ox * ox + oy * oy);
+            double rr = den > 0 ? ox / den : 0.0, ri = den > 0 ? -oy / den : 0.0;  // 1/(ox + i oy)
+            double pr = 1.0, pi = 0.0;
+            for (int k = 0; k < RS; ++k) {
+                rho[o * RS + k] = make_double2(pr, pi);
+                double nr = pr * rr - pi * ri, ni = pr * ri + pi * rr;
+                pr = nr;
+                pi = ni;
+            }
+        }
+    for (int m = 0; m < P; ++m)
+        for (int l = 0; l < P; ++l)
+            binom[m * P + l] = binom_host(m + l, m);
+}
+
+}  // namespace fmm

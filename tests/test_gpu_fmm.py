@@ -1,0 +1,334 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances: plain FP64 form within 1e-12 relative L2 of the oracle FMM at the same depth and p; precision
+form within 1e-6 relative L2 of the oracle FMM (FP32 arithmetic against FP64, same truncation); integer
+results (pair counts) exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import fmm_inputs as fi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-6
+
+
+def rel_l2(a, b):
+    a = np.concatenate([np.ravel(t) for t in a])
+    b = np.concatenate([np.ravel(t) for t in b])
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1008_2410_gb300 import api, build
+
+    build.build()
+    return api
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def run(lib, w, precision="fp64", domain="explicit", graph=False, mode="full", tile=None):
+    f = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain if domain == "explicit" else None,
+                graph=graph)
+    if tile:
+        f.set_p2p_tile(*tile)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    fn = {"full": f.velocity, "near": f.velocity_near, "far": f.velocity_far}[mode]
+    u, v = fn(x, y, g)
+    f.sync()
+    return u.cpu().numpy(), v.cpu().numpy(), f
+
+
+CASES = [
+    ("uniform5k_d3_p10", lambda: fi.uniform(5000, seed_index=31, depth=3, p=10)),
+    ("uniform40k_d5_p17", lambda: fi.uniform(40000, seed_index=32, depth=5, p=17)),
+    ("ragged12345_d4_p20", lambda: fi.uniform(12345, seed_index=33, depth=4, p=20)),
+    ("clustered20k_d5_p14", lambda: fi.clustered(20000, depth=5, p=14)),
+    ("lattice_lamb_oseen_d4_p12", lambda: fi.lattice_lamb_oseen()),
+    ("depth2_p8", lambda: fi.uniform(3000, seed_index=34, depth=2, p=8)),
+    ("depth1", lambda: fi.uniform(1500, seed_index=35, depth=1, p=8)),
+    ("depth0", lambda: fi.uniform(700, seed_index=36, depth=0, p=8)),
+    ("p1_d3", lambda: fi.uniform(2000, seed_index=37, depth=3, p=1)),
+    ("p32_d3", lambda: fi.uniform(2000, seed_index=38, depth=3, p=32)),
+    ("patches64k_d6_p20", lambda: fi.patches(1 << 16, seed_index=39, depth=6, p=20)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_fp64_matches_oracle_fmm(lib, oracle, name, make):
+    w = make()
+    u, v, _ = run(lib, w)
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)
+    assert rel_l2((u, v), (uo, vo)) < TOL64
+    scale = max(np.abs(uo).max(), np.abs(vo).max())
+    assert max(np.abs(u - uo).max(), np.abs(v - vo).max()) < 1e-11 * scale
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_mixed_matches_oracle_fmm(lib, oracle, name, make):
+    w = make()
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)
+    for coarse in (4, -1):
+        f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain, coarse_level=coarse)
+        u, v = f.velocity(dev(w.x), dev(w.y), dev(w.gamma))
+        f.sync()
+        assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < TOL32, coarse
+
+
+@pytest.mark.parametrize("tile", [(64, 1), (64, 2), (128, 1), (128, 2), (32, 2), (128, 4)])
+def test_mixed_tile_shapes(lib, oracle, tile):
+    w = fi.clustered(30000, depth=4, p=12)  # dense leaves: several target chunks and source tiles per leaf
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)
+    u, v, _ = run(lib, w, precision="mixed", tile=tile)
+    assert rel_l2((u, v), (uo, vo)) < TOL32
+
+
+def test_default_domain_bbox_rule(lib, oracle):
+    w = fi.clustered(9000, depth=4, p=12)
+    u, v, _ = run(lib, w, domain=None)
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=None)
+    assert rel_l2((u, v), (uo, vo)) < TOL64
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL32)])
+def test_near_and_far_halves(lib, oracle, precision, tol):
+    w = fi.uniform(20000, seed_index=40, depth=4, p=14)
+    un, vn, _ = run(lib, w, precision=precision, mode="near")
+    uf, vf, _ = run(lib, w, precision=precision, mode="far")
+    uon, von, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, parts="near")
+    uof, vof, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, parts="far")
+    assert rel_l2((un, vn), (uon, von)) < tol
+    assert rel_l2((uf, vf), (uof, vof)) < tol
+
+
+def test_pair_count_exact(lib, oracle):
+    w = fi.lattice_lamb_oseen()
+    f = lib.FMM(w.depth, w.p, w.sigma, domain=w.domain)
+    f.set_count_pairs(True)
+    f.velocity(dev(w.x), dev(w.y), dev(w.gamma))
+    assert f.pair_count() == 8650752
+    w = fi.clustered(15000, depth=5, p=8)
+    f = lib.FMM(w.depth, w.p, w.sigma, domain=w.domain)
+    f.set_count_pairs(True)
+    f.velocity(dev(w.x), dev(w.y), dev(w.gamma))
+    _, _, npairs = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, 2, domain=w.domain, parts="near")
+    assert f.pair_count() == npairs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_deterministic_and_graph_replay_identical(lib, precision):
+    w = fi.clustered(25000, depth=5, p=12)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain)
+    u1, v1 = f.velocity(x, y, g)
+    u2, v2 = f.velocity(x, y, g)
+    fg = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain, graph=True)
+    u3, v3 = fg.velocity(x, y, g)
+    u4, v4 = fg.velocity(x, y, g)  # replay
+    torch.cuda.synchronize()
+    for a, b in ((u1, u2), (v1, v2), (u1, u3), (v1, v3), (u1, u4), (v1, v4)):
+        assert torch.equal(a, b)
+
+
+def test_host_entry_point_equals_device(lib):
+    w = fi.uniform(30000, seed_index=41, depth=5, p=12)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain)
+    u, v = f.velocity(dev(w.x), dev(w.y), dev(w.gamma))
+    uh, vh = f.velocity_host(torch.from_numpy(w.x), torch.from_numpy(w.y), torch.from_numpy(w.gamma))
+    assert torch.equal(u.cpu(), uh) and torch.equal(v.cpu(), vh)
+
+
+def test_edge_cases(lib, oracle):
+    from paper_1008_2410_gb300._lib import FMMError
+
+    f = lib.FMM(3, 8, 0.01, domain=(0.0, 0.0, 1.0))
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    u, v = f.velocity(e, e, e)
+    assert u.numel() == 0
+    # one particle: no other particle acts on it
+    one = dev([0.3])
+    u, v = f.velocity(one, one, one)
+    f.sync()
+    assert u.item() == 0.0 and v.item() == 0.0
+    # coincident particles, points on leaf edges and on the square's upper edge, an empty system of leaves
+    x = np.array([0.25, 0.25, 0.5, 0.125, 1.0, 0.0, 0.999999, 0.6])
+    y = np.array([0.25, 0.25, 0.5, 0.875, 1.0, 0.0, 0.000001, 0.6])
+    g = np.array([1.0, -2.0, 0.5, 0.3, 0.7, -0.1, 0.2, 0.9])
+    for prec, tol in (("fp64", TOL64), ("mixed", TOL32)):
+        f2 = lib.FMM(3, 8, 0.01, precision=prec, domain=(0.0, 0.0, 1.0))
+        u, v = f2.velocity(dev(x), dev(y), dev(g))
+        f2.sync()
+        uo, vo, _ = oracle.fmm(x, y, g, 0.01, 3, 8, domain=(0.0, 0.0, 1.0))
+        assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < tol
+    # every particle in one leaf
+    w = fi.uniform(3000, seed_index=42, depth=3, p=8)
+    xs, ys = 0.1 + 0.01 * w.x, 0.1 + 0.01 * w.y
+    u, v, _ = run(lib, fi.Workload("one_leaf", xs, ys, w.gamma, 1e-3, 3, 8, (0.0, 0.0, 1.0)))
+    uo, vo, _ = oracle.fmm(xs, ys, w.gamma, 1e-3, 3, 8, domain=(0.0, 0.0, 1.0))
+    assert rel_l2((u, v), (uo, vo)) < TOL64
+    # a point outside the explicit square and a NaN are reported as FMM_EINVAL, and the handle stays usable
+    for bad in ([0.5, 1.5], [0.5, float("nan")]):
+        f3 = lib.FMM(3, 8, 0.01, domain=(0.0, 0.0, 1.0))
+        f3.velocity(dev(bad), dev([0.5, 0.5]), dev([1.0, 1.0]))
+        with pytest.raises(FMMError) as ei:
+            f3.sync()
+        assert ei.value.status == 1
+        u, v = f3.velocity(dev([0.2, 0.4]), dev([0.5, 0.5]), dev([1.0, 1.0]))
+        f3.sync()
+    with pytest.raises(FMMError):
+        lib.FMM(13, 8, 0.01)
+    with pytest.raises(FMMError):
+        lib.FMM(3, 33, 0.01)
+    with pytest.raises(FMMError):
+        lib.FMM(3, 8, -1.0)
+
+
+def test_batched_systems_match_single_evaluations(lib, oracle):
+    b = fi.batched(nsys=6, nmin=500, nmax=20000, p=10, seed_index=43)
+    off = b.offsets
+    x = np.concatenate([s.x for s in b.systems])
+    y = np.concatenate([s.y for s in b.systems])
+    g = np.concatenate([s.gamma for s in b.systems])
+    depths = [s.depth for s in b.systems]
+    sigmas = [s.sigma for s in b.systems]
+    doms = [s.domain for s in b.systems]
+    for prec, tol in (("fp64", TOL64), ("mixed", TOL32)):
+        f = lib.FMM(3, b.p, 0.01, precision=prec, graph=True)
+        u, v = f.velocity_batched(off, dev(x), dev(y), dev(g), depths=depths, sigmas=sigmas, domains=doms)
+        f.sync()
+        u, v = u.cpu().numpy(), v.cpu().numpy()
+        for k, s in enumerate(b.systems):
+            uo, vo, _ = oracle.fmm(s.x, s.y, s.gamma, s.sigma, s.depth, b.p, domain=s.domain)
+            sl = slice(off[k], off[k + 1])
+            assert rel_l2((u[sl], v[sl]), (uo, vo)) < tol, (prec, k)
+    # bounding-box rule per system, and an empty system in the middle
+    off2 = np.array([0, off[1], off[1], off[2]])
+    f = lib.FMM(3, b.p, 0.01)
+    n2 = off[2]
+    u, v = f.velocity_batched(off2, dev(x[:n2]), dev(y[:n2]), dev(g[:n2]), depths=[depths[0], 2, depths[1]],
+                              sigmas=[sigmas[0], 1.0, sigmas[1]])
+    f.sync()
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    for k, sys_k in ((0, 0), (2, 1)):
+        s = b.systems[sys_k]
+        uo, vo, _ = oracle.fmm(s.x, s.y, s.gamma, s.sigma, s.depth, b.p, domain=None)
+        sl = slice(off2[k], off2[k + 1])
+        assert rel_l2((u[sl], v[sl]), (uo, vo)) < TOL64
+
+
+def test_adjoint_matches_oracle(lib, oracle):
+    w = fi.uniform(6000, seed_index=44, depth=4, p=12)
+    rs = np.random.default_rng(9)
+    gu, gv = rs.normal(size=w.n), rs.normal(size=w.n)
+    f = lib.FMM(w.depth, w.p, w.sigma, domain=w.domain)
+    dg, dx, dy = f.adjoint(dev(w.x), dev(w.y), dev(w.gamma), dev(gu), dev(gv))
+    f.sync()
+    og, ox, oy = oracle.fmm_adjoint(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, gu, gv, domain=w.domain)
+    assert rel_l2((dg.cpu().numpy(),), (og,)) < 1e-11
+    assert rel_l2((dx.cpu().numpy(), dy.cpu().numpy()), (ox, oy)) < 1e-10
+
+
+def test_autograd_function_finite_differences(lib):
+    w = fi.uniform(3000, seed_index=45, depth=3, p=14)
+    f = lib.FMM(w.depth, w.p, w.sigma, domain=w.domain)
+    x = dev(w.x).requires_grad_(True)
+    y = dev(w.y).requires_grad_(True)
+    g = dev(w.gamma).requires_grad_(True)
+    ustar = dev(np.zeros(w.n))
+    u, v = lib.fmm_velocity(x, y, g, f)
+    L = 0.5 * ((u - ustar) ** 2).sum() + 0.5 * (v**2).sum()
+    L.backward()
+
+    def loss(xx, yy, gg):
+        uu, vv = f.velocity(xx, yy, gg)
+        return float(0.5 * (uu**2).sum() + 0.5 * (vv**2).sum())
+
+    rs = np.random.default_rng(10)
+    for j in rs.choice(w.n, 5, replace=False):
+        for arr, grad, h in ((g, g.grad, 1e-6 / w.n), (x, x.grad, 1e-8), (y, y.grad, 1e-8)):
+            base = arr.detach().clone()
+            p_, m_ = base.clone(), base.clone()
+            p_[j] += h
+            m_[j] -= h
+            args_p = [x.detach(), y.detach(), g.detach()]
+            args_m = [x.detach(), y.detach(), g.detach()]
+            idx = 0 if arr is x else (1 if arr is y else 2)
+            args_p[idx], args_m[idx] = p_, m_
+            fd = (loss(*args_p) - loss(*args_m)) / (2 * h)
+            an = grad[j].item()
+            assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-6 * float(grad.abs().max())), (idx, j, fd, an)
+
+
+def test_autograd_direct_limit_matches_torch_direct_sum(lib):
+    """Depth 1 (every pair near): gradients equal autograd through a torch FP64 Eq. 7 sum at N = 4096."""
+    w = fi.uniform(4096, seed_index=46, depth=1, p=8)
+    f = lib.FMM(1, 8, w.sigma, domain=w.domain)
+    x = dev(w.x).requires_grad_(True)
+    y = dev(w.y).requires_grad_(True)
+    g = dev(w.gamma).requires_grad_(True)
+    u, v = lib.fmm_velocity(x, y, g, f)
+    ustar = dev(np.random.default_rng(11).normal(size=w.n) * 1e-3)
+    L = 0.5 * ((u - ustar) ** 2).sum() + 0.5 * (v**2).sum()
+    L.backward()
+    xr = dev(w.x).requires_grad_(True)
+    yr = dev(w.y).requires_grad_(True)
+    gr = dev(w.gamma).requires_grad_(True)
+    a = xr[:, None] - xr[None, :]
+    b = yr[:, None] - yr[None, :]
+    eye = torch.eye(w.n, dtype=torch.bool, device="cuda")
+    r2 = torch.where(eye, torch.ones_like(a), a * a + b * b)
+    fk = torch.where(eye, torch.zeros_like(a), -torch.expm1(-r2 / (2 * w.sigma**2)) / (2 * math.pi * r2))
+    ur = torch.sum(gr[None, :] * (-b) * fk, dim=1)
+    vr = torch.sum(gr[None, :] * a * fk, dim=1)
+    Lr = 0.5 * ((ur - ustar) ** 2).sum() + 0.5 * (vr**2).sum()
+    Lr.backward()
+    for got, ref in ((g.grad, gr.grad), (x.grad, xr.grad), (y.grad, yr.grad)):
+        assert float((got - ref).norm() / ref.norm()) < 1e-11
+
+
+def test_stage_times_launch_count_and_autotune(lib):
+    w = fi.uniform(50000, seed_index=47, depth=5, p=12)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain)
+    f.set_timing(True)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    n0 = f.kernel_launches()
+    f.velocity(x, y, g)
+    t = f.stage_times()
+    assert len(t) == 8 and all(v >= 0 for v in t) and t[6] > 0
+    assert f.kernel_launches() > n0 + 8
+    prm = f.autotune(x, y, g, 4, 6)
+    assert 4 <= prm["depth"] <= 6
+    assert (prm["p2p_threads"], prm["p2p_targets_per_thread"]) in {(64, 1), (64, 2), (128, 1), (128, 2), (32, 2)}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,graph", [("mixed", True), ("fp64", True)])
+def test_uniform_1m_sampled_parity(lib, oracle, precision, graph):
+    """The 2^20-particle uniform workload (depth 7, p = 17) in the launch configuration the bench times,
+    checked at 2048 sampled targets against the oracle FMM."""
+    w = fi.uniform_1m()
+    u, v, _ = run(lib, w, precision=precision, graph=graph)
+    t = fi.sample_targets(w.n, 2048)
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, targets=t)
+    assert rel_l2((u[t], v[t]), (uo, vo)) < (TOL64 if precision == "fp64" else TOL32)
+
+
+@pytest.mark.slow
+def test_patches_16m_sampled_parity(lib, oracle):
+    """The 2^24-particle 8-patch workload (depth 9, p = 20), precision form, at 512 sampled targets."""
+    w = fi.patches_16m()
+    u, v, _ = run(lib, w, precision="mixed", graph=True)
+    t = fi.sample_targets(w.n, 512)
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, targets=t)
+    assert rel_l2((u[t], v[t]), (uo, vo)) < TOL32

@@ -289,6 +289,20 @@ def test_fmm_shallow_tree_is_direct_sum(oracle):
         assert rel_l2((u, v), (ue, ve)) < 1e-14
 
 
+def test_fmm_near_far_split(oracle):
+    """Stage 9 alone at depth <= 1 is the direct sum; the far part is then zero; near + far is the FMM."""
+    w = fi.uniform(600, seed_index=28)
+    ud, vd = oracle.direct(w.x, w.y, w.gamma, w.sigma)
+    un, vn, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, 1, 6, domain=w.domain, parts="near")
+    uf, vf, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, 1, 6, domain=w.domain, parts="far")
+    assert rel_l2((un, vn), (ud, vd)) < 1e-14 and not np.any(uf) and not np.any(vf)
+    un, vn, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, 3, 9, domain=w.domain, parts="near")
+    uf, vf, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, 3, 9, domain=w.domain, parts="far")
+    u, v, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, 3, 9, domain=w.domain)
+    assert np.allclose(un + uf, u, rtol=0, atol=1e-15 * np.abs(u).max())
+    assert np.allclose(vn + vf, v, rtol=0, atol=1e-15 * np.abs(v).max())
+
+
 def test_fmm_single_source_point_vortex(oracle):
     """One source and one distant target: the far field is the point vortex -i gamma / (2 pi (z_t - z_s))."""
     x = np.array([0.1, 0.83])

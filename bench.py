@@ -226,6 +226,12 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         num = torch.sqrt(((u - u64) ** 2).sum() + ((v - v64) ** 2).sum())
         den = torch.sqrt((u64**2).sum() + (v64**2).sum())
         out["rel_err_vs_fp64_form"] = float(num / den)
+        fc = api.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain, coarse_level=4)
+        uc, vc = fc.velocity(x, y, g)
+        torch.cuda.synchronize()
+        numc = torch.sqrt(((uc - u64) ** 2).sum() + ((vc - v64) ** 2).sum())
+        out["rel_err_vs_fp64_form_fp64_coarse_levels"] = float(numc / den)
+        fc.close()
         out["fp64_form"] = {"value": n / (statistics.median(ms64) / 1e3) / 1e6, "unit": "Mparticles/s",
                             "ms_per_step": statistics.median(ms64)}
         f64.close()
@@ -250,6 +256,15 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     P = SMS * 64
     out["model"] = {"B_actual": n / 4**w.depth, "B_min_for_overlap": model.min_leaf_occupancy_for_overlap(w.p, n, P),
                     "P_warps": P, "B_opt": model.b_opt(w.p)}
+
+    try:
+        from paper_1008_2410_gb300 import _lib as L
+
+        out["probed_peaks"] = L.probe_peaks()
+        out["roofline"]["frac_of_probed_fp32"] = (achieved / out["probed_peaks"]["fp32_tflops"]
+                                                  if achieved else None)
+    except Exception as exc:  # the probe is a report, not part of the metric
+        out["probed_peaks"] = {"error": str(exc)}
 
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, u.cpu().numpy(), v.cpu().numpy())

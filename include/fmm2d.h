@@ -57,7 +57,8 @@ typedef enum {
 typedef enum {
     FMM_FP64 = 0,  /* plain form: every stage in FP64 */
     FMM_MIXED = 1  /* precision form: FP32 near field (leaf-relative split coordinates, small-r series,
-                      compensated sums), FP32 P2M/L2P and fine-level M2M/M2L/L2L, FP64 on coarse levels */
+                      compensated sums), FP32 expansions; FP64 binning (bit-exact leaves) and, optionally,
+                      FP64 coarse levels (fmm_set_coarse_level) */
 } fmm_precision;
 
 /* Creates a handle. tree_depth L in [0, 12] (4^L leaves; L <= 1 means every pair is near field),
@@ -76,7 +77,9 @@ fmm_status fmm_clear_domain(fmm_handle h);
 fmm_status fmm_set_precision(fmm_handle h, fmm_precision mode);
 
 /* In the precision form, levels 2..coarse_level of M2M, M2L and L2L run in FP64 and finer levels in FP32.
- * Default 4; -1 runs every level in FP32. Ignored by FMM_FP64. */
+ * Default -1: every level in FP32 (the radius-scaled translation matrices have entries bounded by 1/2, so the
+ * coarse levels need no extra range; on GB300 an FP64 operation costs about 64 FP32 operations).
+ * Ignored by FMM_FP64. */
 fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level);
 
 /* Changes depth, p or sigma of an existing handle (same ranges as fmm_create). */
@@ -155,6 +158,11 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
                         double *u, double *v, int depth_lo, int depth_hi);
 fmm_status fmm_get_params(fmm_handle h, int *tree_depth, int *p, double *sigma, int *p2p_threads,
                           int *p2p_targets_per_thread);
+
+/* Measured throughput of the units the kernels are bound by, on the current device (a few hundred ms):
+ * out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA TFLOP/s, out[2] SFU ex2+rcp results per second / 1e12,
+ * out[3] SM count. cap >= 4. Allocates and frees 1 MiB of device memory. */
+fmm_status fmm_probe_peaks(double *out, int cap);
 
 /* Human-readable text of a status, and the last error message recorded on the handle. */
 const char *fmm_status_string(fmm_status s);

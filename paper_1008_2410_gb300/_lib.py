@@ -51,6 +51,7 @@ SIGNATURES = {
     "fmm_autotune": (_I, [_P, _I64, _P, _P, _P, _P, _P, _I, _I]),
     "fmm_get_params": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I),
                             ctypes.POINTER(_I)]),
+    "fmm_probe_peaks": (_I, [ctypes.POINTER(_D), _I]),
     "fmm_status_string": (ctypes.c_char_p, [_I]),
     "fmm_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -77,6 +78,16 @@ def load() -> ctypes.CDLL:
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def probe_peaks() -> dict:
+    """Measured FP32 / FP64 FMA TFLOP/s and SFU (ex2 + rcp) rate of the current device."""
+    lib = load()
+    buf = (_D * 4)()
+    st = lib.fmm_probe_peaks(buf, 4)
+    if st != FMM_OK:
+        raise FMMError(st, lib.fmm_status_string(st).decode())
+    return {"fp32_tflops": buf[0], "fp64_tflops": buf[1], "sfu_tops": buf[2], "sms": int(buf[3])}
 
 
 class FMMError(RuntimeError):

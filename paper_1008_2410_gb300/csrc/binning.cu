@@ -56,29 +56,48 @@ __global__ void k_bbox(const SysDev *__restrict__ sys, int nsys, int n, const do
 
 // Root square of every system without an explicit one: centre of the box, side = extent * (1 + 2^-20),
 // at least 1e-300. Explicit IEEE operations keep the result identical to a plain C evaluation.
+__device__ void derive_constants(SysDev &d)
+{
+    int L = d.depth;
+    d.scale = ldexp(1.0, L) / d.S;
+    d.xe = __dadd_rn(d.x0, d.S);
+    d.ye = __dadd_rn(d.y0, d.S);
+    d.wl = ldexp(d.S, -L);
+    d.far_scale = 1.0 / (6.283185307179586476925 * d.wl);
+    double kap = d.wl * d.wl / (2.0 * d.sigma * d.sigma);
+    d.kappa = (float)kap;
+    d.cexp = (float)(-1.4426950408889634074 * kap);
+    d.ythr = (float)(0.5 / kap);
+    d.snear = (float)d.far_scale;
+}
+
 __global__ void k_domain_finalize(SysDev *sys, int nsys, const unsigned long long *minmax)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nsys || sys[k].explicit_domain)
+    if (k >= nsys)
         return;
-    if (sys[k].np == 0 || minmax[4 * k + 1] == 0ull) {
-        sys[k].x0 = 0.0;
-        sys[k].y0 = 0.0;
-        sys[k].S = 1.0;
-        return;
+    SysDev &d = sys[k];
+    if (!d.explicit_domain) {
+        if (d.np == 0 || minmax[4 * k + 1] == 0ull) {
+            d.x0 = 0.0;
+            d.y0 = 0.0;
+            d.S = 1.0;
+        } else {
+            double xmin = double_of(minmax[4 * k + 0]), xmax = double_of(minmax[4 * k + 1]);
+            double ymin = double_of(minmax[4 * k + 2]), ymax = double_of(minmax[4 * k + 3]);
+            double ex = __dsub_rn(xmax, xmin), ey = __dsub_rn(ymax, ymin);
+            double ext = ex > ey ? ex : ey;
+            double side = __dmul_rn(ext, 1.0 + 0x1p-20);
+            if (side < 1e-300)
+                side = 1e-300;
+            double cx = __dmul_rn(0.5, __dadd_rn(xmin, xmax)), cy = __dmul_rn(0.5, __dadd_rn(ymin, ymax));
+            double half = __dmul_rn(0.5, side);
+            d.x0 = __dsub_rn(cx, half);
+            d.y0 = __dsub_rn(cy, half);
+            d.S = side;
+        }
     }
-    double xmin = double_of(minmax[4 * k + 0]), xmax = double_of(minmax[4 * k + 1]);
-    double ymin = double_of(minmax[4 * k + 2]), ymax = double_of(minmax[4 * k + 3]);
-    double ex = __dsub_rn(xmax, xmin), ey = __dsub_rn(ymax, ymin);
-    double ext = ex > ey ? ex : ey;
-    double side = __dmul_rn(ext, 1.0 + 0x1p-20);
-    if (side < 1e-300)
-        side = 1e-300;
-    double cx = __dmul_rn(0.5, __dadd_rn(xmin, xmax)), cy = __dmul_rn(0.5, __dadd_rn(ymin, ymax));
-    double half = __dmul_rn(0.5, side);
-    sys[k].x0 = __dsub_rn(cx, half);
-    sys[k].y0 = __dsub_rn(cy, half);
-    sys[k].S = side;
+    derive_constants(d);
 }
 
 __global__ void k_minmax_init(unsigned long long *minmax, int nsys)
@@ -107,39 +126,72 @@ int launch_domain_finalize(const Work &w, cudaStream_t s)
 
 // ------------------------------------------------------------------ stage 2: leaf keys and histogram
 
-__global__ void k_keys(const SysDev *__restrict__ sys, int nsys, int n, const double *__restrict__ x,
-                       const double *__restrict__ y, int *__restrict__ key, int *__restrict__ cnt,
-                       unsigned int *status)
+__device__ __forceinline__ bool not_finite(double v)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
-        return;
-    int k = nsys == 1 ? 0 : find_sys_by_particle(sys, nsys, i);
-    const SysDev &d = sys[k];
-    double xi = x[i], yi = y[i];
-    int L = d.depth, nside = 1 << L;
-    bool bad = !isfinite(xi) || !isfinite(yi);
-    if (d.explicit_domain) {
-        double xe = __dadd_rn(d.x0, d.S), ye = __dadd_rn(d.y0, d.S);
-        bad = bad || !(xi >= d.x0) || !(xi <= xe) || !(yi >= d.y0) || !(yi <= ye);
-    }
-    if (bad)
-        atomicOr(status, FMM_DEV_OUTSIDE);
-    double scale = ldexp(1.0, L) / d.S;
-    double tx = floor(__dmul_rn(__dsub_rn(xi, d.x0), scale));
-    double ty = floor(__dmul_rn(__dsub_rn(yi, d.y0), scale));
-    int ix = tx < 0.0 ? 0 : (tx > (double)(nside - 1) ? nside - 1 : (int)tx);
-    int iy = ty < 0.0 ? 0 : (ty > (double)(nside - 1) ? nside - 1 : (int)ty);
-    if (!(tx == tx)) ix = 0;  // NaN (already flagged)
-    if (!(ty == ty)) iy = 0;
-    int kk = (int)(d.leaf0 + (int64_t)iy * nside + ix);
-    key[i] = kk;
-    atomicAdd(&cnt[kk], 1);
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff;
 }
 
-int launch_keys(const Work &w, const double *x, const double *y, cudaStream_t s)
+// Leaf column of one coordinate by the floor rule, in IEEE double: t = (c - c0) * scale; clamped to
+// [0, nside - 1]. Returns t through *tout. *below is set when c < c0 (sign of the exact difference).
+__device__ __forceinline__ int leaf_col(double c, double c0, double scale, int nside, double *tout, bool *below)
 {
-    k_keys<<<(w.n + 255) / 256, 256, 0, s>>>(w.sys, w.nsys, w.n, x, y, w.key, w.cnt, w.status);
+    double dd = __dsub_rn(c, c0);
+    double t = __dmul_rn(dd, scale);
+    *tout = t;
+    *below = __double_as_longlong(dd) < 0;  // sign bit: c < c0 (c - c0 == 0 gives +0)
+    if (*below)
+        return 0;
+    if (t >= (double)nside)
+        return nside - 1;
+    return __double2int_rz(t);  // t >= 0: truncation is floor
+}
+
+// Precision form: zeta = t - (i + 1/2) is exact in double; split as hi + lo floats.
+__device__ __forceinline__ void split_rel(double t, int i, float *hi, float *lo)
+{
+    double z = __dsub_rn(t, (double)i + 0.5);
+    float h = __double2float_rn(z);
+    *hi = h;
+    *lo = __double2float_rn(__dsub_rn(z, (double)h));
+}
+
+__global__ void k_keys(Work w, const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ g)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n)
+        return;
+    int k = w.nsys == 1 ? 0 : find_sys_by_particle(w.sys, w.nsys, i);
+    const SysDev &d = w.sys[k];
+    double xi = x[i], yi = y[i];
+    int L = d.depth, nside = 1 << L;
+    double tx, ty;
+    bool bx, by;
+    int ix = leaf_col(xi, d.x0, d.scale, nside, &tx, &bx);
+    int iy = leaf_col(yi, d.y0, d.scale, nside, &ty, &by);
+    bool bad = not_finite(xi) || not_finite(yi);
+    if (d.explicit_domain)
+        bad = bad || bx || by || xi > d.xe || yi > d.ye;
+    if (bad) {
+        atomicOr(w.status, FMM_DEV_OUTSIDE);
+        ix = bad && not_finite(xi) ? 0 : ix;
+        iy = bad && not_finite(yi) ? 0 : iy;
+    }
+    int kk = (int)(d.leaf0 + (int64_t)iy * nside + ix);
+    w.key[i] = kk;
+    atomicAdd(&w.cnt[kk], 1);
+    if (w.mixed) {
+        float hx, lx, hy, ly;
+        split_rel(tx, ix, &hx, &lx);
+        split_rel(ty, iy, &hy, &ly);
+        w.pos4u[i] = make_float4(hx, hy, lx, ly);
+        w.g32u[i] = __double2float_rn(g[i]);
+    }
+}
+
+int launch_keys(const Work &w, const double *x, const double *y, const double *g, cudaStream_t s)
+{
+    k_keys<<<(w.n + 255) / 256, 256, 0, s>>>(w, x, y, g);
     return 1;
 }
 
@@ -241,8 +293,63 @@ __global__ void k_scan_add(int *out, int nin, const int *__restrict__ bsum)
         out[idx] += bsum[idx / SCAN_BLOCK];
 }
 
+// Whole scan in one block when the leaf count is small (one launch instead of three).
+__global__ void __launch_bounds__(1024) k_scan_single(const int *__restrict__ in, int nin, int *__restrict__ out)
+{
+    __shared__ int sh[32];
+    __shared__ int carry_sh;
+    int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0)
+        carry_sh = 0;
+    __syncthreads();
+    for (int base = 0; base < nin; base += 4096) {
+        int v[4], s = 0;
+        for (int j = 0; j < 4; ++j) {
+            int idx = base + t * 4 + j;
+            v[j] = idx < nin ? in[idx] : 0;
+            s += v[j];
+        }
+        int inc = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o)
+                inc += u;
+        }
+        if (lane == 31)
+            sh[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int ws = sh[lane], wi = ws;
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o)
+                    wi += u;
+            }
+            sh[lane] = wi - ws;
+        }
+        __syncthreads();
+        int ex = carry_sh + sh[wid] + inc - s;
+        for (int j = 0; j < 4; ++j) {
+            int idx = base + t * 4 + j;
+            if (idx < nin)
+                out[idx] = ex;
+            ex += v[j];
+        }
+        __syncthreads();
+        if (t == 1023)
+            carry_sh = ex;
+        __syncthreads();
+    }
+    if (t == 0)
+        out[nin] = carry_sh;
+}
+
 int launch_scan(const Work &w, cudaStream_t s)
 {
+    if (w.nleaf <= 65536) {
+        k_scan_single<<<1, 1024, 0, s>>>(w.cnt, w.nleaf, w.start);
+        return 1;
+    }
     int nb = (w.nleaf + SCAN_BLOCK - 1) / SCAN_BLOCK;
     k_scan_block<<<nb, 256, 0, s>>>(w.cnt, w.nleaf, w.start, w.scan_tmp);
     k_scan_top<<<1, 1024, 0, s>>>(w.scan_tmp, nb, w.start + w.nleaf);
@@ -329,29 +436,16 @@ __global__ void k_gather64(int n, const int *__restrict__ perm, const double *__
     }
 }
 
-// Precision form: coordinates relative to the leaf centre in leaf units, split as hi + lo floats so the
-// pair differences keep FP64-level resolution: zeta = (x - x0) * 2^L / S - (ix + 1/2), hi = fl32(zeta),
-// lo = fl32(zeta - hi).
-__global__ void k_gather32(int n, const SysDev *__restrict__ sys, int nsys, const int *__restrict__ perm,
-                           const int *__restrict__ sleaf, const double *__restrict__ x, const double *__restrict__ y,
-                           const double *__restrict__ g, float4 *pos4, float *g32)
+// Precision form: the split leaf-relative coordinates were made by k_keys in caller order; move them.
+__global__ void k_gather32(int n, const int *__restrict__ perm, const float4 *__restrict__ pos4u,
+                           const float *__restrict__ g32u, float4 *pos4, float *g32)
 {
     int pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n)
         return;
     int i = perm[pos];
-    int k = nsys == 1 ? 0 : find_sys_by_particle(sys, nsys, pos);
-    const SysDev &d = sys[k];
-    int L = d.depth;
-    int local = (int)(sleaf[pos] - d.leaf0);
-    int ix = local & ((1 << L) - 1), iy = local >> L;
-    double scale = ldexp(1.0, L) / d.S;
-    double zx = __dsub_rn(__dmul_rn(__dsub_rn(x[i], d.x0), scale), (double)ix + 0.5);
-    double zy = __dsub_rn(__dmul_rn(__dsub_rn(y[i], d.y0), scale), (double)iy + 0.5);
-    float hx = (float)zx, hy = (float)zy;
-    float lx = (float)(zx - (double)hx), ly = (float)(zy - (double)hy);
-    pos4[pos] = make_float4(hx, hy, lx, ly);
-    g32[pos] = (float)g[i];
+    pos4[pos] = pos4u[i];
+    g32[pos] = g32u[i];
 }
 
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
@@ -359,7 +453,7 @@ int launch_gather(const Work &w, const double *x, const double *y, const double 
 {
     int nb = (w.n + 255) / 256;
     if (w.mixed && !gu) {
-        k_gather32<<<nb, 256, 0, s>>>(w.n, w.sys, w.nsys, w.perm, w.sleaf, x, y, g, w.pos4, w.g32);
+        k_gather32<<<nb, 256, 0, s>>>(w.n, w.perm, w.pos4u, w.g32u, w.pos4, w.g32);
         return 1;
     }
     k_gather64<<<nb, 256, 0, s>>>(w.n, w.perm, x, y, g, w.sx, w.sy, w.sg, gu, gv, w.sgu, w.sgv);

@@ -37,6 +37,12 @@ struct SysHost {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// fixed workspace header: status word and pair count, bounding boxes, system descriptors, per-level lists
+const size_t HDR_MINMAX = 256;
+const size_t HDR_SYS = HDR_MINMAX + align256((size_t)FMM_MAXSYS * 32);
+const size_t HDR_LIST = HDR_SYS + align256((size_t)FMM_MAXSYS * sizeof(SysDev));
+const size_t HDR_BYTES = HDR_LIST + align256((size_t)(FMM_MAXL + 2) * FMM_MAXSYS * sizeof(int));
+
 }  // namespace
 
 struct fmm_ctx {
@@ -45,7 +51,7 @@ struct fmm_ctx {
     int has_domain = 0;
     double dom[3] = {0, 0, 1};
     int mixed = 0;
-    int coarse = 4;
+    int coarse = -1;  // precision form: FP32 on every level (radius-scaled translations stay bounded)
     cudaStream_t stream = nullptr;  // caller's stream
     cudaStream_t exec = nullptr;    // internal stream used for graph capture / replay
     cudaStream_t side = nullptr;    // high-priority stream of the multipole sweep
@@ -54,7 +60,9 @@ struct fmm_ctx {
     int timing = 0, count_pairs = 0, use_graph = 0;
     int p2p_threads = 64, p2p_kt = 1;
     int device = 0;
-    // workspace
+    // workspace: a fixed header (status, pair count, bounding boxes, system table and lists) that never moves,
+    // and the per-size arrays carved from `ws`
+    void *hdr = nullptr;
     void *ws = nullptr;
     size_t ws_cap = 0;
     Work w{};
@@ -314,10 +322,10 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 21 AM64
     sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 22 AL64
     sizes[i++] = 0;                                           // 23 (unused)
-    sizes[i++] = (size_t)nsys * 32;                           // 24 minmax
-    sizes[i++] = 64;                                          // 25 status + pair count
-    sizes[i++] = (size_t)nsys * sizeof(SysDev);               // 26 sys
-    sizes[i++] = (h->sys_list.size() + 1) * 4;                // 27 sys_list
+    sizes[i++] = mixed ? np * 16 : 0;                         // 24 pos4u
+    sizes[i++] = mixed ? np * 4 : 0;                          // 25 g32u
+    sizes[i++] = 0;                                           // 26 (unused)
+    sizes[i++] = 0;                                           // 27 (unused)
     sizes[i++] = adjoint ? np * 24 : 0;                       // 28 adj_far
     int count = i;
     Layout lay;
@@ -337,7 +345,6 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
         CU(cudaMalloc(&h->ws, cap));
         h->ws_cap = cap;
         CU(cudaMemset(h->ws, 0, cap));
-        h->uploaded_version = 0;
     }
     size_t sig[6] = {(size_t)n, (size_t)nleaf, (size_t)nbox, (size_t)p, (size_t)(mixed ? 1 : 0) + 2 * (size_t)adjoint,
                      (size_t)h->ws};
@@ -379,11 +386,14 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.sgv = sizes[20] ? (double *)(b + lay.off[20]) : nullptr;
     w.AM64 = sizes[21] ? (double2 *)(b + lay.off[21]) : nullptr;
     w.AL64 = sizes[22] ? (double2 *)(b + lay.off[22]) : nullptr;
-    w.minmax = (unsigned long long *)(b + lay.off[24]);
-    w.status = (unsigned int *)(b + lay.off[25]);
-    w.pair_count = (unsigned long long *)(b + lay.off[25] + 32);
-    w.sys = (SysDev *)(b + lay.off[26]);
-    w.sys_list = (int *)(b + lay.off[27]);
+    w.pos4u = sizes[24] ? (float4 *)(b + lay.off[24]) : nullptr;
+    w.g32u = sizes[25] ? (float *)(b + lay.off[25]) : nullptr;
+    char *hd = (char *)h->hdr;
+    w.status = (unsigned int *)hd;
+    w.pair_count = (unsigned long long *)(hd + 32);
+    w.minmax = (unsigned long long *)(hd + HDR_MINMAX);
+    w.sys = (SysDev *)(hd + HDR_SYS);
+    w.sys_list = (int *)(hd + HDR_LIST);
     w.adj_far = sizes[28] ? (double *)(b + lay.off[28]) : nullptr;
     w.lv = h->lv;
     return FMM_OK;
@@ -448,7 +458,7 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
     if (any_bbox)
         nl += launch_bbox(w, x, y, s);
     nl += launch_domain_finalize(w, s);
-    nl += launch_keys(w, x, y, s);
+    nl += launch_keys(w, x, y, g, s);
     nl += launch_scan(w, s);
     nl += launch_scatter_sort(w, s);
     nl += launch_gather(w, x, y, g, nullptr, nullptr, s);
@@ -618,6 +628,10 @@ fmm_status fmm_create(int tree_depth, int p, double sigma, fmm_handle *out)
     for (int i = 0; i < 8 && e == cudaSuccess; ++i)
         e = cudaEventCreate(&h->ev_t[i]);
     if (e == cudaSuccess)
+        e = cudaMalloc(&h->hdr, HDR_BYTES);
+    if (e == cudaSuccess)
+        e = cudaMemset(h->hdr, 0, HDR_BYTES);
+    if (e == cudaSuccess)
         e = cudaMallocHost(&h->h_status, 64);
     if (e == cudaSuccess) {
         h->h_pairs = (unsigned long long *)((char *)h->h_status + 32);
@@ -653,6 +667,8 @@ fmm_status fmm_destroy(fmm_handle h)
         cudaStreamDestroy(h->exec);
     if (h->ws)
         cudaFree(h->ws);
+    if (h->hdr)
+        cudaFree(h->hdr);
     if (h->tab)
         cudaFree(h->tab);
     if (h->d_io)
@@ -896,7 +912,7 @@ fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const 
     if (!h->has_domain)
         nl += launch_bbox(w, x, y, s);
     nl += launch_domain_finalize(w, s);
-    nl += launch_keys(w, x, y, s);
+    nl += launch_keys(w, x, y, gamma, s);
     nl += launch_scan(w, s);
     nl += launch_scatter_sort(w, s);
     nl += launch_gather(w, x, y, gamma, gu, gv, s);
@@ -1042,8 +1058,8 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
             fclose(f);
         }
     }
-    int tiles[][2] = {{64, 1}, {64, 2}, {128, 1}, {128, 2}, {32, 2}};
-    int ntile = h->mixed ? 5 : 1;
+    int tiles[][2] = {{64, 1}, {32, 2}, {64, 2}, {128, 1}, {128, 2}, {32, 4}, {128, 4}};
+    int ntile = h->mixed ? 7 : 1;
     int save_graph = h->use_graph, save_timing = h->timing;
     h->use_graph = 0;
     h->timing = 0;

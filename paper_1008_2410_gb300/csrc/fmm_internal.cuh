@@ -39,6 +39,15 @@ struct SysDev {
     int depth;
     int explicit_domain;
     int pad[2];
+    // derived once per evaluation by k_domain_finalize (so no per-particle kernel divides in FP64)
+    double scale;                   // 2^L / S
+    double xe, ye;                  // x0 + S, y0 + S
+    double wl;                      // S / 2^L, leaf width
+    double far_scale;               // 1 / (2 pi w_L)
+    float kappa;                    // w_L^2 / (2 sigma^2): r^2 / 2 sigma^2 in leaf units
+    float cexp;                     // -log2(e) kappa: e^(-y) = 2^(cexp r^2)
+    float ythr;                     // 1/2 / kappa: below this r^2 the small-y series is used
+    float snear;                    // 1 / (2 pi w_L) in FP32
 };
 
 // Per-level work lists for the tree sweeps, computed on the host and passed by value. The systems that have
@@ -75,6 +84,8 @@ struct Work {
     double *sx, *sy, *sg;
     float4 *pos4;
     float *g32;
+    float4 *pos4u;            // precision form, caller order (made while binning)
+    float *g32u;
     double2 *near64;
     float2 *near32;
     int *bcount;
@@ -127,7 +138,7 @@ __device__ inline int find_sys_by_leaf(const SysDev *sys, int nsys, int64_t leaf
 // ---- launchers (each returns the number of kernels launched) ----
 int launch_bbox(const Work &w, const double *x, const double *y, cudaStream_t s);
 int launch_domain_finalize(const Work &w, cudaStream_t s);
-int launch_keys(const Work &w, const double *x, const double *y, cudaStream_t s);
+int launch_keys(const Work &w, const double *x, const double *y, const double *g, cudaStream_t s);
 int launch_scan(const Work &w, cudaStream_t s);  // cnt -> start
 int launch_scatter_sort(const Work &w, cudaStream_t s);
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,

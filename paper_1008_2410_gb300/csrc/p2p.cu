@@ -162,37 +162,30 @@ __global__ void __launch_bounds__(128) k_p2p32(Work w, int tile)
     __shared__ __align__(8) uint64_t bar;
     float4 *spos = reinterpret_cast<float4 *>(smem_raw);
     float *sgam = reinterpret_cast<float *>(smem_raw + (size_t)tile * sizeof(float4));
-    int leaf = blockIdx.x;
-    int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
+    const int leaf = blockIdx.x;
+    const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
     if (c == 0)
         return;
-    int k = w.nsys == 1 ? 0 : find_sys_by_leaf(w.sys, w.nsys, leaf);
+    const int k = w.nsys == 1 ? 0 : find_sys_by_leaf(w.sys, w.nsys, leaf);
     const SysDev &d = w.sys[k];
-    int L = d.depth, ns = 1 << L, local = leaf - (int)d.leaf0;
-    int ix = local & (ns - 1), iy = local >> L;
-    double wl = ldexp(d.S, -L);
-    float kappa = (float)(wl * wl / (2.0 * d.sigma * d.sigma));  // y = kappa r^2 in leaf units
-    float cexp = -1.4426950408889634f * kappa;                     // e^-y = 2^(cexp r^2)
-    float ythr = 0.5f / kappa;                                     // r^2 below which the series is used
-    float snear = (float)(1.0 / (TWO_PI * wl));
-    int jx0 = ix > 0 ? ix - 1 : 0, jx1 = ix < ns - 1 ? ix + 1 : ns - 1;
-    int tid = threadIdx.x, T = blockDim.x;
+    const int L = d.depth, ns = 1 << L, local = leaf - (int)d.leaf0;
+    const int ix = local & (ns - 1), iy = local >> L;
+    const float kappa = d.kappa, cexp = d.cexp, ythr = d.ythr, snear = d.snear;
+    const int jx0 = ix > 0 ? ix - 1 : 0, jx1 = ix < ns - 1 ? ix + 1 : ns - 1;
+    const int tid = threadIdx.x, T = blockDim.x;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_proxy_async();
     }
     __syncthreads();
     uint32_t phase = 0;
-    // Every block stages the same tiles in the same order for each chunk of targets.
     for (int t0 = 0; t0 < c; t0 += T * KT) {
         float thx[KT], thy[KT], tlx[KT], tly[KT];
         float su[KT], cu[KT], sv[KT], cv[KT];
-        bool tv[KT];
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
             int e = t0 + tid + q * T;
-            tv[q] = e < c;
-            float4 tp = tv[q] ? w.pos4[s0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 tp = e < c ? w.pos4[s0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
             thx[q] = tp.x;
             thy[q] = tp.y;
             tlx[q] = tp.z;
@@ -200,26 +193,26 @@ __global__ void __launch_bounds__(128) k_p2p32(Work w, int tile)
             su[q] = cu[q] = sv[q] = cv[q] = 0.f;
         }
         for (int dy = -1; dy <= 1; ++dy) {
-            int row = iy + dy;
+            const int row = iy + dy;
             if (row < 0 || row >= ns)
                 continue;
-            int rowleaf = (int)d.leaf0 + row * ns;
-            int r0 = w.start[rowleaf + jx0], r1 = w.start[rowleaf + jx1 + 1];
+            const int rowleaf = (int)d.leaf0 + row * ns;
+            const int r0 = w.start[rowleaf + jx0], r1 = w.start[rowleaf + jx1 + 1];
             if (r1 <= r0)
                 continue;
-            int cb[4];  // column boundaries inside the row run
+            int cb[4];  // column boundaries inside the row run (columns ix-1, ix, ix+1)
+#pragma unroll
             for (int q = 0; q < 3; ++q) {
                 int col = ix - 1 + q;
                 cb[q] = (col < jx0) ? r0 : (col > jx1 ? r1 : w.start[rowleaf + col]);
             }
             cb[3] = r1;
             for (int q0 = r0 & ~3; q0 < r1; q0 += tile) {
-                int a = q0, b = min(q0 + tile, (r1 + 3) & ~3);
+                const int a = q0, b = min(q0 + tile, (r1 + 3) & ~3);
                 __syncthreads();  // everyone is done with the previous tile
                 if (tid == 0) {
                     fence_proxy_async();
-                    uint32_t nbytes = (uint32_t)(b - a) * 20u;
-                    mbar_expect_tx(&bar, nbytes);
+                    mbar_expect_tx(&bar, (uint32_t)(b - a) * 20u);
                     bulk_g2s(spos, w.pos4 + a, (uint32_t)(b - a) * 16u, &bar);
                     bulk_g2s(sgam, w.g32 + a, (uint32_t)(b - a) * 4u, &bar);
                 }
@@ -231,43 +224,53 @@ __global__ void __launch_bounds__(128) k_p2p32(Work w, int tile)
                     return;
                 }
                 phase ^= 1;
-                int lo = max(a, r0), hi = min(q0 + tile, r1);
+                const int lo = max(a, r0), hi = min(q0 + tile, r1);
+#pragma unroll 1
                 for (int col = 0; col < 3; ++col) {
-                    int j0 = max(lo, cb[col]), j1 = min(hi, cb[col + 1]);
+                    const int j0 = max(lo, cb[col]) - a, j1 = min(hi, cb[col + 1]) - a;
                     if (j0 >= j1)
                         continue;
-                    // target coordinates relative to this source leaf's centre: zeta_t - (dc, dy), exact
-                    float dc = (float)(col - 1), drow = (float)dy;
+                    // target relative to this source leaf's centre, zeta_t - (dc, dy), kept exact as hi + lo
+                    const float dc = (float)(col - 1), dr = (float)dy;
                     float ahx[KT], alx[KT], ahy[KT], aly[KT], pu[KT], pv[KT];
 #pragma unroll
                     for (int q = 0; q < KT; ++q) {
-                        float sx_ = thx[q] - dc;
-                        float ex_ = thx[q] - (sx_ + dc);
-                        ahx[q] = sx_;
-                        alx[q] = tlx[q] + ex_;
-                        float sy_ = thy[q] - drow;
-                        float ey_ = thy[q] - (sy_ + drow);
-                        ahy[q] = sy_;
-                        aly[q] = tly[q] + ey_;
+                        float sx = thx[q] - dc;
+                        ahx[q] = sx;
+                        alx[q] = tlx[q] + (thx[q] - (sx + dc));
+                        float sy = thy[q] - dr;
+                        ahy[q] = sy;
+                        aly[q] = tly[q] + (thy[q] - (sy + dr));
                         pu[q] = pv[q] = 0.f;
                     }
-#pragma unroll 2
-                    for (int j = j0 - a; j < j1 - a; ++j) {
-                        float4 sp = spos[j];
-                        float g = sgam[j];
+                    for (int j = j0; j < j1; ++j) {
+                        const float4 sp = spos[j];
+                        const float g = sgam[j];
+                        float dxv[KT], dyv[KT], r2v[KT], fv[KT];
+                        float rmin = 3.0e38f;
 #pragma unroll
                         for (int q = 0; q < KT; ++q) {
-                            float dx = (ahx[q] - sp.x) + (alx[q] - sp.z);
-                            float dyv = (ahy[q] - sp.y) + (aly[q] - sp.w);
-                            float r2 = fmaf(dx, dx, dyv * dyv);
+                            dxv[q] = (ahx[q] - sp.x) + (alx[q] - sp.z);
+                            dyv[q] = (ahy[q] - sp.y) + (aly[q] - sp.w);
+                            float r2 = fmaf(dxv[q], dxv[q], dyv[q] * dyv[q]);
                             float e = ex2_approx(r2 * cexp);
                             float rr = rcp_approx(fmaxf(r2, 1e-30f));
-                            float f = fmaf(-e, rr, rr);
-                            if (r2 < ythr)
-                                f = kappa * small_y_factor(kappa * r2);
-                            float gf = g * f;
-                            pu[q] = fmaf(-dyv, gf, pu[q]);
-                            pv[q] = fmaf(dx, gf, pv[q]);
+                            fv[q] = fmaf(-e, rr, rr);  // (1 - e^-y) / r^2
+                            r2v[q] = r2;
+                            rmin = fminf(rmin, r2);
+                        }
+                        // rare (r < sigma): warp-uniform branch to the series, off the common path
+                        if (__any_sync(0xffffffffu, rmin < ythr)) {
+#pragma unroll
+                            for (int q = 0; q < KT; ++q)
+                                if (r2v[q] < ythr)
+                                    fv[q] = kappa * small_y_factor(kappa * r2v[q]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < KT; ++q) {
+                            const float gf = g * fv[q];
+                            pu[q] = fmaf(-dyv[q], gf, pu[q]);
+                            pv[q] = fmaf(dxv[q], gf, pv[q]);
                         }
                     }
 #pragma unroll
@@ -279,9 +282,11 @@ __global__ void __launch_bounds__(128) k_p2p32(Work w, int tile)
             }
         }
 #pragma unroll
-        for (int q = 0; q < KT; ++q)
-            if (tv[q])
-                w.near32[s0 + t0 + tid + q * T] = make_float2((su[q] + cu[q]) * snear, (sv[q] + cv[q]) * snear);
+        for (int q = 0; q < KT; ++q) {
+            int e = t0 + tid + q * T;
+            if (e < c)
+                w.near32[s0 + e] = make_float2((su[q] + cu[q]) * snear, (sv[q] + cv[q]) * snear);
+        }
     }
 }
 
@@ -293,10 +298,10 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
         k_p2p64<<<w.nleaf, 64, 0, s>>>(w);
         return 1;
     }
-    int tile = 512;
-    size_t sm = (size_t)tile * 20;
     if (threads <= 0)
         threads = 64;
+    int tile = 8 * threads;  // 256 / 512 / 1024 sources: 5, 10, 20 KiB of shared memory per block
+    size_t sm = (size_t)tile * 20;
     if (kt == 2)
         k_p2p32<2><<<w.nleaf, threads, sm, s>>>(w, tile);
     else if (kt == 4)

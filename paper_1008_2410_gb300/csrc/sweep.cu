@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(64) k_p2m(Work w, int adj)
     if (c == 0)
         return;
     int ix = local & ((1 << L) - 1), iy = local >> L;
-    double scale = ldexp(1.0, L) / d.S;
+    double scale = d.scale;
     cx<R> a[PM];
 #pragma unroll
     for (int m = 0; m < PM; ++m)
@@ -224,64 +224,96 @@ int launch_m2m(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, i
 
 // ------------------------------------------------------------------ stage 6: M2L (warp per target box, all levels)
 
-template <typename R, typename S>
+// One warp per target box, lane l = local coefficient. The interaction list (children of the parent's
+// neighbours that are not adjacent, at most 27, empty boxes skipped) is built once; sources are then taken two
+// at a time: lane m scales a~_m by (-1)^(m+1) rho^m into shared memory, and lane l contracts with its column of
+// binomials C(m + l, m), held in registers, before the rho^(l+1) scaling.
+template <int PM, typename R, typename S>
 __device__ void m2l_box(const Work &w, const typename store_of<R>::T *__restrict__ rho, const R *__restrict__ binom,
-                        const S *__restrict__ M, S *Loc, const SysDev &d, int l, int b, cx<R> *alpha)
+                        const S *__restrict__ M, S *Loc, const SysDev &d, int l, int b, cx<R> *alpha, int2 *list)
 {
-    int lane = threadIdx.x & 31, p = w.p;
-    int ns = 1 << l, bx = b & (ns - 1), by = b >> l;
-    int px = bx >> 1, py = by >> 1, np_ = ns >> 1;
-    cx<R> acc = {(R)0, (R)0};
+    const int lane = threadIdx.x & 31, p = w.p;
+    const int ns = 1 << l, bx = b & (ns - 1), by = b >> l;
+    const int px = bx >> 1, py = by >> 1;
     const int RS = 2 * FMM_PMAX + 2;
-    for (int qy = py - 1; qy <= py + 1; ++qy) {
-        if (qy < 0 || qy >= np_)
-            continue;
-        for (int qx = px - 1; qx <= px + 1; ++qx) {
-            if (qx < 0 || qx >= np_)
-                continue;
-            for (int c = 0; c < 4; ++c) {
-                int jx = 2 * qx + (c & 1), jy = 2 * qy + (c >> 1);
-                int ddx = jx - bx, ddy = jy - by;
-                if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1)
-                    continue;
+    // interaction list: lanes 0..35 cover the 6 x 6 children block of the parent's 3 x 3 neighbourhood
+    int cnt = 0;
+    for (int base = 0; base < 36; base += 32) {
+        int q = base + lane;
+        bool ok = false;
+        int2 ent = make_int2(0, 0);
+        if (q < 36) {
+            int jx = 2 * (px - 1) + q % 6, jy = 2 * (py - 1) + q / 6;
+            int ddx = jx - bx, ddy = jy - by;
+            if (jx >= 0 && jy >= 0 && jx < ns && jy < ns && !(ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1)) {
                 int64_t sb = d.box0[l] + (int64_t)jy * ns + jx;
-                if (w.bcount[sb] == 0)
-                    continue;
-                int o = (ddy + 3) * 7 + (ddx + 3);
-                const typename store_of<R>::T *rp = rho + o * RS;
-                if (lane < p) {
-                    cx<R> a = ldc<R>(M, sb * p + lane);
-                    auto r = rp[lane];
-                    cx<R> t = cmul(cx<R>{(R)r.x, (R)r.y}, a);
-                    if (!(lane & 1)) {  // (-1)^(m+1)
-                        t.re = -t.re;
-                        t.im = -t.im;
-                    }
-                    alpha[lane] = t;
+                if (w.bcount[sb] != 0) {
+                    ok = true;
+                    ent = make_int2((int)(sb - d.box0[l]), (ddy + 3) * 7 + (ddx + 3));
                 }
-                __syncwarp();
-                if (lane < p) {
-                    cx<R> beta = {(R)0, (R)0};
-                    for (int m = 0; m < p; ++m) {
-                        R cb = binom[m * FMM_PMAX + lane];
-                        cx<R> am = alpha[m];
-                        beta.re += cb * am.re;
-                        beta.im += cb * am.im;
-                    }
-                    auto r1 = rp[lane + 1];
-                    acc = cadd(acc, cmul(cx<R>{(R)r1.x, (R)r1.y}, beta));
-                }
-                __syncwarp();
             }
         }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok)
+            list[cnt + __popc(m & ((1u << lane) - 1))] = ent;
+        cnt += __popc(m);
+    }
+    __syncwarp();
+    R cb[PM];
+#pragma unroll
+    for (int m = 0; m < PM; ++m)
+        cb[m] = (m < p && lane < p) ? binom[m * FMM_PMAX + lane] : (R)0;
+    cx<R> acc = {(R)0, (R)0};
+    for (int s = 0; s < cnt; s += 2) {
+        const bool two = s + 1 < cnt;
+        const int2 e0 = list[s], e1 = two ? list[s + 1] : list[s];
+        const typename store_of<R>::T *rp0 = rho + e0.y * RS, *rp1 = rho + e1.y * RS;
+        if (lane < p) {
+            const R sg = (lane & 1) ? (R)1 : (R)-1;  // (-1)^(m+1)
+            cx<R> a0 = ldc<R>(M, (d.box0[l] + e0.x) * (int64_t)p + lane);
+            auto r0 = rp0[lane];
+            cx<R> t0 = cmul(cx<R>{(R)r0.x, (R)r0.y}, a0);
+            alpha[lane] = {sg * t0.re, sg * t0.im};
+            cx<R> t1 = {(R)0, (R)0};
+            if (two) {
+                cx<R> a1 = ldc<R>(M, (d.box0[l] + e1.x) * (int64_t)p + lane);
+                auto r1 = rp1[lane];
+                t1 = cmul(cx<R>{(R)r1.x, (R)r1.y}, a1);
+            }
+            alpha[32 + lane] = {sg * t1.re, sg * t1.im};
+        } else {
+            alpha[lane] = {(R)0, (R)0};  // entries m >= p meet zero binomials: keep them finite
+            alpha[32 + lane] = {(R)0, (R)0};
+        }
+        __syncwarp();
+        cx<R> b0 = {(R)0, (R)0}, b1 = {(R)0, (R)0};
+#pragma unroll
+        for (int m = 0; m < PM; ++m) {
+            const cx<R> am = alpha[m], an = alpha[32 + m];
+            b0.re = fma(cb[m], am.re, b0.re);
+            b0.im = fma(cb[m], am.im, b0.im);
+            b1.re = fma(cb[m], an.re, b1.re);
+            b1.im = fma(cb[m], an.im, b1.im);
+        }
+        if (lane < p) {
+            auto q0 = rp0[lane + 1];
+            acc = cadd(acc, cmul(cx<R>{(R)q0.x, (R)q0.y}, b0));
+            if (two) {
+                auto q1 = rp1[lane + 1];
+                acc = cadd(acc, cmul(cx<R>{(R)q1.x, (R)q1.y}, b1));
+            }
+        }
+        __syncwarp();
     }
     if (lane < p)
         stc(Loc, (d.box0[l] + b) * (int64_t)p + lane, acc);
 }
 
+template <int PM>
 __global__ void __launch_bounds__(128) k_m2l(Work w, Tables t, int adj)
 {
-    __shared__ __align__(16) double2 alpha_sh[4][32];
+    __shared__ __align__(16) double2 alpha_sh[4][64];
+    __shared__ int2 list_sh[4][40];
     int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int l = 2;
     while (l < w.lv.maxdepth && gw >= w.lv.m2l_item0[l + 1])
@@ -297,11 +329,11 @@ __global__ void __launch_bounds__(128) k_m2l(Work w, Tables t, int adj)
     int wi = threadIdx.x >> 5;
     if (level_fp64(w, l)) {
         double2 *M = adj ? w.AM64 : w.M64, *Lc = adj ? w.AL64 : w.L64;
-        m2l_box<double, double2>(w, t.rho64, t.binom64, M, Lc, d, l, b,
-                                 reinterpret_cast<cx<double> *>(alpha_sh[wi]));
+        m2l_box<PM, double, double2>(w, t.rho64, t.binom64, M, Lc, d, l, b,
+                                     reinterpret_cast<cx<double> *>(alpha_sh[wi]), list_sh[wi]);
     } else {
-        m2l_box<float, float2>(w, t.rho32, t.binom32, w.M32, w.L32, d, l, b,
-                               reinterpret_cast<cx<float> *>(alpha_sh[wi]));
+        m2l_box<PM, float, float2>(w, t.rho32, t.binom32, w.M32, w.L32, d, l, b,
+                                   reinterpret_cast<cx<float> *>(alpha_sh[wi]), list_sh[wi]);
     }
 }
 
@@ -311,8 +343,19 @@ int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio
     int64_t warps = w.lv.m2l_item0[w.lv.maxdepth + 1];
     if (w.lv.maxdepth < 2 || warps == 0)
         return 0;
-    int64_t blocks = (warps * 32 + 127) / 128;
-    k_m2l<<<(unsigned)blocks, 128, 0, s>>>(w, t, adj);
+    unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
+    if (w.p <= 8)
+        k_m2l<8><<<blocks, 128, 0, s>>>(w, t, adj);
+    else if (w.p <= 12)
+        k_m2l<12><<<blocks, 128, 0, s>>>(w, t, adj);
+    else if (w.p <= 16)
+        k_m2l<16><<<blocks, 128, 0, s>>>(w, t, adj);
+    else if (w.p <= 20)
+        k_m2l<20><<<blocks, 128, 0, s>>>(w, t, adj);
+    else if (w.p <= 24)
+        k_m2l<24><<<blocks, 128, 0, s>>>(w, t, adj);
+    else
+        k_m2l<32><<<blocks, 128, 0, s>>>(w, t, adj);
     return 1;
 }
 
@@ -391,31 +434,39 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
     int k = w.nsys == 1 ? 0 : find_sys_by_particle(w.sys, w.nsys, pos);
     const SysDev &d = w.sys[k];
     int L = d.depth;
-    double fu = 0.0, fv = 0.0;
-    if (use_far && L >= 2) {
-        int local = (int)(w.sleaf[pos] - d.leaf0);
-        int64_t base = (d.box0[L] + local) * (int64_t)w.p;
-        double f = 1.0 / (2.0 * 3.14159265358979323846 * ldexp(d.S, -L));
-        if (level_fp64(w, L)) {
-            cx<double> z;
-            if (w.mixed) {
-                float4 pp = w.pos4[pos];
-                z = {(double)pp.x + (double)pp.z, (double)pp.y + (double)pp.w};
-            } else {
-                int ix = local & ((1 << L) - 1), iy = local >> L;
-                double scale = ldexp(1.0, L) / d.S;
-                z = {(w.sx[pos] - d.x0) * scale - (ix + 0.5), (w.sy[pos] - d.y0) * scale - (iy + 0.5)};
-            }
-            cx<double> s = horner<double>(w.L64, base, w.p, z);
-            fu = s.re * f;
-            fv = -s.im * f;
-        } else {
+    int i = w.perm[pos];
+    bool far = use_far && L >= 2;
+    int64_t base = far ? (d.box0[L] + (int)(w.sleaf[pos] - d.leaf0)) * (int64_t)w.p : 0;
+    if (w.mixed && !level_fp64(w, L)) {
+        // precision form: FP32 far field and sum, one conversion to FP64 at the end
+        float fu = 0.f, fv = 0.f;
+        if (far) {
             float4 pp = w.pos4[pos];
             cx<float> z = {pp.x + pp.z, pp.y + pp.w};
             cx<float> s = horner<float>(w.L32, base, w.p, z);
-            fu = (double)s.re * f;
-            fv = -(double)s.im * f;
+            float fs = (float)d.far_scale;
+            fu = s.re * fs;
+            fv = -s.im * fs;
         }
+        float2 t = use_near ? w.near32[pos] : make_float2(0.f, 0.f);
+        u[i] = (double)(t.x + fu);
+        v[i] = (double)(t.y + fv);
+        return;
+    }
+    double fu = 0.0, fv = 0.0;
+    if (far) {
+        cx<double> z;
+        if (w.mixed) {
+            float4 pp = w.pos4[pos];
+            z = {(double)pp.x + (double)pp.z, (double)pp.y + (double)pp.w};
+        } else {
+            int local = (int)(w.sleaf[pos] - d.leaf0);
+            int ix = local & ((1 << L) - 1), iy = local >> L;
+            z = {(w.sx[pos] - d.x0) * d.scale - (ix + 0.5), (w.sy[pos] - d.y0) * d.scale - (iy + 0.5)};
+        }
+        cx<double> s = horner<double>(w.L64, base, w.p, z);
+        fu = s.re * d.far_scale;
+        fv = -s.im * d.far_scale;
     }
     double nu = 0.0, nv = 0.0;
     if (use_near) {
@@ -429,7 +480,6 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
             nv = t.y;
         }
     }
-    int i = w.perm[pos];
     u[i] = nu + fu;
     v[i] = nv + fv;
 }
@@ -460,7 +510,7 @@ __global__ void k_adjoint_far(Work w)
         int local = (int)(w.sleaf[pos] - d.leaf0);
         int64_t base = (d.box0[L] + local) * (int64_t)w.p;
         int ix = local & ((1 << L) - 1), iy = local >> L;
-        double scale = ldexp(1.0, L) / d.S, wl = ldexp(d.S, -L);
+        double scale = d.scale, wl = d.wl;
         cx<double> z = {(w.sx[pos] - d.x0) * scale - (ix + 0.5), (w.sy[pos] - d.y0) * scale - (iy + 0.5)};
         // forward derivative w' and adjoint phi, phi' by Horner on the polynomial and its derivative
         cx<double> bw = {0, 0}, bwd = {0, 0}, ph = {0, 0}, phd = {0, 0};

@@ -86,7 +86,7 @@ def test_mixed_matches_oracle_fmm(lib, oracle, name, make):
         assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < TOL32, coarse
 
 
-@pytest.mark.parametrize("tile", [(64, 1), (64, 2), (128, 1), (128, 2), (32, 2), (128, 4)])
+@pytest.mark.parametrize("tile", [(64, 1), (64, 2), (128, 1), (128, 2), (32, 2), (32, 4), (128, 4), (96, 1)])
 def test_mixed_tile_shapes(lib, oracle, tile):
     w = fi.clustered(30000, depth=4, p=12)  # dense leaves: several target chunks and source tiles per leaf
     uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)
@@ -309,7 +309,8 @@ def test_stage_times_launch_count_and_autotune(lib):
     assert f.kernel_launches() > n0 + 8
     prm = f.autotune(x, y, g, 4, 6)
     assert 4 <= prm["depth"] <= 6
-    assert (prm["p2p_threads"], prm["p2p_targets_per_thread"]) in {(64, 1), (64, 2), (128, 1), (128, 2), (32, 2)}
+    assert (prm["p2p_threads"], prm["p2p_targets_per_thread"]) in {(64, 1), (32, 2), (64, 2), (128, 1), (128, 2),
+                                                                  (32, 4), (128, 4)}
 
 
 @pytest.mark.slow

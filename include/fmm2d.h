@@ -92,7 +92,9 @@ fmm_status fmm_set_stream(fmm_handle h, void *cuda_stream);
  * same sizes, pointers and parameters replay with one launch. */
 fmm_status fmm_set_graph(fmm_handle h, int enable);
 
-/* Near-field tile shape: targets per thread-block work item and threads per block (0 = automatic).
+/* Near-field tile shape of the precision form: threads 32 (one leaf per thread block) or 64 (two
+ * horizontally adjacent leaves per block, sharing their source tiles); targets_per_thread 2 or 4 (the most
+ * targets one lane takes per pass; passes are balanced over the leaf). 0 = default (64, 4).
  * Set by fmm_autotune; exposed for experiments. */
 fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread);
 

@@ -65,10 +65,10 @@ __device__ void derive_constants(SysDev &d)
     d.wl = ldexp(d.S, -L);
     d.far_scale = 1.0 / (6.283185307179586476925 * d.wl);
     double kap = d.wl * d.wl / (2.0 * d.sigma * d.sigma);
-    d.kappa = (float)kap;
-    d.cexp = (float)(-1.4426950408889634074 * kap);
-    d.ythr = (float)(0.5 / kap);
-    d.snear = (float)d.far_scale;
+    float s = (float)sqrt(1.4426950408889634074 * kap);
+    d.s_unit = s;
+    d.inv_s = 1.0f / s;
+    d.snear = (float)((double)s * d.far_scale);
 }
 
 __global__ void k_domain_finalize(SysDev *sys, int nsys, const unsigned long long *minmax)
@@ -146,10 +146,10 @@ __device__ __forceinline__ int leaf_col(double c, double c0, double scale, int n
     return __double2int_rz(t);  // t >= 0: truncation is floor
 }
 
-// Precision form: zeta = t - (i + 1/2) is exact in double; split as hi + lo floats.
-__device__ __forceinline__ void split_rel(double t, int i, float *hi, float *lo)
+// Precision form: zeta = t - (i + 1/2) is exact in double; s * zeta is split as hi + lo floats (about 48 bits).
+__device__ __forceinline__ void split_rel(double t, int i, double s, float *hi, float *lo)
 {
-    double z = __dsub_rn(t, (double)i + 0.5);
+    double z = __dmul_rn(__dsub_rn(t, (double)i + 0.5), s);
     float h = __double2float_rn(z);
     *hi = h;
     *lo = __double2float_rn(__dsub_rn(z, (double)h));
@@ -182,8 +182,8 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
     atomicAdd(&w.cnt[kk], 1);
     if (w.mixed) {
         float hx, lx, hy, ly;
-        split_rel(tx, ix, &hx, &lx);
-        split_rel(ty, iy, &hy, &ly);
+        split_rel(tx, ix, (double)d.s_unit, &hx, &lx);
+        split_rel(ty, iy, (double)d.s_unit, &hy, &ly);
         w.pos4u[i] = make_float4(hx, hy, lx, ly);
         w.g32u[i] = __double2float_rn(g[i]);
     }
@@ -436,16 +436,19 @@ __global__ void k_gather64(int n, const int *__restrict__ perm, const double *__
     }
 }
 
-// Precision form: the split leaf-relative coordinates were made by k_keys in caller order; move them.
+// Precision form: move the split coordinates made by k_keys into leaf order, each value duplicated.
 __global__ void k_gather32(int n, const int *__restrict__ perm, const float4 *__restrict__ pos4u,
-                           const float *__restrict__ g32u, float4 *pos4, float *g32)
+                           const float *__restrict__ g32u, float4 *eh, float4 *el, float4 *eg)
 {
     int pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n)
         return;
     int i = perm[pos];
-    pos4[pos] = pos4u[i];
-    g32[pos] = g32u[i];
+    float4 p = pos4u[i];
+    float g = g32u[i];
+    eh[pos] = make_float4(p.x, p.x, p.y, p.y);
+    el[pos] = make_float4(p.z, p.z, p.w, p.w);
+    eg[pos] = make_float4(g, g, -g, -g);
 }
 
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
@@ -453,7 +456,7 @@ int launch_gather(const Work &w, const double *x, const double *y, const double 
 {
     int nb = (w.n + 255) / 256;
     if (w.mixed && !gu) {
-        k_gather32<<<nb, 256, 0, s>>>(w.n, w.perm, w.pos4u, w.g32u, w.pos4, w.g32);
+        k_gather32<<<nb, 256, 0, s>>>(w.n, w.perm, w.pos4u, w.g32u, w.eh, w.el, w.eg);
         return 1;
     }
     k_gather64<<<nb, 256, 0, s>>>(w.n, w.perm, x, y, g, w.sx, w.sy, w.sg, gu, gv, w.sgu, w.sgv);

@@ -58,7 +58,7 @@ struct fmm_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_status = nullptr, ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ev_t[8] = {};
     int timing = 0, count_pairs = 0, use_graph = 0;
-    int p2p_threads = 64, p2p_kt = 1;
+    int p2p_threads = 64, p2p_kt = 4;
     int device = 0;
     // workspace: a fixed header (status, pair count, bounding boxes, system table and lists) that never moves,
     // and the per-size arrays carved from `ws`
@@ -308,8 +308,8 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = f64 ? np * 8 : 0;                            // 7 sx
     sizes[i++] = f64 ? np * 8 : 0;                            // 8 sy
     sizes[i++] = f64 ? np * 8 : 0;                            // 9 sg
-    sizes[i++] = mixed ? np * 16 : 0;                         // 10 pos4
-    sizes[i++] = mixed ? np * 4 : 0;                          // 11 g32
+    sizes[i++] = mixed ? np * 48 : 0;                         // 10 eh, el, eg
+    sizes[i++] = 0;                                           // 11 (unused)
     sizes[i++] = mixed ? 0 : np * 16;                         // 12 near64
     sizes[i++] = mixed ? np * 8 : 0;                          // 13 near32
     sizes[i++] = (size_t)nbox * 4 + 16;                       // 14 bcount
@@ -373,8 +373,9 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.sx = sizes[7] ? (double *)(b + lay.off[7]) : nullptr;
     w.sy = sizes[8] ? (double *)(b + lay.off[8]) : nullptr;
     w.sg = sizes[9] ? (double *)(b + lay.off[9]) : nullptr;
-    w.pos4 = sizes[10] ? (float4 *)(b + lay.off[10]) : nullptr;
-    w.g32 = sizes[11] ? (float *)(b + lay.off[11]) : nullptr;
+    w.eh = sizes[10] ? (float4 *)(b + lay.off[10]) : nullptr;
+    w.el = sizes[10] ? w.eh + np : nullptr;
+    w.eg = sizes[10] ? w.el + np : nullptr;
     w.near64 = sizes[12] ? (double2 *)(b + lay.off[12]) : nullptr;
     w.near32 = sizes[13] ? (float2 *)(b + lay.off[13]) : nullptr;
     w.bcount = (int *)(b + lay.off[14]);
@@ -749,10 +750,9 @@ fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread)
     if (threads == 0)
         threads = 64;
     if (targets_per_thread == 0)
-        targets_per_thread = 1;
-    if (threads < 32 || threads > 128 || (threads & 31) ||
-        (targets_per_thread != 1 && targets_per_thread != 2 && targets_per_thread != 4))
-        return set_err(h, FMM_EINVAL, "tile: threads in {32, 64, 96, 128}, targets per thread in {1, 2, 4}");
+        targets_per_thread = 4;
+    if ((threads != 32 && threads != 64) || (targets_per_thread != 2 && targets_per_thread != 4))
+        return set_err(h, FMM_EINVAL, "tile: threads 32 (one leaf per block) or 64 (two), targets per thread 2 or 4");
     h->p2p_threads = threads;
     h->p2p_kt = targets_per_thread;
     return FMM_OK;
@@ -1058,8 +1058,8 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
             fclose(f);
         }
     }
-    int tiles[][2] = {{64, 1}, {32, 2}, {64, 2}, {128, 1}, {128, 2}, {32, 4}, {128, 4}};
-    int ntile = h->mixed ? 7 : 1;
+    int tiles[][2] = {{64, 4}, {64, 2}, {32, 4}, {32, 2}};
+    int ntile = h->mixed ? 4 : 1;
     int save_graph = h->use_graph, save_timing = h->timing;
     h->use_graph = 0;
     h->timing = 0;

@@ -4,8 +4,10 @@
 //   particles in the caller's order : key[n] (global leaf of each particle)
 //   particles in leaf order         : perm[n] (sorted position -> caller index), sleaf[n] (global leaf),
 //                                     FP64 form: sx, sy, sg (absolute coordinates, circulation),
-//                                     precision form: pos4[n] = (xh, yh, xl, yl) leaf-relative split
-//                                     coordinates in leaf units, g32[n]
+//                                     precision form: leaf-relative split coordinates (hi + lo floats) in
+//                                     units of w_L / s (see SysDev::s_unit), each value stored twice so that
+//                                     one 64-bit register pair feeds a packed f32x2 operation on two targets:
+//                                     eh = (xh, xh, yh, yh), el = (xl, xl, yl, yl), eg = (g, g, -g, -g)
 //   leaves                          : cnt[nleaf] (histogram), start[nleaf + 1] (first sorted position)
 //   boxes (levels 2..L of every system, row-major per level): bcount[nbox] (particles in the box),
 //                                     multipoles and locals, p complex coefficients per box, FP64 and/or FP32
@@ -44,10 +46,11 @@ struct SysDev {
     double xe, ye;                  // x0 + S, y0 + S
     double wl;                      // S / 2^L, leaf width
     double far_scale;               // 1 / (2 pi w_L)
-    float kappa;                    // w_L^2 / (2 sigma^2): r^2 / 2 sigma^2 in leaf units
-    float cexp;                     // -log2(e) kappa: e^(-y) = 2^(cexp r^2)
-    float ythr;                     // 1/2 / kappa: below this r^2 the small-y series is used
-    float snear;                    // 1 / (2 pi w_L) in FP32
+    float s_unit;                   // precision form length unit: s = fl32(sqrt(log2(e) w_L^2 / 2 sigma^2)) per leaf
+                                    // width, so that exp(-r^2 / 2 sigma^2) = 2^-(r')^2 with r' = s r / w_L
+    float inv_s;                    // 1 / s
+    float snear;                    // s / (2 pi w_L): scale of the near-field sum in these units
+    float pad_f;
 };
 
 // Per-level work lists for the tree sweeps, computed on the host and passed by value. The systems that have
@@ -82,9 +85,8 @@ struct Work {
     // arrays
     int *key, *cnt, *start, *scan_tmp, *tmp, *perm, *sleaf;
     double *sx, *sy, *sg;
-    float4 *pos4;
-    float *g32;
-    float4 *pos4u;            // precision form, caller order (made while binning)
+    float4 *eh, *el, *eg;     // precision form, leaf order: (xh, xh, yh, yh), (xl, xl, yl, yl), (g, g, -g, -g)
+    float4 *pos4u;            // precision form, caller order (made while binning): (xh, yh, xl, yl)
     float *g32u;
     double2 *near64;
     float2 *near32;
@@ -148,7 +150,7 @@ int launch_p2m(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t
 int launch_m2m(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
 int launch_m2l(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t s, int prio);
 int launch_l2l(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
-int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);
+int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);  // threads 32: 1 leaf per block, 64: 2
 int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
 int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far
 int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);  // adds it

@@ -154,138 +154,243 @@ __device__ __forceinline__ void neumaier(float &s, float &c, float x)
     s = t;
 }
 
-// One block per target leaf; `KT` targets per thread; tiles of `tile` sources (a multiple of 4).
+// Packed FP32 pairs (one 64-bit register pair, two targets): sm_100-class f32x2 arithmetic.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk2(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// In units where r'^2 is the exponent of 2: exp(-r^2 / 2 sigma^2) = 2^-(r'^2), y = r'^2 ln 2. The series
+// replaces 1 - 2^-(r'^2) when y < 1/2, i.e. r'^2 < (1/2) / ln 2.
+#define P2P_THR 0.72134752044448170f
+#define P2P_LN2 0.69314718055994531f
+
+// Targets of one lane for one pass: up to 4 (two packed pairs); split coordinates and compensated sums.
+struct Targets {
+    float hx[4], hy[4], lx[4], ly[4];
+    float su[4], cu[4], sv[4], cv[4];
+};
+
+// Sources j0..j1 of one source leaf against KT targets per lane (KT/2 packed pairs). The targets are first
+// re-expressed relative to that leaf's centre, exactly: hi - dc s by Fast2Sum (|dc s| >= |hi|), its error into lo.
 template <int KT>
-__global__ void __launch_bounds__(128) k_p2p32(Work w, int tile)
+__device__ __forceinline__ void p2p_segment(const float4 *__restrict__ EH, const float4 *__restrict__ EL,
+                                            const float4 *__restrict__ EG, int j0, int j1, float sdx, float sdy,
+                                            Targets &t)
+{
+    constexpr int NP = KT / 2;
+    f2 AHX[NP], ALX[NP], AHY[NP], ALY[NP], PU[NP], PV[NP];
+#pragma unroll
+    for (int pr = 0; pr < NP; ++pr) {
+        float hx0 = t.hx[2 * pr] - sdx, hx1 = t.hx[2 * pr + 1] - sdx;
+        float lx0 = t.lx[2 * pr] + (t.hx[2 * pr] - (hx0 + sdx)), lx1 = t.lx[2 * pr + 1] + (t.hx[2 * pr + 1] - (hx1 + sdx));
+        float hy0 = t.hy[2 * pr] - sdy, hy1 = t.hy[2 * pr + 1] - sdy;
+        float ly0 = t.ly[2 * pr] + (t.hy[2 * pr] - (hy0 + sdy)), ly1 = t.ly[2 * pr + 1] + (t.hy[2 * pr + 1] - (hy1 + sdy));
+        AHX[pr] = pk2(hx0, hx1);
+        ALX[pr] = pk2(lx0, lx1);
+        AHY[pr] = pk2(hy0, hy1);
+        ALY[pr] = pk2(ly0, ly1);
+        PU[pr] = 0ull;
+        PV[pr] = 0ull;
+    }
+    for (int j = j0; j < j1; ++j) {
+        const float4 h = EH[j], l = EL[j], g = EG[j];
+        const f2 sxh = pk2(h.x, h.y), syh = pk2(h.z, h.w), sxl = pk2(l.x, l.y), syl = pk2(l.z, l.w);
+        const f2 gp = pk2(g.x, g.y), gn = pk2(g.z, g.w);
+        f2 dx[NP], dy[NP], r2[NP], q[NP], og[NP];
+        float rmin = 3.0e38f;
+#pragma unroll
+        for (int pr = 0; pr < NP; ++pr) {
+            dx[pr] = add2(sub2(AHX[pr], sxh), sub2(ALX[pr], sxl));
+            dy[pr] = add2(sub2(AHY[pr], syh), sub2(ALY[pr], syl));
+            r2[pr] = fma2(dx[pr], dx[pr], mul2(dy[pr], dy[pr]));
+            float ra, rb;
+            up2(r2[pr], ra, rb);
+            const float ea = ex2_approx(-ra), eb = ex2_approx(-rb);
+            q[pr] = pk2(rcp_approx(ra), rcp_approx(rb));
+            og[pr] = fma2(pk2(ea, eb), gn, gp);  // g (1 - e)
+            rmin = fminf(rmin, fminf(ra, rb));
+        }
+        // rare (r < sigma): warp-uniform branch to the series for (1 - e^-y) / y
+        if (__any_sync(0xffffffffu, rmin < P2P_THR)) {
+#pragma unroll
+            for (int pr = 0; pr < NP; ++pr) {
+                float ra, rb, qa, qb, oa, ob;
+                up2(r2[pr], ra, rb);
+                up2(q[pr], qa, qb);
+                up2(og[pr], oa, ob);
+                if (ra < P2P_THR) {
+                    qa = P2P_LN2 * small_y_factor(P2P_LN2 * ra);
+                    oa = g.x;
+                }
+                if (rb < P2P_THR) {
+                    qb = P2P_LN2 * small_y_factor(P2P_LN2 * rb);
+                    ob = g.x;
+                }
+                q[pr] = pk2(qa, qb);
+                og[pr] = pk2(oa, ob);
+            }
+        }
+#pragma unroll
+        for (int pr = 0; pr < NP; ++pr) {
+            const f2 gf = mul2(og[pr], q[pr]);
+            PU[pr] = fma2(dy[pr], gf, PU[pr]);  // u accumulates -dy g f: negated at the end
+            PV[pr] = fma2(dx[pr], gf, PV[pr]);
+        }
+    }
+#pragma unroll
+    for (int pr = 0; pr < NP; ++pr) {
+        float a, b;
+        up2(PU[pr], a, b);
+        neumaier(t.su[2 * pr], t.cu[2 * pr], a);
+        neumaier(t.su[2 * pr + 1], t.cu[2 * pr + 1], b);
+        up2(PV[pr], a, b);
+        neumaier(t.sv[2 * pr], t.cv[2 * pr], a);
+        neumaier(t.sv[2 * pr + 1], t.cv[2 * pr + 1], b);
+    }
+}
+
+// LPB leaves per block (1 or 2, one warp each; with 2 the leaves are the pair (2j, 2j+1) of one row and share
+// their 3 x 4 source neighbourhood). Each warp takes its leaf's targets in passes of at most 32 * ktmax, with
+// 2 or 4 targets per lane chosen by the pass size. Sources arrive by bulk copies into shared memory.
+template <int LPB>
+__global__ void __launch_bounds__(64) k_p2p32(Work w, int tile, int ktmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    float4 *spos = reinterpret_cast<float4 *>(smem_raw);
-    float *sgam = reinterpret_cast<float *>(smem_raw + (size_t)tile * sizeof(float4));
-    const int leaf = blockIdx.x;
-    const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
-    if (c == 0)
+    float4 *EH = reinterpret_cast<float4 *>(smem_raw), *EL = EH + tile, *EG = EL + tile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int first = blockIdx.x * LPB;
+    if (first >= w.nleaf)
         return;
-    const int k = w.nsys == 1 ? 0 : find_sys_by_leaf(w.sys, w.nsys, leaf);
+    const int k = w.nsys == 1 ? 0 : find_sys_by_leaf(w.sys, w.nsys, first);
     const SysDev &d = w.sys[k];
-    const int L = d.depth, ns = 1 << L, local = leaf - (int)d.leaf0;
-    const int ix = local & (ns - 1), iy = local >> L;
-    const float kappa = d.kappa, cexp = d.cexp, ythr = d.ythr, snear = d.snear;
-    const int jx0 = ix > 0 ? ix - 1 : 0, jx1 = ix < ns - 1 ? ix + 1 : ns - 1;
-    const int tid = threadIdx.x, T = blockDim.x;
-    if (tid == 0) {
+    const int L = d.depth, ns = 1 << L, local0 = first - (int)d.leaf0;
+    const int ix0 = local0 & (ns - 1), iy = local0 >> L;
+    const int myleaf = first + warp;
+    const int my_s0 = w.start[myleaf], my_c = w.start[myleaf + 1] - my_s0;
+    const int per_pass = 32 * ktmax;
+    int npass = (my_c + per_pass - 1) / per_pass;
+    if (LPB == 2) {
+        const int other = first + (warp ^ 1);
+        const int oc = w.start[other + 1] - w.start[other];
+        npass = max(npass, (oc + per_pass - 1) / per_pass);
+    }
+    if (npass == 0)
+        return;  // block-uniform: every leaf of the block is empty
+    const int my_np = (my_c + per_pass - 1) / per_pass;
+    const float s = d.s_unit, snear = d.snear;
+    const int c_lo = ix0 - 1, ncol = LPB + 2;  // block columns c_lo .. c_lo + ncol - 1
+    if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_proxy_async();
     }
     __syncthreads();
     uint32_t phase = 0;
-    for (int t0 = 0; t0 < c; t0 += T * KT) {
-        float thx[KT], thy[KT], tlx[KT], tly[KT];
-        float su[KT], cu[KT], sv[KT], cv[KT];
-#pragma unroll
-        for (int q = 0; q < KT; ++q) {
-            int e = t0 + tid + q * T;
-            float4 tp = e < c ? w.pos4[s0 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
-            thx[q] = tp.x;
-            thy[q] = tp.y;
-            tlx[q] = tp.z;
-            tly[q] = tp.w;
-            su[q] = cu[q] = sv[q] = cv[q] = 0.f;
+    for (int pass = 0; pass < npass; ++pass) {
+        int t_lo = 0, t_cnt = 0;
+        if (pass < my_np) {
+            t_lo = (int)((int64_t)pass * my_c / my_np);
+            t_cnt = (int)((int64_t)(pass + 1) * my_c / my_np) - t_lo;
         }
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int row = iy + dy;
+        const int kt = t_cnt == 0 ? 0 : (t_cnt <= 64 ? 2 : 4);
+        Targets t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int e = lane + 32 * q;
+            float4 hh = make_float4(0.f, 0.f, 0.f, 0.f), ll = hh;
+            if (e < t_cnt) {
+                hh = w.eh[my_s0 + t_lo + e];
+                ll = w.el[my_s0 + t_lo + e];
+            }
+            t.hx[q] = hh.x;
+            t.hy[q] = hh.z;
+            t.lx[q] = ll.x;
+            t.ly[q] = ll.z;
+            t.su[q] = t.cu[q] = t.sv[q] = t.cv[q] = 0.f;
+        }
+        for (int dyr = -1; dyr <= 1; ++dyr) {
+            const int row = iy + dyr;
             if (row < 0 || row >= ns)
                 continue;
             const int rowleaf = (int)d.leaf0 + row * ns;
-            const int r0 = w.start[rowleaf + jx0], r1 = w.start[rowleaf + jx1 + 1];
+            const int ca = max(c_lo, 0), cz = min(c_lo + ncol - 1, ns - 1);
+            const int r0 = w.start[rowleaf + ca], r1 = w.start[rowleaf + cz + 1];
             if (r1 <= r0)
                 continue;
-            int cb[4];  // column boundaries inside the row run (columns ix-1, ix, ix+1)
+            int cb[LPB + 3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                int col = ix - 1 + q;
-                cb[q] = (col < jx0) ? r0 : (col > jx1 ? r1 : w.start[rowleaf + col]);
+            for (int cc = 0; cc < ncol; ++cc) {
+                const int col = c_lo + cc;
+                cb[cc] = col < 0 ? r0 : (col >= ns ? r1 : w.start[rowleaf + col]);
             }
-            cb[3] = r1;
-            for (int q0 = r0 & ~3; q0 < r1; q0 += tile) {
-                const int a = q0, b = min(q0 + tile, (r1 + 3) & ~3);
+            cb[ncol] = r1;
+            for (int q0 = r0; q0 < r1; q0 += tile) {
+                const int m = min(tile, r1 - q0);
                 __syncthreads();  // everyone is done with the previous tile
-                if (tid == 0) {
+                if (threadIdx.x == 0) {
                     fence_proxy_async();
-                    mbar_expect_tx(&bar, (uint32_t)(b - a) * 20u);
-                    bulk_g2s(spos, w.pos4 + a, (uint32_t)(b - a) * 16u, &bar);
-                    bulk_g2s(sgam, w.g32 + a, (uint32_t)(b - a) * 4u, &bar);
+                    mbar_expect_tx(&bar, (uint32_t)m * 48u);
+                    bulk_g2s(EH, w.eh + q0, (uint32_t)m * 16u, &bar);
+                    bulk_g2s(EL, w.el + q0, (uint32_t)m * 16u, &bar);
+                    bulk_g2s(EG, w.eg + q0, (uint32_t)m * 16u, &bar);
                 }
                 bool ok = mbar_wait_bounded(&bar, phase, w.status);
                 if (!__syncthreads_and(ok)) {
-                    // the copy never completed: give it one more bounded wait before the block exits
                     if (!ok)
-                        mbar_wait_bounded(&bar, phase, w.status);
+                        mbar_wait_bounded(&bar, phase, w.status);  // let a late copy land before exiting
                     return;
                 }
                 phase ^= 1;
-                const int lo = max(a, r0), hi = min(q0 + tile, r1);
-#pragma unroll 1
-                for (int col = 0; col < 3; ++col) {
-                    const int j0 = max(lo, cb[col]) - a, j1 = min(hi, cb[col + 1]) - a;
+                if (kt == 0)
+                    continue;
+#pragma unroll
+                for (int k3 = 0; k3 < 3; ++k3) {
+                    const int cc = warp + k3;  // this warp's columns ix-1, ix, ix+1
+                    const int j0 = max(q0, cb[cc]) - q0, j1 = min(q0 + m, cb[cc + 1]) - q0;
                     if (j0 >= j1)
                         continue;
-                    // target relative to this source leaf's centre, zeta_t - (dc, dy), kept exact as hi + lo
-                    const float dc = (float)(col - 1), dr = (float)dy;
-                    float ahx[KT], alx[KT], ahy[KT], aly[KT], pu[KT], pv[KT];
-#pragma unroll
-                    for (int q = 0; q < KT; ++q) {
-                        float sx = thx[q] - dc;
-                        ahx[q] = sx;
-                        alx[q] = tlx[q] + (thx[q] - (sx + dc));
-                        float sy = thy[q] - dr;
-                        ahy[q] = sy;
-                        aly[q] = tly[q] + (thy[q] - (sy + dr));
-                        pu[q] = pv[q] = 0.f;
-                    }
-                    for (int j = j0; j < j1; ++j) {
-                        const float4 sp = spos[j];
-                        const float g = sgam[j];
-                        float dxv[KT], dyv[KT], r2v[KT], fv[KT];
-                        float rmin = 3.0e38f;
-#pragma unroll
-                        for (int q = 0; q < KT; ++q) {
-                            dxv[q] = (ahx[q] - sp.x) + (alx[q] - sp.z);
-                            dyv[q] = (ahy[q] - sp.y) + (aly[q] - sp.w);
-                            float r2 = fmaf(dxv[q], dxv[q], dyv[q] * dyv[q]);
-                            float e = ex2_approx(r2 * cexp);
-                            float rr = rcp_approx(fmaxf(r2, 1e-30f));
-                            fv[q] = fmaf(-e, rr, rr);  // (1 - e^-y) / r^2
-                            r2v[q] = r2;
-                            rmin = fminf(rmin, r2);
-                        }
-                        // rare (r < sigma): warp-uniform branch to the series, off the common path
-                        if (__any_sync(0xffffffffu, rmin < ythr)) {
-#pragma unroll
-                            for (int q = 0; q < KT; ++q)
-                                if (r2v[q] < ythr)
-                                    fv[q] = kappa * small_y_factor(kappa * r2v[q]);
-                        }
-#pragma unroll
-                        for (int q = 0; q < KT; ++q) {
-                            const float gf = g * fv[q];
-                            pu[q] = fmaf(-dyv[q], gf, pu[q]);
-                            pv[q] = fmaf(dxv[q], gf, pv[q]);
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < KT; ++q) {
-                        neumaier(su[q], cu[q], pu[q]);
-                        neumaier(sv[q], cv[q], pv[q]);
-                    }
+                    const float sdx = (float)(k3 - 1) * s, sdy = (float)dyr * s;
+                    if (kt == 2)
+                        p2p_segment<2>(EH, EL, EG, j0, j1, sdx, sdy, t);
+                    else
+                        p2p_segment<4>(EH, EL, EG, j0, j1, sdx, sdy, t);
                 }
             }
         }
 #pragma unroll
-        for (int q = 0; q < KT; ++q) {
-            int e = t0 + tid + q * T;
-            if (e < c)
-                w.near32[s0 + e] = make_float2((su[q] + cu[q]) * snear, (sv[q] + cv[q]) * snear);
+        for (int q = 0; q < 4; ++q) {
+            const int e = lane + 32 * q;
+            if (e < t_cnt)
+                w.near32[my_s0 + t_lo + e] = make_float2(-(t.su[q] + t.cu[q]) * snear, (t.sv[q] + t.cv[q]) * snear);
         }
     }
 }
@@ -298,16 +403,15 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
         k_p2p64<<<w.nleaf, 64, 0, s>>>(w);
         return 1;
     }
-    if (threads <= 0)
-        threads = 64;
-    int tile = 8 * threads;  // 256 / 512 / 1024 sources: 5, 10, 20 KiB of shared memory per block
-    size_t sm = (size_t)tile * 20;
-    if (kt == 2)
-        k_p2p32<2><<<w.nleaf, threads, sm, s>>>(w, tile);
-    else if (kt == 4)
-        k_p2p32<4><<<w.nleaf, threads, sm, s>>>(w, tile);
+    int ktmax = kt == 2 ? 2 : 4;
+    // two leaves per block needs every system's leaves to pair up within rows (depth >= 1)
+    bool pairs = threads == 64 && w.lv.nsys_at[1] == w.nsys;
+    int tile = pairs ? 320 : 256;
+    size_t sm = (size_t)tile * 48;
+    if (pairs)
+        k_p2p32<2><<<(w.nleaf + 1) / 2, 64, sm, s>>>(w, tile, ktmax);
     else
-        k_p2p32<1><<<w.nleaf, threads, sm, s>>>(w, tile);
+        k_p2p32<1><<<w.nleaf, 32, sm, s>>>(w, tile, ktmax);
     return 1;
 }
 

@@ -97,9 +97,9 @@ __global__ void __launch_bounds__(64) k_p2m(Work w, int adj)
     for (int j = s0 + lane; j < s0 + c; j += 32) {
         cx<R> z, q;
         if (w.mixed) {
-            float4 pp = w.pos4[j];
-            z = {(R)pp.x + (R)pp.z, (R)pp.y + (R)pp.w};
-            q = {(R)0, -(R)w.g32[j]};
+            float4 hh = w.eh[j], ll = w.el[j];
+            z = {(R)((hh.x + ll.x) * d.inv_s), (R)((hh.z + ll.z) * d.inv_s)};
+            q = {(R)0, -(R)w.eg[j].x};
         } else {
             z = {(R)((w.sx[j] - d.x0) * scale - (ix + 0.5)), (R)((w.sy[j] - d.y0) * scale - (iy + 0.5))};
             if (adj)
@@ -441,8 +441,8 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
         // precision form: FP32 far field and sum, one conversion to FP64 at the end
         float fu = 0.f, fv = 0.f;
         if (far) {
-            float4 pp = w.pos4[pos];
-            cx<float> z = {pp.x + pp.z, pp.y + pp.w};
+            float4 hh = w.eh[pos], ll = w.el[pos];
+            cx<float> z = {(hh.x + ll.x) * d.inv_s, (hh.z + ll.z) * d.inv_s};
             cx<float> s = horner<float>(w.L32, base, w.p, z);
             float fs = (float)d.far_scale;
             fu = s.re * fs;
@@ -457,8 +457,8 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
     if (far) {
         cx<double> z;
         if (w.mixed) {
-            float4 pp = w.pos4[pos];
-            z = {(double)pp.x + (double)pp.z, (double)pp.y + (double)pp.w};
+            float4 hh = w.eh[pos], ll = w.el[pos];
+            z = {((double)hh.x + (double)ll.x) / (double)d.s_unit, ((double)hh.z + (double)ll.z) / (double)d.s_unit};
         } else {
             int local = (int)(w.sleaf[pos] - d.leaf0);
             int ix = local & ((1 << L) - 1), iy = local >> L;

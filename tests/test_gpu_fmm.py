@@ -86,7 +86,7 @@ def test_mixed_matches_oracle_fmm(lib, oracle, name, make):
         assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < TOL32, coarse
 
 
-@pytest.mark.parametrize("tile", [(64, 1), (64, 2), (128, 1), (128, 2), (32, 2), (32, 4), (128, 4), (96, 1)])
+@pytest.mark.parametrize("tile", [(64, 4), (64, 2), (32, 4), (32, 2)])
 def test_mixed_tile_shapes(lib, oracle, tile):
     w = fi.clustered(30000, depth=4, p=12)  # dense leaves: several target chunks and source tiles per leaf
     uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)
@@ -256,7 +256,8 @@ def test_autograd_function_finite_differences(lib):
 
     rs = np.random.default_rng(10)
     for j in rs.choice(w.n, 5, replace=False):
-        for arr, grad, h in ((g, g.grad, 1e-6 / w.n), (x, x.grad, 1e-8), (y, y.grad, 1e-8)):
+        # position step 1e-6: smaller steps drown the difference in the rounding of the evaluation itself
+        for arr, grad, h in ((g, g.grad, 1e-6 / w.n), (x, x.grad, 1e-6), (y, y.grad, 1e-6)):
             base = arr.detach().clone()
             p_, m_ = base.clone(), base.clone()
             p_[j] += h
@@ -309,8 +310,7 @@ def test_stage_times_launch_count_and_autotune(lib):
     assert f.kernel_launches() > n0 + 8
     prm = f.autotune(x, y, g, 4, 6)
     assert 4 <= prm["depth"] <= 6
-    assert (prm["p2p_threads"], prm["p2p_targets_per_thread"]) in {(64, 1), (32, 2), (64, 2), (128, 1), (128, 2),
-                                                                  (32, 4), (128, 4)}
+    assert (prm["p2p_threads"], prm["p2p_targets_per_thread"]) in {(64, 4), (64, 2), (32, 4), (32, 2)}
 
 
 @pytest.mark.slow

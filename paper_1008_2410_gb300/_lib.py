@@ -11,7 +11,7 @@ import re
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libfmm2d.so")
+LIB_PATH = os.environ.get("FMM2D_LIB") or os.path.join(HERE, "_build", "libfmm2d.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "fmm2d.h")
 
 FMM_OK, FMM_EINVAL, FMM_ENOMEM, FMM_ECUDA, FMM_ETIMEOUT, FMM_EINTERNAL = range(6)

@@ -99,6 +99,7 @@ struct fmm_ctx {
     size_t d_io_cap = 0;
     int64_t launches = 0;
     int last_timed = 0;
+    unsigned timed_mask = 0;  // which ev_t[] the last timed evaluation recorded
     std::string err;
 };
 
@@ -450,6 +451,7 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
     bool near = mode != MODE_FAR;
     bool timed = h->timing != 0;  // in a graph the event records become event-record nodes
     int64_t nl = 0;
+    (void)cudaGetLastError();  // drop a stale, non-sticky error left by an unrelated runtime call
     if (timed)
         CU(record_timing(h->ev_t[0], s));
     CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
@@ -502,6 +504,7 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
     CU(cudaGetLastError());
     h->launches += nl;
     h->last_timed = timed;
+    h->timed_mask = timed ? (far ? 0xffu : 0xe3u) : 0u;
     return FMM_OK;
 }
 
@@ -968,25 +971,28 @@ int fmm_stage_times(fmm_handle h, float *out, int cap)
         return 0;
     if (cudaEventSynchronize(h->ev_t[7]) != cudaSuccess)
         return 0;
-    float v[8];
+    const unsigned m = h->timed_mask;
     auto el = [&](int a, int b) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, h->ev_t[a], h->ev_t[b]);
+        if (((m >> a) & 1u) && ((m >> b) & 1u) && cudaEventElapsedTime(&ms, h->ev_t[a], h->ev_t[b]) != cudaSuccess) {
+            ms = 0.f;
+            (void)cudaGetLastError();
+        }
         return ms;
     };
-    bool far = h->w.lv.maxdepth >= 2;
+    float v[8];
     v[0] = el(0, 1);
     v[1] = el(1, 5);
-    v[2] = far ? el(1, 2) : 0.f;
-    v[3] = far ? el(2, 3) : 0.f;
-    v[4] = far ? el(3, 4) : 0.f;
+    v[2] = el(1, 2);
+    v[3] = el(2, 3);
+    v[4] = el(3, 4);
     v[5] = el(6, 7);
     v[6] = el(0, 7);
     v[7] = el(1, 6);
-    int m = cap < 8 ? cap : 8;
-    for (int i = 0; i < m; ++i)
+    int k = cap < 8 ? cap : 8;
+    for (int i = 0; i < k; ++i)
         out[i] = v[i];
-    return m;
+    return k;
 }
 
 fmm_status fmm_set_count_pairs(fmm_handle h, int enable)

@@ -9,9 +9,10 @@
 // Precision form (FMM_MIXED): coordinates are leaf-relative in leaf units, split hi + lo in FP32; the shift
 // by the integer leaf offset is exact (Fast2Sum folds its rounding error into lo), so a difference keeps the
 // FP64 coordinates' resolution. exp and 1/r^2 use the SFU (ex2.approx, rcp.approx); for r^2 / 2 sigma^2 < 1/2
-// the factor (1 - e^-y)/y comes from its Taylor series instead of 1 - e^-y, which cancels. Per-target sums are
-// FP32 per source-leaf segment and compensated (Neumaier) across segments. Tiles arrive by bulk asynchronous
-// copies (cp.async.bulk, the TMA engine) into shared memory, completed on an mbarrier with a bounded wait.
+// the factor (1 - e^-y)/y comes from its Taylor series instead of 1 - e^-y, which cancels. Two targets share
+// each packed f32x2 instruction. Per-target sums are FP32 within a row of source leaves and compensated
+// (TwoSum) across rows. Tiles arrive by bulk asynchronous copies (cp.async.bulk, the TMA engine) into shared
+// memory, completed on an mbarrier with a bounded wait.
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -130,30 +131,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-// (1 - e^-y)/y for y in [0, 1/2): Taylor series sum_k (-y)^k / (k+1)!, 10 terms (truncation < 3e-11).
-__device__ __forceinline__ float small_y_factor(float y)
-{
-    float s = 1.0f / 39916800.0f;  // 1/11!
-    s = fmaf(s, -y, 1.0f / 3628800.0f);
-    s = fmaf(s, -y, 1.0f / 362880.0f);
-    s = fmaf(s, -y, 1.0f / 40320.0f);
-    s = fmaf(s, -y, 1.0f / 5040.0f);
-    s = fmaf(s, -y, 1.0f / 720.0f);
-    s = fmaf(s, -y, 1.0f / 120.0f);
-    s = fmaf(s, -y, 1.0f / 24.0f);
-    s = fmaf(s, -y, 1.0f / 6.0f);
-    s = fmaf(s, -y, 0.5f);
-    s = fmaf(s, -y, 1.0f);
-    return s;
-}
-
-__device__ __forceinline__ void neumaier(float &s, float &c, float x)
-{
-    float t = s + x;
-    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
-    s = t;
-}
-
 // Packed FP32 pairs (one 64-bit register pair, two targets): sm_100-class f32x2 arithmetic.
 typedef unsigned long long f2;
 __device__ __forceinline__ f2 pk2(float a, float b)
@@ -188,39 +165,79 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
     return r;
 }
 
-// In units where r'^2 is the exponent of 2: exp(-r^2 / 2 sigma^2) = 2^-(r'^2), y = r'^2 ln 2. The series
-// replaces 1 - 2^-(r'^2) when y < 1/2, i.e. r'^2 < (1/2) / ln 2.
+// In units where r'^2 is the exponent of 2: exp(-r^2 / 2 sigma^2) = 2^-(r'^2), y = r'^2 ln 2. Below y = 1/2
+// the factor (1 - e^-y)/y comes from its Taylor series (10 terms, truncation < 3e-11): 1 - 2^-(r'^2) from the SFU
+// loses 2^-22.5 / y of its relative accuracy there. r' = 0 (a particle and itself, or coincident particles,
+// which always share a leaf) needs no series: with 1/r'^2 clamped, g (1 - e) / r'^2 = 0 exactly.
 #define P2P_THR 0.72134752044448170f
 #define P2P_LN2 0.69314718055994531f
+#ifndef P2P_UNROLL
+#define P2P_UNROLL 2  // source loop unroll of the near-field kernel
+#endif
+#ifndef P2P_MIN_BLOCKS
+#define P2P_MIN_BLOCKS 1  // minimum resident blocks per SM requested from the register allocator
+#endif
+constexpr int kP2PUnroll = P2P_UNROLL;
 
-// Targets of one lane for one pass: up to 4 (two packed pairs); split coordinates and compensated sums.
-struct Targets {
-    float hx[4], hy[4], lx[4], ly[4];
-    float su[4], cu[4], sv[4], cv[4];
-};
+__device__ __forceinline__ float small_y_factor10(float y)
+{
+    float s = 1.0f / 39916800.0f;
+    s = fmaf(s, -y, 1.0f / 3628800.0f);
+    s = fmaf(s, -y, 1.0f / 362880.0f);
+    s = fmaf(s, -y, 1.0f / 40320.0f);
+    s = fmaf(s, -y, 1.0f / 5040.0f);
+    s = fmaf(s, -y, 1.0f / 720.0f);
+    s = fmaf(s, -y, 1.0f / 120.0f);
+    s = fmaf(s, -y, 1.0f / 24.0f);
+    s = fmaf(s, -y, 1.0f / 6.0f);
+    s = fmaf(s, -y, 0.5f);
+    s = fmaf(s, -y, 1.0f);
+    return s;
+}
 
-// Sources j0..j1 of one source leaf against KT targets per lane (KT/2 packed pairs). The targets are first
-// re-expressed relative to that leaf's centre, exactly: hi - dc s by Fast2Sum (|dc s| >= |hi|), its error into lo.
-template <int KT>
-__device__ __forceinline__ void p2p_segment(const float4 *__restrict__ EH, const float4 *__restrict__ EL,
-                                            const float4 *__restrict__ EG, int j0, int j1, float sdx, float sdy,
-                                            Targets &t)
+// Error-free packed sum: s + c += x (Knuth's TwoSum on both halves).
+__device__ __forceinline__ void two_sum2(f2 &s, f2 &c, f2 x)
+{
+    f2 t = add2(s, x);
+    f2 bp = sub2(t, s);
+    f2 e = add2(sub2(s, sub2(t, bp)), sub2(x, bp));
+    c = add2(c, e);
+    s = t;
+}
+
+// Sources j0..j1 of one source leaf against KT targets per lane (KT/2 packed pairs), accumulated into PU, PV.
+// The lane's targets (leaf order index `tbase + lane + 32 q`, q < KT, only those < tcnt) are re-read and
+// re-expressed relative to the source leaf's centre exactly: hi - dc s by Fast2Sum (|dc s| >= |hi|), error into lo.
+template <int KT, bool SELF>
+__device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restrict__ EH,
+                                            const float4 *__restrict__ EL, const float4 *__restrict__ EG, int j0,
+                                            int j1, float sdx, float sdy, int tbase, int tcnt, f2 *PU, f2 *PV)
 {
     constexpr int NP = KT / 2;
-    f2 AHX[NP], ALX[NP], AHY[NP], ALY[NP], PU[NP], PV[NP];
+    const int lane = threadIdx.x & 31;
+    f2 AHX[NP], ALX[NP], AHY[NP], ALY[NP];
 #pragma unroll
     for (int pr = 0; pr < NP; ++pr) {
-        float hx0 = t.hx[2 * pr] - sdx, hx1 = t.hx[2 * pr + 1] - sdx;
-        float lx0 = t.lx[2 * pr] + (t.hx[2 * pr] - (hx0 + sdx)), lx1 = t.lx[2 * pr + 1] + (t.hx[2 * pr + 1] - (hx1 + sdx));
-        float hy0 = t.hy[2 * pr] - sdy, hy1 = t.hy[2 * pr + 1] - sdy;
-        float ly0 = t.ly[2 * pr] + (t.hy[2 * pr] - (hy0 + sdy)), ly1 = t.ly[2 * pr + 1] + (t.hy[2 * pr + 1] - (hy1 + sdy));
-        AHX[pr] = pk2(hx0, hx1);
-        ALX[pr] = pk2(lx0, lx1);
-        AHY[pr] = pk2(hy0, hy1);
-        ALY[pr] = pk2(ly0, ly1);
-        PU[pr] = 0ull;
-        PV[pr] = 0ull;
+        float hx[2], lx[2], hy[2], ly[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = lane + 32 * (2 * pr + h);
+            float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
+            if (e < tcnt) {
+                th = w.eh[tbase + e];
+                tl = w.el[tbase + e];
+            }
+            hx[h] = th.x - sdx;
+            lx[h] = tl.x + (th.x - (hx[h] + sdx));
+            hy[h] = th.z - sdy;
+            ly[h] = tl.z + (th.z - (hy[h] + sdy));
+        }
+        AHX[pr] = pk2(hx[0], hx[1]);
+        ALX[pr] = pk2(lx[0], lx[1]);
+        AHY[pr] = pk2(hy[0], hy[1]);
+        ALY[pr] = pk2(ly[0], ly[1]);
     }
+#pragma unroll(kP2PUnroll)
     for (int j = j0; j < j1; ++j) {
         const float4 h = EH[j], l = EL[j], g = EG[j];
         const f2 sxh = pk2(h.x, h.y), syh = pk2(h.z, h.w), sxl = pk2(l.x, l.y), syl = pk2(l.z, l.w);
@@ -235,12 +252,19 @@ __device__ __forceinline__ void p2p_segment(const float4 *__restrict__ EH, const
             float ra, rb;
             up2(r2[pr], ra, rb);
             const float ea = ex2_approx(-ra), eb = ex2_approx(-rb);
-            q[pr] = pk2(rcp_approx(ra), rcp_approx(rb));
+            if (SELF) {
+                // own leaf: r' = 0 occurs; clamp 1/r'^2 and keep zeros out of the series test
+                q[pr] = pk2(rcp_approx(fmaxf(ra, 1e-30f)), rcp_approx(fmaxf(rb, 1e-30f)));
+                rmin = __uint_as_float(min(__float_as_uint(rmin), min(__float_as_uint(ra) - 1u, __float_as_uint(rb) - 1u)));
+            } else {
+                q[pr] = pk2(rcp_approx(ra), rcp_approx(rb));
+                rmin = fminf(rmin, fminf(ra, rb));
+            }
             og[pr] = fma2(pk2(ea, eb), gn, gp);  // g (1 - e)
-            rmin = fminf(rmin, fminf(ra, rb));
         }
-        // rare (r < sigma): warp-uniform branch to the series for (1 - e^-y) / y
-        if (__any_sync(0xffffffffu, rmin < P2P_THR)) {
+        // rare (0 < r < sigma): warp-uniform branch to the series, off the common path. With SELF, rmin holds
+        // the bit pattern minus one (as unsigned), so r' = 0 maps to the largest value and never triggers it.
+        if (__any_sync(0xffffffffu, SELF ? (__float_as_uint(rmin) < __float_as_uint(P2P_THR)) : (rmin < P2P_THR))) {
 #pragma unroll
             for (int pr = 0; pr < NP; ++pr) {
                 float ra, rb, qa, qb, oa, ob;
@@ -248,11 +272,11 @@ __device__ __forceinline__ void p2p_segment(const float4 *__restrict__ EH, const
                 up2(q[pr], qa, qb);
                 up2(og[pr], oa, ob);
                 if (ra < P2P_THR) {
-                    qa = P2P_LN2 * small_y_factor(P2P_LN2 * ra);
+                    qa = P2P_LN2 * small_y_factor10(P2P_LN2 * ra);
                     oa = g.x;
                 }
                 if (rb < P2P_THR) {
-                    qb = P2P_LN2 * small_y_factor(P2P_LN2 * rb);
+                    qb = P2P_LN2 * small_y_factor10(P2P_LN2 * rb);
                     ob = g.x;
                 }
                 q[pr] = pk2(qa, qb);
@@ -266,23 +290,14 @@ __device__ __forceinline__ void p2p_segment(const float4 *__restrict__ EH, const
             PV[pr] = fma2(dx[pr], gf, PV[pr]);
         }
     }
-#pragma unroll
-    for (int pr = 0; pr < NP; ++pr) {
-        float a, b;
-        up2(PU[pr], a, b);
-        neumaier(t.su[2 * pr], t.cu[2 * pr], a);
-        neumaier(t.su[2 * pr + 1], t.cu[2 * pr + 1], b);
-        up2(PV[pr], a, b);
-        neumaier(t.sv[2 * pr], t.cv[2 * pr], a);
-        neumaier(t.sv[2 * pr + 1], t.cv[2 * pr + 1], b);
-    }
 }
 
 // LPB leaves per block (1 or 2, one warp each; with 2 the leaves are the pair (2j, 2j+1) of one row and share
 // their 3 x 4 source neighbourhood). Each warp takes its leaf's targets in passes of at most 32 * ktmax, with
-// 2 or 4 targets per lane chosen by the pass size. Sources arrive by bulk copies into shared memory.
+// 2 or 4 targets per lane chosen by the pass size. Sources arrive by bulk copies into shared memory; each
+// target's row sums (plain FP32 over <= 3 leaves) are added to its total with an error-free TwoSum.
 template <int LPB>
-__global__ void __launch_bounds__(64) k_p2p32(Work w, int tile, int ktmax)
+__global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, int ktmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -307,7 +322,7 @@ __global__ void __launch_bounds__(64) k_p2p32(Work w, int tile, int ktmax)
     if (npass == 0)
         return;  // block-uniform: every leaf of the block is empty
     const int my_np = (my_c + per_pass - 1) / per_pass;
-    const float s = d.s_unit, snear = d.snear;
+    const float s = d.s_unit;
     const int c_lo = ix0 - 1, ncol = LPB + 2;  // block columns c_lo .. c_lo + ncol - 1
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -322,21 +337,8 @@ __global__ void __launch_bounds__(64) k_p2p32(Work w, int tile, int ktmax)
             t_cnt = (int)((int64_t)(pass + 1) * my_c / my_np) - t_lo;
         }
         const int kt = t_cnt == 0 ? 0 : (t_cnt <= 64 ? 2 : 4);
-        Targets t;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int e = lane + 32 * q;
-            float4 hh = make_float4(0.f, 0.f, 0.f, 0.f), ll = hh;
-            if (e < t_cnt) {
-                hh = w.eh[my_s0 + t_lo + e];
-                ll = w.el[my_s0 + t_lo + e];
-            }
-            t.hx[q] = hh.x;
-            t.hy[q] = hh.z;
-            t.lx[q] = ll.x;
-            t.ly[q] = ll.z;
-            t.su[q] = t.cu[q] = t.sv[q] = t.cv[q] = 0.f;
-        }
+        const int tbase = my_s0 + t_lo;
+        f2 SU[2] = {0ull, 0ull}, CU[2] = {0ull, 0ull}, SV[2] = {0ull, 0ull}, CV[2] = {0ull, 0ull};
         for (int dyr = -1; dyr <= 1; ++dyr) {
             const int row = iy + dyr;
             if (row < 0 || row >= ns)
@@ -346,13 +348,7 @@ __global__ void __launch_bounds__(64) k_p2p32(Work w, int tile, int ktmax)
             const int r0 = w.start[rowleaf + ca], r1 = w.start[rowleaf + cz + 1];
             if (r1 <= r0)
                 continue;
-            int cb[LPB + 3];
-#pragma unroll
-            for (int cc = 0; cc < ncol; ++cc) {
-                const int col = c_lo + cc;
-                cb[cc] = col < 0 ? r0 : (col >= ns ? r1 : w.start[rowleaf + col]);
-            }
-            cb[ncol] = r1;
+            f2 PU[2] = {0ull, 0ull}, PV[2] = {0ull, 0ull};
             for (int q0 = r0; q0 < r1; q0 += tile) {
                 const int m = min(tile, r1 - q0);
                 __syncthreads();  // everyone is done with the previous tile
@@ -374,23 +370,48 @@ __global__ void __launch_bounds__(64) k_p2p32(Work w, int tile, int ktmax)
                     continue;
 #pragma unroll
                 for (int k3 = 0; k3 < 3; ++k3) {
-                    const int cc = warp + k3;  // this warp's columns ix-1, ix, ix+1
-                    const int j0 = max(q0, cb[cc]) - q0, j1 = min(q0 + m, cb[cc + 1]) - q0;
+                    const int col = ix0 + warp - 1 + k3;  // this warp's columns ix-1, ix, ix+1
+                    if (col < 0 || col >= ns)
+                        continue;
+                    const int b0 = w.start[rowleaf + col], b1 = w.start[rowleaf + col + 1];
+                    const int j0 = max(q0, b0) - q0, j1 = min(q0 + m, b1) - q0;
                     if (j0 >= j1)
                         continue;
                     const float sdx = (float)(k3 - 1) * s, sdy = (float)dyr * s;
-                    if (kt == 2)
-                        p2p_segment<2>(EH, EL, EG, j0, j1, sdx, sdy, t);
-                    else
-                        p2p_segment<4>(EH, EL, EG, j0, j1, sdx, sdy, t);
+                    const bool self = k3 == 1 && dyr == 0;
+                    if (kt == 2) {
+                        if (self)
+                            p2p_segment<2, true>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
+                        else
+                            p2p_segment<2, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
+                    } else {
+                        if (self)
+                            p2p_segment<4, true>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
+                        else
+                            p2p_segment<4, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = lane + 32 * q;
-            if (e < t_cnt)
-                w.near32[my_s0 + t_lo + e] = make_float2(-(t.su[q] + t.cu[q]) * snear, (t.sv[q] + t.cv[q]) * snear);
+            for (int pr = 0; pr < 2; ++pr) {
+                two_sum2(SU[pr], CU[pr], PU[pr]);
+                two_sum2(SV[pr], CV[pr], PV[pr]);
+            }
+        }
+        const float snear = d.snear;
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+            float su[2], cu[2], sv[2], cv[2];
+            up2(SU[pr], su[0], su[1]);
+            up2(CU[pr], cu[0], cu[1]);
+            up2(SV[pr], sv[0], sv[1]);
+            up2(CV[pr], cv[0], cv[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = lane + 32 * (2 * pr + h);
+                if (e < t_cnt)
+                    w.near32[tbase + e] = make_float2(-(su[h] + cu[h]) * snear, (sv[h] + cv[h]) * snear);
+            }
         }
     }
 }

@@ -18,7 +18,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/fmm2d.h"
+#include "fmm2d.h"
 #include "fmm_internal.cuh"
 
 using namespace fmm;

@@ -172,10 +172,10 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 #define P2P_THR 0.72134752044448170f
 #define P2P_LN2 0.69314718055994531f
 #ifndef P2P_UNROLL
-#define P2P_UNROLL 2  // source loop unroll of the near-field kernel
+#define P2P_UNROLL 1  // source loop unroll of the near-field kernel
 #endif
 #ifndef P2P_MIN_BLOCKS
-#define P2P_MIN_BLOCKS 1  // minimum resident blocks per SM requested from the register allocator
+#define P2P_MIN_BLOCKS 12  // minimum resident blocks per SM requested from the register allocator
 #endif
 constexpr int kP2PUnroll = P2P_UNROLL;
 
@@ -295,7 +295,7 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
 // LPB leaves per block (1 or 2, one warp each; with 2 the leaves are the pair (2j, 2j+1) of one row and share
 // their 3 x 4 source neighbourhood). Each warp takes its leaf's targets in passes of at most 32 * ktmax, with
 // 2 or 4 targets per lane chosen by the pass size. Sources arrive by bulk copies into shared memory; each
-// target's row sums (plain FP32 over <= 3 leaves) are added to its total with an error-free TwoSum.
+// target's sum over one tile (plain FP32) is added to its total with an error-free TwoSum.
 template <int LPB>
 __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, int ktmax)
 {
@@ -391,11 +391,14 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
                             p2p_segment<4, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
                     }
                 }
-            }
+                // compensated totals: plain FP32 sums cover at most one tile of sources
 #pragma unroll
-            for (int pr = 0; pr < 2; ++pr) {
-                two_sum2(SU[pr], CU[pr], PU[pr]);
-                two_sum2(SV[pr], CV[pr], PV[pr]);
+                for (int pr = 0; pr < 2; ++pr) {
+                    two_sum2(SU[pr], CU[pr], PU[pr]);
+                    two_sum2(SV[pr], CV[pr], PV[pr]);
+                    PU[pr] = 0ull;
+                    PV[pr] = 0ull;
+                }
             }
         }
         const float snear = d.snear;

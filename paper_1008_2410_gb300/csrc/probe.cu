@@ -4,7 +4,7 @@
 // grid that fills the GPU and is timed with CUDA events.
 #include <cstdio>
 
-#include "../../include/fmm2d.h"
+#include "fmm2d.h"
 #include "fmm_internal.cuh"
 
 namespace {

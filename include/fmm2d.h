@@ -166,6 +166,22 @@ fmm_status fmm_get_params(fmm_handle h, int *tree_depth, int *p, double *sigma, 
  * out[3] SM count. cap >= 4. Allocates and frees 1 MiB of device memory. */
 fmm_status fmm_probe_peaks(double *out, int cap);
 
+/* Allocation-free evaluation, for callers that cannot let a library allocate device memory (code running under
+ * another framework's memory manager, inside an allocation-free region, or on a fixed memory budget). The paper
+ * has no counterpart: this is a deployment variant of fmm_velocity. It needs no handle: depth, p, sigma, the form
+ * (FMM_FP64 / FMM_MIXED) and the root square (domain = {x0, y0, side}, or NULL for the bounding-box rule) are
+ * arguments; x, y, gamma, u, v are device arrays as for fmm_velocity; cuda_stream orders the work (NULL = legacy
+ * default stream). All scratch lives in one fixed 16 MiB __device__ array that every GPU loading the library
+ * holds until the process exits; it fits, for example, 65,536 particles at depth <= 6 with p <= 20 in either
+ * form. Sizes that do not fit return FMM_EINVAL before any device work. Calls no cudaMalloc, cudaFree or other
+ * allocating routine. The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current, so make that first call before any stream capture. Calls share the array: calls
+ * whose work overlaps on the GPU race on it. Runs the stages one after another on the stream (no second stream),
+ * waits for them, and returns device-detected errors (FMM_EINVAL for a point outside the square) directly. */
+fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, fmm_precision mode, const double *domain,
+                                int64_t n, const double *x, const double *y, const double *gamma, double *u,
+                                double *v, void *cuda_stream);
+
 /* Human-readable text of a status, and the last error message recorded on the handle. */
 const char *fmm_status_string(fmm_status s);
 const char *fmm_last_error(fmm_handle h);

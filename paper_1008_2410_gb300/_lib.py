@@ -52,6 +52,7 @@ SIGNATURES = {
     "fmm_get_params": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I),
                             ctypes.POINTER(_I)]),
     "fmm_probe_peaks": (_I, [ctypes.POINTER(_D), _I]),
+    "fmm_velocity_noalloc": (_I, [_I, _I, _D, _I, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "fmm_status_string": (ctypes.c_char_p, [_I]),
     "fmm_last_error": (ctypes.c_char_p, [_P]),
 }

@@ -200,15 +200,15 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     p2p_avg = statistics.mean(p2p_ms) if p2p_ms else None
     achieved = P2P_FLOPS_PER_PAIR * pairs / (p2p_avg / 1e3) / 1e12 if p2p_avg else None
     traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "p2p_traffic.json")
-    if os.path.exists(tr_path):
+    tr_path = os.path.join(ROOT, "profiles", f"k_p2p32_{args.workload}.txt")
+    if args.precision == "mixed" and os.path.exists(tr_path):
         try:
             import hashlib
 
-            rec = json.load(open(tr_path))
+            rec = dict(line.split(": ", 1) for line in open(tr_path).read().splitlines() if ": " in line)
             src = open(os.path.join(ROOT, "paper_1008_2410_gb300", "csrc", "p2p.cu"), "rb").read()
-            if rec.get("p2p_cu_sha1") == hashlib.sha1(src).hexdigest() and rec.get("workload") == args.workload:
-                traffic = rec.get("dram_bytes_per_launch")
+            if rec.get("p2p_cu_sha1", "").strip() == hashlib.sha1(src).hexdigest():
+                traffic = float(rec["dram_bytes_per_launch"])
         except Exception:
             traffic = None
     out["roofline"] = {"bound": "alu", "kernel": "k_p2p32 (near field, stage 9)" if args.precision == "mixed"

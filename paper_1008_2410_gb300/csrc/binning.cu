@@ -131,28 +131,50 @@ __device__ __forceinline__ bool not_finite(double v)
     return ((__double_as_longlong(v) >> 52) & 0x7ff) == 0x7ff;
 }
 
-// Leaf column of one coordinate by the floor rule, in IEEE double: t = (c - c0) * scale; clamped to
-// [0, nside - 1]. Returns t through *tout. *below is set when c < c0 (sign of the exact difference).
-__device__ __forceinline__ int leaf_col(double c, double c0, double scale, int nside, double *tout, bool *below)
+// Leaf-relative position from the bit pattern of t = (c - c0) * scale (exact IEEE double, t >= 0 for points in
+// the square): returns floor(t) and F = (t - floor(t) - 1/2) * 2^52 as a signed integer, using integer
+// operations only. Callers clamp the index (t >= 2^31, not a valid point, returns 2^30).
+__device__ __forceinline__ int leaf_frac(double t, long long *F)
 {
-    double dd = __dsub_rn(c, c0);
-    double t = __dmul_rn(dd, scale);
-    *tout = t;
-    *below = __double_as_longlong(dd) < 0;  // sign bit: c < c0 (c - c0 == 0 gives +0)
-    if (*below)
+    const unsigned long long T = (unsigned long long)__double_as_longlong(t);
+    const int be = (int)((T >> 52) & 0x7ff);
+    if (be == 0 || (T >> 63)) {  // zero, subnormal or negative: fraction 0
+        *F = -(1ll << 51);
         return 0;
-    if (t >= (double)nside)
-        return nside - 1;
-    return __double2int_rz(t);  // t >= 0: truncation is floor
+    }
+    const int e = be - 1023;
+    const unsigned long long m = (T & 0xfffffffffffffull) | (1ull << 52);
+    if (e < 0) {  // t in (0, 1): t 2^52 = m 2^e
+        *F = (long long)(e > -53 ? (m >> (-e)) : 0ull) - (1ll << 51);
+        return 0;
+    }
+    if (e > 30) {  // far outside any valid square: the caller clamps it to the last leaf
+        *F = 0;
+        return 1 << 30;
+    }
+    const int sh = 52 - e;
+    *F = (long long)((m & ((1ull << sh) - 1)) << e) - (1ll << 51);
+    return (int)(m >> sh);
 }
 
-// Precision form: zeta = t - (i + 1/2) is exact in double; s * zeta is split as hi + lo floats (about 48 bits).
-__device__ __forceinline__ void split_rel(double t, int i, double s, float *hi, float *lo)
+// s * F * 2^-52 as hi + lo floats (about 46 bits): F = A' 2^29 + B' with A' exact in float.
+__device__ __forceinline__ void frac_to_split(long long F, float s, float *hi, float *lo)
 {
-    double z = __dmul_rn(__dsub_rn(t, (double)i + 0.5), s);
-    float h = __double2float_rn(z);
+    const float A = __int2float_rn((int)(F >> 29)) * 0x1p-23f;
+    const float B = __uint2float_rn((unsigned)(F & 0x1fffffffll)) * 0x1p-52f;
+    const float ph = A * s;
+    float pl = fmaf(A, s, -ph);
+    pl = fmaf(B, s, pl);
+    const float h = ph + pl;
     *hi = h;
-    *lo = __double2float_rn(__dsub_rn(z, (double)h));
+    *lo = pl - (h - ph);
+}
+
+// IEEE order of doubles as signed integers (for the upper-edge test without the FP64 pipe).
+__device__ __forceinline__ long long ordered(double v)
+{
+    long long b = __double_as_longlong(v);
+    return b < 0 ? (long long)(0x8000000000000000ull - (unsigned long long)b) : b;
 }
 
 __global__ void k_keys(Work w, const double *__restrict__ x, const double *__restrict__ y,
@@ -163,27 +185,39 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
         return;
     int k = w.nsys == 1 ? 0 : find_sys_by_particle(w.sys, w.nsys, i);
     const SysDev &d = w.sys[k];
-    double xi = x[i], yi = y[i];
-    int L = d.depth, nside = 1 << L;
-    double tx, ty;
-    bool bx, by;
-    int ix = leaf_col(xi, d.x0, d.scale, nside, &tx, &bx);
-    int iy = leaf_col(yi, d.y0, d.scale, nside, &ty, &by);
+    const double xi = x[i], yi = y[i];
+    const int L = d.depth, nside = 1 << L;
+    // the only FP64 operations: the two roundings of the leaf rule, t = (c - c0) * (2^L / S)
+    const double dx = __dsub_rn(xi, d.x0), dy = __dsub_rn(yi, d.y0);
+    const double tx = __dmul_rn(dx, d.scale), ty = __dmul_rn(dy, d.scale);
+    long long Fx, Fy;
+    int ix = leaf_frac(tx, &Fx), iy = leaf_frac(ty, &Fy);
+    if (ix > nside - 1) {  // t >= 2^L: a point on the square's upper edge goes to the last leaf (zeta = 1/2)
+        Fx += 1ll << 52;
+        ix = nside - 1;
+    }
+    if (iy > nside - 1) {
+        Fy += 1ll << 52;
+        iy = nside - 1;
+    }
     bool bad = not_finite(xi) || not_finite(yi);
-    if (d.explicit_domain)
-        bad = bad || bx || by || xi > d.xe || yi > d.ye;
+    if (d.explicit_domain)  // outside: c < c0 (sign of c - c0) or c > c0 + S
+        bad = bad || __double_as_longlong(dx) < 0 || __double_as_longlong(dy) < 0 || ordered(xi) > ordered(d.xe) ||
+              ordered(yi) > ordered(d.ye);
     if (bad) {
         atomicOr(w.status, FMM_DEV_OUTSIDE);
-        ix = bad && not_finite(xi) ? 0 : ix;
-        iy = bad && not_finite(yi) ? 0 : iy;
+        if (not_finite(xi))
+            ix = 0;
+        if (not_finite(yi))
+            iy = 0;
     }
-    int kk = (int)(d.leaf0 + (int64_t)iy * nside + ix);
+    const int kk = (int)(d.leaf0 + (int64_t)iy * nside + ix);
     w.key[i] = kk;
     atomicAdd(&w.cnt[kk], 1);
     if (w.mixed) {
         float hx, lx, hy, ly;
-        split_rel(tx, ix, (double)d.s_unit, &hx, &lx);
-        split_rel(ty, iy, (double)d.s_unit, &hy, &ly);
+        frac_to_split(Fx, d.s_unit, &hx, &lx);
+        frac_to_split(Fy, d.s_unit, &hy, &ly);
         w.pos4u[i] = make_float4(hx, hy, lx, ly);
         w.g32u[i] = __double2float_rn(g[i]);
     }
@@ -369,97 +403,66 @@ __global__ void k_scatter(int n, const int *__restrict__ key, const int *__restr
     tmp[pos] = i;
 }
 
-// One block per leaf: ranks the leaf's caller indices (all distinct) so the leaf keeps the caller's order.
+int launch_scatter_sort(const Work &w, cudaStream_t s)
+{
+    k_scatter<<<(w.n + 255) / 256, 256, 0, s>>>(w.n, w.key, w.start, w.cnt, w.tmp);
+    return 1;
+}
+
+// One block per leaf: ranks the leaf's caller indices (all distinct) so that the leaf keeps the caller's order,
+// then writes the leaf-ordered copies at the ranked positions: FP64 form (x, y, gamma [, gu, gv]); precision
+// form the duplicated split records eh = (xh, xh, yh, yh), el = (xl, xl, yl, yl), eg = (g, g, -g, -g).
 #define SORT_TILE 2048
-__global__ void k_leaf_sort(int nleaf, const int *__restrict__ start, const int *__restrict__ tmp, int *perm,
-                            int *sleaf)
+__global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restrict__ x, const double *__restrict__ y,
+                                                   const double *__restrict__ g, const double *__restrict__ gu,
+                                                   const double *__restrict__ gv, int mixed)
 {
     __shared__ int tile[SORT_TILE];
-    int leaf = blockIdx.x;
-    if (leaf >= nleaf)
-        return;
-    int s0 = start[leaf], c = start[leaf + 1] - s0;
+    const int leaf = blockIdx.x;
+    const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
     if (c <= 0)
         return;
-    if (c == 1) {
-        if (threadIdx.x == 0) {
-            perm[s0] = tmp[s0];
-            sleaf[s0] = leaf;
-        }
-        return;
-    }
     for (int e0 = 0; e0 < c; e0 += blockDim.x) {
-        int e = e0 + threadIdx.x;
-        int v = e < c ? tmp[s0 + e] : 0;
+        const int e = e0 + threadIdx.x;
+        const int v = e < c ? w.tmp[s0 + e] : 0;
         int rank = 0;
         for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
-            int m = min(SORT_TILE, c - f0);
+            const int m = min(SORT_TILE, c - f0);
             __syncthreads();
             for (int j = threadIdx.x; j < m; j += blockDim.x)
-                tile[j] = tmp[s0 + f0 + j];
+                tile[j] = w.tmp[s0 + f0 + j];
             __syncthreads();
             if (e < c)
                 for (int j = 0; j < m; ++j)
                     rank += tile[j] < v;
         }
         if (e < c) {
-            perm[s0 + rank] = v;
-            sleaf[s0 + e] = leaf;
+            const int pos = s0 + rank;
+            w.perm[pos] = v;
+            w.sleaf[pos] = leaf;
+            if (mixed) {
+                const float4 p = w.pos4u[v];
+                const float gg = w.g32u[v];
+                w.eh[pos] = make_float4(p.x, p.x, p.y, p.y);
+                w.el[pos] = make_float4(p.z, p.z, p.w, p.w);
+                w.eg[pos] = make_float4(gg, gg, -gg, -gg);
+            } else {
+                w.sx[pos] = x[v];
+                w.sy[pos] = y[v];
+                w.sg[pos] = g[v];
+                if (gu) {
+                    w.sgu[pos] = gu[v];
+                    w.sgv[pos] = gv[v];
+                }
+            }
         }
     }
-}
-
-int launch_scatter_sort(const Work &w, cudaStream_t s)
-{
-    k_scatter<<<(w.n + 255) / 256, 256, 0, s>>>(w.n, w.key, w.start, w.cnt, w.tmp);
-    k_leaf_sort<<<w.nleaf, 128, 0, s>>>(w.nleaf, w.start, w.tmp, w.perm, w.sleaf);
-    return 2;
-}
-
-// ------------------------------------------------------------------ gather into leaf order
-
-__global__ void k_gather64(int n, const int *__restrict__ perm, const double *__restrict__ x,
-                           const double *__restrict__ y, const double *__restrict__ g, double *sx, double *sy,
-                           double *sg, const double *__restrict__ gu, const double *__restrict__ gv, double *sgu,
-                           double *sgv)
-{
-    int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= n)
-        return;
-    int i = perm[pos];
-    sx[pos] = x[i];
-    sy[pos] = y[i];
-    sg[pos] = g[i];
-    if (gu) {
-        sgu[pos] = gu[i];
-        sgv[pos] = gv[i];
-    }
-}
-
-// Precision form: move the split coordinates made by k_keys into leaf order, each value duplicated.
-__global__ void k_gather32(int n, const int *__restrict__ perm, const float4 *__restrict__ pos4u,
-                           const float *__restrict__ g32u, float4 *eh, float4 *el, float4 *eg)
-{
-    int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= n)
-        return;
-    int i = perm[pos];
-    float4 p = pos4u[i];
-    float g = g32u[i];
-    eh[pos] = make_float4(p.x, p.x, p.y, p.y);
-    el[pos] = make_float4(p.z, p.z, p.w, p.w);
-    eg[pos] = make_float4(g, g, -g, -g);
 }
 
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
                   const double *gv, cudaStream_t s)
 {
-    int nb = (w.n + 255) / 256;
-    if (w.mixed && !gu) {
-        k_gather32<<<nb, 256, 0, s>>>(w.n, w.perm, w.pos4u, w.g32u, w.eh, w.el, w.eg);
-        return 1;
-    }
-    k_gather64<<<nb, 256, 0, s>>>(w.n, w.perm, x, y, g, w.sx, w.sy, w.sg, gu, gv, w.sgu, w.sgv);
+    k_leaf_order<<<w.nleaf, 64, 0, s>>>(w, x, y, g, gu, gv, (w.mixed && !gu) ? 1 : 0);
     return 1;
 }
 

@@ -213,7 +213,7 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
     }
     const int kk = (int)(d.leaf0 + (int64_t)iy * nside + ix);
     w.key[i] = kk;
-    atomicAdd(&w.cnt[kk], 1);
+    w.slot[i] = atomicAdd(&w.cnt[kk], 1);  // arrival slot inside the leaf (the in-leaf order is fixed later)
     if (w.mixed) {
         float hx, lx, hy, ly;
         frac_to_split(Fx, d.s_unit, &hx, &lx);
@@ -393,26 +393,25 @@ int launch_scan(const Work &w, cudaStream_t s)
 
 // ------------------------------------------------------------------ counting-sort scatter and in-leaf order
 
-__global__ void k_scatter(int n, const int *__restrict__ key, const int *__restrict__ start, int *cnt, int *tmp)
+__global__ void k_scatter(int n, const int *__restrict__ key, const int *__restrict__ slot,
+                          const int *__restrict__ start, int *tmp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    int k = key[i];
-    int pos = start[k] + atomicSub(&cnt[k], 1) - 1;  // cnt returns to 0 for the next evaluation
-    tmp[pos] = i;
+    tmp[start[key[i]] + slot[i]] = i;
 }
 
 int launch_scatter_sort(const Work &w, cudaStream_t s)
 {
-    k_scatter<<<(w.n + 255) / 256, 256, 0, s>>>(w.n, w.key, w.start, w.cnt, w.tmp);
+    k_scatter<<<(w.n + 255) / 256, 256, 0, s>>>(w.n, w.key, w.slot, w.start, w.tmp);
     return 1;
 }
 
 // One block per leaf: ranks the leaf's caller indices (all distinct) so that the leaf keeps the caller's order,
 // then writes the leaf-ordered copies at the ranked positions: FP64 form (x, y, gamma [, gu, gv]); precision
 // form the duplicated split records eh = (xh, xh, yh, yh), el = (xl, xl, yl, yl), eg = (g, g, -g, -g).
-#define SORT_TILE 2048
+#define SORT_TILE 256
 __global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restrict__ x, const double *__restrict__ y,
                                                    const double *__restrict__ g, const double *__restrict__ gu,
                                                    const double *__restrict__ gv, int mixed)

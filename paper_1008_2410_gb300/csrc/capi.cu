@@ -167,6 +167,8 @@ static fmm_status poll_status(fmm_handle h, bool block)
 
 static fmm_status ensure_tables(fmm_handle h)
 {
+    if (upload_m2l_constants(h->stream) != 0)
+        return set_err(h, FMM_ECUDA, "constant-table upload failed");
     if (h->tab_p == h->p)
         return FMM_OK;
     const int P = FMM_PMAX, RS = 2 * FMM_PMAX + 2;
@@ -325,7 +327,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = 0;                                           // 23 (unused)
     sizes[i++] = mixed ? np * 16 : 0;                         // 24 pos4u
     sizes[i++] = mixed ? np * 4 : 0;                          // 25 g32u
-    sizes[i++] = 0;                                           // 26 (unused)
+    sizes[i++] = np * 4;                                      // 26 slot
     sizes[i++] = 0;                                           // 27 (unused)
     sizes[i++] = adjoint ? np * 24 : 0;                       // 28 adj_far
     int count = i;
@@ -388,6 +390,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.sgv = sizes[20] ? (double *)(b + lay.off[20]) : nullptr;
     w.AM64 = sizes[21] ? (double2 *)(b + lay.off[21]) : nullptr;
     w.AL64 = sizes[22] ? (double2 *)(b + lay.off[22]) : nullptr;
+    w.slot = (int *)(b + lay.off[26]);
     w.pos4u = sizes[24] ? (float4 *)(b + lay.off[24]) : nullptr;
     w.g32u = sizes[25] ? (float *)(b + lay.off[25]) : nullptr;
     char *hd = (char *)h->hdr;

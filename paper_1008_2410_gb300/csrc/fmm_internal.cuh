@@ -83,7 +83,7 @@ struct Work {
     int nsys;
     int maxdepth;
     // arrays
-    int *key, *cnt, *start, *scan_tmp, *tmp, *perm, *sleaf;
+    int *key, *slot, *cnt, *start, *scan_tmp, *tmp, *perm, *sleaf;
     double *sx, *sy, *sg;
     float4 *eh, *el, *eg;     // precision form, leaf order: (xh, xh, yh, yh), (xl, xl, yl, yl), (g, g, -g, -g)
     float4 *pos4u;            // precision form, caller order (made while binning): (xh, yh, xl, yl)
@@ -157,5 +157,6 @@ int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cu
 int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);
 
 void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom);
+int upload_m2l_constants(cudaStream_t s);  // once per device, before any stream capture; 0 on success
 
 }  // namespace fmm

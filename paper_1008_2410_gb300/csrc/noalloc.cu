@@ -110,6 +110,7 @@ size_t carve_work(unsigned char *b, Work &w, int64_t n, int depth, int p, bool m
         return q;
     };
     w.key = (int *)take(np * 4);
+    w.slot = (int *)take(np * 4);
     w.cnt = (int *)take((size_t)nleaf * 4 + 16);
     w.start = (int *)take((size_t)(nleaf + 1) * 4 + 16);
     w.scan_tmp = (int *)take((size_t)((nleaf + 1023) / 1024 + 2) * 4);
@@ -191,6 +192,8 @@ extern "C" fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, 
     Tables t{};
     carve_tables(base, t);
     if (fresh_tables && upload_tables(t, p, s) != FMM_OK)
+        return FMM_ECUDA;
+    if (upload_m2l_constants(s) != 0)  // constant memory of the module, once per device (no allocation)
         return FMM_ECUDA;
 
     unsigned char *h = base + tab;

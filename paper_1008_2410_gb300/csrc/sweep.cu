@@ -310,11 +310,13 @@ __device__ void m2l_box(const Work &w, const typename store_of<R>::T *__restrict
 }
 
 template <int PM>
-__global__ void __launch_bounds__(128) k_m2l(Work w, Tables t, int adj)
+__global__ void __launch_bounds__(128) k_m2l(Work w, Tables t, int adj, int64_t gw0, int64_t gw1)
 {
     __shared__ __align__(16) double2 alpha_sh[4][64];
     __shared__ int2 list_sh[4][40];
-    int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t gw = gw0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (gw >= gw1)
+        return;
     int l = 2;
     while (l < w.lv.maxdepth && gw >= w.lv.m2l_item0[l + 1])
         ++l;
@@ -337,26 +339,199 @@ __global__ void __launch_bounds__(128) k_m2l(Work w, Tables t, int adj)
     }
 }
 
+// Precision form, FP32 levels: one warp per target box with lane q = source q of its interaction list (at most
+// 27: the children of the parent's 3 x 3 neighbours that are not adjacent, taken from a per-parity offset table).
+// Lane q forms alpha_m = (-1)^(m+1) rho^m a~_m, contracts it with the binomials C(m + l, m) held in constant
+// memory (compile-time indices: the FMAs read their constant operand directly), scales by rho^(l+1), and the
+// 27 partial locals are summed per coefficient through shared memory. P >= p terms are evaluated (zero-padded).
+__constant__ float c_binom[FMM_PMAX][FMM_PMAX];
+__constant__ int2 c_m2l_off[4][27];
+
+static int g_const_ready[64];
+
+static bool m2l_constants_ready()
+{
+    int dev = 0;
+    return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && g_const_ready[dev];
+}
+
+// Uploads the constant tables of k_m2l_src to the current device once (synchronises the stream: call it before
+// any stream capture).
+int upload_m2l_constants(cudaStream_t s)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return -1;
+    if (g_const_ready[dev])
+        return 0;
+    static float bin[FMM_PMAX][FMM_PMAX];
+    static int2 off[4][27];
+    for (int m = 0; m < FMM_PMAX; ++m)
+        for (int l = 0; l < FMM_PMAX; ++l) {
+            double c = 1.0;
+            for (int i = 1; i <= m; ++i)
+                c = c * (double)(l + i) / (double)i;  // C(m + l, m)
+            bin[m][l] = (float)c;
+        }
+    for (int cls = 0; cls < 4; ++cls) {
+        int cx = cls & 1, cy = cls >> 1, q = 0;
+        for (int ry = -2 - cy; ry <= 3 - cy; ++ry)
+            for (int rx = -2 - cx; rx <= 3 - cx; ++rx)
+                if (rx < -1 || rx > 1 || ry < -1 || ry > 1)
+                    off[cls][q++] = make_int2(rx, ry);
+    }
+    if (cudaMemcpyToSymbolAsync(c_binom, bin, sizeof bin, 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_m2l_off, off, sizeof off, 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return -1;
+    g_const_ready[dev] = 1;
+    return 0;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_m2l_src(Work w, int64_t gw0, int64_t gw1)
+{
+    __shared__ float2 part[4][27][P + 1];
+    const int64_t gw = gw0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (gw >= gw1)
+        return;
+    int l = 2;
+    while (l < w.lv.maxdepth && gw >= w.lv.m2l_item0[l + 1])
+        ++l;
+    const int64_t g = gw - w.lv.m2l_item0[l];
+    const int b = (int)(g & (((int64_t)1 << (2 * l)) - 1));
+    const int sidx = (int)(g >> (2 * l));
+    const SysDev &d = w.sys[sys_at_level(w, l, sidx)];
+    if (w.bcount[d.box0[l] + b] == 0)
+        return;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, p = w.p;
+    const int ns = 1 << l, bx = b & (ns - 1), by = b >> l;
+    const int cls = (by & 1) * 2 + (bx & 1);
+    bool valid = false;
+    int64_t sb = 0;
+    float rr = 0.f, ri = 0.f;
+    if (lane < 27) {
+        const int2 o = c_m2l_off[cls][lane];
+        const int jx = bx + o.x, jy = by + o.y;
+        if (jx >= 0 && jy >= 0 && jx < ns && jy < ns) {
+            sb = d.box0[l] + (int64_t)jy * ns + jx;
+            valid = w.bcount[sb] != 0;
+            const float den = (float)(o.x * o.x + o.y * o.y);
+            rr = (float)o.x / den;  // rho = 1 / (dx + i dy)
+            ri = -(float)o.y / den;
+        }
+    }
+    if (valid) {
+        float ar[P], ai[P];
+        const float2 *src = w.M32 + sb * p;
+        float pr = 1.f, pi = 0.f;
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            float2 a = m < p ? src[m] : make_float2(0.f, 0.f);
+            const float sg = (m & 1) ? 1.f : -1.f;  // (-1)^(m+1)
+            ar[m] = sg * (pr * a.x - pi * a.y);
+            ai[m] = sg * (pr * a.y + pi * a.x);
+            const float t = pr * rr - pi * ri;
+            pi = pr * ri + pi * rr;
+            pr = t;
+        }
+        float qr = rr, qi = ri;  // rho^(l+1)
+#pragma unroll
+        for (int ll = 0; ll < P; ++ll) {
+            float br = 0.f, bi = 0.f;
+#pragma unroll
+            for (int m = 0; m < P; ++m) {
+                br = fmaf(c_binom[m][ll], ar[m], br);
+                bi = fmaf(c_binom[m][ll], ai[m], bi);
+            }
+            part[wi][lane][ll] = make_float2(qr * br - qi * bi, qr * bi + qi * br);
+            const float t = qr * rr - qi * ri;
+            qi = qr * ri + qi * rr;
+            qr = t;
+        }
+    } else if (lane < 27) {
+#pragma unroll
+        for (int ll = 0; ll < P; ++ll)
+            part[wi][lane][ll] = make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    if (lane < p) {
+        float sr = 0.f, si = 0.f;
+#pragma unroll 9
+        for (int q = 0; q < 27; ++q) {
+            const float2 v = part[wi][q][lane];
+            sr += v.x;
+            si += v.y;
+        }
+        w.L32[(d.box0[l] + b) * (int64_t)p + lane] = make_float2(sr, si);
+    }
+}
+
+template <int P>
+static void m2l_src_launch(const Work &w, int64_t a, int64_t b, cudaStream_t s)
+{
+    if (b <= a)
+        return;
+    unsigned blocks = (unsigned)(((b - a) * 32 + 127) / 128);
+    k_m2l_src<P><<<blocks, 128, 0, s>>>(w, a, b);
+}
+
+template <int PM>
+static void m2l_box_launch(const Work &w, const Tables &t, int adj, int64_t a, int64_t b, cudaStream_t s)
+{
+    if (b <= a)
+        return;
+    unsigned blocks = (unsigned)(((b - a) * 32 + 127) / 128);
+    k_m2l<PM><<<blocks, 128, 0, s>>>(w, t, adj, a, b);
+}
+
 int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio)
 {
     (void)prio;
-    int64_t warps = w.lv.m2l_item0[w.lv.maxdepth + 1];
-    if (w.lv.maxdepth < 2 || warps == 0)
+    const int64_t total = w.lv.m2l_item0[w.lv.maxdepth + 1];
+    if (w.lv.maxdepth < 2 || total == 0)
         return 0;
-    unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
-    if (w.p <= 8)
-        k_m2l<8><<<blocks, 128, 0, s>>>(w, t, adj);
-    else if (w.p <= 12)
-        k_m2l<12><<<blocks, 128, 0, s>>>(w, t, adj);
-    else if (w.p <= 16)
-        k_m2l<16><<<blocks, 128, 0, s>>>(w, t, adj);
-    else if (w.p <= 20)
-        k_m2l<20><<<blocks, 128, 0, s>>>(w, t, adj);
-    else if (w.p <= 24)
-        k_m2l<24><<<blocks, 128, 0, s>>>(w, t, adj);
-    else
-        k_m2l<32><<<blocks, 128, 0, s>>>(w, t, adj);
-    return 1;
+    // FP64 levels (all levels of the plain form; levels <= coarse_level of the precision form): lane = coefficient
+    int l32 = w.mixed ? max(2, w.coarse_level + 1) : w.lv.maxdepth + 1;  // first FP32 level
+    if (!m2l_constants_ready())
+        l32 = w.lv.maxdepth + 1;  // constants not uploaded on this device: the lane-per-coefficient kernel for all
+    const int64_t split = l32 > w.lv.maxdepth ? total : w.lv.m2l_item0[l32];
+    int n = 0;
+    if (split > 0) {
+        if (w.p <= 8)
+            m2l_box_launch<8>(w, t, adj, 0, split, s);
+        else if (w.p <= 12)
+            m2l_box_launch<12>(w, t, adj, 0, split, s);
+        else if (w.p <= 16)
+            m2l_box_launch<16>(w, t, adj, 0, split, s);
+        else if (w.p <= 20)
+            m2l_box_launch<20>(w, t, adj, 0, split, s);
+        else if (w.p <= 24)
+            m2l_box_launch<24>(w, t, adj, 0, split, s);
+        else
+            m2l_box_launch<32>(w, t, adj, 0, split, s);
+        ++n;
+    }
+    if (split < total) {
+        if (w.p <= 8)
+            m2l_src_launch<8>(w, split, total, s);
+        else if (w.p <= 12)
+            m2l_src_launch<12>(w, split, total, s);
+        else if (w.p <= 14)
+            m2l_src_launch<14>(w, split, total, s);
+        else if (w.p <= 16)
+            m2l_src_launch<16>(w, split, total, s);
+        else if (w.p <= 17)
+            m2l_src_launch<17>(w, split, total, s);
+        else if (w.p <= 20)
+            m2l_src_launch<20>(w, split, total, s);
+        else if (w.p <= 24)
+            m2l_src_launch<24>(w, split, total, s);
+        else
+            m2l_src_launch<32>(w, split, total, s);
+        ++n;
+    }
+    return n;
 }
 
 // ------------------------------------------------------------------ stage 7: L2L (thread per child coefficient)

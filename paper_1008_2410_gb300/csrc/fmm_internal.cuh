@@ -65,7 +65,7 @@ struct LevelInfo {
 
 // Read-only tables that depend on p only.
 struct Tables {
-    double2 *m2m64, *l2l64;   // [4][PMAX][PMAX]  (child position c = cy * 2 + cx; row n / k, column m / l)
+    double2 *m2m64, *l2l64;   // [4][PMAX][PMAX]  (child position c = cy * 2 + cx; [c][input][output])
     float2 *m2m32, *l2l32;
     double2 *rho64;           // [FMM_NOFF][2 PMAX + 2]  (1/delta)^k
     float2 *rho32;

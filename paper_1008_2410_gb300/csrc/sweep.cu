@@ -158,60 +158,73 @@ int launch_p2m(const Work &w, const Tables &t, int adj, cudaStream_t s)
     return 1;
 }
 
-// ------------------------------------------------------------------ stage 5: M2M (thread per parent coefficient)
+// ------------------------------------------------------------------ stage 5: M2M (warp per parent box)
 
-template <typename RA, typename SC, typename SP>
-__global__ void k_m2m(Work w, const double2 *__restrict__ tab64, const float2 *__restrict__ tab32, int l,
-                      const SC *__restrict__ child, SP *parent)
+template <typename RA>
+__device__ __forceinline__ cx<RA> ld_tab(const double2 *__restrict__ t64, const float2 *__restrict__ t32, int i)
 {
-    int p = w.p;
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nb = (int64_t)1 << (2 * l);
-    int64_t total = (int64_t)w.lv.nsys_at[l + 1] * nb * p;
-    if (g >= total)
-        return;
-    int n = (int)(g % p);
-    int64_t rest = g / p;
-    int b = (int)(rest & (nb - 1));
-    int sidx = (int)(rest >> (2 * l));
-    const SysDev &d = w.sys[sys_at_level(w, l + 1, sidx)];
-    int ns = 1 << l, bx = b & (ns - 1), by = b >> l;
-    int64_t pbox = d.box0[l] + b;
-    cx<RA> acc = {(RA)0, (RA)0};
-    int count = 0;
-    for (int c = 0; c < 4; ++c) {
-        int cx_ = c & 1, cy_ = c >> 1;
-        int64_t cbox = d.box0[l + 1] + (int64_t)(2 * by + cy_) * (2 * ns) + (2 * bx + cx_);
-        int cc = w.bcount[cbox];
-        count += cc;
-        if (cc == 0)
-            continue;
-        for (int m = 0; m <= n; ++m) {
-            cx<RA> T;
-            if constexpr (std::is_same<RA, double>::value) {
-                double2 t = tab64[(c * FMM_PMAX + n) * FMM_PMAX + m];
-                T = {(RA)t.x, (RA)t.y};
-            } else {
-                float2 t = tab32[(c * FMM_PMAX + n) * FMM_PMAX + m];
-                T = {(RA)t.x, (RA)t.y};
-            }
-            acc = cadd(acc, cmul(T, ldc<RA>(child, cbox * p + m)));
-        }
+    if constexpr (std::is_same<RA, double>::value) {
+        double2 t = t64[i];
+        return {(RA)t.x, (RA)t.y};
+    } else {
+        float2 t = t32[i];
+        return {(RA)t.x, (RA)t.y};
     }
-    if (n == 0)
+}
+
+// One warp per parent box, lane n = coefficient. The four children's expansions are staged in shared memory
+// with coalesced loads; the table is stored [child][m][n] so that lanes read consecutive entries.
+template <typename RA, typename SC, typename SP>
+__global__ void __launch_bounds__(128) k_m2m(Work w, const double2 *__restrict__ tab64,
+                                             const float2 *__restrict__ tab32, int l, const SC *__restrict__ child,
+                                             SP *parent)
+{
+    __shared__ cx<RA> sh[4][4][FMM_PMAX];
+    const int p = w.p, lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int64_t nb = (int64_t)1 << (2 * l);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= (int64_t)w.lv.nsys_at[l + 1] * nb)
+        return;
+    const int b = (int)(gw & (nb - 1));
+    const int sidx = (int)(gw >> (2 * l));
+    const SysDev &d = w.sys[sys_at_level(w, l + 1, sidx)];
+    const int ns = 1 << l, bx = b & (ns - 1), by = b >> l;
+    const int64_t pbox = d.box0[l] + b;
+    int cnt[4], count = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int64_t cbox = d.box0[l + 1] + (int64_t)(2 * by + (c >> 1)) * (2 * ns) + (2 * bx + (c & 1));
+        cnt[c] = w.bcount[cbox];
+        count += cnt[c];
+        if (lane < p)
+            sh[wi][c][lane] = cnt[c] ? ldc<RA>(child, cbox * p + lane) : cx<RA>{(RA)0, (RA)0};
+    }
+    if (lane == 0)
         w.bcount[pbox] = count;
-    if (count)
-        stc(parent, pbox * p + n, acc);
+    if (count == 0)
+        return;
+    __syncwarp();
+    if (lane >= p)
+        return;
+    cx<RA> acc = {(RA)0, (RA)0};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (!cnt[c])
+            continue;
+        for (int m = 0; m <= lane; ++m)
+            acc = cadd(acc, cmul(ld_tab<RA>(tab64, tab32, (c * FMM_PMAX + m) * FMM_PMAX + lane), sh[wi][c][m]));
+    }
+    stc(parent, pbox * p + lane, acc);
 }
 
 int launch_m2m(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, int prio)
 {
     (void)prio;
-    int64_t total = (int64_t)w.lv.nsys_at[l + 1] * ((int64_t)1 << (2 * l)) * w.p;
-    if (total == 0)
+    const int64_t warps = (int64_t)w.lv.nsys_at[l + 1] * ((int64_t)1 << (2 * l));
+    if (warps == 0)
         return 0;
-    int blocks = (int)((total + 127) / 128);
-    bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
+    const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
+    const bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
     double2 *M64 = adj ? w.AM64 : w.M64;
     if (pd && cd)
         k_m2m<double, double2, double2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, M64, M64);
@@ -534,59 +547,54 @@ int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio
     return n;
 }
 
-// ------------------------------------------------------------------ stage 7: L2L (thread per child coefficient)
+// ------------------------------------------------------------------ stage 7: L2L (block = the 4 children of a parent)
 
+// Four warps, one per child of one parent box at level l, lane k = coefficient; the parent's local expansion is
+// staged once in shared memory; the table is stored [child][j][k] so that lanes read consecutive entries.
 template <typename RA, typename SPa, typename SCh>
-__global__ void k_l2l(Work w, const double2 *__restrict__ tab64, const float2 *__restrict__ tab32, int l,
-                      const SPa *__restrict__ parent, SCh *child)
+__global__ void __launch_bounds__(128) k_l2l(Work w, const double2 *__restrict__ tab64,
+                                             const float2 *__restrict__ tab32, int l, const SPa *__restrict__ parent,
+                                             SCh *child)
 {
-    int p = w.p;
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nb = (int64_t)1 << (2 * (l + 1));
-    int64_t total = (int64_t)w.lv.nsys_at[l + 1] * nb * p;
-    if (g >= total)
+    __shared__ cx<RA> sh[FMM_PMAX];
+    const int p = w.p, lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const int64_t nb = (int64_t)1 << (2 * l);
+    const int64_t g = blockIdx.x;  // parent box over the systems that have level l + 1
+    if (g >= (int64_t)w.lv.nsys_at[l + 1] * nb)
         return;
-    int kk = (int)(g % p);
-    int64_t rest = g / p;
-    int b = (int)(rest & (nb - 1));
-    int sidx = (int)(rest >> (2 * (l + 1)));
+    const int b = (int)(g & (nb - 1));
+    const int sidx = (int)(g >> (2 * l));
     const SysDev &d = w.sys[sys_at_level(w, l + 1, sidx)];
-    int64_t cbox = d.box0[l + 1] + b;
-    if (w.bcount[cbox] == 0)
+    const int64_t pbox = d.box0[l] + b;
+    if (w.bcount[pbox] == 0)
+        return;  // block-uniform: no child has particles
+    if (threadIdx.x < p)
+        sh[threadIdx.x] = ldc<RA>(parent, pbox * p + threadIdx.x);
+    __syncthreads();
+    const int ns = 1 << l, bx = b & (ns - 1), by = b >> l;
+    const int64_t cbox = d.box0[l + 1] + (int64_t)(2 * by + (c >> 1)) * (2 * ns) + (2 * bx + (c & 1));
+    if (lane >= p || w.bcount[cbox] == 0)
         return;
-    int ns = 1 << (l + 1), bx = b & (ns - 1), by = b >> (l + 1);
-    int c = (by & 1) * 2 + (bx & 1);
-    int64_t pbox = d.box0[l] + (int64_t)(by >> 1) * (ns >> 1) + (bx >> 1);
-    cx<RA> acc = ldc<RA>(child, cbox * p + kk);
-    for (int j = kk; j < p; ++j) {
-        cx<RA> T;
-        if constexpr (std::is_same<RA, double>::value) {
-            double2 t = tab64[(c * FMM_PMAX + kk) * FMM_PMAX + j];
-            T = {(RA)t.x, (RA)t.y};
-        } else {
-            float2 t = tab32[(c * FMM_PMAX + kk) * FMM_PMAX + j];
-            T = {(RA)t.x, (RA)t.y};
-        }
-        acc = cadd(acc, cmul(T, ldc<RA>(parent, pbox * p + j)));
-    }
-    stc(child, cbox * p + kk, acc);
+    cx<RA> acc = ldc<RA>(child, cbox * p + lane);
+    for (int j = lane; j < p; ++j)
+        acc = cadd(acc, cmul(ld_tab<RA>(tab64, tab32, (c * FMM_PMAX + j) * FMM_PMAX + lane), sh[j]));
+    stc(child, cbox * p + lane, acc);
 }
 
 int launch_l2l(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, int prio)
 {
     (void)prio;
-    int64_t total = (int64_t)w.lv.nsys_at[l + 1] * ((int64_t)1 << (2 * (l + 1))) * w.p;
-    if (total == 0)
+    const int64_t blocks = (int64_t)w.lv.nsys_at[l + 1] * ((int64_t)1 << (2 * l));
+    if (blocks == 0)
         return 0;
-    int blocks = (int)((total + 127) / 128);
-    bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
+    const bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
     double2 *L64 = adj ? w.AL64 : w.L64;
     if (pd && cd)
-        k_l2l<double, double2, double2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, L64);
+        k_l2l<double, double2, double2><<<(unsigned)blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, L64);
     else if (pd)
-        k_l2l<double, double2, float2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, w.L32);
+        k_l2l<double, double2, float2><<<(unsigned)blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, w.L32);
     else
-        k_l2l<float, float2, float2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, w.L32, w.L32);
+        k_l2l<float, float2, float2><<<(unsigned)blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, w.L32, w.L32);
     return 1;
 }
 
@@ -751,9 +759,11 @@ static double binom_host(int n, int k)
     return c;
 }
 
-// m2m[c][n][m] = C(n, m) delta_c^(n-m) 2^-m, delta_c = ((cx - 1/2) + i (cy - 1/2)) / 2;
-// l2l[c][k][l] = C(l, k) delta_c^(l-k) 2^-(l+1), delta_c = (cx - 1/2) + i (cy - 1/2);
+// m2m[c][m][n] = C(n, m) delta_c^(n-m) 2^-m (m <= n), delta_c = ((cx - 1/2) + i (cy - 1/2)) / 2;
+// l2l[c][j][k] = C(j, k) delta_c^(j-k) 2^-(j+1) (j >= k), delta_c = (cx - 1/2) + i (cy - 1/2);
 // rho[o][k] = (1/delta_o)^k, delta_o = dx + i dy; binom[m][l] = C(m + l, m).
+// Both translation tables are stored with the output index last, so a warp whose lanes are outputs reads
+// consecutive entries.
 void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom)
 {
     (void)p;
@@ -772,20 +782,19 @@ void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *
             prl[k][0] = prl[k - 1][0] * ddx - prl[k - 1][1] * ddy;  // L2L delta
             prl[k][1] = prl[k - 1][0] * ddy + prl[k - 1][1] * ddx;
         }
-        for (int n = 0; n < P; ++n)
-            for (int m = 0; m < P; ++m) {
+        for (int n = 0; n < P; ++n)      // output coefficient
+            for (int m = 0; m < P; ++m) {  // input coefficient
                 double2 t = make_double2(0.0, 0.0), s = make_double2(0.0, 0.0);
                 if (m <= n) {
                     double f = binom_host(n, m) * ldexp(1.0, -m);
                     t = make_double2(f * pre[n - m][0], f * pre[n - m][1]);
                 }
-                m2m[(c * P + n) * P + m] = t;
-                // l2l: row k = n, column l = m (l >= k)
-                if (m >= n) {
+                m2m[(c * P + m) * P + n] = t;
+                if (m >= n) {  // l2l: output k = n, input j = m >= k
                     double f = binom_host(m, n) * ldexp(1.0, -(m + 1));
                     s = make_double2(f * prl[m - n][0], f * prl[m - n][1]);
                 }
-                l2l[(c * P + n) * P + m] = s;
+                l2l[(c * P + m) * P + n] = s;
             }
     }
     const int RS = 2 * FMM_PMAX + 2;

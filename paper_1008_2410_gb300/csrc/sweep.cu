@@ -174,7 +174,7 @@ __device__ __forceinline__ cx<RA> ld_tab(const double2 *__restrict__ t64, const 
 
 // One warp per parent box, lane n = coefficient. The four children's expansions are staged in shared memory
 // with coalesced loads; the table is stored [child][m][n] so that lanes read consecutive entries.
-template <typename RA, typename SC, typename SP>
+template <int PM, typename RA, typename SC, typename SP>
 __global__ void __launch_bounds__(128) k_m2m(Work w, const double2 *__restrict__ tab64,
                                              const float2 *__restrict__ tab32, int l, const SC *__restrict__ child,
                                              SP *parent)
@@ -206,15 +206,31 @@ __global__ void __launch_bounds__(128) k_m2m(Work w, const double2 *__restrict__
     __syncwarp();
     if (lane >= p)
         return;
+    // compile-time trip count (entries with m > n are zero in the table): every load issues at once
     cx<RA> acc = {(RA)0, (RA)0};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         if (!cnt[c])
             continue;
-        for (int m = 0; m <= lane; ++m)
-            acc = cadd(acc, cmul(ld_tab<RA>(tab64, tab32, (c * FMM_PMAX + m) * FMM_PMAX + lane), sh[wi][c][m]));
+#pragma unroll
+        for (int m = 0; m < PM; ++m)
+            if (m < p)
+                acc = cadd(acc, cmul(ld_tab<RA>(tab64, tab32, (c * FMM_PMAX + m) * FMM_PMAX + lane), sh[wi][c][m]));
     }
     stc(parent, pbox * p + lane, acc);
+}
+
+template <int PM>
+static void m2m_launch(const Work &w, const Tables &t, int l, int adj, unsigned blocks, cudaStream_t s)
+{
+    const bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
+    double2 *M64 = adj ? w.AM64 : w.M64;
+    if (pd && cd)
+        k_m2m<PM, double, double2, double2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, M64, M64);
+    else if (pd)
+        k_m2m<PM, double, float2, double2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, w.M32, M64);
+    else
+        k_m2m<PM, float, float2, float2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, w.M32, w.M32);
 }
 
 int launch_m2m(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, int prio)
@@ -224,14 +240,14 @@ int launch_m2m(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, i
     if (warps == 0)
         return 0;
     const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
-    const bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
-    double2 *M64 = adj ? w.AM64 : w.M64;
-    if (pd && cd)
-        k_m2m<double, double2, double2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, M64, M64);
-    else if (pd)
-        k_m2m<double, float2, double2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, w.M32, M64);
+    if (w.p <= 8)
+        m2m_launch<8>(w, t, l, adj, blocks, s);
+    else if (w.p <= 16)
+        m2m_launch<16>(w, t, l, adj, blocks, s);
+    else if (w.p <= 24)
+        m2m_launch<24>(w, t, l, adj, blocks, s);
     else
-        k_m2m<float, float2, float2><<<blocks, 128, 0, s>>>(w, t.m2m64, t.m2m32, l, w.M32, w.M32);
+        m2m_launch<32>(w, t, l, adj, blocks, s);
     return 1;
 }
 
@@ -551,7 +567,7 @@ int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio
 
 // Four warps, one per child of one parent box at level l, lane k = coefficient; the parent's local expansion is
 // staged once in shared memory; the table is stored [child][j][k] so that lanes read consecutive entries.
-template <typename RA, typename SPa, typename SCh>
+template <int PM, typename RA, typename SPa, typename SCh>
 __global__ void __launch_bounds__(128) k_l2l(Work w, const double2 *__restrict__ tab64,
                                              const float2 *__restrict__ tab32, int l, const SPa *__restrict__ parent,
                                              SCh *child)
@@ -576,9 +592,24 @@ __global__ void __launch_bounds__(128) k_l2l(Work w, const double2 *__restrict__
     if (lane >= p || w.bcount[cbox] == 0)
         return;
     cx<RA> acc = ldc<RA>(child, cbox * p + lane);
-    for (int j = lane; j < p; ++j)
-        acc = cadd(acc, cmul(ld_tab<RA>(tab64, tab32, (c * FMM_PMAX + j) * FMM_PMAX + lane), sh[j]));
+#pragma unroll
+    for (int j = 0; j < PM; ++j)  // entries with j < k are zero in the table
+        if (j < p)
+            acc = cadd(acc, cmul(ld_tab<RA>(tab64, tab32, (c * FMM_PMAX + j) * FMM_PMAX + lane), sh[j]));
     stc(child, cbox * p + lane, acc);
+}
+
+template <int PM>
+static void l2l_launch(const Work &w, const Tables &t, int l, int adj, unsigned blocks, cudaStream_t s)
+{
+    const bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
+    double2 *L64 = adj ? w.AL64 : w.L64;
+    if (pd && cd)
+        k_l2l<PM, double, double2, double2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, L64);
+    else if (pd)
+        k_l2l<PM, double, double2, float2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, w.L32);
+    else
+        k_l2l<PM, float, float2, float2><<<blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, w.L32, w.L32);
 }
 
 int launch_l2l(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, int prio)
@@ -587,14 +618,14 @@ int launch_l2l(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, i
     const int64_t blocks = (int64_t)w.lv.nsys_at[l + 1] * ((int64_t)1 << (2 * l));
     if (blocks == 0)
         return 0;
-    const bool pd = level_fp64(w, l), cd = level_fp64(w, l + 1);
-    double2 *L64 = adj ? w.AL64 : w.L64;
-    if (pd && cd)
-        k_l2l<double, double2, double2><<<(unsigned)blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, L64);
-    else if (pd)
-        k_l2l<double, double2, float2><<<(unsigned)blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, L64, w.L32);
+    if (w.p <= 8)
+        l2l_launch<8>(w, t, l, adj, (unsigned)blocks, s);
+    else if (w.p <= 16)
+        l2l_launch<16>(w, t, l, adj, (unsigned)blocks, s);
+    else if (w.p <= 24)
+        l2l_launch<24>(w, t, l, adj, (unsigned)blocks, s);
     else
-        k_l2l<float, float2, float2><<<(unsigned)blocks, 128, 0, s>>>(w, t.l2l64, t.l2l32, l, w.L32, w.L32);
+        l2l_launch<32>(w, t, l, adj, (unsigned)blocks, s);
     return 1;
 }
 
@@ -609,6 +640,23 @@ __device__ __forceinline__ cx<R> horner(const S *__restrict__ b, int64_t base, i
     return acc;
 }
 
+// Horner with a compile-time bound PM >= p: the coefficient loads are independent of the recurrence and all
+// issue before it starts.
+template <int PM, typename R, typename S>
+__device__ __forceinline__ cx<R> horner_u(const S *__restrict__ b, int64_t base, int p, cx<R> z)
+{
+    cx<R> c[PM];
+#pragma unroll
+    for (int l = 0; l < PM; ++l)
+        c[l] = l < p ? ldc<R>(b, base + l) : cx<R>{(R)0, (R)0};
+    cx<R> acc = c[PM - 1];
+#pragma unroll
+    for (int l = PM - 2; l >= 0; --l)
+        acc = cadd(cmul(acc, z), c[l]);
+    return acc;
+}
+
+template <int PM>
 __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict__ u, double *__restrict__ v)
 {
     int pos = blockIdx.x * blockDim.x + threadIdx.x;
@@ -626,7 +674,7 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
         if (far) {
             float4 hh = w.eh[pos], ll = w.el[pos];
             cx<float> z = {(hh.x + ll.x) * d.inv_s, (hh.z + ll.z) * d.inv_s};
-            cx<float> s = horner<float>(w.L32, base, w.p, z);
+            cx<float> s = horner_u<PM, float>(w.L32, base, w.p, z);
             float fs = (float)d.far_scale;
             fu = s.re * fs;
             fv = -s.im * fs;
@@ -669,7 +717,15 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
 
 int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s)
 {
-    k_combine<<<(w.n + 255) / 256, 256, 0, s>>>(w, use_near, use_far, u, v);
+    const unsigned nb = (unsigned)((w.n + 255) / 256);
+    if (w.p <= 8)
+        k_combine<8><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
+    else if (w.p <= 16)
+        k_combine<16><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
+    else if (w.p <= 24)
+        k_combine<24><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
+    else
+        k_combine<32><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
     return 1;
 }
 

@@ -192,6 +192,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                     "stage_ms_eager": dict(zip(["binning", "near", "up", "m2l", "l2l", "l2p_sum", "total",
                                                  "fork_to_join"], st))}
 
+    if args.precision == "mixed":
+        out["m2l"] = m2l_leg(api, w, x, y, g, args.steps, flush, stream)
+
     # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
     f.set_count_pairs(True)
     f.velocity(x, y, g, u, v)
@@ -273,6 +276,85 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         out["cpu_baseline"] = cpu_baseline(w, u.cpu().numpy(), v.cpu().numpy())
     f.close()
     return out
+
+
+def m2l_translations(w) -> int:
+    """M2L translations over non-empty boxes (target and source both non-empty), levels 2..L (§3 stage 6)."""
+    import numpy as np
+
+    L = w.depth
+    if L < 2:
+        return 0
+    x0, y0, side = w.domain
+    ns = 1 << L
+    ix = np.clip(np.floor((w.x - x0) * (ns / side)).astype(np.int64), 0, ns - 1)
+    iy = np.clip(np.floor((w.y - y0) * (ns / side)).astype(np.int64), 0, ns - 1)
+    occ = np.zeros((ns, ns), dtype=bool)
+    occ[iy, ix] = True
+    total = 0
+    for l in range(L, 1, -1):
+        n = 1 << l
+        pad = np.pad(occ, 3)
+        for cy in (0, 1):
+            for cx in (0, 1):
+                tgt = occ[cy::2, cx::2]
+                for dy in range(-2 - cy, 4 - cy):
+                    for dx in range(-2 - cx, 4 - cx):
+                        if -1 <= dx <= 1 and -1 <= dy <= 1:
+                            continue
+                        src = pad[3 + cy + dy:3 + cy + dy + n:2, 3 + cx + dx:3 + cx + dx + n:2]
+                        total += int((tgt & src).sum())
+        occ = occ.reshape(n // 2, 2, n // 2, 2).any(axis=(1, 3))
+    return total
+
+
+def tf32_peak_tflops() -> tuple[float, str]:
+    """Dense TF32 tensor peak: the measured bf16 burst figure x the nominal TF32 / bf16 ratio (1.1 / 2.25)."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["bf16_tflops"]) * 1.1 / 2.25, "of measured (bf16 burst x 1.1/2.25)"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "of fallback (1.9 PFLOP/s bf16 x 1.1/2.25)"
+
+
+def m2l_leg(api, w, x, y, g, steps, flush, stream) -> dict:
+    """M2L (stage 6) timed alone inside far-field-only evaluations, on the tensor cores and on the CUDA cores.
+
+    Algorithmic work: 8 p^2 real flops per translation (p^2 complex multiply-adds), over non-empty boxes; the
+    tensor-core kernel executes 2 (real, imaginary) x 3 (3xTF32) x 2 x 128 x NP x KP flops per offset and tile
+    of 128 boxes (KP = p rounded up to 8, 16, 24 or 32; NP = KP rounded up to 16)."""
+    import statistics as st_
+
+    import torch
+
+    res = {}
+    for engine in ("tensor", "cuda_cores"):
+        fe = api.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain, m2l_engine=engine)
+        fe.set_timing(True)
+        u = torch.empty_like(x)
+        v = torch.empty_like(x)
+        fe.velocity_far(x, y, g, u, v)
+        ts = []
+        for _ in range(max(5, min(steps, 20))):
+            flush.zero_()
+            fe.velocity_far(x, y, g, u, v)
+            ts.append(fe.stage_times()[3])
+        res[engine] = st_.median(ts)
+        fe.close()
+    T = m2l_translations(w)
+    p = w.p
+    KP = 8 if p <= 8 else 16 if p <= 16 else 24 if p <= 24 else 32
+    NP = (KP + 15) // 16 * 16
+    tiles = sum(4 * max(1, 4 ** (l - 1) // 128) for l in range(2, w.depth + 1))
+    tc_flops = tiles * 27 * 2 * 3 * 2 * 128 * NP * KP
+    peak, peak_note = tf32_peak_tflops()
+    t = res["tensor"] / 1e3
+    return {"kernel": "k_m2l_tc (tcgen05.mma kind::tf32, 3xTF32)", "ms": res["tensor"],
+            "cuda_cores_ms": res["cuda_cores"], "translations": T, "flops_per_translation": 8 * p * p,
+            "achieved_algorithmic_tflops": 8 * p * p * T / t / 1e12,
+            "tensor_flops_executed": tc_flops, "achieved_tensor_tflops": tc_flops / t / 1e12,
+            "peak_tf32_tflops": peak, "frac_tensor": tc_flops / t / 1e12 / peak, "peak_note": peak_note,
+            "timing": "stage events around the M2L launch in far-field-only evaluations, L2 flushed"}
 
 
 def cpu_baseline(w, u_gpu, v_gpu) -> dict:

@@ -82,6 +82,20 @@ fmm_status fmm_set_precision(fmm_handle h, fmm_precision mode);
  * Ignored by FMM_FP64. */
 fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level);
 
+/* Where the FP32 levels of M2L (Fig. 1 stage 6, the translation b_l of §3) run in the precision form; both
+ * use the factored radius-scaled form b_l = rho^(l+1) sum_m (-1)^(m+1) C(m+l, m) rho^m a_m, rho = 1/delta.
+ * FMM_M2L_TENSOR (default): per interaction offset, the gathered multipoles of 128 target boxes (scaled by
+ * rho^m) times the signed binomial matrix, which all offsets and levels share, as a dense GEMM on the tensor
+ * cores (tcgen05, 3xTF32: every operand split into two TF32 parts, accumulators in tensor memory, each
+ * offset's product read back, scaled by rho^(l+1) and summed in FP32).
+ * FMM_M2L_CUDA_CORES: one lane per (target, source) pair in FP32 on the CUDA cores. Both agree with the
+ * FP64 form to a few 1e-7 relative.
+ * FP64 levels (the plain form, levels <= coarse_level) and the adjoint always use FP64 CUDA-core kernels.
+ * Returns FMM_EINVAL for any other value. */
+#define FMM_M2L_CUDA_CORES 0
+#define FMM_M2L_TENSOR 1
+fmm_status fmm_set_m2l_engine(fmm_handle h, int engine);
+
 /* Changes depth, p or sigma of an existing handle (same ranges as fmm_create). */
 fmm_status fmm_set_params(fmm_handle h, int tree_depth, int p, double sigma);
 

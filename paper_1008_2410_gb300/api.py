@@ -31,11 +31,12 @@ class FMM:
     """One FMM configuration: tree depth L (4^L leaves), p expansion terms, blob core sigma.
 
     precision: "fp64" (plain form) or "mixed" (precision form). domain: (x0, y0, side) or None for the
-    bounding-box rule. graph: capture and replay the evaluation as a CUDA graph.
+    bounding-box rule. graph: capture and replay the evaluation as a CUDA graph. m2l_engine: "tensor"
+    (tcgen05, default) or "cuda_cores" for the FP32 M2L levels of the precision form.
     """
 
     def __init__(self, depth: int, p: int, sigma: float, precision: str = "fp64", domain=None,
-                 graph: bool = False, coarse_level: int | None = None):
+                 graph: bool = False, coarse_level: int | None = None, m2l_engine: str | None = None):
         self._lib = _lib.load()
         h = ctypes.c_void_p()
         st = self._lib.fmm_create(int(depth), int(p), float(sigma), ctypes.byref(h))
@@ -49,6 +50,8 @@ class FMM:
             self.set_graph(True)
         if coarse_level is not None:
             check(self._lib.fmm_set_coarse_level(self.h, int(coarse_level)), self.h)
+        if m2l_engine is not None:
+            self.set_m2l_engine(m2l_engine)
 
     # -- configuration
     def close(self) -> None:
@@ -66,6 +69,10 @@ class FMM:
         mode = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
         check(self._lib.fmm_set_precision(self.h, mode), self.h)
         self.precision = precision
+
+    def set_m2l_engine(self, engine: str) -> None:
+        code = {"cuda_cores": 0, "tensor": 1}[engine]
+        check(self._lib.fmm_set_m2l_engine(self.h, code), self.h)
 
     def set_domain(self, x0: float, y0: float, side: float) -> None:
         check(self._lib.fmm_set_domain(self.h, float(x0), float(y0), float(side)), self.h)

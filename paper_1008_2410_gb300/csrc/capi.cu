@@ -52,6 +52,7 @@ struct fmm_ctx {
     double dom[3] = {0, 0, 1};
     int mixed = 0;
     int coarse = -1;  // precision form: FP32 on every level (radius-scaled translations stay bounded)
+    int m2l_engine = FMM_M2L_TENSOR;
     cudaStream_t stream = nullptr;  // caller's stream
     cudaStream_t exec = nullptr;    // internal stream used for graph capture / replay
     cudaStream_t side = nullptr;    // high-priority stream of the multipole sweep
@@ -68,6 +69,8 @@ struct fmm_ctx {
     Work w{};
     // tables (depend on p only)
     void *tab = nullptr;
+    void *tab_tc = nullptr;  // tensor-core M2L operand table
+    size_t tab_tc_cap = 0;
     Tables t{};
     int tab_p = -1;
     // host-visible status
@@ -88,7 +91,7 @@ struct fmm_ctx {
     uint64_t layout_version = 1;
     size_t layout_sig[6] = {};
     struct GKey {
-        int mode, n, nsys, mixed, coarse, threads, kt, count_pairs, p, timing;
+        int mode, n, nsys, mixed, coarse, m2l_engine, threads, kt, count_pairs, p, timing;
         uint64_t layout;
         const void *ptr[5];
         uint64_t version;
@@ -169,6 +172,8 @@ static fmm_status ensure_tables(fmm_handle h)
 {
     if (upload_m2l_constants(h->stream) != 0)
         return set_err(h, FMM_ECUDA, "constant-table upload failed");
+    if (prepare_m2l_tc() != 0)
+        return set_err(h, FMM_ECUDA, "tensor-core M2L kernel attributes could not be set");
     if (h->tab_p == h->p)
         return FMM_OK;
     const int P = FMM_PMAX, RS = 2 * FMM_PMAX + 2;
@@ -212,6 +217,20 @@ static fmm_status ensure_tables(fmm_handle h)
     CU(cudaMemcpy(h->t.rho32, rho32.data(), sz[5], cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->t.binom64, bin.data(), sz[6], cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->t.binom32, bin32.data(), sz[7], cudaMemcpyHostToDevice));
+    // tensor-core M2L operands (sized by p's bucket)
+    const size_t tc_bytes = m2l_tc_table_bytes(h->p);
+    if (tc_bytes > h->tab_tc_cap) {
+        if (h->tab_tc)
+            CU(cudaFree(h->tab_tc));
+        h->tab_tc = nullptr;
+        h->tab_tc_cap = 0;
+        CU(cudaMalloc(&h->tab_tc, tc_bytes));
+        h->tab_tc_cap = tc_bytes;
+    }
+    std::vector<unsigned char> tc(tc_bytes);
+    build_m2l_tc_table_host(h->p, tc.data());
+    CU(cudaMemcpy(h->tab_tc, tc.data(), tc_bytes, cudaMemcpyHostToDevice));
+    h->t.m2l_tc = (unsigned char *)h->tab_tc;
     h->tab_p = h->p;
     return FMM_OK;
 }
@@ -364,6 +383,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.p = p;
     w.mixed = mixed ? 1 : 0;
     w.coarse_level = h->coarse;
+    w.m2l_tc = h->m2l_engine == FMM_M2L_TENSOR ? 1 : 0;
     w.nsys = nsys;
     w.maxdepth = h->lv.maxdepth;
     w.key = (int *)(b + lay.off[0]);
@@ -552,6 +572,7 @@ static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x
     key.nsys = (int)h->sys_cfg.size();
     key.mixed = h->w.mixed;
     key.coarse = h->coarse;
+    key.m2l_engine = h->m2l_engine;
     key.threads = h->p2p_threads;
     key.kt = h->p2p_kt;
     key.count_pairs = h->count_pairs;
@@ -678,6 +699,8 @@ fmm_status fmm_destroy(fmm_handle h)
         cudaFree(h->hdr);
     if (h->tab)
         cudaFree(h->tab);
+    if (h->tab_tc)
+        cudaFree(h->tab_tc);
     if (h->d_io)
         cudaFree(h->d_io);
     if (h->h_status)
@@ -720,6 +743,14 @@ fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level)
     if (!h || coarse_level < -1 || coarse_level > FMM_MAXL)
         return FMM_EINVAL;
     h->coarse = coarse_level;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_m2l_engine(fmm_handle h, int engine)
+{
+    if (!h || (engine != FMM_M2L_CUDA_CORES && engine != FMM_M2L_TENSOR))
+        return FMM_EINVAL;
+    h->m2l_engine = engine;
     return FMM_OK;
 }
 

@@ -71,6 +71,7 @@ struct Tables {
     float2 *rho32;
     double *binom64;          // [PMAX][PMAX]  C(m + l, m)
     float *binom32;
+    unsigned char *m2l_tc;    // tensor-core M2L operand B (m2l_tc.cu)
 };
 
 struct Work {
@@ -80,6 +81,7 @@ struct Work {
     int p;
     int mixed;
     int coarse_level;         // levels <= this run in FP64 in the precision form
+    int m2l_tc;               // FP32 M2L levels on the tensor cores (1) or on the CUDA cores (0)
     int nsys;
     int maxdepth;
     // arrays
@@ -105,6 +107,12 @@ struct Work {
     int *sys_list;
     LevelInfo lv;
 };
+
+// System of the sidx-th system that has level l.
+__device__ __forceinline__ int sys_at_level(const Work &w, int l, int sidx)
+{
+    return w.sys_list[w.lv.first_at[l] + sidx];
+}
 
 // Level precision in the precision form: FP64 for l <= coarse_level.
 __host__ __device__ inline bool level_fp64(const Work &w, int l) { return !w.mixed || l <= w.coarse_level; }
@@ -157,6 +165,14 @@ int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cu
 int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);
 
 void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom);
+
+// Tensor-core M2L (m2l_tc.cu): its operand table for p (the signed binomial matrix, TF32 hi and lo), the
+// table's size, the per-device kernel attributes (before any stream capture; 0 on success) and the launch
+// over levels l32 .. maxdepth.
+size_t m2l_tc_table_bytes(int p);
+void build_m2l_tc_table_host(int p, unsigned char *out);
+int prepare_m2l_tc();
+int launch_m2l_tc(const Work &w, const Tables &t, int l32, cudaStream_t s);
 int upload_m2l_constants(cudaStream_t s);  // once per device, before any stream capture; 0 on success
 
 }  // namespace fmm

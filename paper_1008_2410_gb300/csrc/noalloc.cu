@@ -48,7 +48,7 @@ size_t tables_bytes()
     size_t t = 0;
     for (size_t s : kTabSizes)
         t += up256(s);
-    return t;
+    return t + up256(m2l_tc_table_bytes(FMM_PMAX));  // tensor-core M2L operands, largest p bucket
 }
 
 void carve_tables(unsigned char *b, Tables &t)
@@ -67,6 +67,7 @@ void carve_tables(unsigned char *b, Tables &t)
     t.rho32 = (float2 *)p[5];
     t.binom64 = (double *)p[6];
     t.binom32 = (float *)p[7];
+    t.m2l_tc = b + off;
 }
 
 // Host copies of the tables for one p; the copy into the device array is ordered on the caller's stream.
@@ -91,6 +92,11 @@ fmm_status upload_tables(const Tables &t, int p, cudaStream_t s)
     for (int i = 0; i < 8; ++i)
         if (cudaMemcpyAsync(dst[i], src[i], kTabSizes[i], cudaMemcpyHostToDevice, s) != cudaSuccess)
             return FMM_ECUDA;
+    static std::vector<unsigned char> tc;
+    tc.assign(m2l_tc_table_bytes(p), 0);
+    build_m2l_tc_table_host(p, tc.data());
+    if (cudaMemcpyAsync(t.m2l_tc, tc.data(), tc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FMM_ECUDA;
     // pageable sources: make sure the copies have read them before the static buffers are reused
     return cudaStreamSynchronize(s) == cudaSuccess ? FMM_OK : FMM_ECUDA;
 }
@@ -195,10 +201,13 @@ extern "C" fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, 
         return FMM_ECUDA;
     if (upload_m2l_constants(s) != 0)  // constant memory of the module, once per device (no allocation)
         return FMM_ECUDA;
+    if (prepare_m2l_tc() != 0)  // kernel attributes, once per device
+        return FMM_ECUDA;
 
     unsigned char *h = base + tab;
     Work w{};
     carve_work(h + hdr, w, n, tree_depth, p, mixed);
+    w.m2l_tc = 1;  // the defaults of a handle
     w.status = (unsigned int *)(h + hdr_status);
     w.pair_count = (unsigned long long *)(h + hdr_status + 32);
     w.minmax = (unsigned long long *)(h + hdr_minmax);

@@ -7,8 +7,9 @@
 // of columns ix-1..ix+1), staged through shared memory in tiles.
 //
 // Precision form (FMM_MIXED): coordinates are leaf-relative in leaf units, split hi + lo in FP32; the shift
-// by the integer leaf offset is exact (Fast2Sum folds its rounding error into lo), so a difference keeps the
-// FP64 coordinates' resolution. exp and 1/r^2 use the SFU (ex2.approx, rcp.approx); for r^2 / 2 sigma^2 < 1/2
+// by the integer leaf offset is exact (Fast2Sum folds its rounding error into lo). For leaves up to about 38
+// sigma wide one float per coordinate suffices (the source's hi, the target's shifted value rounded once);
+// wider leaves keep both parts, so a difference has the FP64 coordinates' resolution. exp and 1/r^2 use the SFU (ex2.approx, rcp.approx); for r^2 / 2 sigma^2 < 1/2
 // the factor (1 - e^-y)/y comes from its Taylor series instead of 1 - e^-y, which cancels. Two targets share
 // each packed f32x2 instruction. Per-target sums are FP32 within a row of source leaves and compensated
 // (TwoSum) across rows. Tiles arrive by bulk asynchronous copies (cp.async.bulk, the TMA engine) into shared
@@ -170,6 +171,11 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 // loses 2^-22.5 / y of its relative accuracy there. r' = 0 (a particle and itself, or coincident particles,
 // which always share a leaf) needs no series: with 1/r'^2 clamped, g (1 - e) / r'^2 = 0 exactly.
 #define P2P_THR 0.72134752044448170f
+// Largest s (leaf width w_L in units of sqrt(2 / log2 e) sigma) at which the near field keeps one float per
+// coordinate in the leaf frame: the rounding of a source coordinate, |x| <= 3 s / 2, relative to sigma grows
+// with s; at s = 13.6 (64 uniform particles per leaf, sigma = h / 2) it costs 7e-8 relative L2 of the near
+// field, so up to s = 32 it stays below 2e-7. Wider leaves take the hi + lo split form.
+#define P2P_SPLIT_S 32.0f
 #define P2P_LN2 0.69314718055994531f
 #ifndef P2P_UNROLL
 #define P2P_UNROLL 1  // source loop unroll of the near-field kernel
@@ -207,8 +213,10 @@ __device__ __forceinline__ void two_sum2(f2 &s, f2 &c, f2 x)
 
 // Sources j0..j1 of one source leaf against KT targets per lane (KT/2 packed pairs), accumulated into PU, PV.
 // The lane's targets (leaf order index `tbase + lane + 32 q`, q < KT, only those < tcnt) are re-read and
-// re-expressed relative to the source leaf's centre exactly: hi - dc s by Fast2Sum (|dc s| >= |hi|), error into lo.
-template <int KT, bool SELF>
+// re-expressed relative to the source leaf's centre: hi - dc s by Fast2Sum (|dc s| >= |hi|), error into lo.
+// SPLIT keeps the sources' lo parts (differences at FP64-level resolution); otherwise each coordinate is one
+// float (the target's rounded once from its exact shifted hi + lo) and a difference costs one instruction.
+template <int KT, bool SELF, bool SPLIT>
 __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restrict__ EH,
                                             const float4 *__restrict__ EL, const float4 *__restrict__ EG, int j0,
                                             int j1, float sdx, float sdy, int tbase, int tcnt, f2 *PU, f2 *PV)
@@ -231,23 +239,34 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
             lx[h] = tl.x + (th.x - (hx[h] + sdx));
             hy[h] = th.z - sdy;
             ly[h] = tl.z + (th.z - (hy[h] + sdy));
+            if (!SPLIT) {
+                hx[h] += lx[h];
+                hy[h] += ly[h];
+            }
         }
         AHX[pr] = pk2(hx[0], hx[1]);
-        ALX[pr] = pk2(lx[0], lx[1]);
         AHY[pr] = pk2(hy[0], hy[1]);
-        ALY[pr] = pk2(ly[0], ly[1]);
+        if (SPLIT) {
+            ALX[pr] = pk2(lx[0], lx[1]);
+            ALY[pr] = pk2(ly[0], ly[1]);
+        }
     }
 #pragma unroll(kP2PUnroll)
     for (int j = j0; j < j1; ++j) {
-        const float4 h = EH[j], l = EL[j], g = EG[j];
-        const f2 sxh = pk2(h.x, h.y), syh = pk2(h.z, h.w), sxl = pk2(l.x, l.y), syl = pk2(l.z, l.w);
+        const float4 h = EH[j], g = EG[j], l = SPLIT ? EL[j] : h;
+        const f2 sxh = pk2(h.x, h.y), syh = pk2(h.z, h.w);
         const f2 gp = pk2(g.x, g.y), gn = pk2(g.z, g.w);
         f2 dx[NP], dy[NP], r2[NP], q[NP], og[NP];
         float rmin = 3.0e38f;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
-            dx[pr] = add2(sub2(AHX[pr], sxh), sub2(ALX[pr], sxl));
-            dy[pr] = add2(sub2(AHY[pr], syh), sub2(ALY[pr], syl));
+            if (SPLIT) {
+                dx[pr] = add2(sub2(AHX[pr], sxh), sub2(ALX[pr], pk2(l.x, l.y)));
+                dy[pr] = add2(sub2(AHY[pr], syh), sub2(ALY[pr], pk2(l.z, l.w)));
+            } else {
+                dx[pr] = sub2(AHX[pr], sxh);
+                dy[pr] = sub2(AHY[pr], syh);
+            }
             r2[pr] = fma2(dx[pr], dx[pr], mul2(dy[pr], dy[pr]));
             float ra, rb;
             up2(r2[pr], ra, rb);
@@ -312,7 +331,8 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
     const int ix0 = local0 & (ns - 1), iy = local0 >> L;
     const int myleaf = first + warp;
     const int my_s0 = w.start[myleaf], my_c = w.start[myleaf + 1] - my_s0;
-    const int per_pass = 32 * ktmax;
+    const bool split = d.s_unit > P2P_SPLIT_S;  // block-uniform; the split form runs 2 targets per lane
+    const int per_pass = 32 * (split ? 2 : ktmax);
     int npass = (my_c + per_pass - 1) / per_pass;
     if (LPB == 2) {
         const int other = first + (warp ^ 1);
@@ -354,10 +374,11 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
                 __syncthreads();  // everyone is done with the previous tile
                 if (threadIdx.x == 0) {
                     fence_proxy_async();
-                    mbar_expect_tx(&bar, (uint32_t)m * 48u);
+                    mbar_expect_tx(&bar, (uint32_t)m * (split ? 48u : 32u));
                     bulk_g2s(EH, w.eh + q0, (uint32_t)m * 16u, &bar);
-                    bulk_g2s(EL, w.el + q0, (uint32_t)m * 16u, &bar);
                     bulk_g2s(EG, w.eg + q0, (uint32_t)m * 16u, &bar);
+                    if (split)
+                        bulk_g2s(EL, w.el + q0, (uint32_t)m * 16u, &bar);
                 }
                 bool ok = mbar_wait_bounded(&bar, phase, w.status);
                 if (!__syncthreads_and(ok)) {
@@ -379,17 +400,26 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
                         continue;
                     const float sdx = (float)(k3 - 1) * s, sdy = (float)dyr * s;
                     const bool self = k3 == 1 && dyr == 0;
-                    if (kt == 2) {
+#define P2P_SEG(KT, SELF, SPLIT) p2p_segment<KT, SELF, SPLIT>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV)
+                    if (split) {
                         if (self)
-                            p2p_segment<2, true>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
+                            P2P_SEG(2, true, true);
                         else
-                            p2p_segment<2, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
+                            P2P_SEG(2, false, true);
                     } else {
-                        if (self)
-                            p2p_segment<4, true>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
-                        else
-                            p2p_segment<4, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV);
+                        if (kt == 2) {
+                            if (self)
+                                P2P_SEG(2, true, false);
+                            else
+                                P2P_SEG(2, false, false);
+                        } else {
+                            if (self)
+                                P2P_SEG(4, true, false);
+                            else
+                                P2P_SEG(4, false, false);
+                        }
                     }
+#undef P2P_SEG
                 }
                 // compensated totals: plain FP32 sums cover at most one tile of sources
 #pragma unroll

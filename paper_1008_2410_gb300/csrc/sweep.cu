@@ -58,11 +58,6 @@ __device__ __forceinline__ void stc(float2 *p, int64_t i, cx<R> v)
     p[i] = make_float2((float)v.re, (float)v.im);
 }
 
-__device__ __forceinline__ int sys_at_level(const Work &w, int l, int sidx)
-{
-    return w.sys_list[w.lv.first_at[l] + sidx];
-}
-
 // ------------------------------------------------------------------ stage 4: P2M (one warp per leaf)
 
 // Compute type R; coefficients written to the leaf level's array (FP64 or FP32). PM >= p terms are
@@ -541,7 +536,9 @@ int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio
             m2l_box_launch<32>(w, t, adj, 0, split, s);
         ++n;
     }
-    if (split < total) {
+    if (split < total && w.m2l_tc && t.m2l_tc) {
+        n += launch_m2l_tc(w, t, l32, s);
+    } else if (split < total) {
         if (w.p <= 8)
             m2l_src_launch<8>(w, split, total, s);
         else if (w.p <= 12)

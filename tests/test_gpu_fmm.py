@@ -112,6 +112,33 @@ def test_near_and_far_halves(lib, oracle, precision, tol):
     assert rel_l2((uf, vf), (uof, vof)) < tol
 
 
+M2L_CASES = [
+    ("p1_d3", lambda: fi.uniform(2000, seed_index=37, depth=3, p=1)),
+    ("p8_d2", lambda: fi.uniform(3000, seed_index=34, depth=2, p=8)),
+    ("p10_d3", lambda: fi.uniform(5000, seed_index=31, depth=3, p=10)),
+    ("p14_d4", lambda: fi.uniform(20000, seed_index=40, depth=4, p=14)),
+    ("p17_d5", lambda: fi.uniform(40000, seed_index=32, depth=5, p=17)),
+    ("ragged12345_d4_p20", lambda: fi.uniform(12345, seed_index=33, depth=4, p=20)),
+    ("p24_d3", lambda: fi.uniform(4000, seed_index=41, depth=3, p=24)),
+    ("p32_d3", lambda: fi.uniform(2000, seed_index=38, depth=3, p=32)),
+    ("clustered20k_d5_p14", lambda: fi.clustered(20000, depth=5, p=14)),  # empty boxes: zero source rows
+    ("patches64k_d6_p20", lambda: fi.patches(1 << 16, seed_index=39, depth=6, p=20)),  # several tiles a level
+]
+
+
+@pytest.mark.parametrize("engine", ["tensor", "cuda_cores"])
+@pytest.mark.parametrize("name,make", M2L_CASES, ids=[c[0] for c in M2L_CASES])
+def test_far_field_by_m2l_engine(lib, oracle, engine, name, make):
+    """The far field alone (P2M, M2M, M2L, L2L, L2P) of the precision form against the oracle's far part, with
+    the FP32 M2L levels on the tensor cores (3xTF32) and on the CUDA cores."""
+    w = make()
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain, m2l_engine=engine)
+    u, v = f.velocity_far(dev(w.x), dev(w.y), dev(w.gamma))
+    f.sync()
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, parts="far")
+    assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < TOL32
+
+
 def test_pair_count_exact(lib, oracle):
     w = fi.lattice_lamb_oseen()
     f = lib.FMM(w.depth, w.p, w.sigma, domain=w.domain)

@@ -167,7 +167,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                       "l2": "flushed before every timed step (256 MiB write, outside the timed events)",
                       "graph": True, "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
            "gpu_launches": int(launches), "clocks": clk,
-           "p2p_tile": [tuned["p2p_threads"], tuned["p2p_targets_per_thread"]]}
+           "p2p_tile": [tuned["p2p_threads"], tuned["p2p_targets_per_thread"]], "m2l_engine": tuned["m2l_engine"]}
     if rank != 0 and world > 1:
         return None
     if args.quick:

@@ -96,6 +96,9 @@ fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level);
 #define FMM_M2L_TENSOR 1
 fmm_status fmm_set_m2l_engine(fmm_handle h, int engine);
 
+/* The handle's M2L engine (FMM_M2L_TENSOR or FMM_M2L_CUDA_CORES; fmm_autotune may change it), -1 for NULL. */
+int fmm_get_m2l_engine(fmm_handle h);
+
 /* Changes depth, p or sigma of an existing handle (same ranges as fmm_create). */
 fmm_status fmm_set_params(fmm_handle h, int tree_depth, int p, double sigma);
 
@@ -151,9 +154,10 @@ fmm_status fmm_velocity_batched(fmm_handle h, int nsys, const int64_t *offsets, 
 fmm_status fmm_sync(fmm_handle h);
 
 /* Per-stage device times (ms) of the last evaluation when timing is on (fmm_set_timing(h, 1); not with
- * graphs): out[0] binning, [1] near field, [2] up sweep (P2M+M2M), [3] M2L, [4] L2L, [5] L2P+sum,
- * [6] whole evaluation, [7] near field and sweep overlapped (from the fork to the join). Returns the number
- * of values written (at most cap). */
+ * graphs): out[0] binning, [1] near field, [2] up sweep (P2M+M2M), [3] M2L, [4] L2L (and L2P in the
+ * precision form, which evaluates the far field on the sweep stream), [5] the final sum and scatter to input
+ * order (with L2P in the plain form), [6] whole evaluation, [7] near field and sweep overlapped (from the fork
+ * to the join). Returns the number of values written (at most cap). */
 fmm_status fmm_set_timing(fmm_handle h, int enable);
 int fmm_stage_times(fmm_handle h, float *out, int cap);
 
@@ -167,7 +171,8 @@ int64_t fmm_last_pair_count(fmm_handle h);
 int64_t fmm_kernel_launches(fmm_handle h);
 
 /* Picks depth and near-field tile for the handle's p, sigma and precision by timing fmm_velocity on the given
- * particles (device arrays, left unchanged; u, v are scratch outputs). Tries depths depth_lo..depth_hi.
+ * particles (device arrays, left unchanged; u, v are scratch outputs). Tries depths depth_lo..depth_hi; in
+ * the precision form it then times both M2L engines (fmm_set_m2l_engine) and keeps the faster.
  * The choice is stored in the handle and, when the environment variable FMM2D_TUNE_CACHE names a file,
  * cached there keyed by (n, p, precision). */
 fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,

@@ -100,8 +100,9 @@ class FMM:
         s = ctypes.c_double()
         check(self._lib.fmm_get_params(self.h, ctypes.byref(d), ctypes.byref(p), ctypes.byref(s), ctypes.byref(th),
                                        ctypes.byref(kt)), self.h)
+        eng = self._lib.fmm_get_m2l_engine(self.h)
         return {"depth": d.value, "p": p.value, "sigma": s.value, "p2p_threads": th.value,
-                "p2p_targets_per_thread": kt.value}
+                "p2p_targets_per_thread": kt.value, "m2l_engine": {0: "cuda_cores", 1: "tensor"}.get(eng, "?")}
 
     def _stream(self) -> None:
         s = torch.cuda.current_stream()

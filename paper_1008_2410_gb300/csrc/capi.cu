@@ -331,7 +331,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = f64 ? np * 8 : 0;                            // 8 sy
     sizes[i++] = f64 ? np * 8 : 0;                            // 9 sg
     sizes[i++] = mixed ? np * 48 : 0;                         // 10 eh, el, eg
-    sizes[i++] = 0;                                           // 11 (unused)
+    sizes[i++] = mixed ? np * 8 : 0;                          // 11 far32
     sizes[i++] = mixed ? 0 : np * 16;                         // 12 near64
     sizes[i++] = mixed ? np * 8 : 0;                          // 13 near32
     sizes[i++] = (size_t)nbox * 4 + 16;                       // 14 bcount
@@ -401,6 +401,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.eg = sizes[10] ? w.el + np : nullptr;
     w.near64 = sizes[12] ? (double2 *)(b + lay.off[12]) : nullptr;
     w.near32 = sizes[13] ? (float2 *)(b + lay.off[13]) : nullptr;
+    w.far32 = sizes[11] ? (float2 *)(b + lay.off[11]) : nullptr;
     w.bcount = (int *)(b + lay.off[14]);
     w.M64 = (double2 *)(b + lay.off[15]);
     w.L64 = (double2 *)(b + lay.off[16]);
@@ -503,6 +504,7 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
             CU(record_timing(h->ev_t[3], h->side));
         for (int l = 2; l < w.lv.maxdepth; ++l)
             nl += launch_l2l(w, h->t, l, 0, h->side, 1);
+        nl += launch_l2p(w, h->side);  // precision form: the far field before the join
         if (timed)
             CU(record_timing(h->ev_t[4], h->side));
         CU(cudaEventRecord(h->ev_join, h->side));
@@ -753,6 +755,8 @@ fmm_status fmm_set_m2l_engine(fmm_handle h, int engine)
     h->m2l_engine = engine;
     return FMM_OK;
 }
+
+int fmm_get_m2l_engine(fmm_handle h) { return h ? h->m2l_engine : -1; }
 
 fmm_status fmm_set_params(fmm_handle h, int tree_depth, int p, double sigma)
 {
@@ -1084,14 +1088,16 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
         if (f) {
             char line[256];
             while (fgets(line, sizeof line, f)) {
-                int d, th, kt;
+                int d, th, kt, eng = h->m2l_engine;
                 char *bar = strchr(line, '|');
                 if (!bar)
                     continue;
                 *bar = 0;
-                if (strcmp(line, keybuf) == 0 && sscanf(bar + 1, "%d %d %d", &d, &th, &kt) == 3) {
+                if (strcmp(line, keybuf) == 0 && sscanf(bar + 1, "%d %d %d %d", &d, &th, &kt, &eng) >= 3) {
                     fclose(f);
                     h->depth = d;
+                    if (eng == FMM_M2L_CUDA_CORES || eng == FMM_M2L_TENSOR)
+                        h->m2l_engine = eng;
                     return fmm_set_p2p_tile(h, th, kt);
                 }
             }
@@ -1108,43 +1114,58 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
+    // median of 5 timed evaluations after 2 untimed ones; < 0 if an evaluation failed
+    auto time_eval = [&]() -> float {
+        float ts[5];
+        for (int r = 0; r < 7; ++r) {
+            if (cudaEventRecord(e0, h->stream) != cudaSuccess || fmm_velocity(h, n, x, y, gamma, u, v) != FMM_OK ||
+                cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return -1.f;
+            if (r >= 2)
+                cudaEventElapsedTime(&ts[r - 2], e0, e1);
+        }
+        std::sort(ts, ts + 5);
+        return ts[2];
+    };
     for (int d = depth_lo; d <= depth_hi; ++d) {
         for (int ti = 0; ti < ntile; ++ti) {
             h->depth = d;
             h->p2p_threads = tiles[ti][0];
             h->p2p_kt = tiles[ti][1];
-            float ts[5];
-            bool ok = true;
-            for (int r = 0; r < 7 && ok; ++r) {
-                CU(cudaEventRecord(e0, h->stream));
-                ok = fmm_velocity(h, n, x, y, gamma, u, v) == FMM_OK;
-                CU(cudaEventRecord(e1, h->stream));
-                CU(cudaEventSynchronize(e1));
-                if (r >= 2)
-                    cudaEventElapsedTime(&ts[r - 2], e0, e1);
-            }
-            if (!ok)
-                continue;
-            std::sort(ts, ts + 5);
-            if (ts[2] < best) {
-                best = ts[2];
+            const float t = time_eval();
+            if (t >= 0.f && t < best) {
+                best = t;
                 bd = d;
                 bth = tiles[ti][0];
                 bkt = tiles[ti][1];
             }
         }
     }
+    h->depth = bd;
+    h->p2p_threads = bth;
+    h->p2p_kt = bkt;
+    // M2L engine of the precision form's FP32 levels, at the chosen depth and tile
+    int beng = h->m2l_engine;
+    if (h->mixed && best < 1e30f) {
+        float tb = 1e30f;
+        for (int eng : {FMM_M2L_TENSOR, FMM_M2L_CUDA_CORES}) {
+            h->m2l_engine = eng;
+            const float t = time_eval();
+            if (t >= 0.f && t < tb) {
+                tb = t;
+                beng = eng;
+            }
+        }
+    }
+    h->m2l_engine = beng;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->use_graph = save_graph;
     h->timing = save_timing;
-    h->depth = bd;
-    h->p2p_threads = bth;
-    h->p2p_kt = bkt;
     if (cache) {
         FILE *f = fopen(cache, "a");
         if (f) {
-            fprintf(f, "%s|%d %d %d\n", keybuf, bd, bth, bkt);
+            fprintf(f, "%s|%d %d %d %d\n", keybuf, bd, bth, bkt, beng);
             fclose(f);
         }
     }

@@ -82,6 +82,7 @@ struct Work {
     int mixed;
     int coarse_level;         // levels <= this run in FP64 in the precision form
     int m2l_tc;               // FP32 M2L levels on the tensor cores (1) or on the CUDA cores (0)
+    float2 *far32;            // [n] leaf order: FP32 far field (L2P) of the precision form, or null (fused)
     int nsys;
     int maxdepth;
     // arrays
@@ -159,6 +160,7 @@ int launch_m2m(const Work &w, const Tables &t, int level, int adjoint_charges, c
 int launch_m2l(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t s, int prio);
 int launch_l2l(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
 int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);  // threads 32: 1 leaf per block, 64: 2
+int launch_l2p(const Work &w, cudaStream_t s);  // precision form with far32: far field into far32 (stage 8)
 int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
 int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far
 int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);  // adds it

@@ -653,6 +653,43 @@ __device__ __forceinline__ cx<R> horner_u(const S *__restrict__ b, int64_t base,
     return acc;
 }
 
+// Stage 8 alone for the precision form: the FP32 far field of every particle whose leaf level is FP32, in leaf
+// order (runs on the sweep stream, so that only the sum below waits for the near field).
+template <int PM>
+__global__ void k_l2p32(Work w)
+{
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= w.n)
+        return;
+    int k = w.nsys == 1 ? 0 : find_sys_by_particle(w.sys, w.nsys, pos);
+    const SysDev &d = w.sys[k];
+    int L = d.depth;
+    if (L < 2 || level_fp64(w, L))
+        return;
+    int64_t base = (d.box0[L] + (int)(w.sleaf[pos] - d.leaf0)) * (int64_t)w.p;
+    float4 hh = w.eh[pos], ll = w.el[pos];
+    cx<float> z = {(hh.x + ll.x) * d.inv_s, (hh.z + ll.z) * d.inv_s};
+    cx<float> s = horner_u<PM, float>(w.L32, base, w.p, z);
+    float fs = (float)d.far_scale;
+    w.far32[pos] = make_float2(s.re * fs, -s.im * fs);
+}
+
+int launch_l2p(const Work &w, cudaStream_t s)
+{
+    if (!w.mixed || !w.far32)
+        return 0;
+    const unsigned nb = (unsigned)((w.n + 255) / 256);
+    if (w.p <= 8)
+        k_l2p32<8><<<nb, 256, 0, s>>>(w);
+    else if (w.p <= 16)
+        k_l2p32<16><<<nb, 256, 0, s>>>(w);
+    else if (w.p <= 24)
+        k_l2p32<24><<<nb, 256, 0, s>>>(w);
+    else
+        k_l2p32<32><<<nb, 256, 0, s>>>(w);
+    return 1;
+}
+
 template <int PM>
 __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict__ u, double *__restrict__ v)
 {
@@ -668,7 +705,11 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
     if (w.mixed && !level_fp64(w, L)) {
         // precision form: FP32 far field and sum, one conversion to FP64 at the end
         float fu = 0.f, fv = 0.f;
-        if (far) {
+        if (far && w.far32) {
+            const float2 f = w.far32[pos];  // k_l2p32
+            fu = f.x;
+            fv = f.y;
+        } else if (far) {
             float4 hh = w.eh[pos], ll = w.el[pos];
             cx<float> z = {(hh.x + ll.x) * d.inv_s, (hh.z + ll.z) * d.inv_s};
             cx<float> s = horner_u<PM, float>(w.L32, base, w.p, z);

@@ -89,6 +89,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def whole_job(total_ms: float, steps: int, n_per_rank: int, world: int, dist=None, device: str = "cpu"):
+    """(ms per step, Mparticles/s) of the whole job: every rank evaluates its own replica on its own GPU, so the
+    job takes as long as the slowest rank (max over ranks of its timed total) and processes world x n particles
+    per step."""
+    if dist is not None and world > 1:
+        import torch
+
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * n_per_rank / (ms_per_step / 1e3) / 1e6
+
+
 def timed_steps(fn, steps: int, flush, stream, stage_times=None):
     """Per-step device time (ms) with CUDA events on the launching stream; L2 flushed before each step."""
     import torch
@@ -130,8 +144,16 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     f = api.FMM(w.depth, w.p, w.sigma, precision=args.precision, domain=w.domain, graph=True)
-    # the autotuner picks the near-field tile shape for this workload (depth stays the workload's)
-    tuned = f.autotune(x, y, g, w.depth, w.depth)
+    # the autotuner picks the near-field tile shape and the M2L engine for this workload (depth stays the
+    # workload's); --tile pins them instead (for profiling one configuration)
+    if args.tile:
+        th, kt = (int(t) for t in args.tile.split(","))
+        f.set_p2p_tile(th, kt)
+        if args.m2l_engine:
+            f.set_m2l_engine(args.m2l_engine)
+        tuned = f.params()
+    else:
+        tuned = f.autotune(x, y, g, w.depth, w.depth)
     f.set_timing(True)
     u = torch.empty_like(x)
     v = torch.empty_like(x)
@@ -151,13 +173,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         dist.barrier()
     launches = f.kernel_launches() - launches0
     clk = clocks.stop()
-    total = sum(ms)
-    if dist:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    ms_per_step = total / args.steps
-    value = world * n / (ms_per_step / 1e3) / 1e6
+    ms_per_step, value = whole_job(sum(ms), args.steps, n, world, dist, device="cuda")
 
     out = {"metric": METRIC, "value": value, "unit": "Mparticles/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -430,6 +446,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main timing only")
+    ap.add_argument("--tile", default=None, help="near-field tile 'threads,targets' instead of the autotuner's")
+    ap.add_argument("--m2l-engine", default=None, choices=["tensor", "cuda_cores"],
+                    help="M2L engine instead of the autotuner's (with --tile)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

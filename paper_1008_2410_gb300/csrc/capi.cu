@@ -343,7 +343,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = adjoint ? np * 8 : 0;                        // 20 sgv
     sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 21 AM64
     sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 22 AL64
-    sizes[i++] = 0;                                           // 23 (unused)
+    sizes[i++] = mixed ? np * 32 : 0;                         // 23 nearp [4][n]
     sizes[i++] = mixed ? np * 16 : 0;                         // 24 pos4u
     sizes[i++] = mixed ? np * 4 : 0;                          // 25 g32u
     sizes[i++] = np * 4;                                      // 26 slot
@@ -402,6 +402,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.near64 = sizes[12] ? (double2 *)(b + lay.off[12]) : nullptr;
     w.near32 = sizes[13] ? (float2 *)(b + lay.off[13]) : nullptr;
     w.far32 = sizes[11] ? (float2 *)(b + lay.off[11]) : nullptr;
+    w.nearp = sizes[23] ? (float2 *)(b + lay.off[23]) : nullptr;
     w.bcount = (int *)(b + lay.off[14]);
     w.M64 = (double2 *)(b + lay.off[15]);
     w.L64 = (double2 *)(b + lay.off[16]);
@@ -475,6 +476,20 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
     bool near = mode != MODE_FAR;
     bool timed = h->timing != 0;  // in a graph the event records become event-record nodes
     int64_t nl = 0;
+    // symmetric near field (tile 128): reactions land in nearp and the final sum adds them. The host knows a
+    // system takes one-float coordinates only for an explicit square (s is computed here as the device does,
+    // with a margin); otherwise the split-form kernel is launched as well and skips the one-float systems.
+    w.p2p_sym = near && w.mixed && h->p2p_threads == 128 && w.nearp ? 1 : 0;
+    w.p2p_all_plain = 1;
+    for (auto &c : h->sys_cfg) {
+        if (!c.explicit_domain) {
+            w.p2p_all_plain = 0;
+            continue;
+        }
+        const double wl = ldexp(c.dom[2], -c.depth), kap = wl * wl / (2.0 * c.sigma * c.sigma);
+        if (!(sqrt(1.4426950408889634074 * kap) < (double)P2P_SPLIT_S * (1.0 - 1e-6)))
+            w.p2p_all_plain = 0;
+    }
     (void)cudaGetLastError();  // drop a stale, non-sticky error left by an unrelated runtime call
     if (timed)
         CU(record_timing(h->ev_t[0], s));
@@ -792,8 +807,9 @@ fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread)
         threads = 64;
     if (targets_per_thread == 0)
         targets_per_thread = 4;
-    if ((threads != 32 && threads != 64) || (targets_per_thread != 2 && targets_per_thread != 4))
-        return set_err(h, FMM_EINVAL, "tile: threads 32 (one leaf per block) or 64 (two), targets per thread 2 or 4");
+    if ((threads != 32 && threads != 64 && threads != 128) || (targets_per_thread != 2 && targets_per_thread != 4))
+        return set_err(h, FMM_EINVAL,
+                       "tile: threads 32 (one leaf per block), 64 (two) or 128 (symmetric), targets per thread 2 or 4");
     h->p2p_threads = threads;
     h->p2p_kt = targets_per_thread;
     return FMM_OK;
@@ -1104,8 +1120,8 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
             fclose(f);
         }
     }
-    int tiles[][2] = {{64, 4}, {64, 2}, {32, 4}, {32, 2}};
-    int ntile = h->mixed ? 4 : 1;
+    int tiles[][2] = {{64, 4}, {128, 4}, {128, 2}, {64, 2}, {32, 4}, {32, 2}};
+    int ntile = h->mixed ? 6 : 1;
     int save_graph = h->use_graph, save_timing = h->timing;
     h->use_graph = 0;
     h->timing = 0;

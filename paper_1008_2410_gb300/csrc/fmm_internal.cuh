@@ -29,6 +29,12 @@
 #define FMM_DEV_BOUNDS 2u
 #define FMM_DEV_TIMEOUT 4u
 
+// Largest s (leaf width w_L in units of sqrt(2 / log2 e) sigma) at which the near field keeps one float per
+// coordinate in the leaf frame: the rounding of a source coordinate, |x| <= 3 s / 2, relative to sigma grows
+// with s; at s = 13.6 (64 uniform particles per leaf, sigma = h / 2) it costs 7e-8 relative L2 of the near
+// field, so up to s = 32 it stays below 2e-7. Wider leaves take the hi + lo split form.
+#define P2P_SPLIT_S 32.0f
+
 namespace fmm {
 
 // Per-system descriptor, device resident (one per system of a batch; a plain evaluation is a batch of one).
@@ -83,6 +89,10 @@ struct Work {
     int coarse_level;         // levels <= this run in FP64 in the precision form
     int m2l_tc;               // FP32 M2L levels on the tensor cores (1) or on the CUDA cores (0)
     float2 *far32;            // [n] leaf order: FP32 far field (L2P) of the precision form, or null (fused)
+    float2 *nearp;            // [4][n] leaf order: symmetric near field, reactions from the leaf at -P2P
+                              // forward offset d (d = 0..3: (1,0), (1,1), (0,1), (-1,1)), or null
+    int p2p_all_plain;        // host knows every system takes one-float near-field coordinates
+    int p2p_sym;              // this evaluation's near field is the symmetric kernel (nearp holds reactions)
     int nsys;
     int maxdepth;
     // arrays
@@ -159,7 +169,8 @@ int launch_p2m(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t
 int launch_m2m(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
 int launch_m2l(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t s, int prio);
 int launch_l2l(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
-int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);  // threads 32: 1 leaf per block, 64: 2
+int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);  // threads 32: 1 leaf per block, 64: 2,
+                                                                     // 128: symmetric (needs nearp)
 int launch_l2p(const Work &w, cudaStream_t s);  // precision form with far32: far field into far32 (stage 8)
 int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
 int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far

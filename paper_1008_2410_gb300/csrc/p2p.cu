@@ -171,11 +171,6 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 // loses 2^-22.5 / y of its relative accuracy there. r' = 0 (a particle and itself, or coincident particles,
 // which always share a leaf) needs no series: with 1/r'^2 clamped, g (1 - e) / r'^2 = 0 exactly.
 #define P2P_THR 0.72134752044448170f
-// Largest s (leaf width w_L in units of sqrt(2 / log2 e) sigma) at which the near field keeps one float per
-// coordinate in the leaf frame: the rounding of a source coordinate, |x| <= 3 s / 2, relative to sigma grows
-// with s; at s = 13.6 (64 uniform particles per leaf, sigma = h / 2) it costs 7e-8 relative L2 of the near
-// field, so up to s = 32 it stays below 2e-7. Wider leaves take the hi + lo split form.
-#define P2P_SPLIT_S 32.0f
 #define P2P_LN2 0.69314718055994531f
 #ifndef P2P_UNROLL
 #define P2P_UNROLL 1  // source loop unroll of the near-field kernel
@@ -316,7 +311,7 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
 // 2 or 4 targets per lane chosen by the pass size. Sources arrive by bulk copies into shared memory; each
 // target's sum over one tile (plain FP32) is added to its total with an error-free TwoSum.
 template <int LPB>
-__global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, int ktmax)
+__global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, int ktmax, int skip_plain)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -332,6 +327,8 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
     const int myleaf = first + warp;
     const int my_s0 = w.start[myleaf], my_c = w.start[myleaf + 1] - my_s0;
     const bool split = d.s_unit > P2P_SPLIT_S;  // block-uniform; the split form runs 2 targets per lane
+    if (skip_plain && !split)
+        return;  // this system's near field is the symmetric kernel's
     const int per_pass = 32 * (split ? 2 : ktmax);
     int npass = (my_c + per_pass - 1) / per_pass;
     if (LPB == 2) {
@@ -449,6 +446,274 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
     }
 }
 
+// ------------------------------------------------------------------ precision form, symmetric near field
+
+// Each unordered pair of particles in adjacent leaves is evaluated once and acts on both (the kernel is odd:
+// K(-z) = -K(z)). A warp owns a target leaf A and visits A itself and its four "forward" neighbours
+// B = A + c_p2p_fwd[d]; every other adjacent pair of leaves is some other warp's forward pair. Everything is in
+// A's frame (targets rounded once from hi + lo; forward sources shifted by their leaf offset when staged).
+// Sources arrive in chunks of 32, one per lane, in shared memory (A's own particles first, then the forward
+// leaves' particles back to back, so only the stream's ends are padded); in step k of a chunk lane l pairs its
+// KT targets with source (l + k) mod 32, so the 32 lanes meet 32 different sources, and the source's running
+// reaction travels with it (one lane shuffle per step), back at its own lane after 32 steps. The reactions on
+// forward particles go to nearp[d] (written by this warp only, so sums are deterministic); the final sum adds
+// the four backward contributions in a fixed order. Systems whose leaves are wider than the one-float bound
+// (P2P_SPLIT_S) are left to k_p2p32.
+__constant__ int2 c_p2p_fwd[4] = {{1, 0}, {1, 1}, {0, 1}, {-1, 1}};
+
+__device__ __forceinline__ f2 shfl2(f2 v, int src)
+{
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+// One chunk of 32 sources (SH, SG in shared memory) against the lane's KT targets. SELF: the sources are the
+// targets' own leaf (r' = 0 occurs; no reaction). SYM: accumulate the reaction on the source in RU, RV and
+// rotate it with the source.
+template <int KT, bool SELF, bool SYM>
+__device__ __forceinline__ void p2ps_chunk(const float4 *__restrict__ SH, const float4 *__restrict__ SG, int lane,
+                                           const f2 *AX, const f2 *AY, const f2 *GT, const f2 *GTN, f2 *PU, f2 *PV,
+                                           f2 &RU, f2 &RV)
+{
+    constexpr int NP = KT / 2;
+#pragma unroll 1
+    for (int k = 0; k < 32; ++k) {
+        const int m = (lane + k) & 31;
+        const float4 h = SH[m], g = SG[m];
+        const f2 sxh = pk2(h.x, h.y), syh = pk2(h.z, h.w);
+        const f2 gp = pk2(g.x, g.y), gn = pk2(g.z, g.w);
+        f2 dx[NP], dy[NP], e[NP], q[NP], r2[NP];
+        float rmin = 3.0e38f;
+#pragma unroll
+        for (int pr = 0; pr < NP; ++pr) {
+            dx[pr] = sub2(AX[pr], sxh);
+            dy[pr] = sub2(AY[pr], syh);
+            r2[pr] = fma2(dx[pr], dx[pr], mul2(dy[pr], dy[pr]));
+            float ra, rb;
+            up2(r2[pr], ra, rb);
+            e[pr] = pk2(ex2_approx(-ra), ex2_approx(-rb));
+            if (SELF) {
+                q[pr] = pk2(rcp_approx(fmaxf(ra, 1e-30f)), rcp_approx(fmaxf(rb, 1e-30f)));
+                rmin = __uint_as_float(min(__float_as_uint(rmin), min(__float_as_uint(ra) - 1u, __float_as_uint(rb) - 1u)));
+            } else {
+                q[pr] = pk2(rcp_approx(ra), rcp_approx(rb));
+                rmin = fminf(rmin, fminf(ra, rb));
+            }
+        }
+        // rare (0 < r < sigma): the series gives (1 - e) q directly; e := 0, q := series
+        if (__any_sync(0xffffffffu, SELF ? (__float_as_uint(rmin) < __float_as_uint(P2P_THR)) : (rmin < P2P_THR))) {
+#pragma unroll
+            for (int pr = 0; pr < NP; ++pr) {
+                float ra, rb, qa, qb, ea, eb;
+                up2(r2[pr], ra, rb);
+                up2(q[pr], qa, qb);
+                up2(e[pr], ea, eb);
+                if (ra < P2P_THR) {
+                    qa = P2P_LN2 * small_y_factor10(P2P_LN2 * ra);
+                    ea = 0.f;
+                }
+                if (rb < P2P_THR) {
+                    qb = P2P_LN2 * small_y_factor10(P2P_LN2 * rb);
+                    eb = 0.f;
+                }
+                q[pr] = pk2(qa, qb);
+                e[pr] = pk2(ea, eb);
+            }
+        }
+#pragma unroll
+        for (int pr = 0; pr < NP; ++pr) {
+            const f2 gf = mul2(fma2(e[pr], gn, gp), q[pr]);  // gamma_s (1 - e) q
+            PU[pr] = fma2(dy[pr], gf, PU[pr]);                // u accumulates -dy g f: negated at the end
+            PV[pr] = fma2(dx[pr], gf, PV[pr]);
+            if (SYM) {
+                const f2 gr = mul2(fma2(e[pr], GTN[pr], GT[pr]), q[pr]);  // gamma_t (1 - e) q
+                RU = fma2(dy[pr], gr, RU);  // reaction on the source: u += +dy g f, v += -dx g f
+                RV = fma2(dx[pr], gr, RV);
+            }
+        }
+        if (SYM) {  // the source of step k + 1 in this lane sits in lane + 1 now
+            RU = shfl2(RU, (lane + 1) & 31);
+            RV = shfl2(RV, (lane + 1) & 31);
+        }
+    }
+}
+
+#ifndef P2PS_MIN_BLOCKS
+#define P2PS_MIN_BLOCKS 6  // minimum resident 128-thread blocks per SM for the symmetric kernel (80 registers)
+#endif
+
+// Source stream of one target leaf A: A's own particles (padded to a multiple of 32), then the particles of
+// its forward neighbours in order d = 0..3, shifted into A's frame when they are staged. Stream position ->
+// (source index, forward direction d or -1 for A itself, or padding).
+struct SymStream {
+    int a0, ac, selfpad, total;
+    int fb0[4], fpre[5];  // first particle of forward leaf d, prefix of their counts
+    float fsx[4], fsy[4];  // shift of leaf d into A's frame (leaf offset x s)
+};
+
+__device__ __forceinline__ void stream_load(const Work &w, const SymStream &S, int pos, float4 &h, float4 &g,
+                                            int &src, int &dir)
+{
+    src = -1;
+    dir = -1;
+    h = make_float4(-1.0e4f, -1.0e4f, -1.0e4f, -1.0e4f);  // padding: far away, no charge
+    g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pos < S.ac) {
+        src = S.a0 + pos;
+        h = w.eh[src];
+        g = w.eg[src];
+    } else if (pos >= S.selfpad && pos < S.total) {
+        const int f = pos - S.selfpad;
+        // the last leaf d whose prefix is <= f (prefixes never decrease; selects keep S in registers)
+        int dd = 0, fb = S.fb0[0], fp = 0;
+        float sx = S.fsx[0], sy = S.fsy[0];
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+            if (f >= S.fpre[q]) {
+                dd = q;
+                fb = S.fb0[q];
+                fp = S.fpre[q];
+                sx = S.fsx[q];
+                sy = S.fsy[q];
+            }
+        dir = dd;
+        src = fb + (f - fp);
+        const float4 hb = w.eh[src];
+        h = make_float4(hb.x + sx, hb.y + sx, hb.z + sy, hb.w + sy);
+        g = w.eg[src];
+    }
+}
+
+template <int LW>
+__global__ void __launch_bounds__(32 * LW, P2PS_MIN_BLOCKS) k_p2p32s(Work w, int ktmax)
+{
+    __shared__ float4 sh_h[LW][32], sh_g[LW][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int A = blockIdx.x * LW + warp;
+    if (A >= w.nleaf)
+        return;  // warp-uniform; warps never synchronise with each other
+    const int k = w.nsys == 1 ? 0 : find_sys_by_leaf(w.sys, w.nsys, A);
+    const SysDev &d = w.sys[k];
+    if (d.s_unit > P2P_SPLIT_S)
+        return;  // split-coordinate system: k_p2p32
+    const int L = d.depth, ns = 1 << L, local = A - (int)d.leaf0;
+    const int ax = local & (ns - 1), ay = local >> L;
+    SymStream S;
+    S.a0 = w.start[A];
+    S.ac = w.start[A + 1] - S.a0;
+    if (S.ac == 0)
+        return;
+    const float s = d.s_unit, snear = d.snear;
+    const int n = w.n;
+    S.selfpad = (S.ac + 31) & ~31;
+    S.fpre[0] = 0;
+#pragma unroll
+    for (int dd = 0; dd < 4; ++dd) {
+        const int2 o = c_p2p_fwd[dd];
+        const int bx = ax + o.x, by = ay + o.y;
+        int cnt = 0, b0 = 0;
+        if (bx >= 0 && bx < ns && by < ns) {
+            const int B = (int)d.leaf0 + by * ns + bx;
+            b0 = w.start[B];
+            cnt = w.start[B + 1] - b0;
+        }
+        S.fb0[dd] = b0;
+        S.fpre[dd + 1] = S.fpre[dd] + cnt;
+        S.fsx[dd] = (float)o.x * s;
+        S.fsy[dd] = (float)o.y * s;
+    }
+    S.total = S.selfpad + S.fpre[4];
+    float4 *SH = sh_h[warp], *SG = sh_g[warp];
+    const int per_pass = 32 * ktmax;
+    const int np = (S.ac + per_pass - 1) / per_pass;
+    for (int pass = 0; pass < np; ++pass) {
+        const int t_lo = (int)((int64_t)pass * S.ac / np);
+        const int t_cnt = (int)((int64_t)(pass + 1) * S.ac / np) - t_lo;
+        const int kt = t_cnt <= 64 ? 2 : 4;
+        const int tbase = S.a0 + t_lo;
+        // the lane's targets in A's frame, one float per coordinate; charges (and negated) per packed pair
+        f2 AX[2], AY[2], GT[2], GTN[2];
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+            float hx[2], hy[2], gv[2];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int e = lane + 32 * (2 * pr + hh);
+                if (e < t_cnt) {
+                    const float4 th = w.eh[tbase + e], tl = w.el[tbase + e];
+                    hx[hh] = th.x + tl.x;
+                    hy[hh] = th.z + tl.z;
+                    gv[hh] = w.eg[tbase + e].x;
+                } else {
+                    hx[hh] = 1.0e4f;  // padding target: far away, no charge
+                    hy[hh] = 1.0e4f;
+                    gv[hh] = 0.f;
+                }
+            }
+            AX[pr] = pk2(hx[0], hx[1]);
+            AY[pr] = pk2(hy[0], hy[1]);
+            GT[pr] = pk2(gv[0], gv[1]);
+            GTN[pr] = pk2(-gv[0], -gv[1]);
+        }
+        f2 SU[2] = {0ull, 0ull}, CU[2] = {0ull, 0ull}, SV[2] = {0ull, 0ull}, CV[2] = {0ull, 0ull};
+        float4 nh, ng;
+        int nsrc, ndir;
+        stream_load(w, S, lane, nh, ng, nsrc, ndir);
+        for (int c0 = 0; c0 < S.total; c0 += 32) {
+            const int src = nsrc, dir = ndir;
+            __syncwarp();  // the previous chunk is no longer read
+            SH[lane] = nh;
+            SG[lane] = ng;
+            __syncwarp();
+            if (c0 + 32 < S.total)
+                stream_load(w, S, c0 + 32 + lane, nh, ng, nsrc, ndir);  // next chunk, in flight meanwhile
+            f2 PU[2] = {0ull, 0ull}, PV[2] = {0ull, 0ull}, RU = 0ull, RV = 0ull;
+            if (c0 < S.selfpad) {
+                if (kt == 2)
+                    p2ps_chunk<2, true, false>(SH, SG, lane, AX, AY, GT, GTN, PU, PV, RU, RV);
+                else
+                    p2ps_chunk<4, true, false>(SH, SG, lane, AX, AY, GT, GTN, PU, PV, RU, RV);
+            } else {
+                if (kt == 2)
+                    p2ps_chunk<2, false, true>(SH, SG, lane, AX, AY, GT, GTN, PU, PV, RU, RV);
+                else
+                    p2ps_chunk<4, false, true>(SH, SG, lane, AX, AY, GT, GTN, PU, PV, RU, RV);
+                if (dir >= 0) {  // reaction on this lane's source (pass 0 writes, later passes add)
+                    float ru0, ru1, rv0, rv1;
+                    up2(RU, ru0, ru1);
+                    up2(RV, rv0, rv1);
+                    float2 r = make_float2((ru0 + ru1) * snear, -(rv0 + rv1) * snear);
+                    float2 *dst = w.nearp + (int64_t)dir * n + src;
+                    if (pass > 0) {
+                        const float2 old = *dst;
+                        r.x += old.x;
+                        r.y += old.y;
+                    }
+                    *dst = r;
+                }
+            }
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                two_sum2(SU[pr], CU[pr], PU[pr]);
+                two_sum2(SV[pr], CV[pr], PV[pr]);
+            }
+        }
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+            float su[2], cu[2], svv[2], cv[2];
+            up2(SU[pr], su[0], su[1]);
+            up2(CU[pr], cu[0], cu[1]);
+            up2(SV[pr], svv[0], svv[1]);
+            up2(CV[pr], cv[0], cv[1]);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int e = lane + 32 * (2 * pr + hh);
+                if (e < t_cnt)
+                    w.near32[tbase + e] = make_float2(-(su[hh] + cu[hh]) * snear, (svv[hh] + cv[hh]) * snear);
+            }
+        }
+    }
+}
+
 int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
 {
     if (w.nleaf == 0)
@@ -458,14 +723,27 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
         return 1;
     }
     int ktmax = kt == 2 ? 2 : 4;
+    int nl = 0;
+    if (threads == 128 && w.p2p_sym) {
+        // symmetric near field for the one-float systems; k_p2p32 only where a system may need split coordinates
+        constexpr int LW = 4;
+        k_p2p32s<LW><<<(w.nleaf + LW - 1) / LW, 32 * LW, 0, s>>>(w, ktmax);
+        ++nl;
+        if (!w.p2p_all_plain) {
+            const int tile = 256;
+            k_p2p32<1><<<w.nleaf, 32, (size_t)tile * 48, s>>>(w, tile, 2, 1);
+            ++nl;
+        }
+        return nl;
+    }
     // two leaves per block needs every system's leaves to pair up within rows (depth >= 1)
     bool pairs = threads == 64 && w.lv.nsys_at[1] == w.nsys;
     int tile = pairs ? 320 : 256;
     size_t sm = (size_t)tile * 48;
     if (pairs)
-        k_p2p32<2><<<(w.nleaf + 1) / 2, 64, sm, s>>>(w, tile, ktmax);
+        k_p2p32<2><<<(w.nleaf + 1) / 2, 64, sm, s>>>(w, tile, ktmax, 0);
     else
-        k_p2p32<1><<<w.nleaf, 32, sm, s>>>(w, tile, ktmax);
+        k_p2p32<1><<<w.nleaf, 32, sm, s>>>(w, tile, ktmax, 0);
     return 1;
 }
 

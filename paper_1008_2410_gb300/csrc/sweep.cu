@@ -718,6 +718,24 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
             fv = -s.im * fs;
         }
         float2 t = use_near ? w.near32[pos] : make_float2(0.f, 0.f);
+        if (use_near && w.p2p_sym && d.s_unit <= P2P_SPLIT_S) {
+            // symmetric near field: add the reactions from the four backward neighbour leaves, fixed order
+            const int ns = 1 << L, local = (int)(w.sleaf[pos] - d.leaf0);
+            const int ix = local & (ns - 1), iy = local >> L;
+            const int2 fwd[4] = {{1, 0}, {1, 1}, {0, 1}, {-1, 1}};
+#pragma unroll
+            for (int dd = 0; dd < 4; ++dd) {
+                const int ax = ix - fwd[dd].x, ay = iy - fwd[dd].y;
+                if (ax < 0 || ax >= ns || ay < 0)
+                    continue;
+                const int A = (int)d.leaf0 + ay * ns + ax;
+                if (w.start[A + 1] == w.start[A])
+                    continue;  // empty leaf: its warp wrote nothing
+                const float2 r = w.nearp[(int64_t)dd * w.n + pos];
+                t.x += r.x;
+                t.y += r.y;
+            }
+        }
         u[i] = (double)(t.x + fu);
         v[i] = (double)(t.y + fv);
         return;

@@ -86,7 +86,23 @@ def test_mixed_matches_oracle_fmm(lib, oracle, name, make):
         assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < TOL32, coarse
 
 
-@pytest.mark.parametrize("tile", [(64, 4), (64, 2), (32, 4), (32, 2)])
+@pytest.mark.parametrize("domain", ["explicit", "bbox"])
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_mixed_symmetric_near_field_matches_oracle(lib, oracle, name, make, domain):
+    """Tile 128: each adjacent pair evaluated once and applied to both particles (depth 0 and 1 have leaves wider
+    than the one-float bound and go through the target-side kernel; with the bounding-box rule both kernels
+    are launched)."""
+    w = make()
+    dom = w.domain if domain == "explicit" else None
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=dom)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=dom)
+    f.set_p2p_tile(128, 4)
+    u, v = f.velocity(dev(w.x), dev(w.y), dev(w.gamma))
+    f.sync()
+    assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < TOL32
+
+
+@pytest.mark.parametrize("tile", [(64, 4), (64, 2), (32, 4), (32, 2), (128, 4), (128, 2)])
 def test_mixed_tile_shapes(lib, oracle, tile):
     w = fi.clustered(30000, depth=4, p=12)  # dense leaves: several target chunks and source tiles per leaf
     uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)
@@ -161,6 +177,13 @@ def test_deterministic_and_graph_replay_identical(lib, precision):
     u1, v1 = f.velocity(x, y, g)
     u2, v2 = f.velocity(x, y, g)
     fg = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain, graph=True)
+    if precision == "mixed":  # also the symmetric near field (reactions summed in a fixed order)
+        fs = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain)
+        fs.set_p2p_tile(128, 4)
+        us1, vs1 = fs.velocity(x, y, g)
+        us2, vs2 = fs.velocity(x, y, g)
+        torch.cuda.synchronize()
+        assert torch.equal(us1, us2) and torch.equal(vs1, vs2)
     u3, v3 = fg.velocity(x, y, g)
     u4, v4 = fg.velocity(x, y, g)  # replay
     torch.cuda.synchronize()

@@ -14,6 +14,7 @@ compiles it with gcc and exposes thin numpy wrappers. Every function follows the
                          adjacent leaves, the point-vortex kernel for all other pairs
 * ``fmm``             -- the serial FMM of Fig. 1, stages 1-10, with the §3 multipole coefficients
 * ``fmm_adjoint``     -- gradient of sum(gu*u + gv*v) by the transposed stages in reverse order
+* ``advect``          -- Eq. 3: particles moved with the FMM or direct-sum velocity, Runge-Kutta order 2 or 4
 * ``p2m, m2m, m2l, l2l, l2p, multipole_eval`` -- the single-box expansion operations used by ``fmm``
 
 Pins (tests marked ``not gpu``): brute force on tiny inputs, the Lamb-Oseen closed form, impulse invariants,
@@ -84,6 +85,9 @@ def _load():
         lib.oracle_fmm_adjoint.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, _D, _D, _D, _D, _D, _D]
         lib.oracle_fmm_adjoint.restype = ctypes.c_int
+        lib.oracle_advect.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int, _D,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.oracle_advect.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -248,3 +252,19 @@ def fmm_adjoint(x, y, gamma, sigma: float, depth: int, p: int, gu, gv, domain=No
     if rc != 0:
         raise ValueError("oracle_fmm_adjoint failed")
     return dg, dx, dy
+
+
+def advect(x, y, gamma, sigma: float, depth: int, p: int, dt: float, nsteps: int, order: int = 2,
+           domain=None, velocity: str = "fmm"):
+    """Eq. 3: nsteps explicit Runge-Kutta steps (order 2: midpoint rule; order 4: classical) of the particles,
+    each stage's velocity from the FMM (``velocity="fmm"``) or the direct sum (``"direct"``). Returns new
+    (x, y); circulations are unchanged."""
+    xs, ys, g = _f64(x).copy(), _f64(y).copy(), _f64(gamma)
+    mode = {"fmm": 0, "direct": 1}[velocity]
+    rc = _load().oracle_advect(xs.size, _ptr(xs), _ptr(ys), _ptr(g), float(sigma), int(depth), int(p),
+                               _ptr(_dom(domain)), float(dt), int(nsteps), int(order), mode)
+    if rc == -1:
+        raise ValueError("point outside the root square")
+    if rc != 0:
+        raise RuntimeError(f"oracle_advect failed ({rc})")
+    return xs, ys

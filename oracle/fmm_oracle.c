@@ -13,6 +13,7 @@
  *   §3      multipole coefficient m:  a_m = (-i / 2pi) sum_p Gamma_p (z_p - z_c)^m,  t terms (m = 0 .. t-1)
  *   Fig. 1  stages 1 tree, 2 binning, 3 interaction lists, 4 P2M, 5 M2M, 6 M2L, 7 L2L, 8 L2P,
  *           9 near-field direct evaluation, 10 sum
+ *   Eq. 3   (2D Euler) the particles move with the local velocity and keep their circulation
  *
  * Complex velocity: w = u - i v. For a point vortex, u - i v = q / (z - z_j) with q = -i gamma / (2 pi),
  * which is Eq. 6 without the Gaussian factor. Coefficients here are the plain (unscaled) ones of the
@@ -788,4 +789,72 @@ int oracle_fmm_adjoint(int64_t n, const double *x, const double *y, const double
     free(rdy);
     tree_free(&t);
     return 0;
+}
+
+/* ---------------------------------------------------------------- Eq. 3: advection of the particles */
+
+/* In 2D ideal flow the vorticity is constant along particle paths (Eq. 3): the particles move with the local
+ * velocity (Eq. 7, or the FMM approximation of it) and keep their circulation. The paper names no time
+ * integrator; taken here: explicit Runge-Kutta of order 2 (the midpoint rule) or 4 (the classical scheme),
+ *   stage s:   k_s = u(z + c_s dt k_{s-1}),     z <- z + dt sum_s b_s k_s,
+ *   order 2:   c = (0, 1/2),          b = (0, 1)
+ *   order 4:   c = (0, 1/2, 1/2, 1),  b = (1/6, 1/3, 1/3, 1/6)
+ * with the stage velocity from the FMM (mode 0, at depth L and p terms, root square dom or the bounding-box
+ * rule recomputed per stage) or from the direct sum (mode 1). x, y are updated in place.
+ * Returns 0, -1 for a point outside an explicit square, -2 on allocation failure, -3 for bad arguments. */
+int oracle_advect(int64_t n, double *x, double *y, const double *g, double sigma, int L, int p, const double *dom,
+                  double dt, int nsteps, int order, int mode)
+{
+    static const double c2[2] = {0.0, 0.5}, b2[2] = {0.0, 1.0};
+    static const double c4[4] = {0.0, 0.5, 0.5, 1.0}, b4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    if ((order != 2 && order != 4) || (mode != 0 && mode != 1) || n < 0 || nsteps < 0)
+        return -3;
+    if (n == 0)
+        return 0;
+    const int S = order == 2 ? 2 : 4;
+    const double *c = order == 2 ? c2 : c4, *b = order == 2 ? b2 : b4;
+    double *tx = malloc((size_t)n * sizeof(double)), *ty = malloc((size_t)n * sizeof(double));
+    double *ku = malloc((size_t)n * sizeof(double)), *kv = malloc((size_t)n * sizeof(double));
+    double *au = malloc((size_t)n * sizeof(double)), *av = malloc((size_t)n * sizeof(double));
+    int rc = 0;
+    if (!tx || !ty || !ku || !kv || !au || !av)
+        rc = -2;
+    for (int step = 0; step < nsteps && rc == 0; ++step) {
+        for (int64_t i = 0; i < n; ++i) {
+            tx[i] = x[i];
+            ty[i] = y[i];
+            au[i] = 0.0;
+            av[i] = 0.0;
+        }
+        for (int st = 0; st < S && rc == 0; ++st) {
+            if (mode == 1) {
+                oracle_direct(n, tx, ty, g, sigma, n, NULL, ku, kv);
+            } else {
+                int64_t npairs = 0;
+                rc = oracle_fmm(n, tx, ty, g, sigma, L, p, dom, n, NULL, ku, kv, &npairs);
+                if (rc != 0)
+                    break;
+            }
+            for (int64_t i = 0; i < n; ++i) {
+                au[i] += b[st] * ku[i];
+                av[i] += b[st] * kv[i];
+                if (st + 1 < S) {
+                    tx[i] = x[i] + c[st + 1] * dt * ku[i];
+                    ty[i] = y[i] + c[st + 1] * dt * kv[i];
+                }
+            }
+        }
+        if (rc == 0)
+            for (int64_t i = 0; i < n; ++i) {
+                x[i] += dt * au[i];
+                y[i] += dt * av[i];
+            }
+    }
+    free(tx);
+    free(ty);
+    free(ku);
+    free(kv);
+    free(au);
+    free(av);
+    return rc;
 }

@@ -411,3 +411,68 @@ def test_adjoint_direct_limit_matches_autograd(oracle):
     for got, ref in ((dg, g.grad), (dx, x.grad), (dy, y.grad)):
         ref = ref.numpy()
         assert np.max(np.abs(got - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------------------- Eq. 3 (advection)
+
+
+def _exact_pair_rotation(x, y, g, T):
+    """Two point vortices rotate rigidly about their centre of vorticity at Omega = (g1 + g2) / (2 pi d^2)."""
+    d2 = (x[1] - x[0]) ** 2 + (y[1] - y[0]) ** 2
+    om = (g[0] + g[1]) / (2 * math.pi * d2)
+    cx, cy = np.dot(g, x) / g.sum(), np.dot(g, y) / g.sum()
+    c, s = math.cos(om * T), math.sin(om * T)
+    return cx + c * (x - cx) - s * (y - cy), cy + s * (x - cx) + c * (y - cy)
+
+
+def test_advect_two_vortices_closed_form_and_order(oracle):
+    """Blobs far apart (d = 100 sigma: Gaussian factor e^-5000) move as point vortices; RK errors fall by 4
+    (order 2) and 16 (order 4) when dt halves, and RK4 reaches the closed form."""
+    x, y, g = np.array([0.0, 1.0]), np.array([0.0, 0.0]), np.array([1.0, 0.5])
+    T = 0.5 * 2 * math.pi / (g.sum())  # half a radian
+    ex, ey = _exact_pair_rotation(x, y, g, T)
+    for order, ratio in ((2, 4.0), (4, 16.0)):
+        errs = []
+        for nst in (10, 20, 40):
+            xs, ys = oracle.advect(x, y, g, 0.01, 0, 1, T / nst, nst, order=order, velocity="direct")
+            errs.append(np.hypot(xs - ex, ys - ey).max())
+        assert errs[0] / errs[1] == pytest.approx(ratio, rel=0.1) and errs[1] / errs[2] == pytest.approx(ratio, rel=0.1)
+        if order == 4:
+            assert errs[2] < 1e-9
+
+
+def test_advect_lamb_oseen_lattice_rotates_rigidly(oracle):
+    """The blob lattice of a Lamb-Oseen vortex (R12) keeps its axisymmetric field while it moves: every particle
+    turns on its circle at u_theta(r)/r of the Lamb-Oseen closed form with r_c'^2 = r_c^2 + 2 sigma^2."""
+    n1, rc = 64, 0.2
+    h = 2.0 / n1
+    sigma = 2 * h
+    g1 = -1 + (np.arange(n1) + 0.5) * h
+    X, Y = np.meshgrid(g1, g1)
+    x, y = X.ravel(), Y.ravel()
+    r2 = x * x + y * y
+    gam = h * h * np.exp(-r2 / (rc * rc)) / (math.pi * rc * rc)
+    r = np.sqrt(r2)
+    om = (1 - np.exp(-r2 / (rc * rc + 2 * sigma * sigma))) / (2 * math.pi * r2)
+    T = 0.02
+    ex, ey = np.cos(om * T) * x - np.sin(om * T) * y, np.sin(om * T) * x + np.cos(om * T) * y
+    xs, ys = oracle.advect(x, y, gam, sigma, 0, 1, T / 8, 8, order=4, velocity="direct")
+    assert np.hypot(xs - ex, ys - ey).max() < 1e-11  # displacements up to 0.009
+    e2 = []
+    for nst in (8, 16):
+        xs, ys = oracle.advect(x, y, gam, sigma, 0, 1, T / nst, nst, order=2, velocity="direct")
+        e2.append(np.hypot(xs - ex, ys - ey).max())
+    assert e2[0] / e2[1] == pytest.approx(4.0, rel=0.1)
+
+
+def test_advect_fmm_conserves_linear_impulse(oracle):
+    """The truncated FMM operator is antisymmetric, so sum gamma_i u_i = 0 at every stage and every Runge-Kutta
+    step keeps sum gamma_i z_i to rounding."""
+    w = fi.uniform(3000, seed_index=81, depth=3, p=12)
+    g = w.gamma
+    for order in (2, 4):
+        xs, ys = oracle.advect(w.x, w.y, g, w.sigma, w.depth, w.p, 2e-3, 3, order=order, domain=None)
+        scale = np.abs(g).sum()
+        assert abs(np.dot(g, xs) - np.dot(g, w.x)) < 1e-15 * scale
+        assert abs(np.dot(g, ys) - np.dot(g, w.y)) < 1e-15 * scale
+        assert np.hypot(xs - w.x, ys - w.y).max() > 1e-9  # the particles did move

@@ -210,6 +210,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
 
     if args.precision == "mixed":
         out["m2l"] = m2l_leg(api, w, x, y, g, args.steps, flush, stream)
+    out["advect"] = advect_leg(api, w, x, y, g, tuned, args.precision, flush, stream)
 
     # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
     f.set_count_pairs(True)
@@ -371,6 +372,39 @@ def m2l_leg(api, w, x, y, g, steps, flush, stream) -> dict:
             "tensor_flops_executed": tc_flops, "achieved_tensor_tflops": tc_flops / t / 1e12,
             "peak_tf32_tflops": peak, "frac_tensor": tc_flops / t / 1e12 / peak, "peak_note": peak_note,
             "timing": "stage events around the M2L launch in far-field-only evaluations, L2 flushed"}
+
+
+def advect_leg(api, w, x, y, g, tuned, precision, flush, stream) -> dict:
+    """Eq. 3 time stepping through fmm_advect: RK2 (midpoint) steps of the whole workload, two evaluations per
+    step, graph replay, bounding-box root square (particles may leave the unit square); dt moves the fastest
+    particle by 0.05 sigma per step."""
+    import statistics as st_
+
+    import torch
+
+    fa = api.FMM(w.depth, w.p, w.sigma, precision=precision, graph=True)
+    fa.set_p2p_tile(tuned["p2p_threads"], tuned["p2p_targets_per_thread"])
+    if precision == "mixed":
+        fa.set_m2l_engine(tuned["m2l_engine"])
+    u, v = fa.velocity(x, y, g)
+    dt = 0.05 * w.sigma / float(torch.sqrt(u * u + v * v).max())
+    xs, ys = x.clone(), y.clone()
+    fa.advect(xs, ys, g, dt, 2, 2)  # warm-up (captures the graph)
+    steps, ts = 3, []
+    for _ in range(5):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fa.advect(xs, ys, g, dt, steps, 2)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / steps)
+    fa.sync()
+    fa.close()
+    ms = st_.median(ts)
+    return {"scheme": "RK2 midpoint (2 evaluations per step)", "ms_per_step": ms,
+            "value": w.n / (ms / 1e3) / 1e6, "unit": "Mparticle-steps/s", "dt": dt}
 
 
 def cpu_baseline(w, u_gpu, v_gpu) -> dict:

@@ -152,6 +152,17 @@ fmm_status fmm_velocity_batched(fmm_handle h, int nsys, const int64_t *offsets, 
                                 const double *sigmas, const double *domains, const double *x, const double *y,
                                 const double *gamma, double *u, double *v);
 
+/* Particle advection, §2 Eq. 3: in 2D ideal flow the particles move with their velocity (Eq. 7, evaluated by
+ * this handle's FMM in its current configuration) and keep their circulation. Runs nsteps explicit
+ * Runge-Kutta steps of size dt, order 2 (the midpoint rule) or 4 (the classical scheme; the paper names no
+ * integrator), each stage one evaluation. x, y: device arrays of n doubles in any order, updated in place;
+ * gamma: device, unchanged. Scratch of 6 n doubles is owned by the handle and reused. With an explicit root
+ * square, a particle that leaves it makes the next evaluation report FMM_EINVAL (device flag, seen by the
+ * next call or fmm_sync). Asynchronous on the handle's stream. FMM_EINVAL for order other than 2 or 4,
+ * nsteps < 0 or a non-finite dt. */
+fmm_status fmm_advect(fmm_handle h, int64_t n, double *x, double *y, const double *gamma, double dt, int nsteps,
+                      int order);
+
 /* Waits for all work of the handle and returns the first device-side error since the last check. */
 fmm_status fmm_sync(fmm_handle h);
 

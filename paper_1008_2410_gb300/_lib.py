@@ -44,6 +44,7 @@ SIGNATURES = {
     "fmm_velocity_far": (_I, [_P, _I64, _P, _P, _P, _P, _P]),
     "fmm_velocity_adjoint": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fmm_velocity_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "fmm_advect": (_I, [_P, _I64, _P, _P, _P, _D, _I, _I]),
     "fmm_sync": (_I, [_P]),
     "fmm_set_timing": (_I, [_P, _I]),
     "fmm_stage_times": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),

@@ -134,6 +134,12 @@ class FMM:
         """Stages 4-8 alone: the expansions' point-vortex field of all non-adjacent leaves."""
         return self._call(self._lib.fmm_velocity_far, x, y, gamma, u, v)
 
+    def advect(self, x, y, gamma, dt: float, nsteps: int, order: int = 2) -> None:
+        """Eq. 3: nsteps Runge-Kutta steps (order 2 or 4) of the particles, x and y (CUDA float64) in place."""
+        self._stream()
+        check(self._lib.fmm_advect(self.h, x.numel(), _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"), float(dt),
+                                   int(nsteps), int(order)), self.h)
+
     def velocity_host(self, x, y, gamma, u=None, v=None):
         """Same as velocity() for CPU tensors: copies in and out inside the library, synchronous."""
         n = x.numel()

@@ -71,6 +71,8 @@ struct fmm_ctx {
     void *tab = nullptr;
     void *tab_tc = nullptr;  // tensor-core M2L operand table
     size_t tab_tc_cap = 0;
+    double *adv = nullptr;  // advection scratch: stage positions, stage velocity, accumulated increment (6 n)
+    size_t adv_cap = 0;
     Tables t{};
     int tab_p = -1;
     // host-visible status
@@ -718,6 +720,8 @@ fmm_status fmm_destroy(fmm_handle h)
         cudaFree(h->tab);
     if (h->tab_tc)
         cudaFree(h->tab_tc);
+    if (h->adv)
+        cudaFree(h->adv);
     if (h->d_io)
         cudaFree(h->d_io);
     if (h->h_status)
@@ -845,6 +849,48 @@ fmm_status fmm_velocity(fmm_handle h, int64_t n, const double *x, const double *
                         double *v)
 {
     return velocity_mode(h, MODE_FULL, n, x, y, gamma, u, v);
+}
+
+fmm_status fmm_advect(fmm_handle h, int64_t n, double *x, double *y, const double *gamma, double dt, int nsteps,
+                      int order)
+{
+    fmm_status st = check_common(h, n, x, y, gamma, x, y);
+    if (st != FMM_OK)
+        return st;
+    if ((order != 2 && order != 4) || nsteps < 0 || !std::isfinite(dt))
+        return set_err(h, FMM_EINVAL, "advect: order 2 or 4, nsteps >= 0, finite dt");
+    if ((st = poll_status(h, false)) != FMM_OK)
+        return st;
+    if (n == 0 || nsteps == 0)
+        return FMM_OK;
+    const size_t need = (size_t)6 * (size_t)n;
+    if (need > h->adv_cap) {
+        if (h->adv)
+            CU(cudaFree(h->adv));
+        h->adv = nullptr;
+        h->adv_cap = 0;
+        if (cudaMalloc(&h->adv, need * sizeof(double)) != cudaSuccess)
+            return set_err(h, FMM_ENOMEM, "advect scratch (%zu bytes)", need * sizeof(double));
+        h->adv_cap = need;
+    }
+    double *tx = h->adv, *ty = tx + n, *su = ty + n, *sv = su + n, *au = sv + n, *av = au + n;
+    static const double c2[2] = {0.0, 0.5}, b2[2] = {0.0, 1.0};
+    static const double c4[4] = {0.0, 0.5, 0.5, 1.0}, b4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const int S = order == 2 ? 2 : 4;
+    const double *c = order == 2 ? c2 : c4, *b = order == 2 ? b2 : b4;
+    for (int step = 0; step < nsteps; ++step) {
+        // every stage evaluates at (tx, ty) -> (su, sv): the same pointers each time, so a graph replays
+        CU(cudaMemcpyAsync(tx, x, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(ty, y, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        for (int s = 0; s < S; ++s) {
+            if ((st = velocity_mode(h, MODE_FULL, n, tx, ty, gamma, su, sv)) != FMM_OK)
+                return st;
+            h->launches += launch_rk_stage(n, x, y, tx, ty, su, sv, au, av, b[s], s + 1 < S ? c[s + 1] : 0.0, dt,
+                                           s == 0, s + 1 == S, h->stream);
+            CU(cudaGetLastError());
+        }
+    }
+    return FMM_OK;
 }
 
 fmm_status fmm_velocity_near(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,

@@ -171,6 +171,8 @@ int launch_m2l(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t
 int launch_l2l(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
 int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);  // threads 32: 1 leaf per block, 64: 2,
                                                                      // 128: symmetric (needs nearp)
+int launch_rk_stage(int64_t n, double *x, double *y, double *tx, double *ty, const double *u, const double *v,
+                    double *au, double *av, double b, double c_next, double dt, int first, int last, cudaStream_t s);
 int launch_l2p(const Work &w, cudaStream_t s);  // precision form with far32: far field into far32 (stage 8)
 int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
 int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far

@@ -383,3 +383,63 @@ def test_patches_16m_sampled_parity(lib, oracle):
     t = fi.sample_targets(w.n, 512)
     uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, targets=t)
     assert rel_l2((u[t], v[t]), (uo, vo)) < TOL32
+
+
+# ---------------------------------------------------------------------------------------- Eq. 3 (advection)
+
+
+def _advect_case():
+    w = fi.uniform(20000, seed_index=82, depth=4, p=14)
+    return w
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_advect_matches_oracle(lib, oracle, order, precision, tol):
+    """Runge-Kutta steps of the particles (Eq. 3) with FMM velocities: displacement against the oracle's same
+    scheme, bounding-box root square recomputed at every stage on both sides."""
+    w = _advect_case()
+    u0, v0, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=None)
+    dt = 0.05 * w.sigma / float(np.hypot(u0, v0).max())
+    nsteps = 3
+    xo, yo = oracle.advect(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, dt, nsteps, order=order, domain=None)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision=precision)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    f.advect(x, y, g, dt, nsteps, order)
+    f.sync()
+    dx, dy = x.cpu().numpy() - w.x, y.cpu().numpy() - w.y
+    assert rel_l2((dx, dy), (xo - w.x, yo - w.y)) < tol
+    if precision == "fp64":  # linear impulse: sum gamma_i u_i = 0 at every stage
+        assert abs(np.dot(w.gamma, dx)) < 1e-12 * np.dot(np.abs(w.gamma), np.abs(dx))
+        assert abs(np.dot(w.gamma, dy)) < 1e-12 * np.dot(np.abs(w.gamma), np.abs(dy))
+
+
+def test_advect_lamb_oseen_lattice_and_graph_replay(lib, oracle):
+    """The Lamb-Oseen lattice in its explicit square [-1, 1]^2 (FP64 form) follows the oracle's RK4 steps; a
+    graph-replayed handle gives the same bits as an eager one."""
+    w = fi.lattice_lamb_oseen()
+    dt, nsteps = 0.01, 2
+    xo, yo = oracle.advect(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, dt, nsteps, order=4, domain=w.domain)
+    outs = []
+    for graph in (False, True):
+        f = lib.FMM(w.depth, w.p, w.sigma, domain=w.domain, graph=graph)
+        x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+        f.advect(x, y, g, dt, nsteps, 4)
+        f.sync()
+        outs.append((x, y))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    dx, dy = outs[0][0].cpu().numpy() - w.x, outs[0][1].cpu().numpy() - w.y
+    assert rel_l2((dx, dy), (xo - w.x, yo - w.y)) < 1e-10
+
+
+def test_advect_rejects_bad_arguments(lib):
+    w = fi.uniform(100, seed_index=83, depth=2, p=8)
+    f = lib.FMM(w.depth, w.p, w.sigma)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    from paper_1008_2410_gb300._lib import FMMError
+
+    for args in ((0.1, 1, 3), (0.1, -1, 2), (float("nan"), 1, 2)):
+        with pytest.raises(FMMError):
+            f.advect(x, y, g, *args)
+    f.advect(x, y, g, 0.1, 0, 2)  # zero steps: nothing happens
+    assert torch.equal(x, dev(w.x))

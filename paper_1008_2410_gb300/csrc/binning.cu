@@ -378,8 +378,86 @@ __global__ void __launch_bounds__(1024) k_scan_single(const int *__restrict__ in
         out[nin] = carry_sh;
 }
 
+// Up to 16384 counts: thread t owns the 16 consecutive counts from 16 t, all loaded at once (one memory round
+// trip), then a block-wide exclusive scan of the per-thread sums. out[nin] = total.
+__global__ void __launch_bounds__(1024) k_scan_16k(const int *__restrict__ in, int nin, int *__restrict__ out)
+{
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, b0 = 16 * t;
+    int v[16];
+    if (b0 + 16 <= nin) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int4 a = reinterpret_cast<const int4 *>(in + b0)[q];
+            v[4 * q] = a.x;
+            v[4 * q + 1] = a.y;
+            v[4 * q + 2] = a.z;
+            v[4 * q + 3] = a.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            v[j] = b0 + j < nin ? in[b0 + j] : 0;
+    }
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        s += v[j];
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += u;
+    }
+    if (lane == 31)
+        wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const int ws = wsum[lane];
+        int wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o)
+                wi += u;
+        }
+        wsum[lane] = wi - ws;
+    }
+    __syncthreads();
+    int ex = wsum[wid] + inc - s;
+    if (b0 + 16 <= nin) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int4 a;
+            a.x = ex;
+            ex += v[4 * q];
+            a.y = ex;
+            ex += v[4 * q + 1];
+            a.z = ex;
+            ex += v[4 * q + 2];
+            a.w = ex;
+            ex += v[4 * q + 3];
+            reinterpret_cast<int4 *>(out + b0)[q] = a;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (b0 + j < nin)
+                out[b0 + j] = ex;
+            ex += v[j];
+        }
+    }
+    if (t == 1023)
+        out[nin] = ex;  // the total (the padding counts are zero)
+}
+
 int launch_scan(const Work &w, cudaStream_t s)
 {
+    if (w.nleaf <= 16384) {
+        k_scan_16k<<<1, 1024, 0, s>>>(w.cnt, w.nleaf, w.start);
+        return 1;
+    }
     if (w.nleaf <= 65536) {
         k_scan_single<<<1, 1024, 0, s>>>(w.cnt, w.nleaf, w.start);
         return 1;

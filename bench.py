@@ -220,7 +220,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     p2p_avg = statistics.mean(p2p_ms) if p2p_ms else None
     achieved = P2P_FLOPS_PER_PAIR * pairs / (p2p_avg / 1e3) / 1e12 if p2p_avg else None
     traffic = None
-    tr_path = os.path.join(ROOT, "profiles", f"k_p2p32_{args.workload}.txt")
+    kname = "k_p2p32s" if tuned["p2p_threads"] == 128 else "k_p2p32"
+    tr_path = os.path.join(ROOT, "profiles", f"{kname}_{args.workload}.txt")
     if args.precision == "mixed" and os.path.exists(tr_path):
         try:
             import hashlib
@@ -231,7 +232,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
                 traffic = float(rec["dram_bytes_per_launch"])
         except Exception:
             traffic = None
-    out["roofline"] = {"bound": "alu", "kernel": "k_p2p32 (near field, stage 9)" if args.precision == "mixed"
+    out["roofline"] = {"bound": "alu", "kernel": (f"{kname} (near field, stage 9, tile {tuned['p2p_threads']}x"
+                                                   f"{tuned['p2p_targets_per_thread']})") if args.precision == "mixed"
                        else "k_p2p64 (near field, stage 9)",
                        "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                        "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": traffic,

@@ -190,9 +190,11 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         return out
 
     # exposed sweep: full evaluation minus the near-field-only evaluation (same launch configuration)
-    ms_near, _ = timed_steps(lambda: f.velocity_near(x, y, g, u, v), args.steps, flush, stream)
-    ms_far, _ = timed_steps(lambda: f.velocity_far(x, y, g, u, v), args.steps, flush, stream)
-    t_full = statistics.median(ms)
+    nrep = max(20, args.steps)  # medians of at least 20 graph replays
+    ms_near, _ = timed_steps(lambda: f.velocity_near(x, y, g, u, v), nrep, flush, stream)
+    ms_far, _ = timed_steps(lambda: f.velocity_far(x, y, g, u, v), nrep, flush, stream)
+    ms_full = ms if len(ms) >= 20 else timed_steps(step, nrep, flush, stream)[0]
+    t_full = statistics.median(ms_full)
     t_near = statistics.median(ms_near)
     t_far = statistics.median(ms_far)
     f.set_graph(False)
@@ -370,7 +372,10 @@ def m2l_leg(api, w, x, y, g, steps, flush, stream) -> dict:
     t = res["tensor"] / 1e3
     return {"kernel": "k_m2l_tc (tcgen05.mma kind::tf32, 3xTF32)", "ms": res["tensor"],
             "cuda_cores_ms": res["cuda_cores"], "translations": T, "flops_per_translation": 8 * p * p,
+            "paper_flops_per_translation": 2 + 17 * p * p,
             "achieved_algorithmic_tflops": 8 * p * p * T / t / 1e12,
+            "cuda_cores_achieved_algorithmic_tflops": 8 * p * p * T / (res["cuda_cores"] / 1e3) / 1e12,
+            "cuda_cores_frac_of_fp32_peak": 8 * p * p * T / (res["cuda_cores"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
             "tensor_flops_executed": tc_flops, "achieved_tensor_tflops": tc_flops / t / 1e12,
             "peak_tf32_tflops": peak, "frac_tensor": tc_flops / t / 1e12 / peak, "peak_note": peak_note,
             "timing": "stage events around the M2L launch in far-field-only evaluations, L2 flushed"}

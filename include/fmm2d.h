@@ -123,7 +123,9 @@ fmm_status fmm_velocity(fmm_handle h, int64_t n, const double *x, const double *
                         double *u, double *v);
 
 /* Same result from HOST arrays (pageable or pinned): copies the inputs into handle-owned device memory,
- * evaluates, copies u, v back and synchronises the stream before returning. */
+ * evaluates, copies u, v back and synchronises the stream before returning. Page-locked inputs of the
+ * precision form with an explicit root square are not copied first: the key kernel, their only reader,
+ * reads them in place over the host link. */
 fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
                              double *u, double *v);
 

@@ -928,11 +928,28 @@ fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const dou
     }
     double *dx = h->d_io, *dy = dx + n, *dg = dy + n, *du = dg + n, *dv = du + n;
     size_t bytes = (size_t)n * sizeof(double);
-    CU(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(dy, y, bytes, cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(dg, gamma, bytes, cudaMemcpyHostToDevice, h->stream));
+    // Page-locked inputs in the precision form with an explicit square are read once, by the key kernel, so it
+    // reads them in place over the host link (the same bytes cross it, without a copy in front of the kernel).
+    const double *in[3] = {x, y, gamma};
+    bool direct = h->mixed && h->has_domain;
+    for (int k = 0; k < 3 && direct; ++k) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, in[k]) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer)
+            direct = false;
+        else
+            in[k] = (const double *)a.devicePointer;
+    }
+    (void)cudaGetLastError();  // a pageable pointer leaves no sticky error, but clear the attribute query's
+    if (!direct) {
+        CU(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemcpyAsync(dy, y, bytes, cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemcpyAsync(dg, gamma, bytes, cudaMemcpyHostToDevice, h->stream));
+        in[0] = dx;
+        in[1] = dy;
+        in[2] = dg;
+    }
     set_single_system(h, n);
-    if ((st = run_forward(h, MODE_FULL, n, dx, dy, dg, du, dv)) != FMM_OK)
+    if ((st = run_forward(h, MODE_FULL, n, in[0], in[1], in[2], du, dv)) != FMM_OK)
         return st;
     CU(cudaMemcpyAsync(u, du, bytes, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaMemcpyAsync(v, dv, bytes, cudaMemcpyDeviceToHost, h->stream));

@@ -191,12 +191,20 @@ def test_deterministic_and_graph_replay_identical(lib, precision):
         assert torch.equal(a, b)
 
 
-def test_host_entry_point_equals_device(lib):
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("domain", ["explicit", "bbox"])
+def test_host_entry_point_equals_device(lib, pinned, domain):
+    """Host buffers (pageable: copied; page-locked with an explicit square: read in place by the key kernel)
+    give the device entry point's bits."""
     w = fi.uniform(30000, seed_index=41, depth=5, p=12)
-    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain if domain == "explicit" else None)
     u, v = f.velocity(dev(w.x), dev(w.y), dev(w.gamma))
-    uh, vh = f.velocity_host(torch.from_numpy(w.x), torch.from_numpy(w.y), torch.from_numpy(w.gamma))
-    assert torch.equal(u.cpu(), uh) and torch.equal(v.cpu(), vh)
+    hx, hy, hg = (torch.from_numpy(a) for a in (w.x, w.y, w.gamma))
+    if pinned:
+        hx, hy, hg = hx.pin_memory(), hy.pin_memory(), hg.pin_memory()
+    for _ in range(2):
+        uh, vh = f.velocity_host(hx, hy, hg)
+        assert torch.equal(u.cpu(), uh) and torch.equal(v.cpu(), vh)
 
 
 def test_edge_cases(lib, oracle):

@@ -99,6 +99,14 @@ fmm_status fmm_set_m2l_engine(fmm_handle h, int engine);
 /* The handle's M2L engine (FMM_M2L_TENSOR or FMM_M2L_CUDA_CORES; fmm_autotune may change it), -1 for NULL. */
 int fmm_get_m2l_engine(fmm_handle h);
 
+/* A tree depth for n particles in a root square of side `side` with blob core sigma (host only, no device
+ * work): the occupancy depth round(log4(n / leaf_target)) (leaf_target <= 0: 64, the occupancy measured fastest
+ * for the precision form on GB300), reduced until the leaf width w = side / 2^L keeps the Gaussian tail of the
+ * nearest pair that goes through the expansions below tail_tol: exp(-w^2 / 2 sigma^2) <= tail_tol (§2: the far
+ * field uses the point-vortex kernel, so that tail is left out of the sum). Returns the depth in [0, 12], or -1
+ * for n <= 0, sigma <= 0, side <= 0 or tail_tol outside (0, 1). */
+int fmm_suggest_depth(int64_t n, double sigma, double side, double tail_tol, double leaf_target);
+
 /* Changes depth, p or sigma of an existing handle (same ranges as fmm_create). */
 fmm_status fmm_set_params(fmm_handle h, int tree_depth, int p, double sigma);
 

@@ -27,6 +27,15 @@ def _host(t: torch.Tensor, name: str) -> int:
     return t.data_ptr()
 
 
+def suggest_depth(n: int, sigma: float, side: float, tail_tol: float = 1e-12, leaf_target: float = 64.0) -> int:
+    """Tree depth for n particles (occupancy about leaf_target per leaf) whose leaves are wide enough that the
+    Gaussian tail left out of the far field stays below tail_tol (see fmm_suggest_depth)."""
+    d = _lib.load().fmm_suggest_depth(int(n), float(sigma), float(side), float(tail_tol), float(leaf_target))
+    if d < 0:
+        raise ValueError("n, sigma and side must be positive and 0 < tail_tol < 1")
+    return d
+
+
 class FMM:
     """One FMM configuration: tree depth L (4^L leaves), p expansion terms, blob core sigma.
 

@@ -777,6 +777,23 @@ fmm_status fmm_set_m2l_engine(fmm_handle h, int engine)
 
 int fmm_get_m2l_engine(fmm_handle h) { return h ? h->m2l_engine : -1; }
 
+int fmm_suggest_depth(int64_t n, double sigma, double side, double tail_tol, double leaf_target)
+{
+    if (n <= 0 || !(sigma > 0.0) || !(side > 0.0) || !(tail_tol > 0.0 && tail_tol < 1.0))
+        return -1;
+    if (!(leaf_target > 0.0))
+        leaf_target = 64.0;
+    // occupancy: about leaf_target particles per leaf for uniformly spread particles
+    int L = (int)std::lround(std::log((double)n / leaf_target) / std::log(4.0));
+    L = std::max(0, std::min(L, FMM_MAXL));
+    // far-field tail (§2: the expansions use the point-vortex kernel beyond adjacent leaves, and the nearest such
+    // pair is one leaf width w apart): exp(-w^2 / 2 sigma^2) <= tail_tol
+    const double wmin = sigma * std::sqrt(2.0 * std::log(1.0 / tail_tol));
+    while (L > 0 && std::ldexp(side, -L) < wmin)
+        --L;
+    return L;
+}
+
 fmm_status fmm_set_params(fmm_handle h, int tree_depth, int p, double sigma)
 {
     if (!h || tree_depth < 0 || tree_depth > FMM_MAXL || p < 1 || p > FMM_PMAX || !(sigma > 0.0))

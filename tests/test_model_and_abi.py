@@ -4,7 +4,10 @@ import json
 import math
 import os
 
+import numpy as np
 import pytest
+
+import fmm_inputs as fi
 
 from paper_1008_2410_gb300 import model
 
@@ -63,3 +66,41 @@ def test_product_path_has_no_fallback():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text and "fmm_oracle" not in text
+
+
+def test_suggest_depth_rule():
+    """Occupancy depth round(log4(n / 64)), reduced until exp(-w^2 / 2 sigma^2) <= tail_tol for leaf width w."""
+    from paper_1008_2410_gb300 import api
+
+    n = 1 << 20
+    assert api.suggest_depth(n, 0.5 / 1024, 1.0) == 7  # uniform_1m: w / sigma = 16, tail e^-128
+    # the Lamb-Oseen lattice (sigma = 2h, square side 2): depth 4 leaves are 4 sigma wide (tail e^-8 = 3.4e-4)
+    assert api.suggest_depth(128 * 128, 2 * 2 / 128, 2.0, tail_tol=1e-12) == 3
+    assert api.suggest_depth(128 * 128, 2 * 2 / 128, 2.0, tail_tol=1e-3) == 4
+    assert api.suggest_depth(100, 1.0, 1.0) == 0
+    assert api.suggest_depth(1 << 30, 1e-9, 1.0) == 12
+    for bad in ((0, 1.0, 1.0), (10, 0.0, 1.0), (10, 1.0, -1.0)):
+        with pytest.raises(ValueError):
+            api.suggest_depth(*bad)
+    with pytest.raises(ValueError):
+        api.suggest_depth(10, 1.0, 1.0, tail_tol=1.5)
+
+
+def test_suggested_depth_removes_the_far_field_tail(oracle):
+    """§2: the expansions carry the point-vortex kernel, so the FMM converges (in p) to the split sum, which
+    misses the Gaussian tail of pairs beyond adjacent leaves. On the Lamb-Oseen lattice at depth 4 (leaves
+    4 sigma wide) that tail caps the agreement with Eq. 7 near 1e-7; at the suggested depth 3 (8 sigma) the FMM at
+    p = 30 reaches 1e-14."""
+    from paper_1008_2410_gb300 import api
+
+    w = fi.lattice_lamb_oseen()
+    d = api.suggest_depth(w.n, w.sigma, w.domain[2], tail_tol=1e-12)
+    assert d == 3
+    t = fi.sample_targets(w.n, 256)
+    ud, vd = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=t)
+    errs = {}
+    for depth in (4, d):
+        u, v, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, depth, 30, domain=w.domain, targets=t)
+        errs[depth] = float(np.linalg.norm(np.concatenate([u - ud, v - vd])) / np.linalg.norm(np.concatenate([ud, vd])))
+    assert errs[4] > 1e-7  # tail-limited: 1.34e-7 whatever p (measured at p = 20 and 30)
+    assert errs[d] < 1e-12

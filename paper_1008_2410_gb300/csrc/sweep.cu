@@ -365,10 +365,9 @@ __global__ void __launch_bounds__(128) k_m2l(Work w, Tables t, int adj, int64_t 
 
 // Precision form, FP32 levels: one warp per target box with lane q = source q of its interaction list (at most
 // 27: the children of the parent's 3 x 3 neighbours that are not adjacent, taken from a per-parity offset table).
-// Lane q forms alpha_m = (-1)^(m+1) rho^m a~_m, contracts it with the binomials C(m + l, m) held in constant
-// memory (compile-time indices: the FMAs read their constant operand directly), scales by rho^(l+1), and the
-// 27 partial locals are summed per coefficient through shared memory. P >= p terms are evaluated (zero-padded).
-__constant__ float c_binom[FMM_PMAX][FMM_PMAX];
+// Lane q forms x_m = (-1)^(m+1) rho^m a~_m, contracts it with the binomials C(m + l, m) by prefix sums (below),
+// scales by rho^(l+1), and the 27 partial locals are summed per coefficient through shared memory. P >= p terms
+// are evaluated (zero-padded).
 __constant__ int2 c_m2l_off[4][27];
 
 static int g_const_ready[64];
@@ -379,7 +378,7 @@ static bool m2l_constants_ready()
     return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && g_const_ready[dev];
 }
 
-// Uploads the constant tables of k_m2l_src to the current device once (synchronises the stream: call it before
+// Uploads the offset table of k_m2l_src to the current device once (synchronises the stream: call it before
 // any stream capture).
 int upload_m2l_constants(cudaStream_t s)
 {
@@ -388,15 +387,7 @@ int upload_m2l_constants(cudaStream_t s)
         return -1;
     if (g_const_ready[dev])
         return 0;
-    static float bin[FMM_PMAX][FMM_PMAX];
     static int2 off[4][27];
-    for (int m = 0; m < FMM_PMAX; ++m)
-        for (int l = 0; l < FMM_PMAX; ++l) {
-            double c = 1.0;
-            for (int i = 1; i <= m; ++i)
-                c = c * (double)(l + i) / (double)i;  // C(m + l, m)
-            bin[m][l] = (float)c;
-        }
     for (int cls = 0; cls < 4; ++cls) {
         int cx = cls & 1, cy = cls >> 1, q = 0;
         for (int ry = -2 - cy; ry <= 3 - cy; ++ry)
@@ -404,12 +395,30 @@ int upload_m2l_constants(cudaStream_t s)
                 if (rx < -1 || rx > 1 || ry < -1 || ry > 1)
                     off[cls][q++] = make_int2(rx, ry);
     }
-    if (cudaMemcpyToSymbolAsync(c_binom, bin, sizeof bin, 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyToSymbolAsync(c_m2l_off, off, sizeof off, 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    if (cudaMemcpyToSymbolAsync(c_m2l_off, off, sizeof off, 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return -1;
     g_const_ready[dev] = 1;
     return 0;
+}
+
+// packed FP32 pairs (real, imaginary) for the additions of the lane-per-source M2L
+typedef unsigned long long m2l_f2;
+__device__ __forceinline__ m2l_f2 m2l_pk2(float a, float b)
+{
+    m2l_f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void m2l_up2(m2l_f2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ m2l_f2 m2l_add2(m2l_f2 a, m2l_f2 b)
+{
+    m2l_f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
 }
 
 template <int P>
@@ -446,28 +455,39 @@ __global__ void __launch_bounds__(128) k_m2l_src(Work w, int64_t gw0, int64_t gw
         }
     }
     if (valid) {
-        float ar[P], ai[P];
+        m2l_f2 X[P];
         const float2 *src = w.M32 + sb * p;
         float pr = 1.f, pi = 0.f;
 #pragma unroll
         for (int m = 0; m < P; ++m) {
             float2 a = m < p ? src[m] : make_float2(0.f, 0.f);
             const float sg = (m & 1) ? 1.f : -1.f;  // (-1)^(m+1)
-            ar[m] = sg * (pr * a.x - pi * a.y);
-            ai[m] = sg * (pr * a.y + pi * a.x);
+            X[m] = m2l_pk2(sg * (pr * a.x - pi * a.y), sg * (pr * a.y + pi * a.x));
             const float t = pr * rr - pi * ri;
             pi = pr * ri + pi * rr;
             pr = t;
         }
+        // y_l = sum_m C(m+l, m) x_m: with u = 1/(1 - s), sum_l y_l s^l = u X(u) = u (x_0 + u (x_1 + ... + u x_{P-1})),
+        // and multiplying a truncated series by u is a prefix sum of its coefficients: P prefix sums of P terms,
+        // additions only (re and im packed), no binomial table
+        m2l_f2 T[P];
+        T[0] = X[P - 1];
+#pragma unroll
+        for (int k = 1; k < P; ++k)
+            T[k] = 0ull;
+#pragma unroll
+        for (int m = P - 2; m >= -1; --m) {
+#pragma unroll
+            for (int k = 1; k < P; ++k)
+                T[k] = m2l_add2(T[k], T[k - 1]);
+            if (m >= 0)
+                T[0] = m2l_add2(T[0], X[m]);
+        }
         float qr = rr, qi = ri;  // rho^(l+1)
 #pragma unroll
         for (int ll = 0; ll < P; ++ll) {
-            float br = 0.f, bi = 0.f;
-#pragma unroll
-            for (int m = 0; m < P; ++m) {
-                br = fmaf(c_binom[m][ll], ar[m], br);
-                bi = fmaf(c_binom[m][ll], ai[m], bi);
-            }
+            float br, bi;
+            m2l_up2(T[ll], br, bi);
             part[wi][lane][ll] = make_float2(qr * br - qi * bi, qr * bi + qi * br);
             const float t = qr * rr - qi * ri;
             qi = qr * ri + qi * rr;

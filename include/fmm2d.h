@@ -133,7 +133,8 @@ fmm_status fmm_velocity(fmm_handle h, int64_t n, const double *x, const double *
 /* Same result from HOST arrays (pageable or pinned): copies the inputs into handle-owned device memory,
  * evaluates, copies u, v back and synchronises the stream before returning. Page-locked inputs of the
  * precision form with an explicit root square are not copied first: the key kernel, their only reader,
- * reads them in place over the host link. */
+ * reads them in place over the host link; page-locked outputs are written in place by the final sum, which
+ * writes in caller order. */
 fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
                              double *u, double *v);
 

@@ -516,6 +516,7 @@ __global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restr
         if (e < c) {
             const int pos = s0 + rank;
             w.perm[pos] = v;
+            w.iperm[v] = pos;
             w.sleaf[pos] = leaf;
             if (mixed) {
                 const float4 p = w.pos4u[v];

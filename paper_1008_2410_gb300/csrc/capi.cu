@@ -349,7 +349,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = mixed ? np * 16 : 0;                         // 24 pos4u
     sizes[i++] = mixed ? np * 4 : 0;                          // 25 g32u
     sizes[i++] = np * 4;                                      // 26 slot
-    sizes[i++] = 0;                                           // 27 (unused)
+    sizes[i++] = np * 4;                                      // 27 iperm
     sizes[i++] = adjoint ? np * 24 : 0;                       // 28 adj_far
     int count = i;
     Layout lay;
@@ -415,6 +415,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.AM64 = sizes[21] ? (double2 *)(b + lay.off[21]) : nullptr;
     w.AL64 = sizes[22] ? (double2 *)(b + lay.off[22]) : nullptr;
     w.slot = (int *)(b + lay.off[26]);
+    w.iperm = (int *)(b + lay.off[27]);
     w.pos4u = sizes[24] ? (float4 *)(b + lay.off[24]) : nullptr;
     w.g32u = sizes[25] ? (float *)(b + lay.off[25]) : nullptr;
     char *hd = (char *)h->hdr;
@@ -965,11 +966,28 @@ fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const dou
         in[1] = dy;
         in[2] = dg;
     }
+    // page-locked outputs are written in place by the final (caller-order, contiguous) sum kernel
+    double *out[2] = {u, v};
+    bool direct_out = true;
+    for (int k = 0; k < 2 && direct_out; ++k) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, out[k]) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer)
+            direct_out = false;
+        else
+            out[k] = (double *)a.devicePointer;
+    }
+    (void)cudaGetLastError();
+    if (!direct_out) {
+        out[0] = du;
+        out[1] = dv;
+    }
     set_single_system(h, n);
-    if ((st = run_forward(h, MODE_FULL, n, in[0], in[1], in[2], du, dv)) != FMM_OK)
+    if ((st = run_forward(h, MODE_FULL, n, in[0], in[1], in[2], out[0], out[1])) != FMM_OK)
         return st;
-    CU(cudaMemcpyAsync(u, du, bytes, cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(v, dv, bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (!direct_out) {
+        CU(cudaMemcpyAsync(u, du, bytes, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaMemcpyAsync(v, dv, bytes, cudaMemcpyDeviceToHost, h->stream));
+    }
     CU(cudaStreamSynchronize(h->stream));
     return poll_status(h, true);
 }

@@ -122,6 +122,7 @@ size_t carve_work(unsigned char *b, Work &w, int64_t n, int depth, int p, bool m
     w.scan_tmp = (int *)take((size_t)((nleaf + 1023) / 1024 + 2) * 4);
     w.tmp = (int *)take(np * 4);
     w.perm = (int *)take(np * 4);
+    w.iperm = (int *)take(np * 4);
     w.sleaf = (int *)take(np * 4);
     w.sx = (double *)take(mixed ? 0 : np * 8);
     w.sy = (double *)take(mixed ? 0 : np * 8);

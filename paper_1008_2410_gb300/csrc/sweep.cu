@@ -710,16 +710,18 @@ int launch_l2p(const Work &w, cudaStream_t s)
     return 1;
 }
 
+// Stage 10 in caller order: thread i gathers its particle's near and far parts from leaf-order position
+// iperm[i] and writes u[i], v[i] contiguously (so the outputs may also be page-locked host memory).
 template <int PM>
 __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict__ u, double *__restrict__ v)
 {
-    int pos = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= w.n)
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n)
         return;
+    int pos = w.iperm[i];
     int k = w.nsys == 1 ? 0 : find_sys_by_particle(w.sys, w.nsys, pos);
     const SysDev &d = w.sys[k];
     int L = d.depth;
-    int i = w.perm[pos];
     bool far = use_far && L >= 2;
     int64_t base = far ? (d.box0[L] + (int)(w.sleaf[pos] - d.leaf0)) * (int64_t)w.p : 0;
     if (w.mixed && !level_fp64(w, L)) {

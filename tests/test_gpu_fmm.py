@@ -200,10 +200,11 @@ def test_host_entry_point_equals_device(lib, pinned, domain):
     f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain if domain == "explicit" else None)
     u, v = f.velocity(dev(w.x), dev(w.y), dev(w.gamma))
     hx, hy, hg = (torch.from_numpy(a) for a in (w.x, w.y, w.gamma))
+    uo, vo = torch.empty(w.n, dtype=torch.float64), torch.empty(w.n, dtype=torch.float64)
     if pinned:
-        hx, hy, hg = hx.pin_memory(), hy.pin_memory(), hg.pin_memory()
+        hx, hy, hg, uo, vo = (t.pin_memory() for t in (hx, hy, hg, uo, vo))
     for _ in range(2):
-        uh, vh = f.velocity_host(hx, hy, hg)
+        uh, vh = f.velocity_host(hx, hy, hg, uo, vo)
         assert torch.equal(u.cpu(), uh) and torch.equal(v.cpu(), vh)
 
 

@@ -146,6 +146,8 @@ int launch_p2m(const Work &w, const Tables &t, int adj, cudaStream_t s)
         p2m_dispatch<8>(w, adj, s);
     else if (w.p <= 16)
         p2m_dispatch<16>(w, adj, s);
+    else if (w.p <= 20)
+        p2m_dispatch<20>(w, adj, s);
     else if (w.p <= 24)
         p2m_dispatch<24>(w, adj, s);
     else
@@ -239,6 +241,8 @@ int launch_m2m(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, i
         m2m_launch<8>(w, t, l, adj, blocks, s);
     else if (w.p <= 16)
         m2m_launch<16>(w, t, l, adj, blocks, s);
+    else if (w.p <= 20)
+        m2m_launch<20>(w, t, l, adj, blocks, s);
     else if (w.p <= 24)
         m2m_launch<24>(w, t, l, adj, blocks, s);
     else
@@ -639,6 +643,8 @@ int launch_l2l(const Work &w, const Tables &t, int l, int adj, cudaStream_t s, i
         l2l_launch<8>(w, t, l, adj, (unsigned)blocks, s);
     else if (w.p <= 16)
         l2l_launch<16>(w, t, l, adj, (unsigned)blocks, s);
+    else if (w.p <= 20)
+        l2l_launch<20>(w, t, l, adj, (unsigned)blocks, s);
     else if (w.p <= 24)
         l2l_launch<24>(w, t, l, adj, (unsigned)blocks, s);
     else
@@ -703,6 +709,8 @@ int launch_l2p(const Work &w, cudaStream_t s)
         k_l2p32<8><<<nb, 256, 0, s>>>(w);
     else if (w.p <= 16)
         k_l2p32<16><<<nb, 256, 0, s>>>(w);
+    else if (w.p <= 20)
+        k_l2p32<20><<<nb, 256, 0, s>>>(w);
     else if (w.p <= 24)
         k_l2p32<24><<<nb, 256, 0, s>>>(w);
     else
@@ -800,6 +808,8 @@ int launch_combine(const Work &w, int use_near, int use_far, double *u, double *
         k_combine<8><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
     else if (w.p <= 16)
         k_combine<16><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
+    else if (w.p <= 20)
+        k_combine<20><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
     else if (w.p <= 24)
         k_combine<24><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
     else

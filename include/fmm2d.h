@@ -120,7 +120,8 @@ fmm_status fmm_set_graph(fmm_handle h, int enable);
 /* Near-field tile shape of the precision form: threads 32 (one leaf per thread block), 64 (two
  * horizontally adjacent leaves per block, sharing their source tiles) or 128 (symmetric: each pair of
  * particles in adjacent leaves evaluated once and applied to both, one warp per leaf, four warps per block;
- * leaves wider than about 38 sigma still take the target-side kernel); targets_per_thread 2 or 4 (the most
+ * leaves wider than about 38 sigma still take the target-side kernel) or 192 (the 64-thread kernel with each
+ * of the three source rows in its own block, summed at the end); targets_per_thread 2 or 4 (the most
  * targets one lane takes per pass; passes are balanced over the leaf). 0 = default (64, 4).
  * Set by fmm_autotune; exposed for experiments. */
 fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread);

@@ -483,6 +483,7 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
     // system takes one-float coordinates only for an explicit square (s is computed here as the device does,
     // with a margin); otherwise the split-form kernel is launched as well and skips the one-float systems.
     w.p2p_sym = near && w.mixed && h->p2p_threads == 128 && w.nearp ? 1 : 0;
+    w.p2p_rows = near && w.mixed && h->p2p_threads == 192 && w.nearp ? 1 : 0;
     w.p2p_all_plain = 1;
     for (auto &c : h->sys_cfg) {
         if (!c.explicit_domain) {
@@ -829,9 +830,11 @@ fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread)
         threads = 64;
     if (targets_per_thread == 0)
         targets_per_thread = 4;
-    if ((threads != 32 && threads != 64 && threads != 128) || (targets_per_thread != 2 && targets_per_thread != 4))
+    if ((threads != 32 && threads != 64 && threads != 128 && threads != 192) ||
+        (targets_per_thread != 2 && targets_per_thread != 4))
         return set_err(h, FMM_EINVAL,
-                       "tile: threads 32 (one leaf per block), 64 (two) or 128 (symmetric), targets per thread 2 or 4");
+                       "tile: threads 32 (one leaf per block), 64 (two), 128 (symmetric) or 192 (per source row), "
+                       "targets per thread 2 or 4");
     h->p2p_threads = threads;
     h->p2p_kt = targets_per_thread;
     return FMM_OK;
@@ -1218,10 +1221,11 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
             fclose(f);
         }
     }
-    int tiles[][2] = {{64, 4}, {128, 4}, {128, 2}, {64, 2}, {32, 4}, {32, 2}};
-    int ntile = h->mixed ? 6 : 1;
-    int save_graph = h->use_graph, save_timing = h->timing;
-    h->use_graph = 0;
+    int tiles[][2] = {{64, 4}, {128, 4}, {192, 4}, {128, 2}, {192, 2}, {64, 2}, {32, 4}, {32, 2}};
+    int ntile = h->mixed ? 8 : 1;
+    // candidates are timed the way the handle will run them: replayed graphs when the handle uses graphs (the
+    // overlap of the near field with the sweep differs between eager launches and a graph)
+    int save_timing = h->timing;
     h->timing = 0;
     float best = 1e30f;
     int bd = h->depth, bth = h->p2p_threads, bkt = h->p2p_kt;
@@ -1274,7 +1278,6 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
     h->m2l_engine = beng;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->use_graph = save_graph;
     h->timing = save_timing;
     if (cache) {
         FILE *f = fopen(cache, "a");

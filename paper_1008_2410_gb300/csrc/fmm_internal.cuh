@@ -94,6 +94,7 @@ struct Work {
                               // forward offset d (d = 0..3: (1,0), (1,1), (0,1), (-1,1)), or null
     int p2p_all_plain;        // host knows every system takes one-float near-field coordinates
     int p2p_sym;              // this evaluation's near field is the symmetric kernel (nearp holds reactions)
+    int p2p_rows;             // this evaluation's near field comes per source row (nearp[0..2] hold the parts)
     int nsys;
     int maxdepth;
     // arrays
@@ -171,7 +172,7 @@ int launch_m2m(const Work &w, const Tables &t, int level, int adjoint_charges, c
 int launch_m2l(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t s, int prio);
 int launch_l2l(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
 int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);  // threads 32: 1 leaf per block, 64: 2,
-                                                                     // 128: symmetric (needs nearp)
+                                                                     // 128: symmetric, 192: per source row
 int launch_rk_stage(int64_t n, double *x, double *y, double *tx, double *ty, const double *u, const double *v,
                     double *au, double *av, double b, double c_next, double dt, int first, int last, cudaStream_t s);
 int launch_l2p(const Work &w, cudaStream_t s);  // precision form with far32: far field into far32 (stage 8)

@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
         f2 SU[2] = {0ull, 0ull}, CU[2] = {0ull, 0ull}, SV[2] = {0ull, 0ull}, CV[2] = {0ull, 0ull};
         for (int dyr = -1; dyr <= 1; ++dyr) {
             const int row = iy + dyr;
-            if (row < 0 || row >= ns)
-                continue;
+            if (row < 0 || row >= ns || (w.p2p_rows && dyr != (int)blockIdx.y - 1))
+                continue;  // with p2p_rows each block takes one source row (blockIdx.y)
             const int rowleaf = (int)d.leaf0 + row * ns;
             const int ca = max(c_lo, 0), cz = min(c_lo + ncol - 1, ns - 1);
             const int r0 = w.start[rowleaf + ca], r1 = w.start[rowleaf + cz + 1];
@@ -440,7 +440,13 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
             for (int h = 0; h < 2; ++h) {
                 const int e = lane + 32 * (2 * pr + h);
                 if (e < t_cnt)
-                    w.near32[tbase + e] = make_float2(-(su[h] + cu[h]) * snear, (sv[h] + cv[h]) * snear);
+                {
+                    const float2 r = make_float2(-(su[h] + cu[h]) * snear, (sv[h] + cv[h]) * snear);
+                    if (w.p2p_rows)  // one row's part, summed by the final kernel
+                        w.nearp[(int64_t)blockIdx.y * w.n + tbase + e] = r;
+                    else
+                        w.near32[tbase + e] = r;
+                }
             }
         }
     }
@@ -735,6 +741,18 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
             ++nl;
         }
         return nl;
+    }
+    if (threads == 192 && w.p2p_rows) {
+        // the target-side kernel with each of the three source rows of a leaf pair in its own block: three
+        // times the blocks at a third of the length, so the last wave leaves less of the GPU idle
+        const bool pr2 = w.lv.nsys_at[1] == w.nsys;
+        const int tile = pr2 ? 320 : 256;
+        const dim3 grid(pr2 ? (w.nleaf + 1) / 2 : w.nleaf, 3);
+        if (pr2)
+            k_p2p32<2><<<grid, 64, (size_t)tile * 48, s>>>(w, tile, ktmax, 0);
+        else
+            k_p2p32<1><<<grid, 32, (size_t)tile * 48, s>>>(w, tile, ktmax, 0);
+        return 1;
     }
     // two leaves per block needs every system's leaves to pair up within rows (depth >= 1)
     bool pairs = threads == 64 && w.lv.nsys_at[1] == w.nsys;

@@ -747,7 +747,17 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
             fu = s.re * fs;
             fv = -s.im * fs;
         }
-        float2 t = use_near ? w.near32[pos] : make_float2(0.f, 0.f);
+        float2 t = make_float2(0.f, 0.f);
+        if (use_near && w.p2p_rows) {  // the three source rows' parts, fixed order
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float2 q = w.nearp[(int64_t)r * w.n + pos];
+                t.x += q.x;
+                t.y += q.y;
+            }
+        } else if (use_near) {
+            t = w.near32[pos];
+        }
         if (use_near && w.p2p_sym && d.s_unit <= P2P_SPLIT_S) {
             // symmetric near field: add the reactions from the four backward neighbour leaves, fixed order
             const int ns = 1 << L, local = (int)(w.sleaf[pos] - d.leaf0);

@@ -102,7 +102,7 @@ def test_mixed_symmetric_near_field_matches_oracle(lib, oracle, name, make, doma
     assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < TOL32
 
 
-@pytest.mark.parametrize("tile", [(64, 4), (64, 2), (32, 4), (32, 2), (128, 4), (128, 2)])
+@pytest.mark.parametrize("tile", [(64, 4), (64, 2), (32, 4), (32, 2), (128, 4), (128, 2), (192, 4), (192, 2)])
 def test_mixed_tile_shapes(lib, oracle, tile):
     w = fi.clustered(30000, depth=4, p=12)  # dense leaves: several target chunks and source tiles per leaf
     uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)
@@ -369,7 +369,8 @@ def test_stage_times_launch_count_and_autotune(lib):
     assert f.kernel_launches() > n0 + 8
     prm = f.autotune(x, y, g, 4, 6)
     assert 4 <= prm["depth"] <= 6
-    assert (prm["p2p_threads"], prm["p2p_targets_per_thread"]) in {(64, 4), (64, 2), (32, 4), (32, 2)}
+    assert prm["p2p_threads"] in (32, 64, 128, 192) and prm["p2p_targets_per_thread"] in (2, 4)
+    assert prm["m2l_engine"] in ("tensor", "cuda_cores")
 
 
 @pytest.mark.slow

@@ -176,7 +176,7 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 #define P2P_UNROLL 1  // source loop unroll of the near-field kernel
 #endif
 #ifndef P2P_MIN_BLOCKS
-#define P2P_MIN_BLOCKS 12  // minimum resident blocks per SM requested from the register allocator
+#define P2P_MIN_BLOCKS 16  // minimum resident blocks per SM requested from the register allocator (64 registers)
 #endif
 constexpr int kP2PUnroll = P2P_UNROLL;
 
@@ -746,7 +746,7 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
         // the target-side kernel with each of the three source rows of a leaf pair in its own block: three
         // times the blocks at a third of the length, so the last wave leaves less of the GPU idle
         const bool pr2 = w.lv.nsys_at[1] == w.nsys;
-        const int tile = pr2 ? 320 : 256;
+        const int tile = 256;
         const dim3 grid(pr2 ? (w.nleaf + 1) / 2 : w.nleaf, 3);
         if (pr2)
             k_p2p32<2><<<grid, 64, (size_t)tile * 48, s>>>(w, tile, ktmax, 0);
@@ -756,7 +756,7 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
     }
     // two leaves per block needs every system's leaves to pair up within rows (depth >= 1)
     bool pairs = threads == 64 && w.lv.nsys_at[1] == w.nsys;
-    int tile = pairs ? 320 : 256;
+    int tile = 256;  // 16 blocks x 256 x 48 B of shared memory per SM
     size_t sm = (size_t)tile * 48;
     if (pairs)
         k_p2p32<2><<<(w.nleaf + 1) / 2, 64, sm, s>>>(w, tile, ktmax, 0);

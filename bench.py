@@ -213,6 +213,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     if args.precision == "mixed":
         out["m2l"] = m2l_leg(api, w, x, y, g, args.steps, flush, stream)
     out["advect"] = advect_leg(api, w, x, y, g, tuned, args.precision, flush, stream)
+    out["batched"] = batched_leg(api, args.precision, flush, stream)
+    out["adjoint"] = adjoint_leg(api, w, x, y, g, flush, stream)
 
     # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
     f.set_count_pairs(True)
@@ -412,6 +414,50 @@ def advect_leg(api, w, x, y, g, tuned, precision, flush, stream) -> dict:
     ms = st_.median(ts)
     return {"scheme": "RK2 midpoint (2 evaluations per step)", "ms_per_step": ms,
             "value": w.n / (ms / 1e3) / 1e6, "unit": "Mparticle-steps/s", "dt": dt}
+
+
+def batched_leg(api, precision, flush, stream) -> dict:
+    """64 independent uniform systems of uneven size (4096 .. 262144 particles, depth round(log4(N/64)), p = 14)
+    in one evaluation (one launch per stage, graph replay): total particles per second."""
+    import statistics as st_
+
+    import numpy as np
+    import torch
+
+    import fmm_inputs as fi
+
+    bt = fi.batched()
+    xs = np.concatenate([s.x for s in bt.systems])
+    ys = np.concatenate([s.y for s in bt.systems])
+    gs = np.concatenate([s.gamma for s in bt.systems])
+    off = np.concatenate([[0], np.cumsum([s.n for s in bt.systems])])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, y, g = dev(xs), dev(ys), dev(gs)
+    f = api.FMM(bt.systems[0].depth, bt.p, bt.systems[0].sigma, precision=precision, graph=True)
+    kw = dict(depths=[s.depth for s in bt.systems], sigmas=[s.sigma for s in bt.systems],
+              domains=[list(s.domain) for s in bt.systems])
+    u, v = f.velocity_batched(off, x, y, g, **kw)
+    ms, _ = timed_steps(lambda: f.velocity_batched(off, x, y, g, u=u, v=v, **kw), 10, flush, stream)
+    f.close()
+    t = st_.median(ms)
+    return {"systems": len(bt.systems), "particles": int(off[-1]), "ms_per_step": t,
+            "value": int(off[-1]) / (t / 1e3) / 1e6, "unit": "Mparticles/s"}
+
+
+def adjoint_leg(api, w, x, y, g, flush, stream) -> dict:
+    """Exact adjoint (dL/dgamma, dL/dx, dL/dy for L = sum(gu u + gv v)), FP64 form, on the same workload."""
+    import statistics as st_
+
+    import torch
+
+    f = api.FMM(w.depth, w.p, w.sigma, precision="fp64", domain=w.domain)
+    gu = torch.ones_like(x)
+    gv = torch.ones_like(x)
+    f.adjoint(x, y, g, gu, gv)
+    ms, _ = timed_steps(lambda: f.adjoint(x, y, g, gu, gv), 3, flush, stream)
+    f.close()
+    t = st_.median(ms)
+    return {"form": "fp64", "ms_per_step": t, "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s"}
 
 
 def cpu_baseline(w, u_gpu, v_gpu) -> dict:

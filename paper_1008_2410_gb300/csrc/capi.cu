@@ -416,6 +416,11 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.AL64 = sizes[22] ? (double2 *)(b + lay.off[22]) : nullptr;
     w.slot = (int *)(b + lay.off[26]);
     w.iperm = (int *)(b + lay.off[27]);
+    {
+        void *dp = nullptr;  // device view of the page-locked status word (null: copy it instead)
+        w.status_host = cudaHostGetDevicePointer(&dp, h->h_status, 0) == cudaSuccess ? (unsigned int *)dp : nullptr;
+        (void)cudaGetLastError();
+    }
     w.pos4u = sizes[24] ? (float4 *)(b + lay.off[24]) : nullptr;
     w.g32u = sizes[25] ? (float *)(b + lay.off[25]) : nullptr;
     char *hd = (char *)h->hdr;
@@ -542,7 +547,8 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
         nl += launch_pair_count(w, s);
         CU(cudaMemcpyAsync(h->h_pairs, w.pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     }
-    CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    if (!w.status_host)  // the final sum kernel writes it otherwise
+        CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     if (timed)
         CU(record_timing(h->ev_t[7], s));
     CU(cudaGetLastError());

@@ -90,6 +90,7 @@ struct Work {
     int m2l_tc;               // FP32 M2L levels on the tensor cores (1) or on the CUDA cores (0)
     float2 *far32;            // [n] leaf order: FP32 far field (L2P) of the precision form, or null (fused)
     int *iperm;               // [n] caller index -> leaf-order position (inverse of perm)
+    unsigned int *status_host;  // page-locked copy of *status written by the final sum kernel, or null
     float2 *nearp;            // [4][n] leaf order: symmetric near field, reactions from the leaf at -P2P
                               // forward offset d (d = 0..3: (1,0), (1,1), (0,1), (-1,1)), or null
     int p2p_all_plain;        // host knows every system takes one-float near-field coordinates

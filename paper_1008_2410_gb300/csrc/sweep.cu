@@ -724,6 +724,8 @@ template <int PM>
 __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict__ u, double *__restrict__ v)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && w.status_host)
+        *w.status_host = *w.status;  // every earlier stage has finished: hand the status word to the host
     if (i >= w.n)
         return;
     int pos = w.iperm[i];

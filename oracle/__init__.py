@@ -88,6 +88,16 @@ def _load():
         lib.oracle_advect.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int, _D,
                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.oracle_advect.restype = ctypes.c_int
+        lib.oracle_p2l.argtypes = [ctypes.c_int64, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, _D]
+        lib.oracle_adaptive_lists_check.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_int, ctypes.c_int, _D, _I64]
+        lib.oracle_adaptive_lists_check.restype = ctypes.c_int
+        lib.oracle_adaptive_fmm.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_int]
+        lib.oracle_adaptive_fmm.restype = ctypes.c_int
+        lib.oracle_adaptive_split_direct.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int,
+                                                     ctypes.c_int, _D, _D, _D]
+        lib.oracle_adaptive_split_direct.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -268,3 +278,57 @@ def advect(x, y, gamma, sigma: float, depth: int, p: int, dt: float, nsteps: int
     if rc != 0:
         raise RuntimeError(f"oracle_advect failed ({rc})")
     return xs, ys
+
+
+# ---------------------------------------------------------------- adaptive quadtree (§5, uneven densities)
+
+def p2l(x, y, q, centre, p: int) -> np.ndarray:
+    """X-list operator: local expansion about ``centre`` of point charges q_j at (x_j, y_j)."""
+    x, y = _f64(x), _f64(y)
+    q = np.asarray(q, np.complex128)
+    qre, qim = np.ascontiguousarray(q.real), np.ascontiguousarray(q.imag)
+    out = np.zeros(2 * p)
+    _load().oracle_p2l(x.size, _ptr(x), _ptr(y), _ptr(qre), _ptr(qim), float(np.real(centre)),
+                       float(np.imag(centre)), int(p), _ptr(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def adaptive_lists_check(x, y, max_depth: int, leaf_capacity: int, domain=None):
+    """Builds the adaptive tree and its U, V, W, X lists from their definitions. Returns (bad, sizes): bad =
+    the number of ordered leaf pairs whose interaction the lists deliver other than exactly once; sizes =
+    dict of boxes, leaves, total |U|, |V|, |W|, |X|, max |V| and the deepest leaf level."""
+    x, y = _f64(x), _f64(y)
+    sizes = np.zeros(8, np.int64)
+    bad = _load().oracle_adaptive_lists_check(x.size, _ptr(x), _ptr(y), int(max_depth), int(leaf_capacity),
+                                              _ptr(_dom(domain)), _ptr(sizes, _I64))
+    if bad < 0:
+        raise ValueError("oracle_adaptive_lists_check failed")
+    keys = ("boxes", "leaves", "U", "V", "W", "X", "maxV", "deepest")
+    return bad, dict(zip(keys, (int(s) for s in sizes)))
+
+
+def adaptive_fmm(x, y, gamma, sigma: float, max_depth: int, leaf_capacity: int, p: int, domain=None,
+                 parts: str = "both"):
+    """Serial adaptive FMM (U, V, W, X lists). Returns (u, v) in input order."""
+    x, y, g = _f64(x), _f64(y), _f64(gamma)
+    u, v = np.zeros(x.size), np.zeros(x.size)
+    code = {"near": 1, "far": 2, "both": 3}[parts]
+    rc = _load().oracle_adaptive_fmm(x.size, _ptr(x), _ptr(y), _ptr(g), float(sigma), int(max_depth),
+                                     int(leaf_capacity), int(p), _ptr(_dom(domain)), _ptr(u), _ptr(v), code)
+    if rc == -1:
+        raise ValueError("point outside the root square")
+    if rc != 0:
+        raise MemoryError("oracle_adaptive_fmm failed")
+    return u, v
+
+
+def adaptive_split_direct(x, y, gamma, sigma: float, max_depth: int, leaf_capacity: int, domain=None):
+    """Exact sum the adaptive FMM converges to: K_sigma between particles in adjacent (or equal) leaves of the
+    adaptive tree, the point-vortex kernel between all other pairs."""
+    x, y, g = _f64(x), _f64(y), _f64(gamma)
+    u, v = np.zeros(x.size), np.zeros(x.size)
+    rc = _load().oracle_adaptive_split_direct(x.size, _ptr(x), _ptr(y), _ptr(g), float(sigma), int(max_depth),
+                                              int(leaf_capacity), _ptr(_dom(domain)), _ptr(u), _ptr(v))
+    if rc != 0:
+        raise ValueError("oracle_adaptive_split_direct failed")
+    return u, v

@@ -858,3 +858,420 @@ int oracle_advect(int64_t n, double *x, double *y, const double *g, double sigma
     free(av);
     return rc;
 }
+
+/* ================================================================ adaptive quadtree (§5: uneven densities)
+ *
+ * The paper's tree is uniform; its closing section names uneven particle distributions as the next step.
+ * This is the standard adaptive quadtree of Carrier, Greengard and Rokhlin written out plainly:
+ *   - a box is split into its four children while it holds more than B particles and its level is below
+ *     Lmax; the boxes are the squares of the uniform tree (level l, column bx, row by), so a particle's box
+ *     at level l is its depth-Lmax leaf coordinate shifted right by Lmax - l;
+ *   - two boxes are adjacent when their closed squares touch or overlap;
+ *   - U(a), leaf a: every leaf adjacent to a (a included)          -> exact K_sigma (stage 9)
+ *   - V(a): boxes at a's level whose parents are adjacent to a's parent, not adjacent to a  -> M2L (stage 6)
+ *   - W(a), leaf a: boxes below colleagues of a (same-level boxes adjacent to a) whose parent is adjacent
+ *     to a but which are not adjacent to a                          -> multipole evaluated at a's particles
+ *   - X(a): the boxes c with a in W(c) (all leaves)                -> local expansion of c's particles
+ * Every list is found here by testing the definition on every pair of boxes (quadratic in the box count).
+ * Locals exist on levels >= 2 (levels 0 and 1 have no well separated pairs) and multipoles likewise. */
+
+typedef struct {
+    int l, bx, by;
+    int parent;
+    int child[4]; /* -1 for a leaf */
+    int64_t p0, np; /* particles ord[p0 .. p0 + np) */
+    int64_t lo[2], hi[2]; /* closed range of depth-Lmax cells, x and y */
+} abox_t;
+
+typedef struct {
+    int Lmax, B, nbox, cap;
+    double x0, y0, S;
+    abox_t *box;
+    int64_t *ord;  /* particle indices grouped by box (children are sub-ranges of the parent) */
+    int32_t *ix, *iy;
+} atree_t;
+
+static void atree_free(atree_t *t)
+{
+    free(t->box);
+    free(t->ord);
+    free(t->ix);
+    free(t->iy);
+}
+
+static int atree_add(atree_t *t, int l, int bx, int by, int parent, int64_t p0, int64_t np)
+{
+    if (t->nbox == t->cap) {
+        int nc = t->cap ? 2 * t->cap : 64;
+        abox_t *nb = realloc(t->box, sizeof(abox_t) * (size_t)nc);
+        if (!nb)
+            return -1;
+        t->box = nb;
+        t->cap = nc;
+    }
+    abox_t *b = &t->box[t->nbox];
+    b->l = l;
+    b->bx = bx;
+    b->by = by;
+    b->parent = parent;
+    b->child[0] = b->child[1] = b->child[2] = b->child[3] = -1;
+    b->p0 = p0;
+    b->np = np;
+    int sh = t->Lmax - l;
+    b->lo[0] = (int64_t)bx << sh;
+    b->hi[0] = (((int64_t)bx + 1) << sh) - 1;
+    b->lo[1] = (int64_t)by << sh;
+    b->hi[1] = (((int64_t)by + 1) << sh) - 1;
+    return t->nbox++;
+}
+
+/* Builds the tree breadth first, so boxes come in non-decreasing level order and a parent precedes its
+ * children. Particles keep the input order inside every box. */
+static int atree_build(atree_t *t, int64_t n, const double *x, const double *y, int Lmax, int B, const double *dom)
+{
+    memset(t, 0, sizeof(*t));
+    t->Lmax = Lmax;
+    t->B = B;
+    double d[3];
+    if (dom) {
+        d[0] = dom[0];
+        d[1] = dom[1];
+        d[2] = dom[2];
+    } else {
+        oracle_default_domain(n, x, y, d);
+    }
+    t->x0 = d[0];
+    t->y0 = d[1];
+    t->S = d[2];
+    size_t nn = (size_t)(n ? n : 1);
+    t->ix = malloc(sizeof(int32_t) * nn);
+    t->iy = malloc(sizeof(int32_t) * nn);
+    t->ord = malloc(sizeof(int64_t) * nn);
+    int64_t *tmp = malloc(sizeof(int64_t) * nn);
+    if (!t->ix || !t->iy || !t->ord || !tmp) {
+        free(tmp);
+        return -2;
+    }
+    if (oracle_leaf_coords(n, x, y, Lmax, d, dom != NULL, t->ix, t->iy) != 0) {
+        free(tmp);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        t->ord[i] = i;
+    if (atree_add(t, 0, 0, 0, -1, 0, n) < 0) {
+        free(tmp);
+        return -2;
+    }
+    for (int k = 0; k < t->nbox; ++k) {
+        abox_t b = t->box[k];
+        if (b.np <= B || b.l >= Lmax)
+            continue;
+        /* stable partition of the box's particles into its children (child index cy * 2 + cx) */
+        int sh = Lmax - (b.l + 1);
+        int64_t cnt[4] = {0, 0, 0, 0};
+        for (int64_t e = 0; e < b.np; ++e) {
+            int64_t i = t->ord[b.p0 + e];
+            int c = (((t->iy[i] >> sh) & 1) << 1) | ((t->ix[i] >> sh) & 1);
+            cnt[c]++;
+        }
+        int64_t off[4] = {0, cnt[0], cnt[0] + cnt[1], cnt[0] + cnt[1] + cnt[2]};
+        int64_t fill[4] = {off[0], off[1], off[2], off[3]};
+        for (int64_t e = 0; e < b.np; ++e) {
+            int64_t i = t->ord[b.p0 + e];
+            int c = (((t->iy[i] >> sh) & 1) << 1) | ((t->ix[i] >> sh) & 1);
+            tmp[fill[c]++] = i;
+        }
+        memcpy(t->ord + b.p0, tmp, sizeof(int64_t) * (size_t)b.np);
+        for (int c = 0; c < 4; ++c) {
+            int id = atree_add(t, b.l + 1, 2 * b.bx + (c & 1), 2 * b.by + (c >> 1), k, b.p0 + off[c], cnt[c]);
+            if (id < 0) {
+                free(tmp);
+                return -2;
+            }
+            t->box[k].child[c] = id;
+        }
+    }
+    free(tmp);
+    return 0;
+}
+
+static int a_adjacent(const abox_t *a, const abox_t *c)
+{
+    return a->lo[0] <= c->hi[0] + 1 && c->lo[0] <= a->hi[0] + 1 && a->lo[1] <= c->hi[1] + 1 &&
+           c->lo[1] <= a->hi[1] + 1;
+}
+
+static int a_is_leaf(const abox_t *a) { return a->child[0] < 0; }
+
+static int in_U(const atree_t *t, int a, int c)
+{
+    const abox_t *A = &t->box[a], *C = &t->box[c];
+    return a_is_leaf(A) && a_is_leaf(C) && a_adjacent(A, C);
+}
+
+static int in_V(const atree_t *t, int a, int c)
+{
+    const abox_t *A = &t->box[a], *C = &t->box[c];
+    if (A->l < 2 || C->l != A->l || a_adjacent(A, C))
+        return 0;
+    return a_adjacent(&t->box[A->parent], &t->box[C->parent]);
+}
+
+static int in_W(const atree_t *t, int a, int c)
+{
+    const abox_t *A = &t->box[a], *C = &t->box[c];
+    if (!a_is_leaf(A) || C->l <= A->l || a_adjacent(A, C) || !a_adjacent(A, &t->box[C->parent]))
+        return 0;
+    int anc = c; /* c's ancestor at a's level must be a colleague of a */
+    while (t->box[anc].l > A->l)
+        anc = t->box[anc].parent;
+    return a_adjacent(A, &t->box[anc]);
+}
+
+static int in_X(const atree_t *t, int a, int c) { return in_W(t, c, a); }
+
+/* Structural check of the four lists: for every ordered pair of leaves (a, b) the number of ways the
+ * pair's interaction is delivered -- b in U(a); beta in V(alpha); beta in W(a); b in X(alpha), with alpha
+ * ranging over a and its ancestors and beta over b and its ancestors -- must be exactly one. Returns the
+ * number of leaf pairs where it is not; sizes = {boxes, leaves, sum |U|, sum |V|, sum |W|, sum |X|,
+ * max |V|, deepest leaf level}. */
+int oracle_adaptive_lists_check(int64_t n, const double *x, const double *y, int Lmax, int B, const double *dom,
+                                int64_t *sizes)
+{
+    atree_t t;
+    int rc = atree_build(&t, n, x, y, Lmax, B, dom);
+    if (rc != 0) {
+        atree_free(&t);
+        return rc;
+    }
+    int nb = t.nbox;
+    int64_t su = 0, sv = 0, sw = 0, sx = 0, nleaf = 0, maxv = 0, deep = 0;
+    for (int a = 0; a < nb; ++a) {
+        int64_t va = 0;
+        for (int c = 0; c < nb; ++c) {
+            su += in_U(&t, a, c);
+            va += in_V(&t, a, c);
+            sw += in_W(&t, a, c);
+            sx += in_X(&t, a, c);
+        }
+        sv += va;
+        if (va > maxv)
+            maxv = va;
+        if (a_is_leaf(&t.box[a])) {
+            nleaf++;
+            if (t.box[a].l > deep)
+                deep = t.box[a].l;
+        }
+    }
+    int bad = 0;
+    for (int a = 0; a < nb; ++a) {
+        if (!a_is_leaf(&t.box[a]))
+            continue;
+        for (int b = 0; b < nb; ++b) {
+            if (!a_is_leaf(&t.box[b]))
+                continue;
+            int count = in_U(&t, a, b);
+            for (int al = a; al >= 0; al = t.box[al].parent) {
+                for (int be = b; be >= 0; be = t.box[be].parent)
+                    count += in_V(&t, al, be);
+                count += in_X(&t, al, b);
+            }
+            for (int be = b; be >= 0; be = t.box[be].parent)
+                count += in_W(&t, a, be);
+            bad += count != 1;
+        }
+    }
+    if (sizes) {
+        int64_t s[8] = {nb, nleaf, su, sv, sw, sx, maxv, deep};
+        memcpy(sizes, s, sizeof s);
+    }
+    atree_free(&t);
+    return bad;
+}
+
+/* X list operator (P2L): the local expansion about c of point charges q_j at z_j outside its disc, from
+ * 1/(z - z_j) = -sum_l (z - c)^l / (z_j - c)^(l+1):   b_l += -sum_j q_j / (z_j - c)^(l+1).   Accumulates. */
+void oracle_p2l(int64_t np, const double *x, const double *y, const double *qre, const double *qim, double cx,
+                double cy, int p, double *b_out)
+{
+    cplx *b = (cplx *)b_out;
+    for (int64_t j = 0; j < np; ++j) {
+        cplx q = qre[j] + I * qim[j];
+        cplx inv = 1.0 / ((x[j] - cx) + I * (y[j] - cy)), pw = inv;
+        for (int l = 0; l < p; ++l) {
+            b[l] -= q * pw;
+            pw *= inv;
+        }
+    }
+}
+
+static cplx a_centre(const atree_t *t, const abox_t *b)
+{
+    double w = t->S / ldexp(1.0, b->l);
+    return (t->x0 + (b->bx + 0.5) * w) + I * (t->y0 + (b->by + 0.5) * w);
+}
+
+/* The adaptive FMM: P2M at the leaves, M2M up, then level by level M2L (V), P2L (X) and L2L down; at every
+ * leaf L2P, the W multipoles evaluated at its particles, and the exact K_sigma over U. parts: 1 near, 2 far,
+ * 3 both. Output in input order. Returns 0, -1 for a point outside an explicit square, -2 on allocation
+ * failure. */
+int oracle_adaptive_fmm(int64_t n, const double *x, const double *y, const double *g, double sigma, int Lmax,
+                        int B, int p, const double *dom, double *u, double *v, int parts)
+{
+    if (n <= 0)
+        return 0;
+    atree_t t;
+    int rc = atree_build(&t, n, x, y, Lmax, B, dom);
+    if (rc != 0) {
+        atree_free(&t);
+        return rc;
+    }
+    int nb = t.nbox;
+    cplx *mp = calloc((size_t)nb * (size_t)p, sizeof(cplx)), *loc = calloc((size_t)nb * (size_t)p, sizeof(cplx));
+    double *qre = calloc((size_t)n, sizeof(double)), *qim = malloc(sizeof(double) * (size_t)n);
+    double *bx = malloc(sizeof(double) * (size_t)n), *by = malloc(sizeof(double) * (size_t)n);
+    if (!mp || !loc || !qre || !qim || !bx || !by) {
+        rc = -2;
+        goto done;
+    }
+    /* particles in box order, so a box's particles are one contiguous run */
+    for (int64_t e = 0; e < n; ++e) {
+        int64_t i = t.ord[e];
+        bx[e] = x[i];
+        by[e] = y[i];
+        qim[e] = -g[i] / (2.0 * ORACLE_PI); /* q = -i gamma / 2 pi */
+    }
+    /* upward: P2M at leaves on levels >= 2, then M2M from the deepest level up (reverse breadth-first order) */
+    for (int k = nb - 1; k >= 0; --k) {
+        abox_t *b = &t.box[k];
+        if (b->l < 2)
+            continue;
+        cplx c = a_centre(&t, b);
+        if (a_is_leaf(b)) {
+            oracle_p2m(b->np, bx + b->p0, by + b->p0, qre + b->p0, qim + b->p0, creal(c), cimag(c), p,
+                       (double *)(mp + (size_t)k * p));
+        } else {
+            for (int q = 0; q < 4; ++q) {
+                int ch = b->child[q];
+                cplx d = a_centre(&t, &t.box[ch]) - c;
+                oracle_m2m(p, (const double *)(mp + (size_t)ch * p), creal(d), cimag(d), (double *)(mp + (size_t)k * p));
+            }
+        }
+    }
+    /* downward in breadth-first order: a parent's local is complete before its children read it */
+    for (int k = 0; k < nb; ++k) {
+        abox_t *b = &t.box[k];
+        if (b->l < 2)
+            continue;
+        cplx c = a_centre(&t, b);
+        double *lk = (double *)(loc + (size_t)k * p);
+        if (b->l >= 3) {
+            cplx d = c - a_centre(&t, &t.box[b->parent]);
+            oracle_l2l(p, (const double *)(loc + (size_t)b->parent * p), creal(d), cimag(d), lk);
+        }
+        for (int s = 0; s < nb; ++s) {
+            if (in_V(&t, k, s)) {
+                cplx d = a_centre(&t, &t.box[s]) - c;
+                oracle_m2l(p, (const double *)(mp + (size_t)s * p), creal(d), cimag(d), lk);
+            } else if (in_X(&t, k, s)) {
+                const abox_t *S = &t.box[s];
+                oracle_p2l(S->np, bx + S->p0, by + S->p0, qre + S->p0, qim + S->p0, creal(c), cimag(c), p, lk);
+            }
+        }
+    }
+    /* leaves: far (L2P + W) and near (U) */
+    for (int k = 0; k < nb; ++k) {
+        abox_t *b = &t.box[k];
+        if (!a_is_leaf(b) || b->np == 0)
+            continue;
+        cplx c = a_centre(&t, b);
+        for (int64_t e = b->p0; e < b->p0 + b->np; ++e) {
+            int64_t i = t.ord[e];
+            double su = 0.0, sv = 0.0;
+            if (parts & 2) {
+                cplx w = 0.0;
+                double wv[2];
+                if (b->l >= 2) {
+                    oracle_l2p(p, (const double *)(loc + (size_t)k * p), bx[e] - creal(c), by[e] - cimag(c), wv);
+                    w += wv[0] + I * wv[1];
+                }
+                for (int s = 0; s < nb; ++s)
+                    if (in_W(&t, k, s)) {
+                        cplx cs = a_centre(&t, &t.box[s]);
+                        oracle_multipole_eval(p, (const double *)(mp + (size_t)s * p), bx[e] - creal(cs),
+                                              by[e] - cimag(cs), wv);
+                        w += wv[0] + I * wv[1];
+                    }
+                su += creal(w);
+                sv -= cimag(w);
+            }
+            if (parts & 1)
+                for (int s = 0; s < nb; ++s) {
+                    if (!in_U(&t, k, s))
+                        continue;
+                    const abox_t *S = &t.box[s];
+                    for (int64_t f = S->p0; f < S->p0 + S->np; ++f) {
+                        if (f == e)
+                            continue;
+                        double ku, kv;
+                        oracle_kernel(bx[e] - bx[f], by[e] - by[f], sigma, &ku, &kv);
+                        int64_t j = t.ord[f];
+                        su += g[j] * ku;
+                        sv += g[j] * kv;
+                    }
+                }
+            u[i] = su;
+            v[i] = sv;
+        }
+    }
+done:
+    free(mp);
+    free(loc);
+    free(qre);
+    free(qim);
+    free(bx);
+    free(by);
+    atree_free(&t);
+    return rc;
+}
+
+/* The exact sum the adaptive FMM approaches as p grows: K_sigma between particles whose leaves are
+ * adjacent (or equal), the point-vortex kernel between all other pairs. Output in input order. */
+int oracle_adaptive_split_direct(int64_t n, const double *x, const double *y, const double *g, double sigma,
+                                 int Lmax, int B, const double *dom, double *u, double *v)
+{
+    if (n <= 0)
+        return 0;
+    atree_t t;
+    int rc = atree_build(&t, n, x, y, Lmax, B, dom);
+    int *leaf = malloc(sizeof(int) * (size_t)n);
+    if (rc != 0 || !leaf) {
+        free(leaf);
+        atree_free(&t);
+        return rc ? rc : -2;
+    }
+    for (int k = 0; k < t.nbox; ++k)
+        if (a_is_leaf(&t.box[k]))
+            for (int64_t e = t.box[k].p0; e < t.box[k].p0 + t.box[k].np; ++e)
+                leaf[t.ord[e]] = k;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double su = 0.0, sv = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i)
+                continue;
+            double ku, kv;
+            if (a_adjacent(&t.box[leaf[i]], &t.box[leaf[j]]))
+                oracle_kernel(x[i] - x[j], y[i] - y[j], sigma, &ku, &kv);
+            else
+                point_vortex_kernel(x[i] - x[j], y[i] - y[j], &ku, &kv);
+            su += g[j] * ku;
+            sv += g[j] * kv;
+        }
+        u[i] = su;
+        v[i] = sv;
+    }
+    free(leaf);
+    atree_free(&t);
+    return 0;
+}

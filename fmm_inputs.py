@@ -15,6 +15,8 @@ Workloads:
   batched_64          64 systems, N_k log-uniform in [4096, 262144], uniform, gamma ~ N(0, 1)/N_k,
                       sigma_k = 0.5/sqrt(N_k), depth_k = round(log4(N_k / 64)), p = 14
   adjoint_1m          uniform_1m positions; target velocities from gamma + 0.01 N(0, 1)/N
+  two_scale           small adaptive-tree test field: a dense blob (std 0.02), a uniform background and three
+                      isolated points, so that leaves sit on many levels
 """
 from __future__ import annotations
 
@@ -167,3 +169,15 @@ def clustered(n: int, seed_index: int = 11, sigma: float | None = None, depth: i
     if sigma is None:
         sigma = 0.5 / math.sqrt(n)
     return Workload("clustered", x, y, g, sigma, depth, p, (0.0, 0.0, 1.0))
+
+
+def two_scale(n: int, seed_index: int = 21) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Dense blob (60%, std 0.02 around (0.31, 0.62)), uniform background and three isolated points, clipped to
+    [0, 0.999]: leaves of an adaptive tree on many levels, with non-empty W and X lists. Returns (x, y, gamma)."""
+    r = rng(seed_index)
+    m = int(0.6 * n)
+    x = np.concatenate([0.31 + 0.02 * r.standard_normal(m), r.random(n - m - 3), [0.9, 0.91, 0.05]])
+    y = np.concatenate([0.62 + 0.02 * r.standard_normal(m), r.random(n - m - 3), [0.1, 0.1, 0.95]])
+    x, y = np.clip(x, 0.0, 0.999), np.clip(y, 0.0, 0.999)
+    g = r.standard_normal(n) / n
+    return x, y, g

@@ -99,6 +99,23 @@ fmm_status fmm_set_m2l_engine(fmm_handle h, int engine);
 /* The handle's M2L engine (FMM_M2L_TENSOR or FMM_M2L_CUDA_CORES; fmm_autotune may change it), -1 for NULL. */
 int fmm_get_m2l_engine(fmm_handle h);
 
+/* Adaptive quadtree for uneven densities (the paper's closing section names them as the next step beyond its
+ * uniform tree). leaf_capacity = 0 (default): the uniform tree of depth tree_depth. leaf_capacity = B > 0: the
+ * tree is refined where the particles are: a box is split into its four children while it holds more than B
+ * particles and its level is below tree_depth (now the maximum depth). Interactions follow the U, V, W, X
+ * lists of Carrier, Greengard and Rokhlin: the exact K_sigma of Eq. 6 between particles of adjacent leaves
+ * (U), M2L between same-level boxes whose parents are adjacent (V), multipoles of small boxes evaluated at the
+ * particles of a larger adjacent-parent leaf (W) and the particles of a coarse leaf expanded into a small
+ * box's local expansion (X). So the sum is Eq. 7 with K_sigma between adjacent leaves and the point-vortex
+ * kernel elsewhere, as on the uniform tree. The adaptive evaluation computes in FP64 whatever the precision
+ * setting, serves fmm_velocity, fmm_velocity_near / _far, fmm_velocity_host and fmm_advect, and counts no
+ * pairs; fmm_velocity_batched, fmm_velocity_adjoint and fmm_autotune return FMM_EINVAL while it is set.
+ * Returns FMM_EINVAL for NULL or a negative capacity. */
+fmm_status fmm_set_adaptive(fmm_handle h, int leaf_capacity);
+
+/* The handle's leaf capacity (0: uniform tree), -1 for NULL. */
+int fmm_get_adaptive(fmm_handle h);
+
 /* A tree depth for n particles in a root square of side `side` with blob core sigma (host only, no device
  * work): the occupancy depth round(log4(n / leaf_target)) (leaf_target <= 0: 64, the occupancy measured fastest
  * for the precision form on GB300), reduced until the leaf width w = side / 2^L keeps the Gaussian tail of the

@@ -34,6 +34,8 @@ SIGNATURES = {
     "fmm_set_coarse_level": (_I, [_P, _I]),
     "fmm_set_m2l_engine": (_I, [_P, _I]),
     "fmm_get_m2l_engine": (_I, [_P]),
+    "fmm_set_adaptive": (_I, [_P, _I]),
+    "fmm_get_adaptive": (_I, [_P]),
     "fmm_suggest_depth": (_I, [_I64, _D, _D, _D, _D]),
     "fmm_set_params": (_I, [_P, _I, _I, _D]),
     "fmm_set_stream": (_I, [_P, _P]),

@@ -41,11 +41,14 @@ class FMM:
 
     precision: "fp64" (plain form) or "mixed" (precision form). domain: (x0, y0, side) or None for the
     bounding-box rule. graph: capture and replay the evaluation as a CUDA graph. m2l_engine: "tensor"
-    (tcgen05, default) or "cuda_cores" for the FP32 M2L levels of the precision form.
+    (tcgen05, default) or "cuda_cores" for the FP32 M2L levels of the precision form. leaf_capacity: 0 for the
+    uniform tree; B > 0 for the adaptive tree (depth is then its maximum depth; boxes holding more than B
+    particles are split; computed in FP64).
     """
 
     def __init__(self, depth: int, p: int, sigma: float, precision: str = "fp64", domain=None,
-                 graph: bool = False, coarse_level: int | None = None, m2l_engine: str | None = None):
+                 graph: bool = False, coarse_level: int | None = None, m2l_engine: str | None = None,
+                 leaf_capacity: int = 0):
         self._lib = _lib.load()
         h = ctypes.c_void_p()
         st = self._lib.fmm_create(int(depth), int(p), float(sigma), ctypes.byref(h))
@@ -61,6 +64,8 @@ class FMM:
             check(self._lib.fmm_set_coarse_level(self.h, int(coarse_level)), self.h)
         if m2l_engine is not None:
             self.set_m2l_engine(m2l_engine)
+        if leaf_capacity:
+            self.set_adaptive(leaf_capacity)
 
     # -- configuration
     def close(self) -> None:
@@ -82,6 +87,10 @@ class FMM:
     def set_m2l_engine(self, engine: str) -> None:
         code = {"cuda_cores": 0, "tensor": 1}[engine]
         check(self._lib.fmm_set_m2l_engine(self.h, code), self.h)
+
+    def set_adaptive(self, leaf_capacity: int) -> None:
+        """0: uniform tree; B > 0: adaptive tree splitting boxes with more than B particles."""
+        check(self._lib.fmm_set_adaptive(self.h, int(leaf_capacity)), self.h)
 
     def set_domain(self, x0: float, y0: float, side: float) -> None:
         check(self._lib.fmm_set_domain(self.h, float(x0), float(y0), float(side)), self.h)
@@ -111,7 +120,8 @@ class FMM:
                                        ctypes.byref(kt)), self.h)
         eng = self._lib.fmm_get_m2l_engine(self.h)
         return {"depth": d.value, "p": p.value, "sigma": s.value, "p2p_threads": th.value,
-                "p2p_targets_per_thread": kt.value, "m2l_engine": {0: "cuda_cores", 1: "tensor"}.get(eng, "?")}
+                "p2p_targets_per_thread": kt.value, "m2l_engine": {0: "cuda_cores", 1: "tensor"}.get(eng, "?"),
+                "leaf_capacity": self._lib.fmm_get_adaptive(self.h)}
 
     def _stream(self) -> None:
         s = torch.cuda.current_stream()

@@ -211,7 +211,7 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
         if (not_finite(yi))
             iy = 0;
     }
-    const int kk = (int)(d.leaf0 + (int64_t)iy * nside + ix);
+    const int kk = (int)(d.leaf0 + (w.morton ? (int64_t)morton2(ix, iy) : (int64_t)iy * nside + ix));
     w.key[i] = kk;
     w.slot[i] = atomicAdd(&w.cnt[kk], 1);  // arrival slot inside the leaf (the in-leaf order is fixed later)
     if (w.mixed) {

@@ -53,6 +53,7 @@ struct fmm_ctx {
     int mixed = 0;
     int coarse = -1;  // precision form: FP32 on every level (radius-scaled translations stay bounded)
     int m2l_engine = FMM_M2L_TENSOR;
+    int adaptive_cap = 0;  // > 0: adaptive tree (depth = maximum depth), split boxes holding more particles
     cudaStream_t stream = nullptr;  // caller's stream
     cudaStream_t exec = nullptr;    // internal stream used for graph capture / replay
     cudaStream_t side = nullptr;    // high-priority stream of the multipole sweep
@@ -93,7 +94,7 @@ struct fmm_ctx {
     uint64_t layout_version = 1;
     size_t layout_sig[6] = {};
     struct GKey {
-        int mode, n, nsys, mixed, coarse, m2l_engine, threads, kt, count_pairs, p, timing;
+        int mode, n, nsys, mixed, coarse, m2l_engine, threads, kt, count_pairs, p, timing, adaptive;
         uint64_t layout;
         const void *ptr[5];
         uint64_t version;
@@ -317,7 +318,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
                        (long long)n, (long long)nleaf);
     int nsys = (int)h->sys_cfg.size();
     int p = h->p;
-    bool mixed = h->mixed && !adjoint;
+    bool mixed = h->mixed && !adjoint && !h->adaptive_cap;  // the adaptive tree computes in FP64
     bool f64 = !mixed || adjoint;
     size_t np = (size_t)n + 8;
     size_t sizes[40];
@@ -388,6 +389,8 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.m2l_tc = h->m2l_engine == FMM_M2L_TENSOR ? 1 : 0;
     w.nsys = nsys;
     w.maxdepth = h->lv.maxdepth;
+    w.morton = h->adaptive_cap > 0 ? 1 : 0;
+    w.adapt_cap = h->adaptive_cap;
     w.key = (int *)(b + lay.off[0]);
     w.cnt = (int *)(b + lay.off[1]);
     w.start = (int *)(b + lay.off[2]);
@@ -476,9 +479,55 @@ static cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s)
                                                                                 : cudaEventRecordDefault);
 }
 
+// The adaptive tree: the same binning (Morton keys at the maximum depth), the multipole sweep on the side
+// stream concurrent with the near field over the U lists, then the final kernel (adaptive.cu).
+static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const double *x, const double *y,
+                                   const double *g, double *u, double *v)
+{
+    Work &w = h->w;
+    bool far = mode != MODE_NEAR && w.maxdepth >= 1;
+    bool near = mode != MODE_FAR;
+    bool timed = h->timing != 0;
+    int64_t nl = 0;
+    (void)cudaGetLastError();
+    if (timed)
+        CU(record_timing(h->ev_t[0], s));
+    CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
+    if (!h->has_domain)
+        nl += launch_bbox(w, x, y, s);
+    nl += launch_domain_finalize(w, s);
+    nl += launch_keys(w, x, y, g, s);
+    nl += launch_scan(w, s);
+    nl += launch_scatter_sort(w, s);
+    nl += launch_gather(w, x, y, g, nullptr, nullptr, s);
+    if (timed)
+        CU(record_timing(h->ev_t[1], s));
+    if (far && w.maxdepth >= 2) {
+        CU(cudaEventRecord(h->ev_fork, s));
+        CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        nl += launch_adaptive_sweep(w, h->side);
+        CU(cudaEventRecord(h->ev_join, h->side));
+    }
+    if (near)
+        nl += launch_adaptive_near(w, s);
+    if (far && w.maxdepth >= 2)
+        CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+    nl += launch_adaptive_final(w, near ? 1 : 0, far ? 1 : 0, u, v, s);
+    CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    if (timed)
+        CU(record_timing(h->ev_t[7], s));
+    CU(cudaGetLastError());
+    h->launches += nl;
+    h->last_timed = timed;
+    h->timed_mask = timed ? 0x83u : 0u;
+    return FMM_OK;
+}
+
 static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const double *x, const double *y,
                                   const double *g, double *u, double *v)
 {
+    if (h->adaptive_cap > 0)
+        return enqueue_adaptive(h, s, mode, x, y, g, u, v);
     Work &w = h->w;
     bool far = mode != MODE_NEAR && w.lv.maxdepth >= 2;
     bool near = mode != MODE_FAR;
@@ -585,7 +634,7 @@ static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x
     if ((st = upload_systems(h)) != FMM_OK)
         return st;
     if (h->count_pairs)
-        h->pairs_valid = 1;
+        h->pairs_valid = h->adaptive_cap ? 0 : 1;  // the adaptive tree counts no pairs
     if (!h->use_graph) {
         if ((st = enqueue_forward(h, h->stream, mode, x, y, g, u, v)) != FMM_OK)
             return st;
@@ -605,6 +654,7 @@ static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x
     key.count_pairs = h->count_pairs;
     key.p = h->p;
     key.timing = h->timing;
+    key.adaptive = h->adaptive_cap;
     key.layout = h->layout_version;
     key.ptr[0] = x;
     key.ptr[1] = y;
@@ -785,6 +835,19 @@ fmm_status fmm_set_m2l_engine(fmm_handle h, int engine)
 
 int fmm_get_m2l_engine(fmm_handle h) { return h ? h->m2l_engine : -1; }
 
+fmm_status fmm_set_adaptive(fmm_handle h, int leaf_capacity)
+{
+    if (!h || leaf_capacity < 0)
+        return FMM_EINVAL;
+    if (leaf_capacity != h->adaptive_cap) {
+        h->adaptive_cap = leaf_capacity;
+        h->cfg_version++;
+    }
+    return FMM_OK;
+}
+
+int fmm_get_adaptive(fmm_handle h) { return h ? h->adaptive_cap : -1; }
+
 int fmm_suggest_depth(int64_t n, double sigma, double side, double tail_tol, double leaf_target)
 {
     if (n <= 0 || !(sigma > 0.0) || !(side > 0.0) || !(tail_tol > 0.0 && tail_tol < 1.0))
@@ -958,7 +1021,7 @@ fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const dou
     // Page-locked inputs in the precision form with an explicit square are read once, by the key kernel, so it
     // reads them in place over the host link (the same bytes cross it, without a copy in front of the kernel).
     const double *in[3] = {x, y, gamma};
-    bool direct = h->mixed && h->has_domain;
+    bool direct = h->mixed && h->has_domain && !h->adaptive_cap;
     for (int k = 0; k < 3 && direct; ++k) {
         cudaPointerAttributes a{};
         if (cudaPointerGetAttributes(&a, in[k]) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer)
@@ -1007,6 +1070,8 @@ fmm_status fmm_velocity_batched(fmm_handle h, int nsys, const int64_t *offsets, 
 {
     if (!h)
         return FMM_EINVAL;
+    if (h->adaptive_cap)
+        return set_err(h, FMM_EINVAL, "batched systems use the uniform tree (adaptive capacity is set)");
     if (nsys < 1 || nsys > FMM_MAXSYS || !offsets)
         return set_err(h, FMM_EINVAL, "nsys must be in [1, %d] and offsets given", FMM_MAXSYS);
     if (offsets[0] != 0)
@@ -1057,6 +1122,8 @@ fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const 
     fmm_status st = check_common(h, n, x, y, gamma, gu, gv);
     if (st != FMM_OK)
         return st;
+    if (h->adaptive_cap)
+        return set_err(h, FMM_EINVAL, "the adjoint uses the uniform tree (adaptive capacity is set)");
     if ((st = poll_status(h, false)) != FMM_OK)
         return st;
     if (n == 0)
@@ -1200,6 +1267,8 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
     fmm_status st = check_common(h, n, x, y, gamma, u, v);
     if (st != FMM_OK)
         return st;
+    if (h->adaptive_cap)
+        return set_err(h, FMM_EINVAL, "autotune applies to the uniform tree (adaptive capacity is set)");
     if (depth_lo < 0 || depth_hi > FMM_MAXL || depth_lo > depth_hi)
         return set_err(h, FMM_EINVAL, "bad depth range");
     const char *cache = getenv("FMM2D_TUNE_CACHE");

@@ -98,6 +98,8 @@ struct Work {
     int p2p_rows;             // this evaluation's near field comes per source row (nearp[0..2] hold the parts)
     int nsys;
     int maxdepth;
+    int morton;               // leaf keys in Morton order (adaptive tree) instead of row-major
+    int adapt_cap;            // adaptive tree: a box holding more than this many particles is split (0: uniform)
     // arrays
     int *key, *slot, *cnt, *start, *scan_tmp, *tmp, *perm, *sleaf;
     double *sx, *sy, *sg;
@@ -121,6 +123,27 @@ struct Work {
     int *sys_list;
     LevelInfo lv;
 };
+
+// Morton index of cell (x, y): bits of x on the even positions, bits of y on the odd ones (x, y < 2^16).
+__host__ __device__ inline unsigned spread1(unsigned v)
+{
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__host__ __device__ inline unsigned morton2(unsigned x, unsigned y) { return spread1(x) | (spread1(y) << 1); }
+__host__ __device__ inline unsigned compact1(unsigned v)  // inverse of spread1 on the even bits
+{
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0f0f0f0fu;
+    v = (v | (v >> 4)) & 0x00ff00ffu;
+    v = (v | (v >> 8)) & 0x0000ffffu;
+    return v;
+}
 
 // System of the sidx-th system that has level l.
 __device__ __forceinline__ int sys_at_level(const Work &w, int l, int sidx)
@@ -181,6 +204,13 @@ int launch_combine(const Work &w, int use_near, int use_far, double *u, double *
 int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far
 int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);  // adds it
 int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);
+
+// Adaptive tree (adaptive.cu, single system, FP64 form, keys in Morton order): the multipole sweep (P2M,
+// M2M, then per level L2L + M2L over V + P2L over X), the near field over U into near64, and the final kernel
+// (L2P + multipoles of W + near field, scattered to the caller's order).
+int launch_adaptive_sweep(const Work &w, cudaStream_t s);
+int launch_adaptive_near(const Work &w, cudaStream_t s);
+int launch_adaptive_final(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
 
 void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom);
 

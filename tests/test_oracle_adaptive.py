@@ -17,14 +17,7 @@ def rel_l2(a, b):
 
 
 def two_scale(n, seed):
-    """Dense blob plus sparse background plus a few isolated points: leaves on many levels, non-empty W and X."""
-    r = fmm_inputs.rng(seed)
-    m = int(0.6 * n)
-    x = np.concatenate([0.31 + 0.02 * r.standard_normal(m), r.random(n - m - 3), [0.9, 0.91, 0.05]])
-    y = np.concatenate([0.62 + 0.02 * r.standard_normal(m), r.random(n - m - 3), [0.1, 0.1, 0.95]])
-    x, y = np.clip(x, 0.0, 0.999), np.clip(y, 0.0, 0.999)
-    g = r.standard_normal(n) / n
-    return x, y, g
+    return fmm_inputs.two_scale(n, seed)
 
 
 @pytest.mark.parametrize("case", ["two_scale", "patches", "one_blob_at_max_depth", "coincident", "default_domain"])

@@ -215,6 +215,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     out["advect"] = advect_leg(api, w, x, y, g, tuned, args.precision, flush, stream)
     out["batched"] = batched_leg(api, args.precision, flush, stream)
     out["adjoint"] = adjoint_leg(api, w, x, y, g, flush, stream)
+    if args.workload == "patches_16m" or args.adaptive:
+        out["adaptive"] = adaptive_leg(api, w, x, y, g, flush, stream, leaf_capacity=args.adaptive or 64)
 
     # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
     f.set_count_pairs(True)
@@ -460,6 +462,52 @@ def adjoint_leg(api, w, x, y, g, flush, stream) -> dict:
     return {"form": "fp64", "ms_per_step": t, "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s"}
 
 
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak on this machine)
+
+
+def adaptive_leg(api, w, x, y, g, flush, stream, leaf_capacity: int = 64, max_depth: int = 11) -> dict:
+    """The adaptive quadtree (U, V, W, X lists; FP64) on this workload: graph-replay throughput, the near-field
+    kernel against the FP64 rate, pair counts, and the uniform-tree FP64 form on the same input for comparison."""
+    import torch
+
+    f = api.FMM(max_depth, w.p, w.sigma, precision="fp64", domain=w.domain, graph=True, leaf_capacity=leaf_capacity)
+    u, v = torch.empty_like(x), torch.empty_like(x)
+    for _ in range(3):
+        f.velocity(x, y, g, u, v)
+    ms, _ = timed_steps(lambda: f.velocity(x, y, g, u, v), 5, flush, stream)
+    f.set_graph(False)
+    f.set_timing(True)
+    f.set_count_pairs(True)
+    f.velocity(x, y, g, u, v)
+    st = f.stage_times()  # [binning, near, -, -, -, final, total, fork_to_join]
+    pairs = f.pair_count()
+    f.close()
+    t = statistics.median(ms)
+    near_ms = st[1] if st else None
+    achieved = P2P_FLOPS_PER_PAIR * pairs / (near_ms / 1e3) / 1e12 if near_ms else None
+    out = {"leaf_capacity": leaf_capacity, "max_depth": max_depth, "precision": "fp64",
+           "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s", "ms_per_step": t, "near_pairs": pairs,
+           "stage_ms_eager": dict(zip(["binning", "near", "up", "m2l", "l2l", "final", "total", "fork_to_join"], st)),
+           "roofline": {"bound": "alu", "kernel": "k_ad_near (U-list near field, FP64)", "achieved": achieved,
+                        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                        "peak_note": "nominal GB300 FP64 rate; 22 flops per ordered pair"}}
+    fu = api.FMM(w.depth, w.p, w.sigma, precision="fp64", domain=w.domain, graph=True)
+    uu, vu = torch.empty_like(x), torch.empty_like(x)
+    fu.velocity(x, y, g, uu, vu)
+    msu, _ = timed_steps(lambda: fu.velocity(x, y, g, uu, vu), 2, flush, stream)
+    fu.set_count_pairs(True)
+    fu.set_graph(False)
+    fu.velocity(x, y, g, uu, vu)
+    out["uniform_fp64_same_input"] = {"depth": w.depth, "value": w.n / (statistics.median(msu) / 1e3) / 1e6,
+                                      "ms_per_step": statistics.median(msu), "near_pairs": fu.pair_count()}
+    torch.cuda.synchronize()
+    num = torch.sqrt(((u - uu) ** 2).sum() + ((v - vu) ** 2).sum())
+    out["rel_diff_vs_uniform_fp64"] = float(num / torch.sqrt((uu**2).sum() + (vu**2).sum()))
+    fu.close()
+    return out
+
+
 def cpu_baseline(w, u_gpu, v_gpu) -> dict:
     """The FP64 oracle as it stands, on all host cores: one full FMM evaluation of the same workload (or, above
     2^21 particles, its far field plus near field at 4096 sampled targets), plus accuracy figures of the GPU
@@ -532,6 +580,8 @@ def main():
     ap.add_argument("--workload", default="uniform_1m", choices=["uniform_1m", "patches_16m"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adaptive", type=int, default=0,
+                    help="also time the adaptive tree with this leaf capacity (always on for patches_16m)")
     ap.add_argument("--quick", action="store_true", help="main timing only")
     ap.add_argument("--tile", default=None, help="near-field tile 'threads,targets' instead of the autotuner's")
     ap.add_argument("--m2l-engine", default=None, choices=["tensor", "cuda_cores"],

@@ -108,8 +108,9 @@ int fmm_get_m2l_engine(fmm_handle h);
  * particles of a larger adjacent-parent leaf (W) and the particles of a coarse leaf expanded into a small
  * box's local expansion (X). So the sum is Eq. 7 with K_sigma between adjacent leaves and the point-vortex
  * kernel elsewhere, as on the uniform tree. The adaptive evaluation computes in FP64 whatever the precision
- * setting, serves fmm_velocity, fmm_velocity_near / _far, fmm_velocity_host and fmm_advect, and counts no
- * pairs; fmm_velocity_batched, fmm_velocity_adjoint and fmm_autotune return FMM_EINVAL while it is set.
+ * setting, serves fmm_velocity, fmm_velocity_near / _far, fmm_velocity_host and fmm_advect, and counts the
+ * ordered pairs of its U lists when pair counting is on; fmm_velocity_batched, fmm_velocity_adjoint and
+ * fmm_autotune return FMM_EINVAL while it is set.
  * Returns FMM_EINVAL for NULL or a negative capacity. */
 fmm_status fmm_set_adaptive(fmm_handle h, int leaf_capacity);
 

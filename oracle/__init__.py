@@ -296,14 +296,15 @@ def p2l(x, y, q, centre, p: int) -> np.ndarray:
 def adaptive_lists_check(x, y, max_depth: int, leaf_capacity: int, domain=None):
     """Builds the adaptive tree and its U, V, W, X lists from their definitions. Returns (bad, sizes): bad =
     the number of ordered leaf pairs whose interaction the lists deliver other than exactly once; sizes =
-    dict of boxes, leaves, total |U|, |V|, |W|, |X|, max |V| and the deepest leaf level."""
+    dict of boxes, leaves, total |U|, |V|, |W|, |X|, max |V|, the deepest leaf level and the ordered near
+    pairs (i, j != i) of the U lists."""
     x, y = _f64(x), _f64(y)
-    sizes = np.zeros(8, np.int64)
+    sizes = np.zeros(9, np.int64)
     bad = _load().oracle_adaptive_lists_check(x.size, _ptr(x), _ptr(y), int(max_depth), int(leaf_capacity),
                                               _ptr(_dom(domain)), _ptr(sizes, _I64))
     if bad < 0:
         raise ValueError("oracle_adaptive_lists_check failed")
-    keys = ("boxes", "leaves", "U", "V", "W", "X", "maxV", "deepest")
+    keys = ("boxes", "leaves", "U", "V", "W", "X", "maxV", "deepest", "near_pairs")
     return bad, dict(zip(keys, (int(s) for s in sizes)))
 
 

@@ -1034,7 +1034,7 @@ static int in_X(const atree_t *t, int a, int c) { return in_W(t, c, a); }
  * pair's interaction is delivered -- b in U(a); beta in V(alpha); beta in W(a); b in X(alpha), with alpha
  * ranging over a and its ancestors and beta over b and its ancestors -- must be exactly one. Returns the
  * number of leaf pairs where it is not; sizes = {boxes, leaves, sum |U|, sum |V|, sum |W|, sum |X|,
- * max |V|, deepest leaf level}. */
+ * max |V|, deepest leaf level, ordered particle pairs (i, j != i) whose leaves are in each other's U list}. */
 int oracle_adaptive_lists_check(int64_t n, const double *x, const double *y, int Lmax, int B, const double *dom,
                                 int64_t *sizes)
 {
@@ -1045,11 +1045,13 @@ int oracle_adaptive_lists_check(int64_t n, const double *x, const double *y, int
         return rc;
     }
     int nb = t.nbox;
-    int64_t su = 0, sv = 0, sw = 0, sx = 0, nleaf = 0, maxv = 0, deep = 0;
+    int64_t su = 0, sv = 0, sw = 0, sx = 0, nleaf = 0, maxv = 0, deep = 0, pairs = 0;
     for (int a = 0; a < nb; ++a) {
         int64_t va = 0;
         for (int c = 0; c < nb; ++c) {
             su += in_U(&t, a, c);
+            if (in_U(&t, a, c))
+                pairs += t.box[a].np * t.box[c].np;
             va += in_V(&t, a, c);
             sw += in_W(&t, a, c);
             sx += in_X(&t, a, c);
@@ -1082,7 +1084,7 @@ int oracle_adaptive_lists_check(int64_t n, const double *x, const double *y, int
         }
     }
     if (sizes) {
-        int64_t s[8] = {nb, nleaf, su, sv, sw, sx, maxv, deep};
+        int64_t s[9] = {nb, nleaf, su, sv, sw, sx, maxv, deep, pairs - n};
         memcpy(sizes, s, sizeof s);
     }
     atree_free(&t);

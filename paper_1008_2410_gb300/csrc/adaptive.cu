@@ -13,16 +13,18 @@
 //   W(b), leaf b: boxes below b's colleagues whose parent is adjacent to b but which are not themselves
 //         adjacent to b                                    -> multipole evaluated at b's particles
 //   X(b): leaves c with b in W(c), i.e. coarser leaves adjacent to b's parent and not to b -> P2L
-// Expansions exist on levels >= 2 (levels 0 and 1 hold no well separated pair) and are radius scaled, with
-// zeta = (z - c) / w for a box of side w and charges q' = -i gamma (1 / 2pi applied at the end):
+// Expansions exist on levels >= 2 (levels 0 and 1 hold no well separated pair). They use the uniform tree's
+// radius scaling, so its level-independent tables (M2M, L2L, binomials, powers of 1/delta) serve here too;
+// zeta = (z - c) / w for a box of side w, charges q' = -i gamma (1 / 2pi applied at the end):
 //   multipole  a~_m = sum_j q'_j zeta_j^m
-//   local      b~_k = w^k b_k, so that the far field at z is sum_k b~_k zeta^k
-//   M2M        a~P_n = sum_{m<=n} C(n, m) delta^(n-m) 2^-m a~C_m,      delta = (c_child - c_parent) / w_parent
-//   M2L        b~_k += (1/w) sum_m a~_m (-1)^(m+1) C(m+k, m) / delta^(m+k+1),  delta = (c_src - c_tgt) / w
-//   L2L        b~C_k = 2^-k sum_{j>=k} C(j, k) delta^(j-k) b~P_j,      delta = (c_child - c_parent) / w_parent
-//   P2L        b~_k += -(1/w) sum_j q'_j / s_j^(k+1),   s_j = (z_j - c) / w
-//   M2P        w(z) += (1/w_s) sum_m a~_m / t^(m+1),    t = (z - c_s) / w_s
-// This path computes in FP64 throughout.
+//   local      b^_k = w^(k+1) b_k, so that the far field at z is (1/w) sum_k b^_k zeta^k
+//   M2M        a~P_n = sum_{m<=n} C(n, m) delta^(n-m) 2^-m a~C_m,        delta = (c_child - c_parent) / w_parent
+//   M2L        b^_k += rho^(k+1) sum_m C(m+k, m) (-1)^(m+1) rho^m a~_m,  rho = 1 / delta, delta = (c_src - c_tgt) / w
+//   L2L        b^C_k = sum_{j>=k} C(j, k) 2^-(j+1) delta^(j-k) b^P_j,   delta = (c_child - c_parent) / w_child
+//   P2L        b^_k += -sum_j q'_j / s_j^(k+1),                        s_j = (z_j - c) / w
+//   M2P        w(z) += (1/w_s) sum_m a~_m / t^(m+1),                   t = (z - c_s) / w_s
+// Two forms: FP64 throughout, or the precision form (FP32 expansions and FP32 near field on hi + lo split
+// coordinates, FP64 sums per source leaf and at the end).
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -31,6 +33,7 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925;
 constexpr int kStack = 48;  // DFS stack of the U / W walk; depth <= 2 (L - l) + 2 <= 26 for L <= 12
+constexpr int kRS = 2 * FMM_PMAX + 2;  // row length of the 1/delta power table
 
 struct Tree {
     const int *start;
@@ -76,20 +79,36 @@ __device__ __forceinline__ void covering_box(const Tree &t, int &l, int &x, int 
 
 __device__ __forceinline__ int pack_box(int l, int x, int y) { return (l << 26) | (x << 13) | y; }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+// complex arithmetic in R (double or float)
+template <typename R>
+struct cpx {
+    R re, im;
+};
+template <typename R>
+__device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b)
 {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double2 cinv(double2 a)
+template <typename R>
+__device__ __forceinline__ cpx<R> cadd(cpx<R> a, cpx<R> b)
 {
-    const double d = 1.0 / (a.x * a.x + a.y * a.y);
-    return make_double2(a.x * d, -a.y * d);
+    return {a.re + b.re, a.im + b.im};
 }
-__device__ __forceinline__ double2 cpow(double2 a, int e)  // a^e, e >= 0, by repeated squaring
+template <typename R>
+__device__ __forceinline__ cpx<R> cscale(cpx<R> a, R s)
 {
-    double2 r = make_double2(1.0, 0.0);
+    return {a.re * s, a.im * s};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> cinv(cpx<R> a)
+{
+    const R d = (R)1 / (a.re * a.re + a.im * a.im);
+    return {a.re * d, -a.im * d};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> cpow(cpx<R> a, int e)  // a^e, e >= 0, by repeated squaring
+{
+    cpx<R> r = {(R)1, (R)0};
     while (e > 0) {
         if (e & 1)
             r = cmul(r, a);
@@ -99,27 +118,71 @@ __device__ __forceinline__ double2 cpow(double2 a, int e)  // a^e, e >= 0, by re
     return r;
 }
 
+// Storage of the expansions: FP64 form double2 (M64 / L64), precision form float2 (M32 / L32).
+template <typename R>
+struct Store;
+template <>
+struct Store<double> {
+    using S = double2;
+    __device__ static double2 *mp(const Work &w) { return w.M64; }
+    __device__ static double2 *loc(const Work &w) { return w.L64; }
+    __device__ static const double2 *m2m(const Tables &t) { return t.m2m64; }
+    __device__ static const double2 *l2l(const Tables &t) { return t.l2l64; }
+    __device__ static const double2 *rho(const Tables &t) { return t.rho64; }
+    __device__ static const double *binom(const Tables &t) { return t.binom64; }
+};
+template <>
+struct Store<float> {
+    using S = float2;
+    __device__ static float2 *mp(const Work &w) { return w.M32; }
+    __device__ static float2 *loc(const Work &w) { return w.L32; }
+    __device__ static const float2 *m2m(const Tables &t) { return t.m2m32; }
+    __device__ static const float2 *l2l(const Tables &t) { return t.l2l32; }
+    __device__ static const float2 *rho(const Tables &t) { return t.rho32; }
+    __device__ static const float *binom(const Tables &t) { return t.binom32; }
+};
+
+template <typename R, typename S>
+__device__ __forceinline__ cpx<R> ld(const S *p)
+{
+    const S v = *p;
+    return {(R)v.x, (R)v.y};
+}
+template <typename R, typename S>
+__device__ __forceinline__ void st(S *p, cpx<R> v)
+{
+    p->x = v.re;
+    p->y = v.im;
+}
+
+template <typename R>
+__device__ __forceinline__ typename Store<R>::S *mp_of(const Work &w, int l, unsigned m)
+{
+    return Store<R>::mp(w) + ((size_t)w.sys[0].box0[l] + m) * w.p;
+}
+template <typename R>
+__device__ __forceinline__ typename Store<R>::S *loc_of(const Work &w, int l, unsigned m)
+{
+    return Store<R>::loc(w) + ((size_t)w.sys[0].box0[l] + m) * w.p;
+}
+
 __device__ __forceinline__ double2 centre(const SysDev &d, int l, int x, int y)
 {
     const double w = ldexp(d.S, -l);
     return make_double2(d.x0 + (x + 0.5) * w, d.y0 + (y + 0.5) * w);
 }
 
-__device__ __forceinline__ double2 *mp_of(const Work &w, int l, unsigned m)
-{
-    return w.M64 + ((size_t)w.sys[0].box0[l] + m) * w.p;
-}
-__device__ __forceinline__ double2 *loc_of(const Work &w, int l, unsigned m)
-{
-    return w.L64 + ((size_t)w.sys[0].box0[l] + m) * w.p;
-}
-
 // ------------------------------------------------------------------ stage 4: P2M at the leaves of level l
 
+// One warp per box, lane m = coefficient; the box's particles pass through shared memory 32 at a time, their
+// leaf-relative positions formed in FP64.
+template <typename R>
 __global__ void __launch_bounds__(128) k_ad_p2m(Work w, int l)
 {
-    const unsigned m = blockIdx.x * 4 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+    __shared__ cpx<R> sz[4][32];
+    __shared__ R sgm[4][32];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned m = blockIdx.x * 4 + wi;
     const SysDev &d = w.sys[0];
     const Tree t{w.start, d.depth, w.adapt_cap};
     if (m >= (1u << (2 * l)))
@@ -127,24 +190,35 @@ __global__ void __launch_bounds__(128) k_ad_p2m(Work w, int l)
     const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
     if (!box_exists(t, l, bx, by) || box_split(t, l, bx, by))
         return;
-    const int j0 = box_first(t, l, m), j1 = j0 + box_count(t, l, m);
+    const int j0 = box_first(t, l, m), cnt = box_count(t, l, m);
     const double2 c = centre(d, l, bx, by);
     const double iw = ldexp(1.0, l) / d.S;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int j = j0; j < j1; ++j) {
-        const double2 z = make_double2((w.sx[j] - c.x) * iw, (w.sy[j] - c.y) * iw);
-        const double2 q = make_double2(0.0, -w.sg[j]);
-        acc = cadd(acc, cmul(q, cpow(z, lane)));
+    cpx<R> acc = {(R)0, (R)0};
+    for (int e0 = 0; e0 < cnt; e0 += 32) {
+        if (e0 + lane < cnt) {
+            const int j = j0 + e0 + lane;
+            sz[wi][lane] = {(R)((w.sx[j] - c.x) * iw), (R)((w.sy[j] - c.y) * iw)};
+            sgm[wi][lane] = (R)w.sg[j];
+        }
+        __syncwarp();
+        const int ne = min(32, cnt - e0);
+        for (int e = 0; e < ne; ++e) {
+            const cpx<R> zp = cpow(sz[wi][e], lane);
+            const R g = sgm[wi][e];
+            acc = cadd(acc, cpx<R>{g * zp.im, -g * zp.re});  // q' zeta^m with q' = -i gamma
+        }
+        __syncwarp();
     }
     if (lane < w.p)
-        mp_of(w, l, m)[lane] = acc;
+        st(mp_of<R>(w, l, m) + lane, acc);
 }
 
 // ------------------------------------------------------------------ stage 5: M2M into the split boxes of level l
 
-__global__ void __launch_bounds__(128) k_ad_m2m(Work w, int l)
+template <typename R>
+__global__ void __launch_bounds__(128) k_ad_m2m(Work w, Tables tb, int l)
 {
-    __shared__ double2 sa[4][4][FMM_PMAX];
+    __shared__ cpx<R> sa[4][4][FMM_PMAX];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned m = blockIdx.x * 4 + wi;
     const SysDev &d = w.sys[0];
@@ -154,33 +228,28 @@ __global__ void __launch_bounds__(128) k_ad_m2m(Work w, int l)
     const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
     if (!box_exists(t, l, bx, by) || !box_split(t, l, bx, by))
         return;
-    const int p = w.p;
+    const int p = w.p, P = FMM_PMAX;
     for (int c = 0; c < 4; ++c)
         if (lane < p)
-            sa[wi][c][lane] = mp_of(w, l + 1, 4 * m + c)[lane];
+            sa[wi][c][lane] = ld<R>(mp_of<R>(w, l + 1, 4 * m + c) + lane);
     __syncwarp();
     if (lane >= p)
         return;
-    const int n = lane;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int c = 0; c < 4; ++c) {
-        const double2 dl = make_double2(((c & 1) - 0.5) * 0.5, ((c >> 1) - 0.5) * 0.5);
-        double2 pw = make_double2(1.0, 0.0);  // delta^(n - k), k from n down to 0
-        double C = 1.0;                       // C(n, k)
-        for (int k = n; k >= 0; --k) {
-            acc = cadd(acc, cscale(cmul(pw, sa[wi][c][k]), C * ldexp(1.0, -k)));
-            pw = cmul(pw, dl);
-            C = C * (double)k / (double)(n - k + 1);
-        }
-    }
-    mp_of(w, l, m)[n] = acc;
+    const auto *T = Store<R>::m2m(tb);  // [c][input m][output n]
+    cpx<R> acc = {(R)0, (R)0};
+    for (int c = 0; c < 4; ++c)
+        for (int k = 0; k <= lane; ++k)
+            acc = cadd(acc, cmul(ld<R>(T + (c * P + k) * P + lane), sa[wi][c][k]));
+    st(mp_of<R>(w, l, m) + lane, acc);
 }
 
 // ------------------------------------------------------------------ stages 6-7: locals of level l (L2L + V + X)
 
-__global__ void __launch_bounds__(128) k_ad_down(Work w, int l)
+template <typename R>
+__global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
 {
-    __shared__ double2 sa[4][FMM_PMAX];
+    __shared__ cpx<R> sa[4][32];
+    __shared__ R sgm[4][32];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned m = blockIdx.x * 4 + wi;
     const SysDev &d = w.sys[0];
@@ -190,28 +259,22 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, int l)
     const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
     if (!box_exists(t, l, bx, by))
         return;
-    const int p = w.p, L = d.depth, nside = 1 << l;
+    const int p = w.p, P = FMM_PMAX, L = d.depth, nside = 1 << l;
     const int k = lane < p ? lane : p - 1;  // lanes >= p shadow the last coefficient and do not store
-    const double iw = ldexp(1.0, l) / d.S;
-    double2 acc = make_double2(0.0, 0.0);
+    cpx<R> acc = {(R)0, (R)0};
     // L2L from the parent
     if (l >= 3) {
         if (lane < p)
-            sa[wi][lane] = loc_of(w, l - 1, m >> 2)[lane];
+            sa[wi][lane] = ld<R>(loc_of<R>(w, l - 1, m >> 2) + lane);
         __syncwarp();
-        const double2 dl = make_double2(((bx & 1) - 0.5) * 0.5, ((by & 1) - 0.5) * 0.5);
-        double2 pw = make_double2(1.0, 0.0);  // delta^(j - k)
-        double C = 1.0;                       // C(j, k)
-        double2 s = make_double2(0.0, 0.0);
-        for (int j = k; j < p; ++j) {
-            s = cadd(s, cscale(cmul(pw, sa[wi][j]), C));
-            pw = cmul(pw, dl);
-            C = C * (double)(j + 1) / (double)(j + 1 - k);
-        }
-        acc = cscale(s, ldexp(1.0, -k));
+        const auto *T = Store<R>::l2l(tb) + (((by & 1) << 1) | (bx & 1)) * P * P;  // [input j][output k]
+        for (int j = k; j < p; ++j)
+            acc = cadd(acc, cmul(ld<R>(T + j * P + k), sa[wi][j]));
         __syncwarp();
     }
-    // V: M2L from the children of the parent's neighbours that are not adjacent to b
+    // V: M2L from the children of the parent's neighbours that are not adjacent to b (factored form)
+    const auto *rho = Store<R>::rho(tb);
+    const auto *binom = Store<R>::binom(tb);
     const int px = bx >> 1, py = by >> 1;
     for (int sy = 2 * py - 2; sy <= 2 * py + 3; ++sy) {
         for (int sx = 2 * px - 2; sx <= 2 * px + 3; ++sx) {
@@ -224,26 +287,24 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, int l)
             const unsigned ms = morton2(sx, sy);
             if (box_count(t, l, ms) == 0)
                 continue;
-            if (lane < p)
-                sa[wi][lane] = mp_of(w, l, ms)[lane];
-            __syncwarp();
-            const double2 inv = cinv(make_double2((double)(sx - bx), (double)(sy - by)));
-            double2 pw = cpow(inv, k + 1);  // delta^-(m + k + 1)
-            double C = 1.0;                 // C(m + k, m)
-            double2 s = make_double2(0.0, 0.0);
-            for (int mm = 0; mm < p; ++mm) {
-                const double sg = (mm & 1) ? C : -C;
-                s = cadd(s, cscale(cmul(pw, sa[wi][mm]), sg));
-                pw = cmul(pw, inv);
-                C = C * (double)(mm + k + 1) / (double)(mm + 1);
+            const auto *rp = rho + ((sy - by + 3) * 7 + (sx - bx + 3)) * kRS;
+            if (lane < p) {  // alpha_m = (-1)^(m+1) rho^m a~_m
+                const cpx<R> a = cmul(ld<R>(rp + lane), ld<R>(mp_of<R>(w, l, ms) + lane));
+                sa[wi][lane] = (lane & 1) ? a : cpx<R>{-a.re, -a.im};
             }
-            acc = cadd(acc, cscale(s, iw));
+            __syncwarp();
+            cpx<R> s = {(R)0, (R)0};
+            for (int mm = 0; mm < p; ++mm)
+                s = cadd(s, cscale(sa[wi][mm], (R)binom[mm * P + k]));
+            acc = cadd(acc, cmul(ld<R>(rp + k + 1), s));
             __syncwarp();
         }
     }
     // X: P2L from the coarser leaves adjacent to the parent but not to b
     int seen[8];
     int nseen = 0;
+    const double2 c = centre(d, l, bx, by);
+    const double iw = ldexp(1.0, l) / d.S;
     for (int dy = -1; dy <= 1; ++dy) {
         for (int dx = -1; dx <= 1; ++dx) {
             if (dx == 0 && dy == 0)
@@ -264,22 +325,30 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, int l)
                 continue;
             seen[nseen++] = id;
             const unsigned mq = morton2(qx, qy);
-            const int j0 = box_first(t, lq, mq), j1 = j0 + box_count(t, lq, mq);
-            const double2 c = centre(d, l, bx, by);
-            double2 s = make_double2(0.0, 0.0);
-            for (int j = j0; j < j1; ++j) {
-                const double2 inv = cinv(make_double2((w.sx[j] - c.x) * iw, (w.sy[j] - c.y) * iw));
-                const double2 q = make_double2(0.0, -w.sg[j]);
-                s = cadd(s, cmul(q, cpow(inv, k + 1)));
+            const int j0 = box_first(t, lq, mq), cnt = box_count(t, lq, mq);
+            for (int e0 = 0; e0 < cnt; e0 += 32) {
+                if (e0 + lane < cnt) {  // 1 / s_j, s_j = (z_j - c) / w, formed in FP64
+                    const int j = j0 + e0 + lane;
+                    const double ax = (w.sx[j] - c.x) * iw, ay = (w.sy[j] - c.y) * iw, id2 = 1.0 / (ax * ax + ay * ay);
+                    sa[wi][lane] = {(R)(ax * id2), (R)(-ay * id2)};
+                    sgm[wi][lane] = (R)w.sg[j];
+                }
+                __syncwarp();
+                const int ne = min(32, cnt - e0);
+                for (int e = 0; e < ne; ++e) {
+                    const cpx<R> ip = cpow(sa[wi][e], k + 1);
+                    const R g = sgm[wi][e];
+                    acc = cadd(acc, cpx<R>{-g * ip.im, g * ip.re});  // -q' s^-(k+1), q' = -i gamma
+                }
+                __syncwarp();
             }
-            acc = cadd(acc, cscale(s, -iw));
         }
     }
     if (lane < p)
-        loc_of(w, l, m)[lane] = acc;
+        st(loc_of<R>(w, l, m) + lane, acc);
 }
 
-// ------------------------------------------------------------------ leaf of a sorted particle
+// ------------------------------------------------------------------ leaf of a sorted particle, U / W walk
 
 __device__ __forceinline__ void particle_leaf(const Tree &t, unsigned kf, int &l, int &x, int &y)
 {
@@ -362,7 +431,7 @@ __device__ __forceinline__ void walk_uw(const Work &w, const Tree &t, int l, int
 
 // ------------------------------------------------------------------ stage 9: near field over U
 
-__global__ void __launch_bounds__(128) k_ad_near(Work w)
+__global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pairs)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.n)
@@ -374,7 +443,9 @@ __global__ void __launch_bounds__(128) k_ad_near(Work w)
     const double xi = w.sx[i], yi = w.sy[i];
     const double k2 = 1.0 / (2.0 * d.sigma * d.sigma);
     double su = 0.0, sv = 0.0;
+    long long np = -1;  // ordered pairs (i, j), j != i
     auto near = [&](int j0, int j1) {
+        np += j1 - j0;
         for (int j = j0; j < j1; ++j) {
             const double ax = xi - w.sx[j], ay = yi - w.sy[j];
             const double r2 = ax * ax + ay * ay;
@@ -388,10 +459,83 @@ __global__ void __launch_bounds__(128) k_ad_near(Work w)
     auto none = [](int, int, int) {};
     walk_uw(w, t, l, bx, by, near, none);
     w.near64[i] = make_double2(su, sv);
+    if (pairs)
+        atomicAdd(pairs, (unsigned long long)np);
+}
+
+// Precision form: positions in depth-L cell units X = (x - x0) 2^L / S split into hi + lo floats, so that a
+// displacement (hi_i - hi_j) + (lo_i - lo_j) keeps about 2^-24 of its own size; circulation as a float.
+__global__ void k_ad_split(Work w)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n)
+        return;
+    const SysDev &d = w.sys[0];
+    const double X = (w.sx[i] - d.x0) * d.scale, Y = (w.sy[i] - d.y0) * d.scale;
+    const float hx = (float)X, hy = (float)Y;
+    w.eh[i] = make_float4(hx, hy, (float)(X - (double)hx), (float)(Y - (double)hy));
+    w.eg[i].x = (float)w.sg[i];
+}
+
+// f(x) = (1 - e^-x) / x: the Taylor series sum_k (-x)^k / (k+1)! below x = 1/2 (truncation < 1e-8 relative),
+// the exponential above (cancellation < 2e-7 relative).
+__device__ __forceinline__ float blob_factor(float x)
+{
+    if (x < 0.5f) {
+        float s = 1.0f / 362880.0f;
+        s = fmaf(s, -x, 1.0f / 40320.0f);
+        s = fmaf(s, -x, 1.0f / 5040.0f);
+        s = fmaf(s, -x, 1.0f / 720.0f);
+        s = fmaf(s, -x, 1.0f / 120.0f);
+        s = fmaf(s, -x, 1.0f / 24.0f);
+        s = fmaf(s, -x, 1.0f / 6.0f);
+        s = fmaf(s, -x, 0.5f);
+        return fmaf(s, -x, 1.0f);
+    }
+    return __fdividef(1.0f - __expf(-x), x);
+}
+
+// K_sigma in cell units (r = w_L r_c): K = (-dy_c, dx_c) f(kappa r_c^2) kappa / (2 pi w_L), kappa = w_L^2 / 2 sigma^2.
+// FP32 pair terms, summed in FP32 per source leaf and in FP64 across leaves.
+__global__ void __launch_bounds__(128) k_ad_near32(Work w, unsigned long long *pairs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n)
+        return;
+    const SysDev &d = w.sys[0];
+    const Tree t{w.start, d.depth, w.adapt_cap};
+    int l, bx, by;
+    particle_leaf(t, (unsigned)w.sleaf[i], l, bx, by);
+    const float4 pi = w.eh[i];
+    const double kap = d.wl * d.wl / (2.0 * d.sigma * d.sigma);
+    const float kf = (float)kap;
+    double su = 0.0, sv = 0.0;
+    long long np = -1;
+    auto near = [&](int j0, int j1) {
+        np += j1 - j0;
+        float pu = 0.0f, pv = 0.0f;
+        for (int j = j0; j < j1; ++j) {
+            const float4 pj = w.eh[j];
+            const float g = w.eg[j].x;
+            const float ax = (pi.x - pj.x) + (pi.z - pj.z), ay = (pi.y - pj.y) + (pi.w - pj.w);
+            const float f = g * blob_factor(kf * fmaf(ax, ax, ay * ay));
+            pu = fmaf(-ay, f, pu);
+            pv = fmaf(ax, f, pv);
+        }
+        su += (double)pu;
+        sv += (double)pv;
+    };
+    auto none = [](int, int, int) {};
+    walk_uw(w, t, l, bx, by, near, none);
+    const double sc = kap / (kTwoPi * d.wl);
+    w.near64[i] = make_double2(su * sc, sv * sc);
+    if (pairs)
+        atomicAdd(pairs, (unsigned long long)np);
 }
 
 // ------------------------------------------------------------------ stages 8 + 10: L2P, W, sum, unsort
 
+template <typename R>
 __global__ void __launch_bounds__(128) k_ad_final(Work w, int use_near, int use_far, double *u, double *v)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -405,29 +549,34 @@ __global__ void __launch_bounds__(128) k_ad_final(Work w, int use_near, int use_
         particle_leaf(t, (unsigned)w.sleaf[i], l, bx, by);
         const double xi = w.sx[i], yi = w.sy[i];
         const int p = w.p;
-        double2 wf = make_double2(0.0, 0.0);
+        double wr = 0.0, wi = 0.0;
         if (l >= 2) {
             const double2 c = centre(d, l, bx, by);
             const double iw = ldexp(1.0, l) / d.S;
-            const double2 z = make_double2((xi - c.x) * iw, (yi - c.y) * iw);
-            const double2 *b = loc_of(w, l, morton2(bx, by));
+            const cpx<R> z = {(R)((xi - c.x) * iw), (R)((yi - c.y) * iw)};
+            const auto *b = loc_of<R>(w, l, morton2(bx, by));
+            cpx<R> s = {(R)0, (R)0};
             for (int k = p - 1; k >= 0; --k)
-                wf = cadd(cmul(wf, z), b[k]);
+                s = cadd(cmul(s, z), ld<R>(b + k));
+            wr += (double)s.re * iw;
+            wi += (double)s.im * iw;
         }
         auto none = [](int, int) {};
         auto far = [&](int ls, int sx, int sy) {
             const double2 c = centre(d, ls, sx, sy);
             const double iws = ldexp(1.0, ls) / d.S;
-            const double2 uinv = cinv(make_double2((xi - c.x) * iws, (yi - c.y) * iws));
-            const double2 *a = mp_of(w, ls, morton2(sx, sy));
-            double2 s = make_double2(0.0, 0.0);
+            const double ax = (xi - c.x) * iws, ay = (yi - c.y) * iws, id2 = 1.0 / (ax * ax + ay * ay);
+            const cpx<R> uinv = {(R)(ax * id2), (R)(-ay * id2)};
+            const auto *a = mp_of<R>(w, ls, morton2(sx, sy));
+            cpx<R> s = {(R)0, (R)0};
             for (int mm = p - 1; mm >= 0; --mm)
-                s = cmul(cadd(s, a[mm]), uinv);
-            wf = cadd(wf, cscale(s, iws));
+                s = cmul(cadd(s, ld<R>(a + mm)), uinv);
+            wr += (double)s.re * iws;
+            wi += (double)s.im * iws;
         };
         walk_uw(w, t, l, bx, by, none, far);
-        ru = wf.x / kTwoPi;
-        rv = -wf.y / kTwoPi;
+        ru = wr / kTwoPi;
+        rv = -wi / kTwoPi;
     }
     if (use_near) {
         const double2 nr = w.near64[i];
@@ -439,30 +588,45 @@ __global__ void __launch_bounds__(128) k_ad_final(Work w, int use_near, int use_
     v[pos] = rv;
 }
 
-}  // namespace
-
-int launch_adaptive_sweep(const Work &w, cudaStream_t s)
+template <typename R>
+int sweep_levels(const Work &w, const Tables &t, cudaStream_t s)
 {
     const int L = w.maxdepth;
     int nl = 0;
+    auto grid = [](int l) { return (unsigned)(((1ull << (2 * l)) + 3) / 4); };
     for (int l = 2; l <= L; ++l, ++nl)
-        k_ad_p2m<<<(unsigned)(((1ull << (2 * l)) + 3) / 4), 128, 0, s>>>(w, l);
+        k_ad_p2m<R><<<grid(l), 128, 0, s>>>(w, l);
     for (int l = L - 1; l >= 2; --l, ++nl)
-        k_ad_m2m<<<(unsigned)(((1ull << (2 * l)) + 3) / 4), 128, 0, s>>>(w, l);
+        k_ad_m2m<R><<<grid(l), 128, 0, s>>>(w, t, l);
     for (int l = 2; l <= L; ++l, ++nl)
-        k_ad_down<<<(unsigned)(((1ull << (2 * l)) + 3) / 4), 128, 0, s>>>(w, l);
+        k_ad_down<R><<<grid(l), 128, 0, s>>>(w, t, l);
     return nl;
 }
 
-int launch_adaptive_near(const Work &w, cudaStream_t s)
+}  // namespace
+
+int launch_adaptive_sweep(const Work &w, const Tables &t, cudaStream_t s)
 {
-    k_ad_near<<<(w.n + 127) / 128, 128, 0, s>>>(w);
+    return w.ad_mixed ? sweep_levels<float>(w, t, s) : sweep_levels<double>(w, t, s);
+}
+
+int launch_adaptive_near(const Work &w, unsigned long long *pairs, cudaStream_t s)
+{
+    if (w.ad_mixed) {
+        k_ad_split<<<(w.n + 255) / 256, 256, 0, s>>>(w);
+        k_ad_near32<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs);
+        return 2;
+    }
+    k_ad_near<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs);
     return 1;
 }
 
 int launch_adaptive_final(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s)
 {
-    k_ad_final<<<(w.n + 127) / 128, 128, 0, s>>>(w, use_near, use_far, u, v);
+    if (w.ad_mixed)
+        k_ad_final<float><<<(w.n + 127) / 128, 128, 0, s>>>(w, use_near, use_far, u, v);
+    else
+        k_ad_final<double><<<(w.n + 127) / 128, 128, 0, s>>>(w, use_near, use_far, u, v);
     return 1;
 }
 

@@ -318,7 +318,8 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
                        (long long)n, (long long)nleaf);
     int nsys = (int)h->sys_cfg.size();
     int p = h->p;
-    bool mixed = h->mixed && !adjoint && !h->adaptive_cap;  // the adaptive tree computes in FP64
+    bool mixed = h->mixed && !adjoint && !h->adaptive_cap;  // the adaptive tree bins in the FP64 form
+    bool ad_mixed = h->mixed && !adjoint && h->adaptive_cap;  // ... and keeps FP32 expansions / split positions
     bool f64 = !mixed || adjoint;
     size_t np = (size_t)n + 8;
     size_t sizes[40];
@@ -333,15 +334,15 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = f64 ? np * 8 : 0;                            // 7 sx
     sizes[i++] = f64 ? np * 8 : 0;                            // 8 sy
     sizes[i++] = f64 ? np * 8 : 0;                            // 9 sg
-    sizes[i++] = mixed ? np * 48 : 0;                         // 10 eh, el, eg
+    sizes[i++] = (mixed || ad_mixed) ? np * 48 : 0;           // 10 eh, el, eg
     sizes[i++] = mixed ? np * 8 : 0;                          // 11 far32
     sizes[i++] = mixed ? 0 : np * 16;                         // 12 near64
     sizes[i++] = mixed ? np * 8 : 0;                          // 13 near32
     sizes[i++] = (size_t)nbox * 4 + 16;                       // 14 bcount
     sizes[i++] = (size_t)nbox * p * 16;                       // 15 M64
     sizes[i++] = (size_t)nbox * p * 16;                       // 16 L64
-    sizes[i++] = mixed ? (size_t)nbox * p * 8 : 0;            // 17 M32
-    sizes[i++] = mixed ? (size_t)nbox * p * 8 : 0;            // 18 L32
+    sizes[i++] = (mixed || ad_mixed) ? (size_t)nbox * p * 8 : 0;  // 17 M32
+    sizes[i++] = (mixed || ad_mixed) ? (size_t)nbox * p * 8 : 0;  // 18 L32
     sizes[i++] = adjoint ? np * 8 : 0;                        // 19 sgu
     sizes[i++] = adjoint ? np * 8 : 0;                        // 20 sgv
     sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 21 AM64
@@ -371,7 +372,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
         h->ws_cap = cap;
         CU(cudaMemset(h->ws, 0, cap));
     }
-    size_t sig[6] = {(size_t)n, (size_t)nleaf, (size_t)nbox, (size_t)p, (size_t)(mixed ? 1 : 0) + 2 * (size_t)adjoint,
+    size_t sig[6] = {(size_t)n, (size_t)nleaf, (size_t)nbox, (size_t)p, (size_t)(mixed ? 1 : 0) + 2 * (size_t)adjoint + 4 * (size_t)ad_mixed,
                      (size_t)h->ws};
     if (memcmp(sig, h->layout_sig, sizeof sig) != 0) {
         memcpy(h->layout_sig, sig, sizeof sig);
@@ -391,6 +392,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.maxdepth = h->lv.maxdepth;
     w.morton = h->adaptive_cap > 0 ? 1 : 0;
     w.adapt_cap = h->adaptive_cap;
+    w.ad_mixed = ad_mixed ? 1 : 0;
     w.key = (int *)(b + lay.off[0]);
     w.cnt = (int *)(b + lay.off[1]);
     w.start = (int *)(b + lay.off[2]);
@@ -505,21 +507,30 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     if (far && w.maxdepth >= 2) {
         CU(cudaEventRecord(h->ev_fork, s));
         CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        nl += launch_adaptive_sweep(w, h->side);
+        nl += launch_adaptive_sweep(w, h->t, h->side);
         CU(cudaEventRecord(h->ev_join, h->side));
     }
+    const bool count = near && h->count_pairs;
+    if (count)
+        CU(cudaMemsetAsync(w.pair_count, 0, sizeof(unsigned long long), s));
     if (near)
-        nl += launch_adaptive_near(w, s);
+        nl += launch_adaptive_near(w, count ? w.pair_count : nullptr, s);
+    if (timed)
+        CU(record_timing(h->ev_t[5], s));
     if (far && w.maxdepth >= 2)
         CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+    if (timed)
+        CU(record_timing(h->ev_t[6], s));
     nl += launch_adaptive_final(w, near ? 1 : 0, far ? 1 : 0, u, v, s);
+    if (count)
+        CU(cudaMemcpyAsync(h->h_pairs, w.pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     if (timed)
         CU(record_timing(h->ev_t[7], s));
     CU(cudaGetLastError());
     h->launches += nl;
     h->last_timed = timed;
-    h->timed_mask = timed ? 0x83u : 0u;
+    h->timed_mask = timed ? 0xe3u : 0u;  // binning, near field, final kernel, total
     return FMM_OK;
 }
 
@@ -634,7 +645,7 @@ static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x
     if ((st = upload_systems(h)) != FMM_OK)
         return st;
     if (h->count_pairs)
-        h->pairs_valid = h->adaptive_cap ? 0 : 1;  // the adaptive tree counts no pairs
+        h->pairs_valid = 1;
     if (!h->use_graph) {
         if ((st = enqueue_forward(h, h->stream, mode, x, y, g, u, v)) != FMM_OK)
             return st;

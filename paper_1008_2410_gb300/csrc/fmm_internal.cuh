@@ -100,6 +100,7 @@ struct Work {
     int maxdepth;
     int morton;               // leaf keys in Morton order (adaptive tree) instead of row-major
     int adapt_cap;            // adaptive tree: a box holding more than this many particles is split (0: uniform)
+    int ad_mixed;             // adaptive tree in the precision form (FP32 expansions and near field)
     // arrays
     int *key, *slot, *cnt, *start, *scan_tmp, *tmp, *perm, *sleaf;
     double *sx, *sy, *sg;
@@ -205,11 +206,11 @@ int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, 
 int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);  // adds it
 int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);
 
-// Adaptive tree (adaptive.cu, single system, FP64 form, keys in Morton order): the multipole sweep (P2M,
+// Adaptive tree (adaptive.cu, single system, keys in Morton order, sorted FP64 particles): the multipole sweep (P2M,
 // M2M, then per level L2L + M2L over V + P2L over X), the near field over U into near64, and the final kernel
 // (L2P + multipoles of W + near field, scattered to the caller's order).
-int launch_adaptive_sweep(const Work &w, cudaStream_t s);
-int launch_adaptive_near(const Work &w, cudaStream_t s);
+int launch_adaptive_sweep(const Work &w, const Tables &t, cudaStream_t s);
+int launch_adaptive_near(const Work &w, unsigned long long *pairs, cudaStream_t s);  // pairs: null or a count
 int launch_adaptive_final(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
 
 void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom);

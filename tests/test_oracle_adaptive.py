@@ -20,6 +20,28 @@ def two_scale(n, seed):
     return fmm_inputs.two_scale(n, seed)
 
 
+def brute_near_pairs(x, y, L, B):
+    """Ordered pairs (i, j != i) whose adaptive leaves touch, by brute force over particles in numpy: a particle's
+    leaf is its box at the first level whose box holds at most B particles (or at level L); the leaves' closed
+    squares are compared in depth-L cells. Unit square domain."""
+    ix = np.minimum(np.floor(np.asarray(x) * 2**L), 2**L - 1).astype(np.int64)
+    iy = np.minimum(np.floor(np.asarray(y) * 2**L), 2**L - 1).astype(np.int64)
+    lev = np.full(ix.size, L)
+    done = np.zeros(ix.size, bool)
+    for l in range(L + 1):
+        key = (ix >> (L - l)) * (1 << l) + (iy >> (L - l))
+        _, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
+        stop = (cnt[inv] <= B) & ~done
+        lev[stop] = l
+        done |= stop
+    sh = L - lev
+    x0, y0 = (ix >> sh) << sh, (iy >> sh) << sh
+    x1, y1 = x0 + (1 << sh) - 1, y0 + (1 << sh) - 1
+    adj = ((x0[:, None] <= x1[None, :] + 1) & (x0[None, :] <= x1[:, None] + 1) &
+           (y0[:, None] <= y1[None, :] + 1) & (y0[None, :] <= y1[:, None] + 1))
+    return int(adj.sum()) - ix.size
+
+
 @pytest.mark.parametrize("case", ["two_scale", "patches", "one_blob_at_max_depth", "coincident", "default_domain"])
 def test_lists_deliver_every_leaf_pair_once(case):
     dom = (0.0, 0.0, 1.0)
@@ -48,6 +70,8 @@ def test_lists_deliver_every_leaf_pair_once(case):
     assert bad == 0, s
     assert s["maxV"] <= 27
     assert s["U"] >= s["leaves"]
+    if case in ("two_scale", "one_blob_at_max_depth", "coincident"):
+        assert s["near_pairs"] == brute_near_pairs(x, y, L, B)
     if case in ("two_scale", "patches", "default_domain"):
         assert s["W"] > 0 and s["X"] > 0 and s["W"] == s["X"], s  # X is W transposed
         assert s["deepest"] >= 5

@@ -216,7 +216,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     out["batched"] = batched_leg(api, args.precision, flush, stream)
     out["adjoint"] = adjoint_leg(api, w, x, y, g, flush, stream)
     if args.workload == "patches_16m" or args.adaptive:
-        out["adaptive"] = adaptive_leg(api, w, x, y, g, flush, stream, leaf_capacity=args.adaptive or 64)
+        f.velocity(x, y, g, u, v)
+        out["adaptive"] = adaptive_leg(api, w, x, y, g, u, v, args.precision, flush, stream,
+                                       leaf_capacity=args.adaptive or 64)
 
     # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
     f.set_count_pairs(True)
@@ -465,46 +467,60 @@ def adjoint_leg(api, w, x, y, g, flush, stream) -> dict:
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak on this machine)
 
 
-def adaptive_leg(api, w, x, y, g, flush, stream, leaf_capacity: int = 64, max_depth: int = 11) -> dict:
-    """The adaptive quadtree (U, V, W, X lists; FP64) on this workload: graph-replay throughput, the near-field
-    kernel against the FP64 rate, pair counts, and the uniform-tree FP64 form on the same input for comparison."""
+def adaptive_leg(api, w, x, y, g, u_uni, v_uni, precision, flush, stream, leaf_capacity: int = 64,
+                 max_depth: int = 11) -> dict:
+    """The adaptive quadtree (U, V, W, X lists) on this workload in the run's precision: graph-replay
+    throughput (median of 20), its near-field kernel against the FP32 (or FP64) rate, near pairs, the
+    difference from the uniform-tree result of the main run and, for the precision form, from the FP64 form
+    of the adaptive tree."""
     import torch
 
-    f = api.FMM(max_depth, w.p, w.sigma, precision="fp64", domain=w.domain, graph=True, leaf_capacity=leaf_capacity)
+    f = api.FMM(max_depth, w.p, w.sigma, precision=precision, domain=w.domain, graph=True,
+                leaf_capacity=leaf_capacity)
     u, v = torch.empty_like(x), torch.empty_like(x)
     for _ in range(3):
         f.velocity(x, y, g, u, v)
-    ms, _ = timed_steps(lambda: f.velocity(x, y, g, u, v), 5, flush, stream)
+    ms, _ = timed_steps(lambda: f.velocity(x, y, g, u, v), 20, flush, stream)
     f.set_graph(False)
     f.set_timing(True)
     f.set_count_pairs(True)
     f.velocity(x, y, g, u, v)
     st = f.stage_times()  # [binning, near, -, -, -, final, total, fork_to_join]
     pairs = f.pair_count()
+    f.set_count_pairs(False)
+    # the near-field kernel alone (no sweep beside it): median of 5 near-only evaluations
+    near_alone = []
+    for _ in range(5):
+        flush.zero_()
+        f.velocity_near(x, y, g, u2 := torch.empty_like(x), v2 := torch.empty_like(x))
+        sa = f.stage_times()
+        if sa:
+            near_alone.append(sa[1])
     f.close()
     t = statistics.median(ms)
-    near_ms = st[1] if st else None
+    near_ms = statistics.median(near_alone) if near_alone else None
     achieved = P2P_FLOPS_PER_PAIR * pairs / (near_ms / 1e3) / 1e12 if near_ms else None
-    out = {"leaf_capacity": leaf_capacity, "max_depth": max_depth, "precision": "fp64",
+    peak = FP32_PEAK_TFLOPS if precision == "mixed" else FP64_PEAK_TFLOPS
+    out = {"leaf_capacity": leaf_capacity, "max_depth": max_depth, "precision": precision,
            "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s", "ms_per_step": t, "near_pairs": pairs,
            "stage_ms_eager": dict(zip(["binning", "near", "up", "m2l", "l2l", "final", "total", "fork_to_join"], st)),
-           "roofline": {"bound": "alu", "kernel": "k_ad_near (U-list near field, FP64)", "achieved": achieved,
-                        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                        "peak_note": "nominal GB300 FP64 rate; 22 flops per ordered pair"}}
-    fu = api.FMM(w.depth, w.p, w.sigma, precision="fp64", domain=w.domain, graph=True)
-    uu, vu = torch.empty_like(x), torch.empty_like(x)
-    fu.velocity(x, y, g, uu, vu)
-    msu, _ = timed_steps(lambda: fu.velocity(x, y, g, uu, vu), 2, flush, stream)
-    fu.set_count_pairs(True)
-    fu.set_graph(False)
-    fu.velocity(x, y, g, uu, vu)
-    out["uniform_fp64_same_input"] = {"depth": w.depth, "value": w.n / (statistics.median(msu) / 1e3) / 1e6,
-                                      "ms_per_step": statistics.median(msu), "near_pairs": fu.pair_count()}
+           "roofline_near": {"bound": "alu", "kernel": "k_ad_near32" if precision == "mixed" else "k_ad_near",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak if achieved else None,
+                             "avg_launch_ms": near_ms,
+                             "note": ("near stage (split + near kernel) timed alone in near-only evaluations; "
+                                      "22 flops per ordered pair; peak " +
+                                      ("FP32 FMA derived" if precision == "mixed" else "nominal FP64"))}}
     torch.cuda.synchronize()
-    num = torch.sqrt(((u - uu) ** 2).sum() + ((v - vu) ** 2).sum())
-    out["rel_diff_vs_uniform_fp64"] = float(num / torch.sqrt((uu**2).sum() + (vu**2).sum()))
-    fu.close()
+    den = torch.sqrt((u_uni**2).sum() + (v_uni**2).sum())
+    out["rel_diff_vs_uniform_tree"] = float(torch.sqrt(((u - u_uni) ** 2).sum() + ((v - v_uni) ** 2).sum()) / den)
+    if precision == "mixed":
+        f64 = api.FMM(max_depth, w.p, w.sigma, precision="fp64", domain=w.domain, leaf_capacity=leaf_capacity)
+        u64, v64 = f64.velocity(x, y, g)
+        torch.cuda.synchronize()
+        d64 = torch.sqrt((u64**2).sum() + (v64**2).sum())
+        out["rel_err_vs_fp64_form"] = float(torch.sqrt(((u - u64) ** 2).sum() + ((v - v64) ** 2).sum()) / d64)
+        f64.close()
     return out
 
 

@@ -172,45 +172,99 @@ __device__ __forceinline__ double2 centre(const SysDev &d, int l, int x, int y)
     return make_double2(d.x0 + (x + 0.5) * w, d.y0 + (y + 0.5) * w);
 }
 
-// ------------------------------------------------------------------ stage 4: P2M at the leaves of level l
+// ------------------------------------------------------------------ existing boxes of every level
 
-// One warp per box, lane m = coefficient; the box's particles pass through shared memory 32 at a time, their
-// leaf-relative positions formed in FP64.
-template <typename R>
-__global__ void __launch_bounds__(128) k_ad_p2m(Work w, int l)
+// The boxes of level l + 1 are the four children of each box of level l holding more than B particles. One
+// thread per box of levels 1 .. L-1; each level's index range is padded to a multiple of 32 so that a warp
+// appends its children with one atomic.
+__global__ void k_ad_enum(Work w)
 {
-    __shared__ cpx<R> sz[4][32];
-    __shared__ R sgm[4][32];
-    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned m = blockIdx.x * 4 + wi;
     const SysDev &d = w.sys[0];
     const Tree t{w.start, d.depth, w.adapt_cap};
-    if (m >= (1u << (2 * l)))
-        return;
-    const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
-    if (!box_exists(t, l, bx, by) || box_split(t, l, bx, by))
-        return;
-    const int j0 = box_first(t, l, m), cnt = box_count(t, l, m);
-    const double2 c = centre(d, l, bx, by);
-    const double iw = ldexp(1.0, l) / d.S;
-    cpx<R> acc = {(R)0, (R)0};
-    for (int e0 = 0; e0 < cnt; e0 += 32) {
-        if (e0 + lane < cnt) {
-            const int j = j0 + e0 + lane;
-            sz[wi][lane] = {(R)((w.sx[j] - c.x) * iw), (R)((w.sy[j] - c.y) * iw)};
-            sgm[wi][lane] = (R)w.sg[j];
-        }
-        __syncwarp();
-        const int ne = min(32, cnt - e0);
-        for (int e = 0; e < ne; ++e) {
-            const cpx<R> zp = cpow(sz[wi][e], lane);
-            const R g = sgm[wi][e];
-            acc = cadd(acc, cpx<R>{g * zp.im, -g * zp.re});  // q' zeta^m with q' = -i gamma
-        }
-        __syncwarp();
+    const int L = d.depth;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int lp = 1;
+    int64_t base = 0;
+    while (lp < L && g >= base + (((1ll << (2 * lp)) + 31) & ~31ll)) {
+        base += ((1ll << (2 * lp)) + 31) & ~31ll;
+        ++lp;
     }
-    if (lane < w.p)
-        st(mp_of<R>(w, l, m) + lane, acc);
+    if (lp >= L)
+        return;  // whole warps leave together: every level range is a multiple of 32
+    const int64_t m = g - base;
+    const bool split = m < (1ll << (2 * lp)) && box_count(t, lp, (unsigned)m) > t.B;
+    const unsigned mask = __ballot_sync(0xffffffffu, split);
+    if (!mask)
+        return;
+    const int lane = threadIdx.x & 31;
+    int pos = 0;
+    if (lane == __ffs(mask) - 1)
+        pos = atomicAdd(&w.ad_cnt[lp + 1], 4 * __popc(mask));
+    pos = __shfl_sync(0xffffffffu, pos, __ffs(mask) - 1) + 4 * __popc(mask & ((1u << lane) - 1));
+    if (split) {
+        int *lst = w.ad_list + d.box0[lp + 1];
+        for (int c = 0; c < 4; ++c)
+            lst[pos + c] = (int)(4 * m + c);
+    }
+}
+
+int64_t enum_threads(int L)
+{
+    int64_t t = 0;
+    for (int l = 1; l < L; ++l)
+        t += ((1ll << (2 * l)) + 31) & ~31ll;
+    return t;
+}
+
+constexpr int kSweepBlocks = 152 * 16;  // grid of the list-driven sweep kernels (4 warps per block)
+
+// ------------------------------------------------------------------ stage 4: P2M at the leaves of level l
+
+// One warp per leaf; lane = particle (32 at a time), each lane accumulating the PM coefficients of its particles
+// in registers (powers by repeated multiplication), then a butterfly sum over the warp. Positions relative to
+// the box centre are formed in FP64.
+template <typename R, int PM>
+__global__ void __launch_bounds__(128) k_ad_p2m(Work w, int l)
+{
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SysDev &d = w.sys[0];
+    const Tree t{w.start, d.depth, w.adapt_cap};
+    const int nbx = w.ad_cnt[l], p = w.p;
+    const double iw = ldexp(1.0, l) / d.S;
+    for (int idx = blockIdx.x * 4 + wi; idx < nbx; idx += gridDim.x * 4) {
+        const unsigned m = (unsigned)w.ad_list[d.box0[l] + idx];
+        const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
+        if (box_split(t, l, bx, by))
+            continue;
+        const int j0 = box_first(t, l, m), cnt = box_count(t, l, m);
+        const double2 c = centre(d, l, bx, by);
+        cpx<R> acc[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            acc[k] = {(R)0, (R)0};
+        for (int e = lane; e < cnt; e += 32) {
+            const int j = j0 + e;
+            const cpx<R> z = {(R)((w.sx[j] - c.x) * iw), (R)((w.sy[j] - c.y) * iw)};
+            const R g = (R)w.sg[j];
+            cpx<R> pw = {(R)0, -g};  // q' = -i gamma
+#pragma unroll
+            for (int k = 0; k < PM; ++k) {
+                acc[k] = cadd(acc[k], pw);
+                pw = cmul(pw, z);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[k].re += __shfl_xor_sync(0xffffffffu, acc[k].re, o);
+                acc[k].im += __shfl_xor_sync(0xffffffffu, acc[k].im, o);
+            }
+        auto *dst = mp_of<R>(w, l, m);
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            if (lane == k && k < p)
+                st(dst + k, acc[k]);
+    }
 }
 
 // ------------------------------------------------------------------ stage 5: M2M into the split boxes of level l
@@ -220,132 +274,165 @@ __global__ void __launch_bounds__(128) k_ad_m2m(Work w, Tables tb, int l)
 {
     __shared__ cpx<R> sa[4][4][FMM_PMAX];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned m = blockIdx.x * 4 + wi;
     const SysDev &d = w.sys[0];
     const Tree t{w.start, d.depth, w.adapt_cap};
-    if (m >= (1u << (2 * l)))
-        return;
-    const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
-    if (!box_exists(t, l, bx, by) || !box_split(t, l, bx, by))
-        return;
-    const int p = w.p, P = FMM_PMAX;
-    for (int c = 0; c < 4; ++c)
-        if (lane < p)
-            sa[wi][c][lane] = ld<R>(mp_of<R>(w, l + 1, 4 * m + c) + lane);
-    __syncwarp();
-    if (lane >= p)
-        return;
+    const int nbx = w.ad_cnt[l], p = w.p, P = FMM_PMAX;
     const auto *T = Store<R>::m2m(tb);  // [c][input m][output n]
-    cpx<R> acc = {(R)0, (R)0};
-    for (int c = 0; c < 4; ++c)
-        for (int k = 0; k <= lane; ++k)
-            acc = cadd(acc, cmul(ld<R>(T + (c * P + k) * P + lane), sa[wi][c][k]));
-    st(mp_of<R>(w, l, m) + lane, acc);
+    for (int idx = blockIdx.x * 4 + wi; idx < nbx; idx += gridDim.x * 4) {
+        const unsigned m = (unsigned)w.ad_list[d.box0[l] + idx];
+        const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
+        if (!box_split(t, l, bx, by))
+            continue;
+        __syncwarp();
+        for (int c = 0; c < 4; ++c)
+            if (lane < p)
+                sa[wi][c][lane] = ld<R>(mp_of<R>(w, l + 1, 4 * m + c) + lane);
+        __syncwarp();
+        if (lane < p) {
+            cpx<R> acc = {(R)0, (R)0};
+            for (int c = 0; c < 4; ++c)
+                for (int k = 0; k <= lane; ++k)
+                    acc = cadd(acc, cmul(ld<R>(T + (c * P + k) * P + lane), sa[wi][c][k]));
+            st(mp_of<R>(w, l, m) + lane, acc);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ stages 6-7: locals of level l (L2L + V + X)
 
-template <typename R>
+// One warp per existing box of level l, lane k = local coefficient; the binomial column C(m + k, m) stays in
+// registers (PM >= p, entries m >= p zero) and the V sources are taken two at a time.
+template <typename R, int PM>
 __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
 {
-    __shared__ cpx<R> sa[4][32];
+    __shared__ cpx<R> sa[4][2][32];
     __shared__ R sgm[4][32];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned m = blockIdx.x * 4 + wi;
     const SysDev &d = w.sys[0];
     const Tree t{w.start, d.depth, w.adapt_cap};
-    if (m >= (1u << (2 * l)))
-        return;
-    const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
-    if (!box_exists(t, l, bx, by))
-        return;
-    const int p = w.p, P = FMM_PMAX, L = d.depth, nside = 1 << l;
+    const int nbx = w.ad_cnt[l], p = w.p, P = FMM_PMAX, L = d.depth, nside = 1 << l;
     const int k = lane < p ? lane : p - 1;  // lanes >= p shadow the last coefficient and do not store
-    cpx<R> acc = {(R)0, (R)0};
-    // L2L from the parent
-    if (l >= 3) {
-        if (lane < p)
-            sa[wi][lane] = ld<R>(loc_of<R>(w, l - 1, m >> 2) + lane);
-        __syncwarp();
-        const auto *T = Store<R>::l2l(tb) + (((by & 1) << 1) | (bx & 1)) * P * P;  // [input j][output k]
-        for (int j = k; j < p; ++j)
-            acc = cadd(acc, cmul(ld<R>(T + j * P + k), sa[wi][j]));
-        __syncwarp();
-    }
-    // V: M2L from the children of the parent's neighbours that are not adjacent to b (factored form)
     const auto *rho = Store<R>::rho(tb);
     const auto *binom = Store<R>::binom(tb);
-    const int px = bx >> 1, py = by >> 1;
-    for (int sy = 2 * py - 2; sy <= 2 * py + 3; ++sy) {
-        for (int sx = 2 * px - 2; sx <= 2 * px + 3; ++sx) {
-            if (sx < 0 || sy < 0 || sx >= nside || sy >= nside)
-                continue;
-            if (abs(sx - bx) <= 1 && abs(sy - by) <= 1)
-                continue;
-            if (!box_exists(t, l, sx, sy))
-                continue;
-            const unsigned ms = morton2(sx, sy);
-            if (box_count(t, l, ms) == 0)
-                continue;
-            const auto *rp = rho + ((sy - by + 3) * 7 + (sx - bx + 3)) * kRS;
-            if (lane < p) {  // alpha_m = (-1)^(m+1) rho^m a~_m
-                const cpx<R> a = cmul(ld<R>(rp + lane), ld<R>(mp_of<R>(w, l, ms) + lane));
-                sa[wi][lane] = (lane & 1) ? a : cpx<R>{-a.re, -a.im};
-            }
-            __syncwarp();
-            cpx<R> s = {(R)0, (R)0};
-            for (int mm = 0; mm < p; ++mm)
-                s = cadd(s, cscale(sa[wi][mm], (R)binom[mm * P + k]));
-            acc = cadd(acc, cmul(ld<R>(rp + k + 1), s));
-            __syncwarp();
-        }
-    }
-    // X: P2L from the coarser leaves adjacent to the parent but not to b
-    int seen[8];
-    int nseen = 0;
-    const double2 c = centre(d, l, bx, by);
+    R cb[PM];
+#pragma unroll
+    for (int mm = 0; mm < PM; ++mm)
+        cb[mm] = mm < p ? (R)binom[mm * P + k] : (R)0;
     const double iw = ldexp(1.0, l) / d.S;
-    for (int dy = -1; dy <= 1; ++dy) {
-        for (int dx = -1; dx <= 1; ++dx) {
-            if (dx == 0 && dy == 0)
-                continue;
-            int lq = l - 1, qx = px + dx, qy = py + dy;
-            if (qx < 0 || qy < 0 || qx >= (nside >> 1) || qy >= (nside >> 1))
-                continue;
-            covering_box(t, lq, qx, qy);
-            if (lq == l - 1 && box_split(t, lq, qx, qy))
-                continue;
-            if (adjacent(L, l, bx, by, lq, qx, qy))
-                continue;
-            const int id = pack_box(lq, qx, qy);
-            bool dup = false;
-            for (int e = 0; e < nseen; ++e)
-                dup |= seen[e] == id;
-            if (dup)
-                continue;
-            seen[nseen++] = id;
-            const unsigned mq = morton2(qx, qy);
-            const int j0 = box_first(t, lq, mq), cnt = box_count(t, lq, mq);
-            for (int e0 = 0; e0 < cnt; e0 += 32) {
-                if (e0 + lane < cnt) {  // 1 / s_j, s_j = (z_j - c) / w, formed in FP64
-                    const int j = j0 + e0 + lane;
-                    const double ax = (w.sx[j] - c.x) * iw, ay = (w.sy[j] - c.y) * iw, id2 = 1.0 / (ax * ax + ay * ay);
-                    sa[wi][lane] = {(R)(ax * id2), (R)(-ay * id2)};
-                    sgm[wi][lane] = (R)w.sg[j];
+    for (int idx = blockIdx.x * 4 + wi; idx < nbx; idx += gridDim.x * 4) {
+        const unsigned m = (unsigned)w.ad_list[d.box0[l] + idx];
+        const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
+        cpx<R> acc = {(R)0, (R)0};
+        __syncwarp();
+        // L2L from the parent
+        if (l >= 3) {
+            if (lane < p)
+                sa[wi][0][lane] = ld<R>(loc_of<R>(w, l - 1, m >> 2) + lane);
+            __syncwarp();
+            const auto *T = Store<R>::l2l(tb) + (((by & 1) << 1) | (bx & 1)) * P * P;  // [input j][output k]
+            for (int j = k; j < p; ++j)
+                acc = cadd(acc, cmul(ld<R>(T + j * P + k), sa[wi][0][j]));
+            __syncwarp();
+        }
+        // V: M2L from the children of the parent's neighbours that are not adjacent to b (factored form)
+        const int px = bx >> 1, py = by >> 1;
+        int pend = -1;  // a source waiting for its partner: offset index << 24 | Morton index
+        for (int q = 0; q <= 36; ++q) {
+            int ent = -1;
+            if (q < 36) {
+                const int sx = 2 * px - 2 + q % 6, sy = 2 * py - 2 + q / 6;
+                if (sx < 0 || sy < 0 || sx >= nside || sy >= nside || (abs(sx - bx) <= 1 && abs(sy - by) <= 1) ||
+                    !box_exists(t, l, sx, sy))
+                    continue;
+                const unsigned ms = morton2(sx, sy);
+                if (box_count(t, l, ms) == 0)
+                    continue;
+                ent = (((sy - by + 3) * 7 + (sx - bx + 3)) << 24) | (int)ms;
+                if (pend < 0) {
+                    pend = ent;
+                    continue;
                 }
-                __syncwarp();
-                const int ne = min(32, cnt - e0);
-                for (int e = 0; e < ne; ++e) {
-                    const cpx<R> ip = cpow(sa[wi][e], k + 1);
-                    const R g = sgm[wi][e];
-                    acc = cadd(acc, cpx<R>{-g * ip.im, g * ip.re});  // -q' s^-(k+1), q' = -i gamma
+            } else if (pend < 0) {
+                break;
+            }
+            // contract pend (and ent, if any)
+            const int e0 = pend, e1 = ent;
+            pend = -1;
+            const auto *r0 = rho + (e0 >> 24) * kRS;
+            const auto *r1 = rho + ((e1 >= 0 ? e1 : e0) >> 24) * kRS;
+            if (lane < p) {  // alpha_m = (-1)^(m+1) rho^m a~_m
+                const cpx<R> a0 = cmul(ld<R>(r0 + lane), ld<R>(mp_of<R>(w, l, e0 & 0xffffff) + lane));
+                sa[wi][0][lane] = (lane & 1) ? a0 : cpx<R>{-a0.re, -a0.im};
+                cpx<R> a1 = {(R)0, (R)0};
+                if (e1 >= 0)
+                    a1 = cmul(ld<R>(r1 + lane), ld<R>(mp_of<R>(w, l, e1 & 0xffffff) + lane));
+                sa[wi][1][lane] = (lane & 1) ? a1 : cpx<R>{-a1.re, -a1.im};
+            } else {
+                sa[wi][0][lane] = {(R)0, (R)0};
+                sa[wi][1][lane] = {(R)0, (R)0};
+            }
+            __syncwarp();
+            cpx<R> s0 = {(R)0, (R)0}, s1 = {(R)0, (R)0};
+#pragma unroll
+            for (int mm = 0; mm < PM; ++mm) {
+                const cpx<R> x0 = sa[wi][0][mm], x1 = sa[wi][1][mm];
+                s0.re = fma(cb[mm], x0.re, s0.re);
+                s0.im = fma(cb[mm], x0.im, s0.im);
+                s1.re = fma(cb[mm], x1.re, s1.re);
+                s1.im = fma(cb[mm], x1.im, s1.im);
+            }
+            acc = cadd(acc, cmul(ld<R>(r0 + k + 1), s0));
+            if (e1 >= 0)
+                acc = cadd(acc, cmul(ld<R>(r1 + k + 1), s1));
+            __syncwarp();
+        }
+        // X: P2L from the coarser leaves adjacent to the parent but not to b
+        int seen[8];
+        int nseen = 0;
+        const double2 c = centre(d, l, bx, by);
+        for (int dy = -1; dy <= 1; ++dy) {
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0)
+                    continue;
+                int lq = l - 1, qx = px + dx, qy = py + dy;
+                if (qx < 0 || qy < 0 || qx >= (nside >> 1) || qy >= (nside >> 1))
+                    continue;
+                covering_box(t, lq, qx, qy);
+                if (lq == l - 1 && box_split(t, lq, qx, qy))
+                    continue;
+                if (adjacent(L, l, bx, by, lq, qx, qy))
+                    continue;
+                const int id = pack_box(lq, qx, qy);
+                bool dup = false;
+                for (int e = 0; e < nseen; ++e)
+                    dup |= seen[e] == id;
+                if (dup)
+                    continue;
+                seen[nseen++] = id;
+                const unsigned mq = morton2(qx, qy);
+                const int j0 = box_first(t, lq, mq), cnt = box_count(t, lq, mq);
+                for (int e0 = 0; e0 < cnt; e0 += 32) {
+                    if (e0 + lane < cnt) {  // 1 / s_j, s_j = (z_j - c) / w, formed in FP64
+                        const int j = j0 + e0 + lane;
+                        const double ax = (w.sx[j] - c.x) * iw, ay = (w.sy[j] - c.y) * iw;
+                        const double id2 = 1.0 / (ax * ax + ay * ay);
+                        sa[wi][0][lane] = {(R)(ax * id2), (R)(-ay * id2)};
+                        sgm[wi][lane] = (R)w.sg[j];
+                    }
+                    __syncwarp();
+                    const int ne = min(32, cnt - e0);
+                    for (int e = 0; e < ne; ++e) {
+                        const cpx<R> ip = cpow(sa[wi][0][e], k + 1);
+                        const R g = sgm[wi][e];
+                        acc = cadd(acc, cpx<R>{-g * ip.im, g * ip.re});  // -q' s^-(k+1), q' = -i gamma
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
         }
+        if (lane < p)
+            st(loc_of<R>(w, l, m) + lane, acc);
     }
-    if (lane < p)
-        st(loc_of<R>(w, l, m) + lane, acc);
 }
 
 // ------------------------------------------------------------------ leaf of a sorted particle, U / W walk
@@ -588,26 +675,39 @@ __global__ void __launch_bounds__(128) k_ad_final(Work w, int use_near, int use_
     v[pos] = rv;
 }
 
-template <typename R>
+template <typename R, int PM>
 int sweep_levels(const Work &w, const Tables &t, cudaStream_t s)
 {
     const int L = w.maxdepth;
-    int nl = 0;
-    auto grid = [](int l) { return (unsigned)(((1ull << (2 * l)) + 3) / 4); };
+    int nl = 1;
+    const int64_t ne = enum_threads(L);
+    k_ad_enum<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(w);
     for (int l = 2; l <= L; ++l, ++nl)
-        k_ad_p2m<R><<<grid(l), 128, 0, s>>>(w, l);
+        k_ad_p2m<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, l);
     for (int l = L - 1; l >= 2; --l, ++nl)
-        k_ad_m2m<R><<<grid(l), 128, 0, s>>>(w, t, l);
+        k_ad_m2m<R><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
     for (int l = 2; l <= L; ++l, ++nl)
-        k_ad_down<R><<<grid(l), 128, 0, s>>>(w, t, l);
+        k_ad_down<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
     return nl;
+}
+
+template <typename R>
+int sweep_bucket(const Work &w, const Tables &t, cudaStream_t s)
+{
+    if (w.p <= 8)
+        return sweep_levels<R, 8>(w, t, s);
+    if (w.p <= 16)
+        return sweep_levels<R, 16>(w, t, s);
+    if (w.p <= 24)
+        return sweep_levels<R, 24>(w, t, s);
+    return sweep_levels<R, 32>(w, t, s);
 }
 
 }  // namespace
 
 int launch_adaptive_sweep(const Work &w, const Tables &t, cudaStream_t s)
 {
-    return w.ad_mixed ? sweep_levels<float>(w, t, s) : sweep_levels<double>(w, t, s);
+    return w.ad_mixed ? sweep_bucket<float>(w, t, s) : sweep_bucket<double>(w, t, s);
 }
 
 int launch_adaptive_near(const Work &w, unsigned long long *pairs, cudaStream_t s)

@@ -495,42 +495,62 @@ __global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restr
                                                    const double *__restrict__ gv, int mixed)
 {
     __shared__ int tile[SORT_TILE];
-    const int leaf = blockIdx.x;
-    const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
-    if (c <= 0)
-        return;
-    for (int e0 = 0; e0 < c; e0 += blockDim.x) {
-        const int e = e0 + threadIdx.x;
-        const int v = e < c ? w.tmp[s0 + e] : 0;
-        int rank = 0;
-        for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
-            const int m = min(SORT_TILE, c - f0);
+    __shared__ int busy[64];
+    __shared__ int nbusy;
+    const bool one = gridDim.x >= w.nleaf;  // one block per leaf
+    // otherwise chunks of 64 leaves, strided over the grid: the block lists the chunk's non-empty leaves first
+    for (int base = one ? blockIdx.x : blockIdx.x * 64; base < w.nleaf; base += one ? gridDim.x : gridDim.x * 64) {
+        int nb = 1;
+        if (!one) {
             __syncthreads();
-            for (int j = threadIdx.x; j < m; j += blockDim.x)
-                tile[j] = w.tmp[s0 + f0 + j];
+            if (threadIdx.x == 0)
+                nbusy = 0;
             __syncthreads();
-            if (e < c)
-                for (int j = 0; j < m; ++j)
-                    rank += tile[j] < v;
+            const int lf = base + (int)threadIdx.x;
+            if (threadIdx.x < 64 && lf < w.nleaf && w.start[lf + 1] > w.start[lf])
+                busy[atomicAdd(&nbusy, 1)] = lf;
+            __syncthreads();
+            nb = nbusy;
         }
-        if (e < c) {
-            const int pos = s0 + rank;
-            w.perm[pos] = v;
-            w.iperm[v] = pos;
-            w.sleaf[pos] = leaf;
-            if (mixed) {
-                const float4 p = w.pos4u[v];
-                const float gg = w.g32u[v];
-                w.eh[pos] = make_float4(p.x, p.x, p.y, p.y);
-                w.el[pos] = make_float4(p.z, p.z, p.w, p.w);
-                w.eg[pos] = make_float4(gg, gg, -gg, -gg);
-            } else {
-                w.sx[pos] = x[v];
-                w.sy[pos] = y[v];
-                w.sg[pos] = g[v];
-                if (gu) {
-                    w.sgu[pos] = gu[v];
-                    w.sgv[pos] = gv[v];
+        for (int ib = 0; ib < nb; ++ib) {
+            const int leaf = one ? base : busy[ib];
+            const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
+            if (c <= 0)
+                continue;
+            for (int e0 = 0; e0 < c; e0 += blockDim.x) {
+                const int e = e0 + threadIdx.x;
+                const int v = e < c ? w.tmp[s0 + e] : 0;
+                int rank = 0;
+                for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
+                    const int m = min(SORT_TILE, c - f0);
+                    __syncthreads();
+                    for (int j = threadIdx.x; j < m; j += blockDim.x)
+                        tile[j] = w.tmp[s0 + f0 + j];
+                    __syncthreads();
+                    if (e < c)
+                        for (int j = 0; j < m; ++j)
+                            rank += tile[j] < v;
+                }
+                if (e < c) {
+                    const int pos = s0 + rank;
+                    w.perm[pos] = v;
+                    w.iperm[v] = pos;
+                    w.sleaf[pos] = leaf;
+                    if (mixed) {
+                        const float4 p = w.pos4u[v];
+                        const float gg = w.g32u[v];
+                        w.eh[pos] = make_float4(p.x, p.x, p.y, p.y);
+                        w.el[pos] = make_float4(p.z, p.z, p.w, p.w);
+                        w.eg[pos] = make_float4(gg, gg, -gg, -gg);
+                    } else {
+                        w.sx[pos] = x[v];
+                        w.sy[pos] = y[v];
+                        w.sg[pos] = g[v];
+                        if (gu) {
+                            w.sgu[pos] = gu[v];
+                            w.sgv[pos] = gv[v];
+                        }
+                    }
                 }
             }
         }
@@ -540,7 +560,10 @@ __global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restr
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
                   const double *gv, cudaStream_t s)
 {
-    k_leaf_order<<<w.nleaf, 64, 0, s>>>(w, x, y, g, gu, gv, (w.mixed && !gu) ? 1 : 0);
+    // one block per leaf up to 2^16 leaves; beyond (deep uniform trees, the adaptive tree's depth-L cells, mostly
+    // empty) a fixed grid of 32 blocks per SM strides over them
+    const int grid = w.nleaf <= 65536 ? w.nleaf : 152 * 32;
+    k_leaf_order<<<grid, 64, 0, s>>>(w, x, y, g, gu, gv, (w.mixed && !gu) ? 1 : 0);
     return 1;
 }
 

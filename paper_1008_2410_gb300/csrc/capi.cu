@@ -353,6 +353,8 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = np * 4;                                      // 26 slot
     sizes[i++] = np * 4;                                      // 27 iperm
     sizes[i++] = adjoint ? np * 24 : 0;                       // 28 adj_far
+    sizes[i++] = h->adaptive_cap ? (size_t)nbox * 4 + 16 : 0;   // 29 ad_list
+    sizes[i++] = h->adaptive_cap ? (FMM_MAXL + 2) * 4 : 0;      // 30 ad_cnt
     int count = i;
     Layout lay;
     size_t total = 0;
@@ -435,6 +437,8 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.sys = (SysDev *)(hd + HDR_SYS);
     w.sys_list = (int *)(hd + HDR_LIST);
     w.adj_far = sizes[28] ? (double *)(b + lay.off[28]) : nullptr;
+    w.ad_list = sizes[29] ? (int *)(b + lay.off[29]) : nullptr;
+    w.ad_cnt = sizes[30] ? (int *)(b + lay.off[30]) : nullptr;
     w.lv = h->lv;
     return FMM_OK;
 }
@@ -505,6 +509,7 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     if (timed)
         CU(record_timing(h->ev_t[1], s));
     if (far && w.maxdepth >= 2) {
+        CU(cudaMemsetAsync(w.ad_cnt, 0, (FMM_MAXL + 2) * sizeof(int), s));
         CU(cudaEventRecord(h->ev_fork, s));
         CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         nl += launch_adaptive_sweep(w, h->t, h->side);

@@ -101,6 +101,8 @@ struct Work {
     int morton;               // leaf keys in Morton order (adaptive tree) instead of row-major
     int adapt_cap;            // adaptive tree: a box holding more than this many particles is split (0: uniform)
     int ad_mixed;             // adaptive tree in the precision form (FP32 expansions and near field)
+    int *ad_list;             // adaptive tree: Morton indices of the existing boxes of level l at [box0[l], ...)
+    int *ad_cnt;              // [FMM_MAXL + 2] adaptive tree: number of existing boxes per level
     // arrays
     int *key, *slot, *cnt, *start, *scan_tmp, *tmp, *perm, *sleaf;
     double *sx, *sy, *sg;

@@ -218,7 +218,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     if args.workload == "patches_16m" or args.adaptive:
         f.velocity(x, y, g, u, v)
         out["adaptive"] = adaptive_leg(api, w, x, y, g, u, v, args.precision, flush, stream,
-                                       leaf_capacity=args.adaptive or 64)
+                                       leaf_capacity=args.adaptive or 48)
 
     # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
     f.set_count_pairs(True)
@@ -467,7 +467,7 @@ def adjoint_leg(api, w, x, y, g, flush, stream) -> dict:
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak on this machine)
 
 
-def adaptive_leg(api, w, x, y, g, u_uni, v_uni, precision, flush, stream, leaf_capacity: int = 64,
+def adaptive_leg(api, w, x, y, g, u_uni, v_uni, precision, flush, stream, leaf_capacity: int = 48,
                  max_depth: int = 11) -> dict:
     """The adaptive quadtree (U, V, W, X lists) on this workload in the run's precision: graph-replay
     throughput (median of 20), its near-field kernel against the FP32 (or FP64) rate, near pairs, the
@@ -490,9 +490,10 @@ def adaptive_leg(api, w, x, y, g, u_uni, v_uni, precision, flush, stream, leaf_c
     f.set_count_pairs(False)
     # the near-field kernel alone (no sweep beside it): median of 5 near-only evaluations
     near_alone = []
+    u2, v2 = torch.empty_like(x), torch.empty_like(x)
     for _ in range(5):
         flush.zero_()
-        f.velocity_near(x, y, g, u2 := torch.empty_like(x), v2 := torch.empty_like(x))
+        f.velocity_near(x, y, g, u2, v2)
         sa = f.stage_times()
         if sa:
             near_alone.append(sa[1])
@@ -597,7 +598,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adaptive", type=int, default=0,
-                    help="also time the adaptive tree with this leaf capacity (always on for patches_16m)")
+                    help="also time the adaptive tree with this leaf capacity (always on for patches_16m, capacity 48)")
     ap.add_argument("--quick", action="store_true", help="main timing only")
     ap.add_argument("--tile", default=None, help="near-field tile 'threads,targets' instead of the autotuner's")
     ap.add_argument("--m2l-engine", default=None, choices=["tensor", "cuda_cores"],

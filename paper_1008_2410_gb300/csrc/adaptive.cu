@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
 {
     __shared__ cpx<R> sa[4][2][32];
     __shared__ R sgm[4][32];
+    __shared__ int vl[4][28];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const SysDev &d = w.sys[0];
     const Tree t{w.start, d.depth, w.adapt_cap};
@@ -334,30 +335,31 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
                 acc = cadd(acc, cmul(ld<R>(T + j * P + k), sa[wi][0][j]));
             __syncwarp();
         }
-        // V: M2L from the children of the parent's neighbours that are not adjacent to b (factored form)
+        // V: M2L from the children of the parent's neighbours that are not adjacent to b (factored form). The 36
+        // candidates of the parent's 6 x 6 children block are tested one per lane and compacted by ballot.
         const int px = bx >> 1, py = by >> 1;
-        int pend = -1;  // a source waiting for its partner: offset index << 24 | Morton index
-        for (int q = 0; q <= 36; ++q) {
-            int ent = -1;
+        int nv = 0;
+        for (int base = 0; base < 36; base += 32) {
+            const int q = base + lane;
+            bool ok = false;
+            int ent = 0;
             if (q < 36) {
                 const int sx = 2 * px - 2 + q % 6, sy = 2 * py - 2 + q / 6;
-                if (sx < 0 || sy < 0 || sx >= nside || sy >= nside || (abs(sx - bx) <= 1 && abs(sy - by) <= 1) ||
-                    !box_exists(t, l, sx, sy))
-                    continue;
-                const unsigned ms = morton2(sx, sy);
-                if (box_count(t, l, ms) == 0)
-                    continue;
-                ent = (((sy - by + 3) * 7 + (sx - bx + 3)) << 24) | (int)ms;
-                if (pend < 0) {
-                    pend = ent;
-                    continue;
+                if (sx >= 0 && sy >= 0 && sx < nside && sy < nside && !(abs(sx - bx) <= 1 && abs(sy - by) <= 1) &&
+                    box_exists(t, l, sx, sy)) {
+                    const unsigned ms = morton2(sx, sy);
+                    ok = box_count(t, l, ms) > 0;
+                    ent = (((sy - by + 3) * 7 + (sx - bx + 3)) << 24) | (int)ms;
                 }
-            } else if (pend < 0) {
-                break;
             }
-            // contract pend (and ent, if any)
-            const int e0 = pend, e1 = ent;
-            pend = -1;
+            const unsigned mk = __ballot_sync(0xffffffffu, ok);
+            if (ok)
+                vl[wi][nv + __popc(mk & ((1u << lane) - 1))] = ent;
+            nv += __popc(mk);
+        }
+        __syncwarp();
+        for (int sidx = 0; sidx < nv; sidx += 2) {
+            const int e0 = vl[wi][sidx], e1 = sidx + 1 < nv ? vl[wi][sidx + 1] : -1;
             const auto *r0 = rho + (e0 >> 24) * kRS;
             const auto *r1 = rho + ((e1 >= 0 ? e1 : e0) >> 24) * kRS;
             if (lane < p) {  // alpha_m = (-1)^(m+1) rho^m a~_m
@@ -386,48 +388,49 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
                 acc = cadd(acc, cmul(ld<R>(r1 + k + 1), s1));
             __syncwarp();
         }
-        // X: P2L from the coarser leaves adjacent to the parent but not to b
-        int seen[8];
-        int nseen = 0;
-        const double2 c = centre(d, l, bx, by);
-        for (int dy = -1; dy <= 1; ++dy) {
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (dx == 0 && dy == 0)
-                    continue;
-                int lq = l - 1, qx = px + dx, qy = py + dy;
-                if (qx < 0 || qy < 0 || qx >= (nside >> 1) || qy >= (nside >> 1))
-                    continue;
+        // X: P2L from the coarser leaves adjacent to the parent but not to b. Lanes 0..7 each take one of the
+        // parent's neighbour cells, find the leaf covering it, and keep it unless a lower lane found the same.
+        int xid = -1;
+        if (lane < 8) {
+            const int dxy = lane < 4 ? lane : lane + 1;  // 3 x 3 block without its centre
+            int lq = l - 1, qx = px + dxy % 3 - 1, qy = py + dxy / 3 - 1;
+            if (qx >= 0 && qy >= 0 && qx < (nside >> 1) && qy < (nside >> 1)) {
                 covering_box(t, lq, qx, qy);
-                if (lq == l - 1 && box_split(t, lq, qx, qy))
-                    continue;
-                if (adjacent(L, l, bx, by, lq, qx, qy))
-                    continue;
-                const int id = pack_box(lq, qx, qy);
-                bool dup = false;
-                for (int e = 0; e < nseen; ++e)
-                    dup |= seen[e] == id;
-                if (dup)
-                    continue;
-                seen[nseen++] = id;
-                const unsigned mq = morton2(qx, qy);
-                const int j0 = box_first(t, lq, mq), cnt = box_count(t, lq, mq);
-                for (int e0 = 0; e0 < cnt; e0 += 32) {
-                    if (e0 + lane < cnt) {  // 1 / s_j, s_j = (z_j - c) / w, formed in FP64
-                        const int j = j0 + e0 + lane;
-                        const double ax = (w.sx[j] - c.x) * iw, ay = (w.sy[j] - c.y) * iw;
-                        const double id2 = 1.0 / (ax * ax + ay * ay);
-                        sa[wi][0][lane] = {(R)(ax * id2), (R)(-ay * id2)};
-                        sgm[wi][lane] = (R)w.sg[j];
-                    }
-                    __syncwarp();
-                    const int ne = min(32, cnt - e0);
-                    for (int e = 0; e < ne; ++e) {
-                        const cpx<R> ip = cpow(sa[wi][0][e], k + 1);
-                        const R g = sgm[wi][e];
-                        acc = cadd(acc, cpx<R>{-g * ip.im, g * ip.re});  // -q' s^-(k+1), q' = -i gamma
-                    }
-                    __syncwarp();
+                if (!(lq == l - 1 && box_split(t, lq, qx, qy)) && !adjacent(L, l, bx, by, lq, qx, qy) &&
+                    box_count(t, lq, morton2(qx, qy)) > 0)
+                    xid = pack_box(lq, qx, qy);
+            }
+        }
+        bool keep = xid >= 0;
+        for (int o = 0; o < 8; ++o) {
+            const int other = __shfl_sync(0xffffffffu, xid, o);
+            keep = keep && !(o < lane && other == xid);
+        }
+        unsigned xm = __ballot_sync(0xffffffffu, keep);
+        const double2 c = centre(d, l, bx, by);
+        while (xm) {
+            const int src = __ffs(xm) - 1;
+            xm &= xm - 1;
+            const int id = __shfl_sync(0xffffffffu, xid, src);
+            const int lq = id >> 26, qx = (id >> 13) & 0x1fff, qy = id & 0x1fff;
+            const unsigned mq = morton2(qx, qy);
+            const int j0 = box_first(t, lq, mq), cnt = box_count(t, lq, mq);
+            for (int e0 = 0; e0 < cnt; e0 += 32) {
+                if (e0 + lane < cnt) {  // 1 / s_j, s_j = (z_j - c) / w, formed in FP64
+                    const int j = j0 + e0 + lane;
+                    const double ax = (w.sx[j] - c.x) * iw, ay = (w.sy[j] - c.y) * iw;
+                    const double id2 = 1.0 / (ax * ax + ay * ay);
+                    sa[wi][0][lane] = {(R)(ax * id2), (R)(-ay * id2)};
+                    sgm[wi][lane] = (R)w.sg[j];
                 }
+                __syncwarp();
+                const int ne = min(32, cnt - e0);
+                for (int e = 0; e < ne; ++e) {
+                    const cpx<R> ip = cpow(sa[wi][0][e], k + 1);
+                    const R g = sgm[wi][e];
+                    acc = cadd(acc, cpx<R>{-g * ip.im, g * ip.re});  // -q' s^-(k+1), q' = -i gamma
+                }
+                __syncwarp();
             }
         }
         if (lane < p)
@@ -437,11 +440,19 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
 
 // ------------------------------------------------------------------ leaf of a sorted particle, U / W walk
 
+// The leaf is the first level whose box around the particle holds at most B particles (or level L); the count of
+// that box never grows with the level, so the level is found by bisection.
 __device__ __forceinline__ void particle_leaf(const Tree &t, unsigned kf, int &l, int &x, int &y)
 {
-    int lv = 0;
-    while (lv < t.L && box_count(t, lv, kf >> (2 * (t.L - lv))) > t.B)
-        ++lv;
+    int lo = 0, hi = t.L;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (box_count(t, mid, kf >> (2 * (t.L - mid))) <= t.B)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const int lv = lo;
     const unsigned m = kf >> (2 * (t.L - lv));
     l = lv;
     x = (int)compact1(m);
@@ -550,25 +561,42 @@ __global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pai
         atomicAdd(pairs, (unsigned long long)np);
 }
 
-// Precision form: positions in depth-L cell units X = (x - x0) 2^L / S split into hi + lo floats, so that a
-// displacement (hi_i - hi_j) + (lo_i - lo_j) keeps about 2^-24 of its own size; circulation as a float.
+// Precision form: positions in units u = sigma sqrt(2 / log2 e), X = (x - x0) / u, split into hi + lo floats so that
+// a displacement (hi_i - hi_j) + (lo_i - lo_j) keeps about 2^-24 of its own size; circulation as a float. In
+// these units exp(-r^2 / 2 sigma^2) = 2^-(R^2), R = r / u.
 __global__ void k_ad_split(Work w)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.n)
         return;
     const SysDev &d = w.sys[0];
-    const double X = (w.sx[i] - d.x0) * d.scale, Y = (w.sy[i] - d.y0) * d.scale;
+    const double X = (w.sx[i] - d.x0) * d.iu, Y = (w.sy[i] - d.y0) * d.iu;
     const float hx = (float)X, hy = (float)Y;
     w.eh[i] = make_float4(hx, hy, (float)(X - (double)hx), (float)(Y - (double)hy));
     w.eg[i].x = (float)w.sg[i];
 }
 
-// f(x) = (1 - e^-x) / x: the Taylor series sum_k (-x)^k / (k+1)! below x = 1/2 (truncation < 1e-8 relative),
-// the exponential above (cancellation < 2e-7 relative).
-__device__ __forceinline__ float blob_factor(float x)
+__device__ __forceinline__ float ex2_approx(float v)
 {
-    if (x < 0.5f) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// q(R^2) = (1 - 2^-R^2) / R^2 = ln2 f(x), f(x) = (1 - e^-x) / x, x = R^2 ln 2: the Taylor series
+// f = sum_k (-x)^k / (k+1)! below x = 1/2 (truncation < 1e-8 relative), the exponential above (cancellation
+// < 2e-7 relative).
+__device__ __forceinline__ float blob_q(float R2)
+{
+    constexpr float kLn2 = 0.693147180559945309f;
+    if (R2 < 0.5f / kLn2) {
+        const float x = R2 * kLn2;
         float s = 1.0f / 362880.0f;
         s = fmaf(s, -x, 1.0f / 40320.0f);
         s = fmaf(s, -x, 1.0f / 5040.0f);
@@ -577,13 +605,13 @@ __device__ __forceinline__ float blob_factor(float x)
         s = fmaf(s, -x, 1.0f / 24.0f);
         s = fmaf(s, -x, 1.0f / 6.0f);
         s = fmaf(s, -x, 0.5f);
-        return fmaf(s, -x, 1.0f);
+        return kLn2 * fmaf(s, -x, 1.0f);
     }
-    return __fdividef(1.0f - __expf(-x), x);
+    return (1.0f - ex2_approx(-R2)) * rcp_approx(R2);
 }
 
-// K_sigma in cell units (r = w_L r_c): K = (-dy_c, dx_c) f(kappa r_c^2) kappa / (2 pi w_L), kappa = w_L^2 / 2 sigma^2.
-// FP32 pair terms, summed in FP32 per source leaf and in FP64 across leaves.
+// K_sigma in units u: K = (-dY, dX) q(R^2) / (2 pi u). FP32 pair terms, summed in FP32 per source leaf and in
+// FP64 across leaves.
 __global__ void __launch_bounds__(128) k_ad_near32(Work w, unsigned long long *pairs)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -594,18 +622,17 @@ __global__ void __launch_bounds__(128) k_ad_near32(Work w, unsigned long long *p
     int l, bx, by;
     particle_leaf(t, (unsigned)w.sleaf[i], l, bx, by);
     const float4 pi = w.eh[i];
-    const double kap = d.wl * d.wl / (2.0 * d.sigma * d.sigma);
-    const float kf = (float)kap;
     double su = 0.0, sv = 0.0;
     long long np = -1;
     auto near = [&](int j0, int j1) {
         np += j1 - j0;
         float pu = 0.0f, pv = 0.0f;
+#pragma unroll 2
         for (int j = j0; j < j1; ++j) {
             const float4 pj = w.eh[j];
             const float g = w.eg[j].x;
             const float ax = (pi.x - pj.x) + (pi.z - pj.z), ay = (pi.y - pj.y) + (pi.w - pj.w);
-            const float f = g * blob_factor(kf * fmaf(ax, ax, ay * ay));
+            const float f = g * blob_q(fmaf(ax, ax, ay * ay));
             pu = fmaf(-ay, f, pu);
             pv = fmaf(ax, f, pv);
         }
@@ -614,7 +641,7 @@ __global__ void __launch_bounds__(128) k_ad_near32(Work w, unsigned long long *p
     };
     auto none = [](int, int, int) {};
     walk_uw(w, t, l, bx, by, near, none);
-    const double sc = kap / (kTwoPi * d.wl);
+    const double sc = d.iu / kTwoPi;  // 1 / (2 pi u)
     w.near64[i] = make_double2(su * sc, sv * sc);
     if (pairs)
         atomicAdd(pairs, (unsigned long long)np);

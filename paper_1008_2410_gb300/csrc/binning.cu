@@ -69,6 +69,7 @@ __device__ void derive_constants(SysDev &d)
     d.s_unit = s;
     d.inv_s = 1.0f / s;
     d.snear = (float)((double)s * d.far_scale);
+    d.iu = sqrt(1.4426950408889634074 / (2.0 * d.sigma * d.sigma));
 }
 
 __global__ void k_domain_finalize(SysDev *sys, int nsys, const unsigned long long *minmax)
@@ -486,82 +487,125 @@ int launch_scatter_sort(const Work &w, cudaStream_t s)
     return 1;
 }
 
-// One block per leaf: ranks the leaf's caller indices (all distinct) so that the leaf keeps the caller's order,
-// then writes the leaf-ordered copies at the ranked positions: FP64 form (x, y, gamma [, gu, gv]); precision
-// form the duplicated split records eh = (xh, xh, yh, yh), el = (xl, xl, yl, yl), eg = (g, g, -g, -g).
 #define SORT_TILE 256
+
+// Writes the leaf-ordered copies of caller particle v at sorted position pos: FP64 form (x, y, gamma [, gu, gv]);
+// precision form the duplicated split records eh = (xh, xh, yh, yh), el = (xl, xl, yl, yl), eg = (g, g, -g, -g).
+__device__ __forceinline__ void place_particle(const Work &w, int v, int pos, int leaf, const double *__restrict__ x,
+                                               const double *__restrict__ y, const double *__restrict__ g,
+                                               const double *__restrict__ gu, const double *__restrict__ gv, int mixed)
+{
+    w.perm[pos] = v;
+    if (!w.morton)  // the adaptive tree reads no inverse permutation
+        w.iperm[v] = pos;
+    w.sleaf[pos] = leaf;
+    if (mixed) {
+        const float4 p = w.pos4u[v];
+        const float gg = w.g32u[v];
+        w.eh[pos] = make_float4(p.x, p.x, p.y, p.y);
+        w.el[pos] = make_float4(p.z, p.z, p.w, p.w);
+        w.eg[pos] = make_float4(gg, gg, -gg, -gg);
+    } else {
+        w.sx[pos] = x[v];
+        w.sy[pos] = y[v];
+        w.sg[pos] = g[v];
+        if (gu) {
+            w.sgu[pos] = gu[v];
+            w.sgv[pos] = gv[v];
+        }
+    }
+}
+
+// Ranks one leaf's caller indices (all distinct) with the whole block so that the leaf keeps the caller's order.
+__device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, int *tile, const double *x, const double *y,
+                                                 const double *g, const double *gu, const double *gv, int mixed)
+{
+    const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
+    for (int e0 = 0; e0 < c; e0 += blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        const int v = e < c ? w.tmp[s0 + e] : 0;
+        int rank = 0;
+        for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
+            const int m = min(SORT_TILE, c - f0);
+            __syncthreads();
+            for (int j = threadIdx.x; j < m; j += blockDim.x)
+                tile[j] = w.tmp[s0 + f0 + j];
+            __syncthreads();
+            if (e < c)
+                for (int j = 0; j < m; ++j)
+                    rank += tile[j] < v;
+        }
+        if (e < c)
+            place_particle(w, v, s0 + rank, leaf, x, y, g, gu, gv, mixed);
+    }
+}
+
+// Leaf order. Up to 2^16 leaves: one block per leaf. Beyond (deep uniform trees, the adaptive tree's depth-L
+// cells, mostly empty): each block strides over chunks of 64 leaves, lists the chunk's non-empty ones, ranks
+// those of at most 128 particles with one warp each (shuffles, no block barrier) and the rest with the block.
 __global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restrict__ x, const double *__restrict__ y,
                                                    const double *__restrict__ g, const double *__restrict__ gu,
                                                    const double *__restrict__ gv, int mixed)
 {
     __shared__ int tile[SORT_TILE];
-    __shared__ int busy[64];
-    __shared__ int nbusy;
-    const bool one = gridDim.x >= w.nleaf;  // one block per leaf
-    // otherwise chunks of 64 leaves, strided over the grid: the block lists the chunk's non-empty leaves first
-    for (int base = one ? blockIdx.x : blockIdx.x * 64; base < w.nleaf; base += one ? gridDim.x : gridDim.x * 64) {
-        int nb = 1;
-        if (!one) {
-            __syncthreads();
-            if (threadIdx.x == 0)
-                nbusy = 0;
-            __syncthreads();
-            const int lf = base + (int)threadIdx.x;
-            if (threadIdx.x < 64 && lf < w.nleaf && w.start[lf + 1] > w.start[lf])
-                busy[atomicAdd(&nbusy, 1)] = lf;
-            __syncthreads();
-            nb = nbusy;
+    __shared__ int small[64], big[64];
+    __shared__ int nsmall, nbig;
+    if (gridDim.x >= w.nleaf) {
+        order_leaf_block(w, blockIdx.x, tile, x, y, g, gu, gv, mixed);
+        return;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = blockIdx.x * 64; base < w.nleaf; base += gridDim.x * 64) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            nsmall = 0;
+            nbig = 0;
         }
-        for (int ib = 0; ib < nb; ++ib) {
-            const int leaf = one ? base : busy[ib];
+        __syncthreads();
+        const int lf = base + (int)threadIdx.x;
+        if (lf < w.nleaf) {
+            const int c = w.start[lf + 1] - w.start[lf];
+            if (c > 128)
+                big[atomicAdd(&nbig, 1)] = lf;
+            else if (c > 0)
+                small[atomicAdd(&nsmall, 1)] = lf;
+        }
+        __syncthreads();
+        for (int ib = wid; ib < nsmall; ib += 2) {  // up to 4 particles per lane, ranked by shuffles
+            const int leaf = small[ib];
             const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
-            if (c <= 0)
-                continue;
-            for (int e0 = 0; e0 < c; e0 += blockDim.x) {
-                const int e = e0 + threadIdx.x;
-                const int v = e < c ? w.tmp[s0 + e] : 0;
-                int rank = 0;
-                for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
-                    const int m = min(SORT_TILE, c - f0);
-                    __syncthreads();
-                    for (int j = threadIdx.x; j < m; j += blockDim.x)
-                        tile[j] = w.tmp[s0 + f0 + j];
-                    __syncthreads();
-                    if (e < c)
-                        for (int j = 0; j < m; ++j)
-                            rank += tile[j] < v;
-                }
-                if (e < c) {
-                    const int pos = s0 + rank;
-                    w.perm[pos] = v;
-                    w.iperm[v] = pos;
-                    w.sleaf[pos] = leaf;
-                    if (mixed) {
-                        const float4 p = w.pos4u[v];
-                        const float gg = w.g32u[v];
-                        w.eh[pos] = make_float4(p.x, p.x, p.y, p.y);
-                        w.el[pos] = make_float4(p.z, p.z, p.w, p.w);
-                        w.eg[pos] = make_float4(gg, gg, -gg, -gg);
-                    } else {
-                        w.sx[pos] = x[v];
-                        w.sy[pos] = y[v];
-                        w.sg[pos] = g[v];
-                        if (gu) {
-                            w.sgu[pos] = gu[v];
-                            w.sgv[pos] = gv[v];
-                        }
-                    }
+            const int rounds = (c + 31) >> 5;
+            int v[4], rank[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[q] = (q < rounds && lane + 32 * q < c) ? w.tmp[s0 + lane + 32 * q] : 0x7fffffff;  // pad ranks last
+                rank[q] = 0;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r >= rounds)
+                    break;
+                for (int j = 0; j < 32; ++j) {
+                    const int o = __shfl_sync(0xffffffffu, v[r], j);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        rank[q] += o < v[q];
                 }
             }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (lane + 32 * q < c)
+                    place_particle(w, v[q], s0 + rank[q], leaf, x, y, g, gu, gv, mixed);
         }
+        const int nb = nbig;
+        for (int ib = 0; ib < nb; ++ib)
+            order_leaf_block(w, big[ib], tile, x, y, g, gu, gv, mixed);
     }
 }
 
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
                   const double *gv, cudaStream_t s)
 {
-    // one block per leaf up to 2^16 leaves; beyond (deep uniform trees, the adaptive tree's depth-L cells, mostly
-    // empty) a fixed grid of 32 blocks per SM strides over them
     const int grid = w.nleaf <= 65536 ? w.nleaf : 152 * 32;
     k_leaf_order<<<grid, 64, 0, s>>>(w, x, y, g, gu, gv, (w.mixed && !gu) ? 1 : 0);
     return 1;

@@ -57,6 +57,7 @@ struct SysDev {
     float inv_s;                    // 1 / s
     float snear;                    // s / (2 pi w_L): scale of the near-field sum in these units
     float pad_f;
+    double iu;                      // adaptive tree's precision form: 1 / u, u = sigma sqrt(2 / log2 e)
 };
 
 // Per-level work lists for the tree sweeps, computed on the host and passed by value. The systems that have

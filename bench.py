@@ -40,6 +40,9 @@ def workload(name: str):
     if name == "patches_16m":
         return fi.patches_16m(), ("N=2^24 from 8 Gaussian patches (std 0.05, circulations +-1), sigma=0.5/sqrt(N), "
                                   "uniform depth 9, p=20")
+    if name == "patches_4m":  # a smaller case of the same recipe, for counter captures
+        return (fi.patches(1 << 22, seed_index=2, depth=8, p=20, name="patches_4m"),
+                "N=2^22 from 8 Gaussian patches, sigma=0.5/sqrt(N), uniform depth 8, p=20")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -218,7 +221,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     if args.workload == "patches_16m" or args.adaptive:
         f.velocity(x, y, g, u, v)
         out["adaptive"] = adaptive_leg(api, w, x, y, g, u, v, args.precision, flush, stream,
-                                       leaf_capacity=args.adaptive or 48)
+                                       leaf_capacity=args.adaptive or 48, max_depth=args.max_depth)
 
     # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
     f.set_count_pairs(True)
@@ -588,18 +591,42 @@ def run_reference(args, rank: int, world: int) -> dict | None:
             "e2e": {"value": value, "unit": "Mparticles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_profile_once(args) -> dict:
+    """One eager evaluation on the workload (the uniform tree, or the adaptive tree with --adaptive B and
+    --max-depth), for kernel launch lists and counter captures; no timing."""
+    import numpy as np
+    import torch
+
+    from paper_1008_2410_gb300 import api
+
+    w, desc = workload(args.workload)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    depth = args.max_depth if args.adaptive else w.depth
+    f = api.FMM(depth, w.p, w.sigma, precision=args.precision, domain=w.domain, leaf_capacity=args.adaptive)
+    if args.tile:
+        f.set_p2p_tile(*(int(t) for t in args.tile.split(",")))
+    u, v = f.velocity(x, y, g)
+    f.sync()
+    return {"profile_once": args.workload, "precision": args.precision, "depth": depth,
+            "leaf_capacity": args.adaptive, "max_abs_u": float(u.abs().max())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="uniform_1m", choices=["uniform_1m", "patches_16m"])
+    ap.add_argument("--workload", default="uniform_1m", choices=["uniform_1m", "patches_16m", "patches_4m"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adaptive", type=int, default=0,
                     help="also time the adaptive tree with this leaf capacity (always on for patches_16m, capacity 48)")
     ap.add_argument("--quick", action="store_true", help="main timing only")
+    ap.add_argument("--max-depth", type=int, default=11, help="maximum depth of the adaptive tree")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="one eager evaluation, no timing (for ncu launch lists and captures)")
     ap.add_argument("--tile", default=None, help="near-field tile 'threads,targets' instead of the autotuner's")
     ap.add_argument("--m2l-engine", default=None, choices=["tensor", "cuda_cores"],
                     help="M2L engine instead of the autotuner's (with --tile)")
@@ -609,7 +636,9 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.impl == "reference":
+    if args.profile_once:
+        out = run_profile_once(args)
+    elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
         if world > 1:

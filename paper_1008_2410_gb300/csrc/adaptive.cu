@@ -527,9 +527,30 @@ __device__ __forceinline__ void walk_uw(const Work &w, const Tree &t, int l, int
     }
 }
 
-// ------------------------------------------------------------------ stage 9: near field over U
+// W list: the multipole of box (ls, sx, sy) evaluated at (xi, yi), (1/w_s) sum_m a~_m / t^(m+1) with
+// t = (z - c_s) / w_s formed in FP64, added to (wr, wi) (complex velocity w = u - i v without 1 / 2pi).
+template <typename R>
+__device__ __forceinline__ void m2p_add(const Work &w, const SysDev &d, double xi, double yi, int ls, int sx, int sy,
+                                        double &wr, double &wi)
+{
+    const double2 c = centre(d, ls, sx, sy);
+    const double iws = ldexp(1.0, ls) / d.S;
+    const double ax = (xi - c.x) * iws, ay = (yi - c.y) * iws, id2 = 1.0 / (ax * ax + ay * ay);
+    const cpx<R> uinv = {(R)(ax * id2), (R)(-ay * id2)};
+    const auto *a = mp_of<R>(w, ls, morton2(sx, sy));
+    cpx<R> s = {(R)0, (R)0};
+    for (int mm = w.p - 1; mm >= 0; --mm)
+        s = cmul(cadd(s, ld<R>(a + mm)), uinv);
+    wr += (double)s.re * iws;
+    wi += (double)s.im * iws;
+}
 
-__global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pairs)
+// ------------------------------------------------------------------ stage 9 (U) and the W multipoles
+
+// The near-field kernels walk U and W once per target: exact K_sigma over U (use_near) and the multipoles of W
+// (use_far, after the upward pass). near64 receives both, in velocity form.
+
+__global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pairs, int use_near, int use_far)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.n)
@@ -540,10 +561,12 @@ __global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pai
     particle_leaf(t, (unsigned)w.sleaf[i], l, bx, by);
     const double xi = w.sx[i], yi = w.sy[i];
     const double k2 = 1.0 / (2.0 * d.sigma * d.sigma);
-    double su = 0.0, sv = 0.0;
+    double su = 0.0, sv = 0.0, wr = 0.0, wi = 0.0;
     long long np = -1;  // ordered pairs (i, j), j != i
     auto near = [&](int j0, int j1) {
         np += j1 - j0;
+        if (!use_near)
+            return;
         for (int j = j0; j < j1; ++j) {
             const double ax = xi - w.sx[j], ay = yi - w.sy[j];
             const double r2 = ax * ax + ay * ay;
@@ -554,10 +577,13 @@ __global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pai
             }
         }
     };
-    auto none = [](int, int, int) {};
-    walk_uw(w, t, l, bx, by, near, none);
-    w.near64[i] = make_double2(su, sv);
-    if (pairs)
+    auto far = [&](int ls, int sx, int sy) {
+        if (use_far)
+            m2p_add<double>(w, d, xi, yi, ls, sx, sy, wr, wi);
+    };
+    walk_uw(w, t, l, bx, by, near, far);
+    w.near64[i] = make_double2(su + wr / kTwoPi, sv - wi / kTwoPi);
+    if (pairs && use_near)
         atomicAdd(pairs, (unsigned long long)np);
 }
 
@@ -612,7 +638,7 @@ __device__ __forceinline__ float blob_q(float R2)
 
 // K_sigma in units u: K = (-dY, dX) q(R^2) / (2 pi u). FP32 pair terms, summed in FP32 per source leaf and in
 // FP64 across leaves.
-__global__ void __launch_bounds__(128) k_ad_near32(Work w, unsigned long long *pairs)
+__global__ void __launch_bounds__(128) k_ad_near32(Work w, unsigned long long *pairs, int use_near, int use_far)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.n)
@@ -622,80 +648,76 @@ __global__ void __launch_bounds__(128) k_ad_near32(Work w, unsigned long long *p
     int l, bx, by;
     particle_leaf(t, (unsigned)w.sleaf[i], l, bx, by);
     const float4 pi = w.eh[i];
-    double su = 0.0, sv = 0.0;
+    double su = 0.0, sv = 0.0, wr = 0.0, wi = 0.0;
     long long np = -1;
     auto near = [&](int j0, int j1) {
         np += j1 - j0;
-        float pu = 0.0f, pv = 0.0f;
+        if (!use_near)
+            return;
+        float pu0 = 0.0f, pv0 = 0.0f, pu1 = 0.0f, pv1 = 0.0f;  // two chains: even and odd sources
+        int j = j0;
 #pragma unroll 2
-        for (int j = j0; j < j1; ++j) {
-            const float4 pj = w.eh[j];
-            const float g = w.eg[j].x;
-            const float ax = (pi.x - pj.x) + (pi.z - pj.z), ay = (pi.y - pj.y) + (pi.w - pj.w);
-            const float f = g * blob_q(fmaf(ax, ax, ay * ay));
-            pu = fmaf(-ay, f, pu);
-            pv = fmaf(ax, f, pv);
+        for (; j + 1 < j1; j += 2) {
+            const float4 pa = w.eh[j], pb = w.eh[j + 1];
+            const float ga = w.eg[j].x, gb = w.eg[j + 1].x;
+            const float ax = (pi.x - pa.x) + (pi.z - pa.z), ay = (pi.y - pa.y) + (pi.w - pa.w);
+            const float bx = (pi.x - pb.x) + (pi.z - pb.z), by = (pi.y - pb.y) + (pi.w - pb.w);
+            const float fa = ga * blob_q(fmaf(ax, ax, ay * ay)), fb = gb * blob_q(fmaf(bx, bx, by * by));
+            pu0 = fmaf(-ay, fa, pu0);
+            pv0 = fmaf(ax, fa, pv0);
+            pu1 = fmaf(-by, fb, pu1);
+            pv1 = fmaf(bx, fb, pv1);
         }
-        su += (double)pu;
-        sv += (double)pv;
+        if (j < j1) {
+            const float4 pa = w.eh[j];
+            const float ga = w.eg[j].x;
+            const float ax = (pi.x - pa.x) + (pi.z - pa.z), ay = (pi.y - pa.y) + (pi.w - pa.w);
+            const float fa = ga * blob_q(fmaf(ax, ax, ay * ay));
+            pu0 = fmaf(-ay, fa, pu0);
+            pv0 = fmaf(ax, fa, pv0);
+        }
+        su += (double)(pu0 + pu1);
+        sv += (double)(pv0 + pv1);
     };
-    auto none = [](int, int, int) {};
-    walk_uw(w, t, l, bx, by, near, none);
+    auto far = [&](int ls, int sx, int sy) {
+        if (use_far)
+            m2p_add<float>(w, d, w.sx[i], w.sy[i], ls, sx, sy, wr, wi);
+    };
+    walk_uw(w, t, l, bx, by, near, far);
     const double sc = d.iu / kTwoPi;  // 1 / (2 pi u)
-    w.near64[i] = make_double2(su * sc, sv * sc);
-    if (pairs)
+    w.near64[i] = make_double2(su * sc + wr / kTwoPi, sv * sc - wi / kTwoPi);
+    if (pairs && use_near)
         atomicAdd(pairs, (unsigned long long)np);
 }
 
-// ------------------------------------------------------------------ stages 8 + 10: L2P, W, sum, unsort
+// ------------------------------------------------------------------ stages 8 + 10: L2P, sum, unsort
 
+// near64 already holds U and W; this adds the local expansion of the particle's leaf (levels >= 2) and writes
+// the caller's order.
 template <typename R>
-__global__ void __launch_bounds__(128) k_ad_final(Work w, int use_near, int use_far, double *u, double *v)
+__global__ void __launch_bounds__(128) k_ad_final(Work w, int use_far, double *u, double *v)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.n)
         return;
     const SysDev &d = w.sys[0];
-    double ru = 0.0, rv = 0.0;
+    const double2 nr = w.near64[i];
+    double ru = nr.x, rv = nr.y;
     if (use_far) {
         const Tree t{w.start, d.depth, w.adapt_cap};
         int l, bx, by;
         particle_leaf(t, (unsigned)w.sleaf[i], l, bx, by);
-        const double xi = w.sx[i], yi = w.sy[i];
-        const int p = w.p;
-        double wr = 0.0, wi = 0.0;
         if (l >= 2) {
             const double2 c = centre(d, l, bx, by);
             const double iw = ldexp(1.0, l) / d.S;
-            const cpx<R> z = {(R)((xi - c.x) * iw), (R)((yi - c.y) * iw)};
+            const cpx<R> z = {(R)((w.sx[i] - c.x) * iw), (R)((w.sy[i] - c.y) * iw)};
             const auto *b = loc_of<R>(w, l, morton2(bx, by));
             cpx<R> s = {(R)0, (R)0};
-            for (int k = p - 1; k >= 0; --k)
+            for (int k = w.p - 1; k >= 0; --k)
                 s = cadd(cmul(s, z), ld<R>(b + k));
-            wr += (double)s.re * iw;
-            wi += (double)s.im * iw;
+            ru += (double)s.re * iw / kTwoPi;
+            rv -= (double)s.im * iw / kTwoPi;
         }
-        auto none = [](int, int) {};
-        auto far = [&](int ls, int sx, int sy) {
-            const double2 c = centre(d, ls, sx, sy);
-            const double iws = ldexp(1.0, ls) / d.S;
-            const double ax = (xi - c.x) * iws, ay = (yi - c.y) * iws, id2 = 1.0 / (ax * ax + ay * ay);
-            const cpx<R> uinv = {(R)(ax * id2), (R)(-ay * id2)};
-            const auto *a = mp_of<R>(w, ls, morton2(sx, sy));
-            cpx<R> s = {(R)0, (R)0};
-            for (int mm = p - 1; mm >= 0; --mm)
-                s = cmul(cadd(s, ld<R>(a + mm)), uinv);
-            wr += (double)s.re * iws;
-            wi += (double)s.im * iws;
-        };
-        walk_uw(w, t, l, bx, by, none, far);
-        ru = wr / kTwoPi;
-        rv = -wi / kTwoPi;
-    }
-    if (use_near) {
-        const double2 nr = w.near64[i];
-        ru += nr.x;
-        rv += nr.y;
     }
     const int pos = w.perm[i];
     u[pos] = ru;
@@ -703,57 +725,74 @@ __global__ void __launch_bounds__(128) k_ad_final(Work w, int use_near, int use_
 }
 
 template <typename R, int PM>
-int sweep_levels(const Work &w, const Tables &t, cudaStream_t s)
+int sweep_levels(const Work &w, const Tables &t, int part, cudaStream_t s)
 {
     const int L = w.maxdepth;
-    int nl = 1;
-    const int64_t ne = enum_threads(L);
-    k_ad_enum<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(w);
-    for (int l = 2; l <= L; ++l, ++nl)
-        k_ad_p2m<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, l);
-    for (int l = L - 1; l >= 2; --l, ++nl)
-        k_ad_m2m<R><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
-    for (int l = 2; l <= L; ++l, ++nl)
-        k_ad_down<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
+    int nl = 0;
+    if (part == 0) {  // upward: box lists, P2M, M2M
+        const int64_t ne = enum_threads(L);
+        k_ad_enum<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(w);
+        ++nl;
+        for (int l = 2; l <= L; ++l, ++nl)
+            k_ad_p2m<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, l);
+        for (int l = L - 1; l >= 2; --l, ++nl)
+            k_ad_m2m<R><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
+    } else {  // downward: L2L + M2L + P2L per level
+        for (int l = 2; l <= L; ++l, ++nl)
+            k_ad_down<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
+    }
     return nl;
 }
 
 template <typename R>
-int sweep_bucket(const Work &w, const Tables &t, cudaStream_t s)
+int sweep_bucket(const Work &w, const Tables &t, int part, cudaStream_t s)
 {
     if (w.p <= 8)
-        return sweep_levels<R, 8>(w, t, s);
+        return sweep_levels<R, 8>(w, t, part, s);
     if (w.p <= 16)
-        return sweep_levels<R, 16>(w, t, s);
+        return sweep_levels<R, 16>(w, t, part, s);
+    if (w.p <= 20)
+        return sweep_levels<R, 20>(w, t, part, s);
     if (w.p <= 24)
-        return sweep_levels<R, 24>(w, t, s);
-    return sweep_levels<R, 32>(w, t, s);
+        return sweep_levels<R, 24>(w, t, part, s);
+    return sweep_levels<R, 32>(w, t, part, s);
 }
 
 }  // namespace
 
-int launch_adaptive_sweep(const Work &w, const Tables &t, cudaStream_t s)
+int launch_adaptive_up(const Work &w, const Tables &t, cudaStream_t s)
 {
-    return w.ad_mixed ? sweep_bucket<float>(w, t, s) : sweep_bucket<double>(w, t, s);
+    return w.ad_mixed ? sweep_bucket<float>(w, t, 0, s) : sweep_bucket<double>(w, t, 0, s);
 }
 
-int launch_adaptive_near(const Work &w, unsigned long long *pairs, cudaStream_t s)
+int launch_adaptive_down(const Work &w, const Tables &t, cudaStream_t s)
 {
-    if (w.ad_mixed) {
-        k_ad_split<<<(w.n + 255) / 256, 256, 0, s>>>(w);
-        k_ad_near32<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs);
-        return 2;
-    }
-    k_ad_near<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs);
+    return w.ad_mixed ? sweep_bucket<float>(w, t, 1, s) : sweep_bucket<double>(w, t, 1, s);
+}
+
+int launch_adaptive_split(const Work &w, cudaStream_t s)
+{
+    if (!w.ad_mixed)
+        return 0;
+    k_ad_split<<<(w.n + 255) / 256, 256, 0, s>>>(w);
     return 1;
 }
 
-int launch_adaptive_final(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s)
+int launch_adaptive_near(const Work &w, unsigned long long *pairs, int use_near, int use_far, cudaStream_t s)
 {
     if (w.ad_mixed)
-        k_ad_final<float><<<(w.n + 127) / 128, 128, 0, s>>>(w, use_near, use_far, u, v);
+        k_ad_near32<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs, use_near, use_far);
     else
-        k_ad_final<double><<<(w.n + 127) / 128, 128, 0, s>>>(w, use_near, use_far, u, v);
+        k_ad_near<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs, use_near, use_far);
+    return 1;
+}
+
+int launch_adaptive_final(const Work &w, int use_far, double *u, double *v, cudaStream_t s)
+{
+    if (w.ad_mixed)
+        k_ad_final<float><<<(w.n + 127) / 128, 128, 0, s>>>(w, use_far, u, v);
+    else
+        k_ad_final<double><<<(w.n + 127) / 128, 128, 0, s>>>(w, use_far, u, v);
     return 1;
 }
 

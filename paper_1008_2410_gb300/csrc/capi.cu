@@ -58,6 +58,7 @@ struct fmm_ctx {
     cudaStream_t exec = nullptr;    // internal stream used for graph capture / replay
     cudaStream_t side = nullptr;    // high-priority stream of the multipole sweep
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_status = nullptr, ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_up = nullptr;  // adaptive tree: the upward pass is done (side stream)
     cudaEvent_t ev_t[8] = {};
     int timing = 0, count_pairs = 0, use_graph = 0;
     int p2p_threads = 64, p2p_kt = 4;
@@ -508,25 +509,30 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     nl += launch_gather(w, x, y, g, nullptr, nullptr, s);
     if (timed)
         CU(record_timing(h->ev_t[1], s));
-    if (far && w.maxdepth >= 2) {
+    const bool sweep = far && w.maxdepth >= 2;
+    if (sweep) {
         CU(cudaMemsetAsync(w.ad_cnt, 0, (FMM_MAXL + 2) * sizeof(int), s));
         CU(cudaEventRecord(h->ev_fork, s));
         CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        nl += launch_adaptive_sweep(w, h->t, h->side);
+        nl += launch_adaptive_up(w, h->t, h->side);
+        CU(cudaEventRecord(h->ev_up, h->side));
+        nl += launch_adaptive_down(w, h->t, h->side);
         CU(cudaEventRecord(h->ev_join, h->side));
     }
     const bool count = near && h->count_pairs;
     if (count)
         CU(cudaMemsetAsync(w.pair_count, 0, sizeof(unsigned long long), s));
-    if (near)
-        nl += launch_adaptive_near(w, count ? w.pair_count : nullptr, s);
+    nl += launch_adaptive_split(w, s);
+    if (sweep)  // the W multipoles are read by the near-field walk
+        CU(cudaStreamWaitEvent(s, h->ev_up, 0));
+    nl += launch_adaptive_near(w, count ? w.pair_count : nullptr, near ? 1 : 0, sweep ? 1 : 0, s);
     if (timed)
         CU(record_timing(h->ev_t[5], s));
-    if (far && w.maxdepth >= 2)
+    if (sweep)
         CU(cudaStreamWaitEvent(s, h->ev_join, 0));
     if (timed)
         CU(record_timing(h->ev_t[6], s));
-    nl += launch_adaptive_final(w, near ? 1 : 0, far ? 1 : 0, u, v, s);
+    nl += launch_adaptive_final(w, sweep ? 1 : 0, u, v, s);
     if (count)
         CU(cudaMemcpyAsync(h->h_pairs, w.pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
@@ -742,7 +748,7 @@ fmm_status fmm_create(int tree_depth, int p, double sigma, fmm_handle *out)
         e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&h->exec, cudaStreamNonBlocking);
-    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_join, &h->ev_status, &h->ev_in, &h->ev_out};
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_join, &h->ev_status, &h->ev_in, &h->ev_out, &h->ev_up};
     for (auto ev : evs)
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
@@ -775,7 +781,7 @@ fmm_status fmm_destroy(fmm_handle h)
         cudaDeviceSynchronize();
     if (h->gexec)
         cudaGraphExecDestroy(h->gexec);
-    cudaEvent_t evs[] = {h->ev_fork, h->ev_join, h->ev_status, h->ev_in, h->ev_out};
+    cudaEvent_t evs[] = {h->ev_fork, h->ev_join, h->ev_status, h->ev_in, h->ev_out, h->ev_up};
     for (auto ev : evs)
         if (ev)
             cudaEventDestroy(ev);

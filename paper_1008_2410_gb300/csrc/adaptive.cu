@@ -124,6 +124,7 @@ struct Store;
 template <>
 struct Store<double> {
     using S = double2;
+    using V2 = double4_16a;  // two complex coefficients
     __device__ static double2 *mp(const Work &w) { return w.M64; }
     __device__ static double2 *loc(const Work &w) { return w.L64; }
     __device__ static const double2 *m2m(const Tables &t) { return t.m2m64; }
@@ -134,6 +135,7 @@ struct Store<double> {
 template <>
 struct Store<float> {
     using S = float2;
+    using V2 = float4;  // two complex coefficients
     __device__ static float2 *mp(const Work &w) { return w.M32; }
     __device__ static float2 *loc(const Work &w) { return w.L32; }
     __device__ static const float2 *m2m(const Tables &t) { return t.m2m32; }
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(128) k_ad_m2m(Work w, Tables tb, int l)
 template <typename R, int PM>
 __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
 {
-    __shared__ cpx<R> sa[4][2][32];
+    __shared__ __align__(16) cpx<R> sa[4][2][32];
     __shared__ R sgm[4][32];
     __shared__ int vl[4][28];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -375,13 +377,19 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
             }
             __syncwarp();
             cpx<R> s0 = {(R)0, (R)0}, s1 = {(R)0, (R)0};
+            using V2 = typename Store<R>::V2;  // two coefficients in one shared-memory load (16 B for FP32)
+            const V2 *q0 = reinterpret_cast<const V2 *>(sa[wi][0]), *q1 = reinterpret_cast<const V2 *>(sa[wi][1]);
 #pragma unroll
-            for (int mm = 0; mm < PM; ++mm) {
-                const cpx<R> x0 = sa[wi][0][mm], x1 = sa[wi][1][mm];
-                s0.re = fma(cb[mm], x0.re, s0.re);
-                s0.im = fma(cb[mm], x0.im, s0.im);
-                s1.re = fma(cb[mm], x1.re, s1.re);
-                s1.im = fma(cb[mm], x1.im, s1.im);
+            for (int mm = 0; mm < PM; mm += 2) {
+                const V2 a = q0[mm >> 1], b = q1[mm >> 1];
+                s0.re = fma(cb[mm], a.x, s0.re);
+                s0.im = fma(cb[mm], a.y, s0.im);
+                s1.re = fma(cb[mm], b.x, s1.re);
+                s1.im = fma(cb[mm], b.y, s1.im);
+                s0.re = fma(cb[mm + 1], a.z, s0.re);
+                s0.im = fma(cb[mm + 1], a.w, s0.im);
+                s1.re = fma(cb[mm + 1], b.z, s1.re);
+                s1.im = fma(cb[mm + 1], b.w, s1.im);
             }
             acc = cadd(acc, cmul(ld<R>(r0 + k + 1), s0));
             if (e1 >= 0)
@@ -530,8 +538,8 @@ __device__ __forceinline__ void walk_uw(const Work &w, const Tree &t, int l, int
 // W list: the multipole of box (ls, sx, sy) evaluated at (xi, yi), (1/w_s) sum_m a~_m / t^(m+1) with
 // t = (z - c_s) / w_s formed in FP64, added to (wr, wi) (complex velocity w = u - i v without 1 / 2pi).
 template <typename R>
-__device__ __forceinline__ void m2p_add(const Work &w, const SysDev &d, double xi, double yi, int ls, int sx, int sy,
-                                        double &wr, double &wi)
+__device__ __noinline__ void m2p_add(const Work &w, const SysDev &d, double xi, double yi, int ls, int sx, int sy,
+                                     double &wr, double &wi)
 {
     const double2 c = centre(d, ls, sx, sy);
     const double iws = ldexp(1.0, ls) / d.S;
@@ -638,7 +646,7 @@ __device__ __forceinline__ float blob_q(float R2)
 
 // K_sigma in units u: K = (-dY, dX) q(R^2) / (2 pi u). FP32 pair terms, summed in FP32 per source leaf and in
 // FP64 across leaves.
-__global__ void __launch_bounds__(128) k_ad_near32(Work w, unsigned long long *pairs, int use_near, int use_far)
+__global__ void __launch_bounds__(128, 10) k_ad_near32(Work w, unsigned long long *pairs, int use_near, int use_far)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.n)

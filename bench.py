@@ -222,6 +222,8 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         f.velocity(x, y, g, u, v)
         out["adaptive"] = adaptive_leg(api, w, x, y, g, u, v, args.precision, flush, stream,
                                        leaf_capacity=args.adaptive or 48, max_depth=args.max_depth)
+    elif args.workload == "uniform_1m" and not args.no_clustered:
+        out["clustered_patches_16m"] = clustered_leg(api, args.precision, flush, stream, args.max_depth)
 
     # roofline of the dominant kernel: near-field P2P, 22 flops per ordered pair (§3)
     f.set_count_pairs(True)
@@ -528,6 +530,42 @@ def adaptive_leg(api, w, x, y, g, u_uni, v_uni, precision, flush, stream, leaf_c
     return out
 
 
+def clustered_leg(api, precision, flush, stream, max_depth: int = 11, leaf_capacity: int = 48) -> dict:
+    """The clustered workload (patches_16m, 2^24 particles from 8 Gaussian patches) on both trees in the run's
+    precision: the uniform depth-9 tree (autotuned near-field tile and M2L engine) and the adaptive tree
+    (leaf capacity 48, maximum depth 11), graph replays, medians of 10; their relative difference."""
+    import numpy as np
+    import torch
+
+    w, _ = workload("patches_16m")
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    fu = api.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain, graph=True)
+    tuned = fu.autotune(x, y, g, w.depth, w.depth)
+    uu, vu = torch.empty_like(x), torch.empty_like(x)
+    for _ in range(3):
+        fu.velocity(x, y, g, uu, vu)
+    msu, _ = timed_steps(lambda: fu.velocity(x, y, g, uu, vu), 10, flush, stream)
+    fu.close()
+    fa = api.FMM(max_depth, w.p, w.sigma, precision=precision, domain=w.domain, graph=True,
+                 leaf_capacity=leaf_capacity)
+    ua, va = torch.empty_like(x), torch.empty_like(x)
+    for _ in range(3):
+        fa.velocity(x, y, g, ua, va)
+    msa, _ = timed_steps(lambda: fa.velocity(x, y, g, ua, va), 10, flush, stream)
+    fa.close()
+    torch.cuda.synchronize()
+    den = torch.sqrt((uu**2).sum() + (vu**2).sum())
+    tu, ta = statistics.median(msu), statistics.median(msa)
+    return {"n": w.n, "p": w.p, "precision": precision,
+            "uniform_tree": {"depth": w.depth, "value": w.n / (tu / 1e3) / 1e6, "unit": "Mparticles/s",
+                             "ms_per_step": tu, "p2p_tile": [tuned["p2p_threads"], tuned["p2p_targets_per_thread"]],
+                             "m2l_engine": tuned["m2l_engine"]},
+            "adaptive_tree": {"max_depth": max_depth, "leaf_capacity": leaf_capacity,
+                              "value": w.n / (ta / 1e3) / 1e6, "unit": "Mparticles/s", "ms_per_step": ta},
+            "rel_diff_adaptive_vs_uniform": float(torch.sqrt(((ua - uu) ** 2).sum() + ((va - vu) ** 2).sum()) / den)}
+
+
 def cpu_baseline(w, u_gpu, v_gpu) -> dict:
     """The FP64 oracle as it stands, on all host cores: one full FMM evaluation of the same workload (or, above
     2^21 particles, its far field plus near field at 4096 sampled targets), plus accuracy figures of the GPU
@@ -621,6 +659,8 @@ def main():
     ap.add_argument("--workload", default="uniform_1m", choices=["uniform_1m", "patches_16m", "patches_4m"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clustered", action="store_true",
+                    help="skip the clustered-workload leg (both trees on patches_16m) of the default run")
     ap.add_argument("--adaptive", type=int, default=0,
                     help="also time the adaptive tree with this leaf capacity (always on for patches_16m, capacity 48)")
     ap.add_argument("--quick", action="store_true", help="main timing only")

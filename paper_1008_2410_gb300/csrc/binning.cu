@@ -540,9 +540,10 @@ __device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, int *t
     }
 }
 
-// Leaf order. Up to 2^16 leaves: one block per leaf. Beyond (deep uniform trees, the adaptive tree's depth-L
-// cells, mostly empty): each block strides over chunks of 64 leaves, lists the chunk's non-empty ones, ranks
-// those of at most 128 particles with one warp each (shuffles, no block barrier) and the rest with the block.
+// Leaf order. The uniform tree (and any tree up to 2^16 leaves): one block per leaf. The adaptive tree's depth-L
+// cells (millions, mostly empty, a few tens of particles at most): each block strides over chunks of 64 cells,
+// lists the chunk's non-empty ones, ranks those of at most 128 particles with one warp each (shuffles, no block
+// barrier) and the rest with the block.
 __global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restrict__ x, const double *__restrict__ y,
                                                    const double *__restrict__ g, const double *__restrict__ gu,
                                                    const double *__restrict__ gv, int mixed)
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restr
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
                   const double *gv, cudaStream_t s)
 {
-    const int grid = w.nleaf <= 65536 ? w.nleaf : 152 * 32;
+    const int grid = (w.nleaf <= 65536 || !w.morton) ? w.nleaf : 152 * 32;
     k_leaf_order<<<grid, 64, 0, s>>>(w, x, y, g, gu, gv, (w.mixed && !gu) ? 1 : 0);
     return 1;
 }

@@ -174,3 +174,20 @@ def test_adaptive_patches_16m_sampled_against_direct_sum(api, precision):
     t = fi.sample_targets(w.n, 256, seed_index=8)
     du, dv = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=t)
     assert rel_l2((u[t], v[t]), (du, dv)) < 1e-5
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adaptive_host_entry_matches_device(api, pinned, precision):
+    """fmm_velocity_host on the adaptive tree (inputs copied in, outputs copied out) gives the device path's
+    result bit for bit."""
+    x, y, g = fi.two_scale(4000, 34)
+    dom = (0.0, 0.0, 1.0)
+    f = api.FMM(9, 14, 1e-3, precision=precision, domain=dom, leaf_capacity=24)
+    ud, vd = f.velocity(dev(x), dev(y), dev(g))
+    f.sync()
+    hx, hy, hg = (torch.from_numpy(np.ascontiguousarray(a)) for a in (x, y, g))
+    if pinned:
+        hx, hy, hg = hx.pin_memory(), hy.pin_memory(), hg.pin_memory()
+    uh, vh = f.velocity_host(hx, hy, hg)
+    assert np.array_equal(ud.cpu().numpy(), np.asarray(uh)) and np.array_equal(vd.cpu().numpy(), np.asarray(vh))

@@ -535,22 +535,31 @@ __device__ __forceinline__ void walk_uw(const Work &w, const Tree &t, int l, int
     }
 }
 
-// W list: the multipole of box (ls, sx, sy) evaluated at (xi, yi), (1/w_s) sum_m a~_m / t^(m+1) with
-// t = (z - c_s) / w_s formed in FP64, added to (wr, wi) (complex velocity w = u - i v without 1 / 2pi).
+// W list: a multipole a~ (p terms) evaluated at t = (ax, ay) = (z - c_s) / w_s: sum_m a~_m / t^(m+1). Out of line
+// (scalar arguments only, so that no large structure is copied to the stack), which keeps the walk's registers
+// low.
 template <typename R>
-__device__ __noinline__ void m2p_add(const Work &w, const SysDev &d, double xi, double yi, int ls, int sx, int sy,
-                                     double &wr, double &wi)
+__device__ __noinline__ double2 m2p_eval(const typename Store<R>::S *a, int p, double ax, double ay)
+{
+    const double id2 = 1.0 / (ax * ax + ay * ay);
+    const cpx<R> uinv = {(R)(ax * id2), (R)(-ay * id2)};
+    cpx<R> s = {(R)0, (R)0};
+    for (int mm = p - 1; mm >= 0; --mm)
+        s = cmul(cadd(s, ld<R>(a + mm)), uinv);
+    return make_double2((double)s.re, (double)s.im);
+}
+
+// The multipole of W box (ls, sx, sy) at (xi, yi), (1/w_s) sum_m a~_m / t^(m+1), t formed in FP64, added to
+// (wr, wi) (complex velocity w = u - i v without 1 / 2pi).
+template <typename R>
+__device__ __forceinline__ void m2p_add(const Work &w, const SysDev &d, double xi, double yi, int ls, int sx, int sy,
+                                        double &wr, double &wi)
 {
     const double2 c = centre(d, ls, sx, sy);
     const double iws = ldexp(1.0, ls) / d.S;
-    const double ax = (xi - c.x) * iws, ay = (yi - c.y) * iws, id2 = 1.0 / (ax * ax + ay * ay);
-    const cpx<R> uinv = {(R)(ax * id2), (R)(-ay * id2)};
-    const auto *a = mp_of<R>(w, ls, morton2(sx, sy));
-    cpx<R> s = {(R)0, (R)0};
-    for (int mm = w.p - 1; mm >= 0; --mm)
-        s = cmul(cadd(s, ld<R>(a + mm)), uinv);
-    wr += (double)s.re * iws;
-    wi += (double)s.im * iws;
+    const double2 r = m2p_eval<R>(mp_of<R>(w, ls, morton2(sx, sy)), w.p, (xi - c.x) * iws, (yi - c.y) * iws);
+    wr += r.x * iws;
+    wi += r.y * iws;
 }
 
 // ------------------------------------------------------------------ stage 9 (U) and the W multipoles
@@ -644,8 +653,40 @@ __device__ __forceinline__ float blob_q(float R2)
     return (1.0f - ex2_approx(-R2)) * rcp_approx(R2);
 }
 
-// K_sigma in units u: K = (-dY, dX) q(R^2) / (2 pi u). FP32 pair terms, summed in FP32 per source leaf and in
-// FP64 across leaves.
+// Pairs of one target with the sources [j0, j1): FP32 terms in two chains (even and odd sources), returned as an
+// FP32 partial (sum of -dY q g, sum of dX q g).
+__device__ __forceinline__ float2 near_range(const Work &w, float4 pi, int j0, int j1)
+{
+    float pu0 = 0.0f, pv0 = 0.0f, pu1 = 0.0f, pv1 = 0.0f;
+    int j = j0;
+#pragma unroll 2
+    for (; j + 1 < j1; j += 2) {
+        const float4 pa = w.eh[j], pb = w.eh[j + 1];
+        const float ga = w.eg[j].x, gb = w.eg[j + 1].x;
+        const float ax = (pi.x - pa.x) + (pi.z - pa.z), ay = (pi.y - pa.y) + (pi.w - pa.w);
+        const float bx = (pi.x - pb.x) + (pi.z - pb.z), by = (pi.y - pb.y) + (pi.w - pb.w);
+        const float fa = ga * blob_q(fmaf(ax, ax, ay * ay)), fb = gb * blob_q(fmaf(bx, bx, by * by));
+        pu0 = fmaf(-ay, fa, pu0);
+        pv0 = fmaf(ax, fa, pv0);
+        pu1 = fmaf(-by, fb, pu1);
+        pv1 = fmaf(bx, fb, pv1);
+    }
+    if (j < j1) {
+        const float4 pa = w.eh[j];
+        const float ga = w.eg[j].x;
+        const float ax = (pi.x - pa.x) + (pi.z - pa.z), ay = (pi.y - pa.y) + (pi.w - pa.w);
+        const float fa = ga * blob_q(fmaf(ax, ax, ay * ay));
+        pu0 = fmaf(-ay, fa, pu0);
+        pv0 = fmaf(ax, fa, pv0);
+    }
+    return make_float2(pu0 + pu1, pv0 + pv1);
+}
+
+// K_sigma in units u: K = (-dY, dX) q(R^2) / (2 pi u). The walk only records the U source ranges (in shared
+// memory, range-major so that a warp's accesses fall in distinct banks) and evaluates the W multipoles; one loop
+// over the recorded ranges then runs the pairs, so that lanes whose leaves reach their sources through different
+// branches of the walk meet in the same loop. FP32 sums per range, FP64 across ranges.
+constexpr int kRanges = 16;
 __global__ void __launch_bounds__(128, 10) k_ad_near32(Work w, unsigned long long *pairs, int use_near, int use_far)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -658,40 +699,32 @@ __global__ void __launch_bounds__(128, 10) k_ad_near32(Work w, unsigned long lon
     const float4 pi = w.eh[i];
     double su = 0.0, sv = 0.0, wr = 0.0, wi = 0.0;
     long long np = -1;
+    __shared__ int2 rg_s[kRanges][128];
+    int2 *rg = &rg_s[0][threadIdx.x];  // range r of this thread at rg[128 r]
+    int nr = 0;
+    auto run = [&]() {
+        for (int r = 0; r < nr; ++r) {
+            const int2 q = rg[128 * r];
+            const float2 part = near_range(w, pi, q.x, q.y);
+            su += (double)part.x;
+            sv += (double)part.y;
+        }
+        nr = 0;
+    };
     auto near = [&](int j0, int j1) {
         np += j1 - j0;
-        if (!use_near)
+        if (!use_near || j1 <= j0)
             return;
-        float pu0 = 0.0f, pv0 = 0.0f, pu1 = 0.0f, pv1 = 0.0f;  // two chains: even and odd sources
-        int j = j0;
-#pragma unroll 2
-        for (; j + 1 < j1; j += 2) {
-            const float4 pa = w.eh[j], pb = w.eh[j + 1];
-            const float ga = w.eg[j].x, gb = w.eg[j + 1].x;
-            const float ax = (pi.x - pa.x) + (pi.z - pa.z), ay = (pi.y - pa.y) + (pi.w - pa.w);
-            const float bx = (pi.x - pb.x) + (pi.z - pb.z), by = (pi.y - pb.y) + (pi.w - pb.w);
-            const float fa = ga * blob_q(fmaf(ax, ax, ay * ay)), fb = gb * blob_q(fmaf(bx, bx, by * by));
-            pu0 = fmaf(-ay, fa, pu0);
-            pv0 = fmaf(ax, fa, pv0);
-            pu1 = fmaf(-by, fb, pu1);
-            pv1 = fmaf(bx, fb, pv1);
-        }
-        if (j < j1) {
-            const float4 pa = w.eh[j];
-            const float ga = w.eg[j].x;
-            const float ax = (pi.x - pa.x) + (pi.z - pa.z), ay = (pi.y - pa.y) + (pi.w - pa.w);
-            const float fa = ga * blob_q(fmaf(ax, ax, ay * ay));
-            pu0 = fmaf(-ay, fa, pu0);
-            pv0 = fmaf(ax, fa, pv0);
-        }
-        su += (double)(pu0 + pu1);
-        sv += (double)(pv0 + pv1);
+        if (nr == kRanges)
+            run();
+        rg[128 * nr++] = make_int2(j0, j1);
     };
     auto far = [&](int ls, int sx, int sy) {
         if (use_far)
             m2p_add<float>(w, d, w.sx[i], w.sy[i], ls, sx, sy, wr, wi);
     };
     walk_uw(w, t, l, bx, by, near, far);
+    run();
     const double sc = d.iu / kTwoPi;  // 1 / (2 pi u)
     w.near64[i] = make_double2(su * sc + wr / kTwoPi, sv * sc - wi / kTwoPi);
     if (pairs && use_near)

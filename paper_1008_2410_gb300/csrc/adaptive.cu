@@ -562,12 +562,28 @@ __device__ __forceinline__ void m2p_add(const Work &w, const SysDev &d, double x
     wi += r.y * iws;
 }
 
-// ------------------------------------------------------------------ stage 9 (U) and the W multipoles
+// Stage 8, L2P: the local expansion of leaf (l, bx, by), l >= 2, at (xi, yi): (1/w) sum_k b^_k zeta^k with
+// zeta = (z - c) / w formed in FP64; returned as the complex velocity w = u - i v without 1 / 2pi.
+template <typename R>
+__device__ __forceinline__ double2 l2p_eval(const Work &w, const SysDev &d, int l, int bx, int by, double xi, double yi)
+{
+    const double2 c = centre(d, l, bx, by);
+    const double iw = ldexp(1.0, l) / d.S;
+    const cpx<R> z = {(R)((xi - c.x) * iw), (R)((yi - c.y) * iw)};
+    const auto *b = loc_of<R>(w, l, morton2(bx, by));
+    cpx<R> s = {(R)0, (R)0};
+    for (int k = w.p - 1; k >= 0; --k)
+        s = cadd(cmul(s, z), ld<R>(b + k));
+    return make_double2((double)s.re * iw, (double)s.im * iw);
+}
 
-// The near-field kernels walk U and W once per target: exact K_sigma over U (use_near) and the multipoles of W
-// (use_far, after the upward pass). near64 receives both, in velocity form.
+// ------------------------------------------------------------------ stages 8-10: U, W, L2P, sum, unsort
 
-__global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pairs, int use_near, int use_far)
+// One thread per target, after the whole sweep: one walk of U and W, the exact K_sigma over U (use_near), the
+// multipoles of W and the leaf's local expansion (use_far), the sum written in the caller's order.
+
+__global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pairs, int use_near, int use_far, double *u,
+                                                double *v)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.n)
@@ -599,7 +615,14 @@ __global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pai
             m2p_add<double>(w, d, xi, yi, ls, sx, sy, wr, wi);
     };
     walk_uw(w, t, l, bx, by, near, far);
-    w.near64[i] = make_double2(su + wr / kTwoPi, sv - wi / kTwoPi);
+    if (use_far && l >= 2) {
+        const double2 b = l2p_eval<double>(w, d, l, bx, by, xi, yi);
+        wr += b.x;
+        wi += b.y;
+    }
+    const int pos = w.perm[i];
+    u[pos] = su + wr / kTwoPi;
+    v[pos] = sv - wi / kTwoPi;
     if (pairs && use_near)
         atomicAdd(pairs, (unsigned long long)np);
 }
@@ -687,7 +710,8 @@ __device__ __forceinline__ float2 near_range(const Work &w, float4 pi, int j0, i
 // over the recorded ranges then runs the pairs, so that lanes whose leaves reach their sources through different
 // branches of the walk meet in the same loop. FP32 sums per range, FP64 across ranges.
 constexpr int kRanges = 16;
-__global__ void __launch_bounds__(128, 10) k_ad_near32(Work w, unsigned long long *pairs, int use_near, int use_far)
+__global__ void __launch_bounds__(128, 10) k_ad_near32(Work w, unsigned long long *pairs, int use_near, int use_far,
+                                                       double *u, double *v)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.n)
@@ -726,43 +750,16 @@ __global__ void __launch_bounds__(128, 10) k_ad_near32(Work w, unsigned long lon
     walk_uw(w, t, l, bx, by, near, far);
     run();
     const double sc = d.iu / kTwoPi;  // 1 / (2 pi u)
-    w.near64[i] = make_double2(su * sc + wr / kTwoPi, sv * sc - wi / kTwoPi);
-    if (pairs && use_near)
-        atomicAdd(pairs, (unsigned long long)np);
-}
-
-// ------------------------------------------------------------------ stages 8 + 10: L2P, sum, unsort
-
-// near64 already holds U and W; this adds the local expansion of the particle's leaf (levels >= 2) and writes
-// the caller's order.
-template <typename R>
-__global__ void __launch_bounds__(128) k_ad_final(Work w, int use_far, double *u, double *v)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.n)
-        return;
-    const SysDev &d = w.sys[0];
-    const double2 nr = w.near64[i];
-    double ru = nr.x, rv = nr.y;
-    if (use_far) {
-        const Tree t{w.start, d.depth, w.adapt_cap};
-        int l, bx, by;
-        particle_leaf(t, (unsigned)w.sleaf[i], l, bx, by);
-        if (l >= 2) {
-            const double2 c = centre(d, l, bx, by);
-            const double iw = ldexp(1.0, l) / d.S;
-            const cpx<R> z = {(R)((w.sx[i] - c.x) * iw), (R)((w.sy[i] - c.y) * iw)};
-            const auto *b = loc_of<R>(w, l, morton2(bx, by));
-            cpx<R> s = {(R)0, (R)0};
-            for (int k = w.p - 1; k >= 0; --k)
-                s = cadd(cmul(s, z), ld<R>(b + k));
-            ru += (double)s.re * iw / kTwoPi;
-            rv -= (double)s.im * iw / kTwoPi;
-        }
+    if (use_far && l >= 2) {
+        const double2 b = l2p_eval<float>(w, d, l, bx, by, w.sx[i], w.sy[i]);
+        wr += b.x;
+        wi += b.y;
     }
     const int pos = w.perm[i];
-    u[pos] = ru;
-    v[pos] = rv;
+    u[pos] = su * sc + wr / kTwoPi;
+    v[pos] = sv * sc - wi / kTwoPi;
+    if (pairs && use_near)
+        atomicAdd(pairs, (unsigned long long)np);
 }
 
 template <typename R, int PM>
@@ -819,21 +816,13 @@ int launch_adaptive_split(const Work &w, cudaStream_t s)
     return 1;
 }
 
-int launch_adaptive_near(const Work &w, unsigned long long *pairs, int use_near, int use_far, cudaStream_t s)
+int launch_adaptive_near(const Work &w, unsigned long long *pairs, int use_near, int use_far, double *u, double *v,
+                         cudaStream_t s)
 {
     if (w.ad_mixed)
-        k_ad_near32<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs, use_near, use_far);
+        k_ad_near32<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs, use_near, use_far, u, v);
     else
-        k_ad_near<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs, use_near, use_far);
-    return 1;
-}
-
-int launch_adaptive_final(const Work &w, int use_far, double *u, double *v, cudaStream_t s)
-{
-    if (w.ad_mixed)
-        k_ad_final<float><<<(w.n + 127) / 128, 128, 0, s>>>(w, use_far, u, v);
-    else
-        k_ad_final<double><<<(w.n + 127) / 128, 128, 0, s>>>(w, use_far, u, v);
+        k_ad_near<<<(w.n + 127) / 128, 128, 0, s>>>(w, pairs, use_near, use_far, u, v);
     return 1;
 }
 

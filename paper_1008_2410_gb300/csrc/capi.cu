@@ -58,7 +58,6 @@ struct fmm_ctx {
     cudaStream_t exec = nullptr;    // internal stream used for graph capture / replay
     cudaStream_t side = nullptr;    // high-priority stream of the multipole sweep
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_status = nullptr, ev_in = nullptr, ev_out = nullptr;
-    cudaEvent_t ev_up = nullptr;  // adaptive tree: the upward pass is done (side stream)
     cudaEvent_t ev_t[8] = {};
     int timing = 0, count_pairs = 0, use_graph = 0;
     int p2p_threads = 64, p2p_kt = 4;
@@ -515,7 +514,6 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
         CU(cudaEventRecord(h->ev_fork, s));
         CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         nl += launch_adaptive_up(w, h->t, h->side);
-        CU(cudaEventRecord(h->ev_up, h->side));
         nl += launch_adaptive_down(w, h->t, h->side);
         CU(cudaEventRecord(h->ev_join, h->side));
     }
@@ -523,16 +521,11 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     if (count)
         CU(cudaMemsetAsync(w.pair_count, 0, sizeof(unsigned long long), s));
     nl += launch_adaptive_split(w, s);
-    if (sweep)  // the W multipoles are read by the near-field walk
-        CU(cudaStreamWaitEvent(s, h->ev_up, 0));
-    nl += launch_adaptive_near(w, count ? w.pair_count : nullptr, near ? 1 : 0, sweep ? 1 : 0, s);
+    if (sweep)  // the walk reads the W multipoles and the leaf's local expansion
+        CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+    nl += launch_adaptive_near(w, count ? w.pair_count : nullptr, near ? 1 : 0, sweep ? 1 : 0, u, v, s);
     if (timed)
         CU(record_timing(h->ev_t[5], s));
-    if (sweep)
-        CU(cudaStreamWaitEvent(s, h->ev_join, 0));
-    if (timed)
-        CU(record_timing(h->ev_t[6], s));
-    nl += launch_adaptive_final(w, sweep ? 1 : 0, u, v, s);
     if (count)
         CU(cudaMemcpyAsync(h->h_pairs, w.pair_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
@@ -541,7 +534,7 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     CU(cudaGetLastError());
     h->launches += nl;
     h->last_timed = timed;
-    h->timed_mask = timed ? 0xe3u : 0u;  // binning, near field, final kernel, total
+    h->timed_mask = timed ? 0xa3u : 0u;  // binning, near-field walk (after the sweep when far), total
     return FMM_OK;
 }
 
@@ -748,7 +741,7 @@ fmm_status fmm_create(int tree_depth, int p, double sigma, fmm_handle *out)
         e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&h->exec, cudaStreamNonBlocking);
-    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_join, &h->ev_status, &h->ev_in, &h->ev_out, &h->ev_up};
+    cudaEvent_t *evs[] = {&h->ev_fork, &h->ev_join, &h->ev_status, &h->ev_in, &h->ev_out};
     for (auto ev : evs)
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
@@ -781,7 +774,7 @@ fmm_status fmm_destroy(fmm_handle h)
         cudaDeviceSynchronize();
     if (h->gexec)
         cudaGraphExecDestroy(h->gexec);
-    cudaEvent_t evs[] = {h->ev_fork, h->ev_join, h->ev_status, h->ev_in, h->ev_out, h->ev_up};
+    cudaEvent_t evs[] = {h->ev_fork, h->ev_join, h->ev_status, h->ev_in, h->ev_out};
     for (auto ev : evs)
         if (ev)
             cudaEventDestroy(ev);

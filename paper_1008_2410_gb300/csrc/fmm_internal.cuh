@@ -211,14 +211,14 @@ int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaSt
 
 // Adaptive tree (adaptive.cu, single system, keys in Morton order, sorted FP64 particles). Side stream: the upward
 // pass (box lists, P2M, M2M), then the downward pass (per level L2L + M2L over V + P2L over X). Main stream: the
-// split coordinates of the precision form, the walk of U and W per target (exact K_sigma over U if use_near, the
-// multipoles of W if use_far, after the upward pass) into near64, then the final kernel (L2P of the leaf's
-// local if use_far, after the downward pass; scattered to the caller's order).
+// split coordinates of the precision form, then (after the sweep) one kernel per target: a walk of U and W,
+// exact K_sigma over U if use_near, the multipoles of W and the leaf's local if use_far, written in the caller's
+// order.
 int launch_adaptive_up(const Work &w, const Tables &t, cudaStream_t s);
 int launch_adaptive_down(const Work &w, const Tables &t, cudaStream_t s);
 int launch_adaptive_split(const Work &w, cudaStream_t s);
-int launch_adaptive_near(const Work &w, unsigned long long *pairs, int use_near, int use_far, cudaStream_t s);
-int launch_adaptive_final(const Work &w, int use_far, double *u, double *v, cudaStream_t s);
+int launch_adaptive_near(const Work &w, unsigned long long *pairs, int use_near, int use_far, double *u, double *v,
+                         cudaStream_t s);
 
 void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom);
 

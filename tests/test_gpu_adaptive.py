@@ -52,6 +52,14 @@ def blob_at_max_depth():
     return x, y, r.standard_normal(500) / 500
 
 
+def tight_blob():
+    """A cluster of 300 points in a 2e-4 square plus a sparse background: refinement down to the maximum depth 12."""
+    r = fi.rng(38)
+    x = np.concatenate([0.6 + 2e-4 * r.random(300), r.random(200)])
+    y = np.concatenate([0.3 + 2e-4 * r.random(300), r.random(200)])
+    return x, y, r.standard_normal(500) / 500
+
+
 def coincident():
     r = fi.rng(24)
     x = np.concatenate([np.full(50, 0.7), r.random(400)])
@@ -67,6 +75,10 @@ CASES = [
     ("blob_at_max_depth_L5_B8_p12", blob_at_max_depth, 1e-3, 5, 8, 12, (0.0, 0.0, 1.0)),
     ("coincident_L7_B10_p12", coincident, 1e-3, 7, 10, 12, (0.0, 0.0, 1.0)),
     ("ragged_B1_L6_p8", lambda: fi.two_scale(777, 30), 2e-3, 6, 1, 8, (0.0, 0.0, 1.0)),
+    ("p1_L7_B12", lambda: fi.two_scale(1500, 35), 2e-3, 7, 12, 1, (0.0, 0.0, 1.0)),
+    ("p24_L8_B16", lambda: fi.two_scale(2000, 36), 2e-3, 8, 16, 24, (0.0, 0.0, 1.0)),
+    ("p32_L8_B16", lambda: fi.two_scale(2000, 37), 2e-3, 8, 16, 32, (0.0, 0.0, 1.0)),
+    ("depth12_tight_blob_B4_p12", lambda: tight_blob(), 2e-5, 12, 4, 12, (0.0, 0.0, 1.0)),
 ]
 
 

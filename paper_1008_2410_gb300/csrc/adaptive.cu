@@ -300,20 +300,101 @@ __global__ void __launch_bounds__(128) k_ad_m2m(Work w, Tables tb, int l)
     }
 }
 
+// ------------------------------------------------------------------ X list: P2L into the locals of level l
+
+// One warp per existing box of level l. Lanes 0..7 each take one of the parent's neighbour cells, find the leaf
+// covering it and keep it if it is coarser, not adjacent to the box and not already found by a lower lane; then
+// the particles of the kept leaves run one per lane, each lane accumulating all p coefficients
+// b^_k = -sum_j q'_j s_j^-(k+1), s_j = (z_j - c) / w, in registers (powers by repeated multiplication, 1 / s_j
+// formed in FP64), and a butterfly sum over the warp gives the box's X part. Writes every existing box's local
+// (zero without an X list); the downward pass adds L2L and M2L to it.
+template <typename R, int PM>
+__global__ void __launch_bounds__(128) k_ad_p2l(Work w, int l)
+{
+    const int lane = threadIdx.x & 31;
+    const SysDev &d = w.sys[0];
+    const Tree t{w.start, d.depth, w.adapt_cap};
+    const int nbx = w.ad_cnt[l], p = w.p, L = d.depth, nside = 1 << l;
+    const double iw = ldexp(1.0, l) / d.S;
+    for (int idx = blockIdx.x * 4 + (threadIdx.x >> 5); idx < nbx; idx += gridDim.x * 4) {
+        const unsigned m = (unsigned)w.ad_list[d.box0[l] + idx];
+        const int bx = (int)compact1(m), by = (int)compact1(m >> 1), px = bx >> 1, py = by >> 1;
+        int xid = -1;
+        if (lane < 8) {
+            const int dxy = lane < 4 ? lane : lane + 1;  // 3 x 3 block without its centre
+            int lq = l - 1, qx = px + dxy % 3 - 1, qy = py + dxy / 3 - 1;
+            if (qx >= 0 && qy >= 0 && qx < (nside >> 1) && qy < (nside >> 1)) {
+                covering_box(t, lq, qx, qy);
+                if (!(lq == l - 1 && box_split(t, lq, qx, qy)) && !adjacent(L, l, bx, by, lq, qx, qy) &&
+                    box_count(t, lq, morton2(qx, qy)) > 0)
+                    xid = pack_box(lq, qx, qy);
+            }
+        }
+        bool keep = xid >= 0;
+        for (int o = 0; o < 8; ++o) {
+            const int other = __shfl_sync(0xffffffffu, xid, o);
+            keep = keep && !(o < lane && other == xid);
+        }
+        unsigned xm = __ballot_sync(0xffffffffu, keep);
+        auto *dst = loc_of<R>(w, l, m);
+        if (!xm) {
+            if (lane < p)
+                st(dst + lane, cpx<R>{(R)0, (R)0});
+            continue;
+        }
+        cpx<R> acc[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            acc[k] = {(R)0, (R)0};
+        const double2 c = centre(d, l, bx, by);
+        while (xm) {
+            const int src = __ffs(xm) - 1;
+            xm &= xm - 1;
+            const int id = __shfl_sync(0xffffffffu, xid, src);
+            const int lq = id >> 26, qx = (id >> 13) & 0x1fff, qy = id & 0x1fff;
+            const unsigned mq = morton2(qx, qy);
+            const int j0 = box_first(t, lq, mq), cnt = box_count(t, lq, mq);
+            for (int e = lane; e < cnt; e += 32) {
+                const int j = j0 + e;
+                const double ax = (w.sx[j] - c.x) * iw, ay = (w.sy[j] - c.y) * iw;
+                const double id2 = 1.0 / (ax * ax + ay * ay);
+                const cpx<R> is = {(R)(ax * id2), (R)(-ay * id2)};
+                const R g = (R)w.sg[j];
+                cpx<R> pw = {-g * is.im, g * is.re};  // -q' / s with q' = -i gamma: i gamma / s
+#pragma unroll
+                for (int k = 0; k < PM; ++k) {
+                    acc[k] = cadd(acc[k], pw);
+                    pw = cmul(pw, is);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[k].re += __shfl_xor_sync(0xffffffffu, acc[k].re, o);
+                acc[k].im += __shfl_xor_sync(0xffffffffu, acc[k].im, o);
+            }
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            if (lane == k && k < p)
+                st(dst + k, acc[k]);
+    }
+}
+
 // ------------------------------------------------------------------ stages 6-7: locals of level l (L2L + V + X)
 
-// One warp per existing box of level l, lane k = local coefficient; the binomial column C(m + k, m) stays in
-// registers (PM >= p, entries m >= p zero) and the V sources are taken two at a time.
+// One warp per existing box of level l, lane k = local coefficient: adds L2L from the parent and M2L over V to the
+// X-list part left by k_ad_p2l. The binomial column C(m + k, m) stays in registers (PM >= p, entries m >= p zero)
+// and the V sources are taken two at a time.
 template <typename R, int PM>
 __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
 {
     __shared__ __align__(16) cpx<R> sa[4][2][32];
-    __shared__ R sgm[4][32];
     __shared__ int vl[4][28];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const SysDev &d = w.sys[0];
     const Tree t{w.start, d.depth, w.adapt_cap};
-    const int nbx = w.ad_cnt[l], p = w.p, P = FMM_PMAX, L = d.depth, nside = 1 << l;
+    const int nbx = w.ad_cnt[l], p = w.p, P = FMM_PMAX, nside = 1 << l;
     const int k = lane < p ? lane : p - 1;  // lanes >= p shadow the last coefficient and do not store
     const auto *rho = Store<R>::rho(tb);
     const auto *binom = Store<R>::binom(tb);
@@ -321,11 +402,11 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
 #pragma unroll
     for (int mm = 0; mm < PM; ++mm)
         cb[mm] = mm < p ? (R)binom[mm * P + k] : (R)0;
-    const double iw = ldexp(1.0, l) / d.S;
     for (int idx = blockIdx.x * 4 + wi; idx < nbx; idx += gridDim.x * 4) {
         const unsigned m = (unsigned)w.ad_list[d.box0[l] + idx];
         const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
-        cpx<R> acc = {(R)0, (R)0};
+        // the X-list part (k_ad_p2l) is already in the local
+        cpx<R> acc = lane < p ? ld<R>(loc_of<R>(w, l, m) + lane) : cpx<R>{(R)0, (R)0};
         __syncwarp();
         // L2L from the parent
         if (l >= 3) {
@@ -395,51 +476,6 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
             if (e1 >= 0)
                 acc = cadd(acc, cmul(ld<R>(r1 + k + 1), s1));
             __syncwarp();
-        }
-        // X: P2L from the coarser leaves adjacent to the parent but not to b. Lanes 0..7 each take one of the
-        // parent's neighbour cells, find the leaf covering it, and keep it unless a lower lane found the same.
-        int xid = -1;
-        if (lane < 8) {
-            const int dxy = lane < 4 ? lane : lane + 1;  // 3 x 3 block without its centre
-            int lq = l - 1, qx = px + dxy % 3 - 1, qy = py + dxy / 3 - 1;
-            if (qx >= 0 && qy >= 0 && qx < (nside >> 1) && qy < (nside >> 1)) {
-                covering_box(t, lq, qx, qy);
-                if (!(lq == l - 1 && box_split(t, lq, qx, qy)) && !adjacent(L, l, bx, by, lq, qx, qy) &&
-                    box_count(t, lq, morton2(qx, qy)) > 0)
-                    xid = pack_box(lq, qx, qy);
-            }
-        }
-        bool keep = xid >= 0;
-        for (int o = 0; o < 8; ++o) {
-            const int other = __shfl_sync(0xffffffffu, xid, o);
-            keep = keep && !(o < lane && other == xid);
-        }
-        unsigned xm = __ballot_sync(0xffffffffu, keep);
-        const double2 c = centre(d, l, bx, by);
-        while (xm) {
-            const int src = __ffs(xm) - 1;
-            xm &= xm - 1;
-            const int id = __shfl_sync(0xffffffffu, xid, src);
-            const int lq = id >> 26, qx = (id >> 13) & 0x1fff, qy = id & 0x1fff;
-            const unsigned mq = morton2(qx, qy);
-            const int j0 = box_first(t, lq, mq), cnt = box_count(t, lq, mq);
-            for (int e0 = 0; e0 < cnt; e0 += 32) {
-                if (e0 + lane < cnt) {  // 1 / s_j, s_j = (z_j - c) / w, formed in FP64
-                    const int j = j0 + e0 + lane;
-                    const double ax = (w.sx[j] - c.x) * iw, ay = (w.sy[j] - c.y) * iw;
-                    const double id2 = 1.0 / (ax * ax + ay * ay);
-                    sa[wi][0][lane] = {(R)(ax * id2), (R)(-ay * id2)};
-                    sgm[wi][lane] = (R)w.sg[j];
-                }
-                __syncwarp();
-                const int ne = min(32, cnt - e0);
-                for (int e = 0; e < ne; ++e) {
-                    const cpx<R> ip = cpow(sa[wi][0][e], k + 1);
-                    const R g = sgm[wi][e];
-                    acc = cadd(acc, cpx<R>{-g * ip.im, g * ip.re});  // -q' s^-(k+1), q' = -i gamma
-                }
-                __syncwarp();
-            }
         }
         if (lane < p)
             st(loc_of<R>(w, l, m) + lane, acc);
@@ -767,10 +803,12 @@ int sweep_levels(const Work &w, const Tables &t, int part, cudaStream_t s)
 {
     const int L = w.maxdepth;
     int nl = 0;
-    if (part == 0) {  // upward: box lists, P2M, M2M
+    if (part == 0) {  // box lists, P2L over X (particles only), then upward: P2M, M2M
         const int64_t ne = enum_threads(L);
         k_ad_enum<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(w);
         ++nl;
+        for (int l = 2; l <= L; ++l, ++nl)
+            k_ad_p2l<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, l);
         for (int l = 2; l <= L; ++l, ++nl)
             k_ad_p2m<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, l);
         for (int l = L - 1; l >= 2; --l, ++nl)

@@ -336,11 +336,11 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = f64 ? np * 8 : 0;                            // 9 sg
     sizes[i++] = (mixed || ad_mixed) ? np * 48 : 0;           // 10 eh, el, eg
     sizes[i++] = mixed ? np * 8 : 0;                          // 11 far32
-    sizes[i++] = mixed ? 0 : np * 16;                         // 12 near64
+    sizes[i++] = (mixed || h->adaptive_cap) ? 0 : np * 16;    // 12 near64 (the adaptive walk writes u, v itself)
     sizes[i++] = mixed ? np * 8 : 0;                          // 13 near32
     sizes[i++] = (size_t)nbox * 4 + 16;                       // 14 bcount
-    sizes[i++] = (size_t)nbox * p * 16;                       // 15 M64
-    sizes[i++] = (size_t)nbox * p * 16;                       // 16 L64
+    sizes[i++] = ad_mixed ? 0 : (size_t)nbox * p * 16;        // 15 M64 (the adaptive precision form keeps FP32 only)
+    sizes[i++] = ad_mixed ? 0 : (size_t)nbox * p * 16;        // 16 L64
     sizes[i++] = (mixed || ad_mixed) ? (size_t)nbox * p * 8 : 0;  // 17 M32
     sizes[i++] = (mixed || ad_mixed) ? (size_t)nbox * p * 8 : 0;  // 18 L32
     sizes[i++] = adjoint ? np * 8 : 0;                        // 19 sgu
@@ -413,8 +413,8 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.far32 = sizes[11] ? (float2 *)(b + lay.off[11]) : nullptr;
     w.nearp = sizes[23] ? (float2 *)(b + lay.off[23]) : nullptr;
     w.bcount = (int *)(b + lay.off[14]);
-    w.M64 = (double2 *)(b + lay.off[15]);
-    w.L64 = (double2 *)(b + lay.off[16]);
+    w.M64 = sizes[15] ? (double2 *)(b + lay.off[15]) : nullptr;
+    w.L64 = sizes[16] ? (double2 *)(b + lay.off[16]) : nullptr;
     w.M32 = sizes[17] ? (float2 *)(b + lay.off[17]) : nullptr;
     w.L32 = sizes[18] ? (float2 *)(b + lay.off[18]) : nullptr;
     w.sgu = sizes[19] ? (double *)(b + lay.off[19]) : nullptr;

@@ -153,7 +153,7 @@ fmm_status fmm_velocity(fmm_handle h, int64_t n, const double *x, const double *
  * evaluates, copies u, v back and synchronises the stream before returning. Page-locked inputs of the
  * precision form with an explicit root square are not copied first: the key kernel, their only reader,
  * reads them in place over the host link; page-locked outputs are written in place by the final sum, which
- * writes in caller order. */
+ * writes in caller order. On the adaptive tree (fmm_set_adaptive) inputs and outputs are always copied. */
 fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
                              double *u, double *v);
 

@@ -1053,9 +1053,10 @@ fmm_status fmm_velocity_host(fmm_handle h, int64_t n, const double *x, const dou
         in[1] = dy;
         in[2] = dg;
     }
-    // page-locked outputs are written in place by the final (caller-order, contiguous) sum kernel
+    // page-locked outputs are written in place by the uniform tree's final (caller-order, contiguous) sum kernel;
+    // the adaptive tree's walk writes through the permutation (scattered), so its outputs take one copy each
     double *out[2] = {u, v};
-    bool direct_out = true;
+    bool direct_out = h->adaptive_cap == 0;
     for (int k = 0; k < 2 && direct_out; ++k) {
         cudaPointerAttributes a{};
         if (cudaPointerGetAttributes(&a, out[k]) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer)

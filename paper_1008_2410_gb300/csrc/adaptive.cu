@@ -663,20 +663,10 @@ __global__ void __launch_bounds__(128) k_ad_near(Work w, unsigned long long *pai
         atomicAdd(pairs, (unsigned long long)np);
 }
 
-// Precision form: positions in units u = sigma sqrt(2 / log2 e), X = (x - x0) / u, split into hi + lo floats so that
-// a displacement (hi_i - hi_j) + (lo_i - lo_j) keeps about 2^-24 of its own size; circulation as a float. In
-// these units exp(-r^2 / 2 sigma^2) = 2^-(R^2), R = r / u.
-__global__ void k_ad_split(Work w)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.n)
-        return;
-    const SysDev &d = w.sys[0];
-    const double X = (w.sx[i] - d.x0) * d.iu, Y = (w.sy[i] - d.y0) * d.iu;
-    const float hx = (float)X, hy = (float)Y;
-    w.eh[i] = make_float4(hx, hy, (float)(X - (double)hx), (float)(Y - (double)hy));
-    w.eg[i].x = (float)w.sg[i];
-}
+// Precision form: positions in units u = sigma sqrt(2 / log2 e), X = (x - x0) / u, split into hi + lo floats
+// (eh = (xh, yh, xl, yl), written with the circulation eg.x by the leaf-order kernel) so that a displacement
+// (hi_i - hi_j) + (lo_i - lo_j) keeps about 2^-24 of its own size. In these units exp(-r^2 / 2 sigma^2) = 2^-(R^2),
+// R = r / u.
 
 __device__ __forceinline__ float ex2_approx(float v)
 {
@@ -846,13 +836,6 @@ int launch_adaptive_down(const Work &w, const Tables &t, cudaStream_t s)
     return w.ad_mixed ? sweep_bucket<float>(w, t, 1, s) : sweep_bucket<double>(w, t, 1, s);
 }
 
-int launch_adaptive_split(const Work &w, cudaStream_t s)
-{
-    if (!w.ad_mixed)
-        return 0;
-    k_ad_split<<<(w.n + 255) / 256, 256, 0, s>>>(w);
-    return 1;
-}
 
 int launch_adaptive_near(const Work &w, unsigned long long *pairs, int use_near, int use_far, double *u, double *v,
                          cudaStream_t s)

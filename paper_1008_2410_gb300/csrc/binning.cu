@@ -506,12 +506,20 @@ __device__ __forceinline__ void place_particle(const Work &w, int v, int pos, in
         w.el[pos] = make_float4(p.z, p.z, p.w, p.w);
         w.eg[pos] = make_float4(gg, gg, -gg, -gg);
     } else {
-        w.sx[pos] = x[v];
-        w.sy[pos] = y[v];
-        w.sg[pos] = g[v];
+        const double xv = x[v], yv = y[v], gv0 = g[v];
+        w.sx[pos] = xv;
+        w.sy[pos] = yv;
+        w.sg[pos] = gv0;
         if (gu) {
             w.sgu[pos] = gu[v];
             w.sgv[pos] = gv[v];
+        }
+        if (w.ad_mixed) {  // adaptive precision form: hi + lo floats in units u = sigma sqrt(2 / log2 e)
+            const SysDev &d = w.sys[0];
+            const double X = (xv - d.x0) * d.iu, Y = (yv - d.y0) * d.iu;
+            const float hx = (float)X, hy = (float)Y;
+            w.eh[pos] = make_float4(hx, hy, (float)(X - (double)hx), (float)(Y - (double)hy));
+            w.eg[pos].x = (float)gv0;
         }
     }
 }

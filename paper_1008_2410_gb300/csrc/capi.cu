@@ -520,7 +520,6 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     const bool count = near && h->count_pairs;
     if (count)
         CU(cudaMemsetAsync(w.pair_count, 0, sizeof(unsigned long long), s));
-    nl += launch_adaptive_split(w, s);
     if (sweep)  // the walk reads the W multipoles and the leaf's local expansion
         CU(cudaStreamWaitEvent(s, h->ev_join, 0));
     nl += launch_adaptive_near(w, count ? w.pair_count : nullptr, near ? 1 : 0, sweep ? 1 : 0, u, v, s);

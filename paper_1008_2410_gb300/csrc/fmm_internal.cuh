@@ -209,14 +209,13 @@ int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, 
 int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);  // adds it
 int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);
 
-// Adaptive tree (adaptive.cu, single system, keys in Morton order, sorted FP64 particles). Side stream: the upward
-// pass (box lists, P2M, M2M), then the downward pass (per level L2L + M2L over V + P2L over X). Main stream: the
-// split coordinates of the precision form, then (after the sweep) one kernel per target: a walk of U and W,
-// exact K_sigma over U if use_near, the multipoles of W and the leaf's local if use_far, written in the caller's
-// order.
+// Adaptive tree (adaptive.cu, single system, keys in Morton order, sorted FP64 particles and, in the precision form,
+// the split records written by the leaf-order kernel). Side stream: the upward pass (box lists, P2L over X, P2M,
+// M2M), then the downward pass (per level L2L + M2L over V). Main stream, after the sweep, one kernel per target:
+// a walk of U and W, exact K_sigma over U if use_near, the multipoles of W and the leaf's local if use_far,
+// written in the caller's order.
 int launch_adaptive_up(const Work &w, const Tables &t, cudaStream_t s);
 int launch_adaptive_down(const Work &w, const Tables &t, cudaStream_t s);
-int launch_adaptive_split(const Work &w, cudaStream_t s);
 int launch_adaptive_near(const Work &w, unsigned long long *pairs, int use_near, int use_far, double *u, double *v,
                          cudaStream_t s);
 

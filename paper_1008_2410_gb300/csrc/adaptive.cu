@@ -708,7 +708,7 @@ __device__ __forceinline__ float2 near_range(const Work &w, float4 pi, int j0, i
 {
     float pu0 = 0.0f, pv0 = 0.0f, pu1 = 0.0f, pv1 = 0.0f;
     int j = j0;
-#pragma unroll 2
+#pragma unroll 4
     for (; j + 1 < j1; j += 2) {
         const float4 pa = w.eh[j], pb = w.eh[j + 1];
         const float ga = w.eg[j].x, gb = w.eg[j + 1].x;
@@ -736,7 +736,7 @@ __device__ __forceinline__ float2 near_range(const Work &w, float4 pi, int j0, i
 // over the recorded ranges then runs the pairs, so that lanes whose leaves reach their sources through different
 // branches of the walk meet in the same loop. FP32 sums per range, FP64 across ranges.
 constexpr int kRanges = 16;
-__global__ void __launch_bounds__(128, 10) k_ad_near32(Work w, unsigned long long *pairs, int use_near, int use_far,
+__global__ void __launch_bounds__(128, 8) k_ad_near32(Work w, unsigned long long *pairs, int use_near, int use_far,
                                                        double *u, double *v)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

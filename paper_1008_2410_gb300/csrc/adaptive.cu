@@ -94,29 +94,6 @@ __device__ __forceinline__ cpx<R> cadd(cpx<R> a, cpx<R> b)
 {
     return {a.re + b.re, a.im + b.im};
 }
-template <typename R>
-__device__ __forceinline__ cpx<R> cscale(cpx<R> a, R s)
-{
-    return {a.re * s, a.im * s};
-}
-template <typename R>
-__device__ __forceinline__ cpx<R> cinv(cpx<R> a)
-{
-    const R d = (R)1 / (a.re * a.re + a.im * a.im);
-    return {a.re * d, -a.im * d};
-}
-template <typename R>
-__device__ __forceinline__ cpx<R> cpow(cpx<R> a, int e)  // a^e, e >= 0, by repeated squaring
-{
-    cpx<R> r = {(R)1, (R)0};
-    while (e > 0) {
-        if (e & 1)
-            r = cmul(r, a);
-        a = cmul(a, a);
-        e >>= 1;
-    }
-    return r;
-}
 
 // Storage of the expansions: FP64 form double2 (M64 / L64), precision form float2 (M32 / L32).
 template <typename R>

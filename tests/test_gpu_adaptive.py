@@ -203,3 +203,17 @@ def test_adaptive_host_entry_matches_device(api, pinned, precision):
         hx, hy, hg = hx.pin_memory(), hy.pin_memory(), hg.pin_memory()
     uh, vh = f.velocity_host(hx, hy, hg)
     assert np.array_equal(ud.cpu().numpy(), np.asarray(uh)) and np.array_equal(vd.cpu().numpy(), np.asarray(vh))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adaptive_empty_and_single_particle(api, precision):
+    """n = 0 is a no-op; one particle feels no velocity (K_sigma(0) = 0, nothing else to interact with)."""
+    f = api.FMM(8, 12, 1e-3, precision=precision, domain=(0.0, 0.0, 1.0), leaf_capacity=16)
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    u0, v0 = f.velocity(e, e, e)
+    f.sync()
+    assert u0.numel() == 0 and v0.numel() == 0
+    one = lambda a: dev(np.array([a]))
+    u1, v1 = f.velocity(one(0.3), one(0.7), one(1.0))
+    f.sync()
+    assert float(u1.abs().max()) == 0.0 and float(v1.abs().max()) == 0.0

@@ -109,8 +109,8 @@ int fmm_get_m2l_engine(fmm_handle h);
  * box's local expansion (X). So the sum is Eq. 7 with K_sigma between adjacent leaves and the point-vortex
  * kernel elsewhere, as on the uniform tree. The adaptive evaluation computes in FP64 whatever the precision
  * setting, serves fmm_velocity, fmm_velocity_near / _far, fmm_velocity_host and fmm_advect, and counts the
- * ordered pairs of its U lists when pair counting is on; fmm_velocity_batched, fmm_velocity_adjoint and
- * fmm_autotune return FMM_EINVAL while it is set.
+ * ordered pairs of its U lists when pair counting is on; fmm_autotune then picks the leaf capacity (and the
+ * maximum depth within its range); fmm_velocity_batched and fmm_velocity_adjoint return FMM_EINVAL while it is set.
  * Returns FMM_EINVAL for NULL or a negative capacity. */
 fmm_status fmm_set_adaptive(fmm_handle h, int leaf_capacity);
 
@@ -215,9 +215,11 @@ int64_t fmm_kernel_launches(fmm_handle h);
 
 /* Picks depth and near-field tile for the handle's p, sigma and precision by timing fmm_velocity on the given
  * particles (device arrays, left unchanged; u, v are scratch outputs). Tries depths depth_lo..depth_hi; in
- * the precision form it then times both M2L engines (fmm_set_m2l_engine) and keeps the faster.
+ * the precision form it then times both M2L engines (fmm_set_m2l_engine) and keeps the faster. With a leaf
+ * capacity set (fmm_set_adaptive) it instead times the adaptive tree with capacities 16, 24, 32, 48, 64, 96 and
+ * 128 at each maximum depth depth_lo..depth_hi and keeps the fastest pair.
  * The choice is stored in the handle and, when the environment variable FMM2D_TUNE_CACHE names a file,
- * cached there keyed by (n, p, precision). */
+ * cached there keyed by (n, p, precision, tree kind). */
 fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
                         double *u, double *v, int depth_lo, int depth_hi);
 fmm_status fmm_get_params(fmm_handle h, int *tree_depth, int *p, double *sigma, int *p2p_threads,

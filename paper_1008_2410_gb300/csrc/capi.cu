@@ -715,6 +715,78 @@ static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x
     return FMM_OK;
 }
 
+// Median of 5 timed evaluations (after 2 untimed ones) of the handle as configured, in ms; < 0 if one failed.
+static float time_evaluation(fmm_handle h, int64_t n, const double *x, const double *y, const double *g, double *u,
+                             double *v, cudaEvent_t e0, cudaEvent_t e1);
+
+// Adaptive tree: the leaf capacity (and the maximum depth within [depth_lo, depth_hi]) of the fastest evaluation,
+// timed as the handle runs (graph replays when it uses graphs); cached like the uniform tree's choice.
+static fmm_status autotune_adaptive(fmm_handle h, int64_t n, const double *x, const double *y, const double *g,
+                                    double *u, double *v, int depth_lo, int depth_hi)
+{
+    const char *cache = getenv("FMM2D_TUNE_CACHE");
+    char keybuf[192];
+    snprintf(keybuf, sizeof keybuf, "adaptive n=%lld p=%d mixed=%d sigma=%.17g lo=%d hi=%d", (long long)n, h->p,
+             h->mixed, h->sigma, depth_lo, depth_hi);
+    if (cache) {
+        FILE *f = fopen(cache, "r");
+        if (f) {
+            char line[256];
+            while (fgets(line, sizeof line, f)) {
+                int d, cap;
+                char *bar = strchr(line, '|');
+                if (!bar)
+                    continue;
+                *bar = 0;
+                if (strcmp(line, keybuf) == 0 && sscanf(bar + 1, "%d %d", &d, &cap) == 2 && cap > 0) {
+                    fclose(f);
+                    h->depth = d;
+                    h->adaptive_cap = cap;
+                    h->cfg_version++;
+                    return FMM_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    static const int caps[] = {16, 24, 32, 48, 64, 96, 128};
+    const int save_timing = h->timing;
+    h->timing = 0;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bd = h->depth, bcap = h->adaptive_cap;
+    for (int d = depth_lo; d <= depth_hi; ++d)
+        for (int cap : caps) {
+            h->depth = d;
+            h->adaptive_cap = cap;
+            h->cfg_version++;
+            const float t = time_evaluation(h, n, x, y, g, u, v, e0, e1);
+            if (t >= 0.f && t < best) {
+                best = t;
+                bd = d;
+                bcap = cap;
+            }
+        }
+    h->depth = bd;
+    h->adaptive_cap = bcap;
+    h->cfg_version++;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->timing = save_timing;
+    if (best >= 1e30f)
+        return set_err(h, FMM_ECUDA, "no candidate ran");
+    if (cache) {
+        FILE *f = fopen(cache, "a");
+        if (f) {
+            fprintf(f, "%s|%d %d\n", keybuf, bd, bcap);
+            fclose(f);
+        }
+    }
+    return FMM_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -1282,10 +1354,10 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
     fmm_status st = check_common(h, n, x, y, gamma, u, v);
     if (st != FMM_OK)
         return st;
-    if (h->adaptive_cap)
-        return set_err(h, FMM_EINVAL, "autotune applies to the uniform tree (adaptive capacity is set)");
     if (depth_lo < 0 || depth_hi > FMM_MAXL || depth_lo > depth_hi)
         return set_err(h, FMM_EINVAL, "bad depth range");
+    if (h->adaptive_cap)
+        return autotune_adaptive(h, n, x, y, gamma, u, v, depth_lo, depth_hi);
     const char *cache = getenv("FMM2D_TUNE_CACHE");
     char keybuf[160];
     snprintf(keybuf, sizeof keybuf, "n=%lld p=%d mixed=%d sigma=%.17g lo=%d hi=%d", (long long)n, h->p, h->mixed,
@@ -1322,19 +1394,7 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    // median of 5 timed evaluations after 2 untimed ones; < 0 if an evaluation failed
-    auto time_eval = [&]() -> float {
-        float ts[5];
-        for (int r = 0; r < 7; ++r) {
-            if (cudaEventRecord(e0, h->stream) != cudaSuccess || fmm_velocity(h, n, x, y, gamma, u, v) != FMM_OK ||
-                cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
-                return -1.f;
-            if (r >= 2)
-                cudaEventElapsedTime(&ts[r - 2], e0, e1);
-        }
-        std::sort(ts, ts + 5);
-        return ts[2];
-    };
+    auto time_eval = [&]() -> float { return time_evaluation(h, n, x, y, gamma, u, v, e0, e1); };
     for (int d = depth_lo; d <= depth_hi; ++d) {
         for (int ti = 0; ti < ntile; ++ti) {
             h->depth = d;
@@ -1397,3 +1457,18 @@ const char *fmm_status_string(fmm_status s)
 const char *fmm_last_error(fmm_handle h) { return h ? h->err.c_str() : "no handle"; }
 
 }  // extern "C"
+
+static float time_evaluation(fmm_handle h, int64_t n, const double *x, const double *y, const double *g, double *u,
+                             double *v, cudaEvent_t e0, cudaEvent_t e1)
+{
+    float ts[5];
+    for (int r = 0; r < 7; ++r) {
+        if (cudaEventRecord(e0, h->stream) != cudaSuccess || fmm_velocity(h, n, x, y, g, u, v) != FMM_OK ||
+            cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+            return -1.f;
+        if (r >= 2)
+            cudaEventElapsedTime(&ts[r - 2], e0, e1);
+    }
+    std::sort(ts, ts + 5);
+    return ts[2];
+}

@@ -218,3 +218,16 @@ def test_adaptive_empty_and_single_particle(api, precision):
     u1, v1 = f.velocity(one(0.3), one(0.7), one(1.0))
     f.sync()
     assert float(u1.abs().max()) == 0.0 and float(v1.abs().max()) == 0.0
+
+
+def test_adaptive_autotune_picks_a_capacity(api):
+    """fmm_autotune on an adaptive handle keeps the fastest of the listed leaf capacities (and a maximum depth in
+    range), and the tuned handle still matches the oracle at the chosen parameters."""
+    x, y, g = fi.two_scale(20000, 39)
+    f = api.FMM(9, 12, 1e-3, precision="mixed", domain=(0.0, 0.0, 1.0), leaf_capacity=64)
+    tuned = f.autotune(dev(x), dev(y), dev(g), 8, 9)
+    assert tuned["leaf_capacity"] in (16, 24, 32, 48, 64, 96, 128) and 8 <= tuned["depth"] <= 9
+    u, v = f.velocity(dev(x), dev(y), dev(g))
+    f.sync()
+    ref = oracle.adaptive_fmm(x, y, g, 1e-3, tuned["depth"], tuned["leaf_capacity"], 12, domain=(0.0, 0.0, 1.0))
+    assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), ref) < TOL32

@@ -106,11 +106,12 @@ def whole_job(total_ms: float, steps: int, n_per_rank: int, world: int, dist=Non
     return ms_per_step, world * n_per_rank / (ms_per_step / 1e3) / 1e6
 
 
-def timed_steps(fn, steps: int, flush, stream, stage_times=None):
-    """Per-step device time (ms) with CUDA events on the launching stream; L2 flushed before each step."""
+def timed_steps(fn, steps: int, flush, stream, stage_times=None, stage_index: int = 1):
+    """Per-step device time (ms) with CUDA events on the launching stream; L2 flushed before each step. With
+    stage_times, also the handle's stage time number stage_index of every step (1: near field, 7: fork to join)."""
     import torch
 
-    ms, p2p = [], []
+    ms, stage = [], []
     for _ in range(steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -122,9 +123,43 @@ def timed_steps(fn, steps: int, flush, stream, stage_times=None):
         ms.append(e0.elapsed_time(e1))
         if stage_times is not None:
             t = stage_times()
-            if len(t) >= 2:
-                p2p.append(t[1])
-    return ms, p2p
+            if len(t) > stage_index:
+                stage.append(t[stage_index])
+    return ms, stage
+
+
+def overlap(f, x, y, g, u, v, flush, stream, nrep: int = 20, ms_full=None) -> dict:
+    """The paper's overlap claim (Fig. 1: the near field hides the sweep), measured on one handle in graph replays
+    (the handle's launch configuration), medians of nrep steps with L2 flushed before each:
+      sweep alone  = the sweep stream's fork-to-join span inside far-only replays (the handle's stage events are
+                     event nodes of the graph; stages 4-7, and L2P where it runs on that stream);
+      exposed      = T(full evaluation) - T(near-field-only evaluation);
+      hidden       = 1 - exposed / sweep alone.
+    A warm-up call precedes each series, so graph captures stay outside the timed steps."""
+    f.set_timing(True)
+    full = ms_full
+    if not full or len(full) < nrep:
+        f.velocity(x, y, g, u, v)
+        full = timed_steps(lambda: f.velocity(x, y, g, u, v), nrep, flush, stream)[0]
+    f.velocity_near(x, y, g, u, v)
+    near = timed_steps(lambda: f.velocity_near(x, y, g, u, v), nrep, flush, stream)[0]
+    f.velocity_far(x, y, g, u, v)
+    far, fork_join = timed_steps(lambda: f.velocity_far(x, y, g, u, v), nrep, flush, stream, f.stage_times, 7)
+    f.velocity(x, y, g, u, v)  # leave the full evaluation's graph in place
+    t_full, t_near, t_far = (statistics.median(a) for a in (full, near, far))
+    sweep = statistics.median(fork_join) if fork_join else None
+    exposed = max(t_full - t_near, 0.0)
+    return {"exposed_sweep_ms": exposed, "sweep_alone_ms": sweep,
+            "hidden_fraction": (max(0.0, 1.0 - exposed / sweep) if sweep else None),
+            "full_ms": t_full, "near_only_ms": t_near, "far_only_ms": t_far, "replays": nrep,
+            "timing": "graph replays, medians, L2 flushed; sweep alone = fork-to-join in far-only replays"}
+
+
+def arm_config(args, desc: str, world: int) -> dict:
+    """The workload both arms report (the reference arm times the oracle on the same workload and metric)."""
+    return {"workload": f"{args.workload}: {desc}", "precision": args.precision,
+            "l2": "flushed before every timed step (256 MiB write, outside the timed events)",
+            "graph": True, "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"}
 
 
 def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
@@ -182,9 +217,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64 (precision form)" if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; the paper uses no dataset)",
-           "config": {"workload": f"{args.workload}: {desc}", "precision": args.precision,
-                      "l2": "flushed before every timed step (256 MiB write, outside the timed events)",
-                      "graph": True, "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+           "config": arm_config(args, desc, world),
            "gpu_launches": int(launches), "clocks": clk,
            "p2p_tile": [tuned["p2p_threads"], tuned["p2p_targets_per_thread"]], "m2l_engine": tuned["m2l_engine"]}
     if rank != 0 and world > 1:
@@ -192,26 +225,16 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     if args.quick:
         return out
 
-    # exposed sweep: full evaluation minus the near-field-only evaluation (same launch configuration)
-    nrep = max(20, args.steps)  # medians of at least 20 graph replays
-    ms_near, _ = timed_steps(lambda: f.velocity_near(x, y, g, u, v), nrep, flush, stream)
-    ms_far, _ = timed_steps(lambda: f.velocity_far(x, y, g, u, v), nrep, flush, stream)
-    ms_full = ms if len(ms) >= 20 else timed_steps(step, nrep, flush, stream)[0]
-    t_full = statistics.median(ms_full)
-    t_near = statistics.median(ms_near)
-    t_far = statistics.median(ms_far)
+    # exposed sweep: full evaluation minus the near-field-only evaluation; the sweep alone from its fork-to-join
+    # span in far-only replays (same handle, same graph launch configuration)
+    ov = overlap(f, x, y, g, u, v, flush, stream, max(20, args.steps), ms_full=ms)
     f.set_graph(False)
     f.velocity(x, y, g, u, v)
     st = f.stage_times()  # [bin, near, up, m2l, l2l, combine, total, overlapped]
     f.set_graph(True)
-    sweep_alone = max(t_far - st[0] - st[5], 1e-6) if st else None
-    exposed = max(t_full - t_near, 0.0)
-    out["exposed_sweep_ms"] = exposed
-    out["sweep"] = {"full_ms": t_full, "near_only_ms": t_near, "far_only_ms": t_far,
-                    "sweep_alone_ms": sweep_alone,
-                    "hidden_fraction": None if not sweep_alone else max(0.0, 1.0 - exposed / sweep_alone),
-                    "stage_ms_eager": dict(zip(["binning", "near", "up", "m2l", "l2l", "l2p_sum", "total",
-                                                 "fork_to_join"], st))}
+    out["exposed_sweep_ms"] = ov["exposed_sweep_ms"]
+    ov["stage_ms_eager"] = dict(zip(["binning", "near", "up", "m2l", "l2l", "l2p_sum", "total", "fork_to_join"], st))
+    out["sweep"] = ov
 
     if args.precision == "mixed":
         out["m2l"] = m2l_leg(api, w, x, y, g, args.steps, flush, stream)
@@ -486,6 +509,8 @@ def adaptive_leg(api, w, x, y, g, u_uni, v_uni, precision, flush, stream, leaf_c
     for _ in range(3):
         f.velocity(x, y, g, u, v)
     ms, _ = timed_steps(lambda: f.velocity(x, y, g, u, v), 20, flush, stream)
+    u_s, v_s = torch.empty_like(x), torch.empty_like(x)
+    ov = overlap(f, x, y, g, u_s, v_s, flush, stream, 20, ms_full=ms)
     f.set_graph(False)
     f.set_timing(True)
     f.set_count_pairs(True)
@@ -509,7 +534,9 @@ def adaptive_leg(api, w, x, y, g, u_uni, v_uni, precision, flush, stream, leaf_c
     peak = FP32_PEAK_TFLOPS if precision == "mixed" else FP64_PEAK_TFLOPS
     out = {"leaf_capacity": leaf_capacity, "max_depth": max_depth, "precision": precision,
            "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s", "ms_per_step": t, "near_pairs": pairs,
-           "stage_ms_eager": dict(zip(["binning", "near", "up", "m2l", "l2l", "final", "total", "fork_to_join"], st)),
+           "sweep": ov, "exposed_sweep_ms": ov["exposed_sweep_ms"], "hidden_fraction": ov["hidden_fraction"],
+           "stage_ms_eager": dict(zip(["binning", "near", "up_lists_p2l_p2m_m2m", "down_l2l_m2l", "w_list_l2p",
+                                       "final", "total", "fork_to_join"], st)),
            "roofline_near": {"bound": "alu", "kernel": "k_ad_near32" if precision == "mixed" else "k_ad_near",
                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak if achieved else None,
@@ -547,6 +574,8 @@ def clustered_leg(api, precision, flush, stream, max_depth: int = 11, leaf_capac
     for _ in range(3):
         fu.velocity(x, y, g, uu, vu)
     msu, _ = timed_steps(lambda: fu.velocity(x, y, g, uu, vu), 10, flush, stream)
+    u_s, v_s = torch.empty_like(x), torch.empty_like(x)
+    ov_u = overlap(fu, x, y, g, u_s, v_s, flush, stream, 20)
     fu.close()
     fa = api.FMM(max_depth, w.p, w.sigma, precision=precision, domain=w.domain, graph=True,
                  leaf_capacity=leaf_capacity)
@@ -554,6 +583,8 @@ def clustered_leg(api, precision, flush, stream, max_depth: int = 11, leaf_capac
     for _ in range(3):
         fa.velocity(x, y, g, ua, va)
     msa, _ = timed_steps(lambda: fa.velocity(x, y, g, ua, va), 10, flush, stream)
+    ov_a = overlap(fa, x, y, g, u_s, v_s, flush, stream, 20)
+    fa.set_timing(False)
     # the autotuner's leaf capacity (maximum depth 11 kept) on a second handle
     ft = api.FMM(max_depth, w.p, w.sigma, precision=precision, domain=w.domain, graph=True, leaf_capacity=leaf_capacity)
     tuned_a = ft.autotune(x, y, g, max_depth, max_depth)
@@ -578,9 +609,13 @@ def clustered_leg(api, precision, flush, stream, max_depth: int = 11, leaf_capac
     return {"n": w.n, "p": w.p, "precision": precision,
             "uniform_tree": {"depth": w.depth, "value": w.n / (tu / 1e3) / 1e6, "unit": "Mparticles/s",
                              "ms_per_step": tu, "p2p_tile": [tuned["p2p_threads"], tuned["p2p_targets_per_thread"]],
-                             "m2l_engine": tuned["m2l_engine"]},
+                             "m2l_engine": tuned["m2l_engine"], "sweep": ov_u,
+                             "exposed_sweep_ms": ov_u["exposed_sweep_ms"],
+                             "hidden_fraction": ov_u["hidden_fraction"]},
             "adaptive_tree": {"max_depth": max_depth, "leaf_capacity": leaf_capacity,
                               "value": w.n / (ta / 1e3) / 1e6, "unit": "Mparticles/s", "ms_per_step": ta,
+                              "sweep": ov_a, "exposed_sweep_ms": ov_a["exposed_sweep_ms"],
+                              "hidden_fraction": ov_a["hidden_fraction"],
                               "e2e": {"value": w.n / te / 1e6, "unit": "Mparticles/s", "ms_per_step": te * 1e3,
                                       "h2d_bytes_per_step": 3 * 8 * w.n, "d2h_bytes_per_step": 2 * 8 * w.n},
                               "autotuned": {"leaf_capacity": tuned_a["leaf_capacity"],
@@ -632,7 +667,7 @@ def run_reference(args, rank: int, world: int) -> dict | None:
     t = None if full else fi.sample_targets(w.n, 4096)
     count = w.n if full else 4096
     steps = max(1, args.steps)
-    warm = max(0, min(args.warmup, 1))
+    warm = max(0, args.warmup)
     for _ in range(warm):
         oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, targets=t)
     times = []
@@ -646,9 +681,9 @@ def run_reference(args, rank: int, world: int) -> dict | None:
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mparticles/s", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; the paper uses no dataset)",
-            "config": {"workload": f"{args.workload}: {desc}", "precision": "fp64 (CPU oracle)"},
+            "config": arm_config(args, desc, world),
             "cpu_baseline": {"value": value, "unit": "Mparticles/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "precision": "fp64 (the CPU oracle)"},
             "e2e": {"value": value, "unit": "Mparticles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -12,7 +12,8 @@
  *   3 interaction lists (implicit on the uniform tree)     4 P2M  5 M2M  6 M2L  7 L2L  8 L2P
  *   9 near-field direct sum (P2P)                          10 sum of near and far parts
  * Stage 9 runs on the caller's stream while stages 4-7 run concurrently on a second, high-priority stream
- * (Fig. 1: no dependency between {4,5,6,7} and {9}); stage 8 is fused into stage 10 after the join.
+ * (Fig. 1: no dependency between {4,5,6,7} and {9}). Stage 8 runs on that second stream too in the precision
+ * form (the far field is ready at the join); in the plain FP64 form it is fused into stage 10 after the join.
  *
  * Conventions for every call:
  *   - Array arguments of fmm_velocity*, fmm_velocity_adjoint and fmm_velocity_batched are DEVICE pointers
@@ -84,12 +85,12 @@ fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level);
 
 /* Where the FP32 levels of M2L (Fig. 1 stage 6, the translation b_l of §3) run in the precision form; both
  * use the factored radius-scaled form b_l = rho^(l+1) sum_m (-1)^(m+1) C(m+l, m) rho^m a_m, rho = 1/delta.
- * FMM_M2L_TENSOR (default): per interaction offset, the gathered multipoles of 128 target boxes (scaled by
+ * FMM_M2L_TENSOR: per interaction offset, the gathered multipoles of 128 target boxes (scaled by
  * rho^m) times the signed binomial matrix, which all offsets and levels share, as a dense GEMM on the tensor
  * cores (tcgen05, 3xTF32: every operand split into two TF32 parts, accumulators in tensor memory, each
  * offset's product read back, scaled by rho^(l+1) and summed in FP32).
- * FMM_M2L_CUDA_CORES: one lane per (target, source) pair in FP32 on the CUDA cores. Both agree with the
- * FP64 form to a few 1e-7 relative.
+ * FMM_M2L_CUDA_CORES (default): one lane per (target, source) pair in FP32 on the CUDA cores. Both agree with
+ * the FP64 form to a few 1e-7 relative. fmm_autotune times both and keeps the faster.
  * FP64 levels (the plain form, levels <= coarse_level) and the adjoint always use FP64 CUDA-core kernels.
  * Returns FMM_EINVAL for any other value. */
 #define FMM_M2L_CUDA_CORES 0
@@ -107,9 +108,12 @@ int fmm_get_m2l_engine(fmm_handle h);
  * (U), M2L between same-level boxes whose parents are adjacent (V), multipoles of small boxes evaluated at the
  * particles of a larger adjacent-parent leaf (W) and the particles of a coarse leaf expanded into a small
  * box's local expansion (X). So the sum is Eq. 7 with K_sigma between adjacent leaves and the point-vortex
- * kernel elsewhere, as on the uniform tree. The adaptive evaluation computes in FP64 whatever the precision
- * setting, serves fmm_velocity, fmm_velocity_near / _far, fmm_velocity_host and fmm_advect, and counts the
- * ordered pairs of its U lists when pair counting is on; fmm_autotune then picks the leaf capacity (and the
+ * kernel elsewhere, as on the uniform tree. The adaptive evaluation has both forms: FMM_FP64 computes every
+ * stage in FP64; FMM_MIXED keeps FP64 binning and sorted coordinates, evaluates the U-list pairs in FP32 on
+ * split (hi + lo) coordinates (FP32 sums per source leaf, FP64 across leaves), and keeps the multipole and
+ * local expansions (P2M, M2M, M2L, L2L, P2L, W-list and L2P evaluations) in FP32. It serves fmm_velocity,
+ * fmm_velocity_near / _far, fmm_velocity_host and fmm_advect, and counts the ordered pairs of its U lists
+ * when pair counting is on; fmm_autotune then picks the leaf capacity (and the
  * maximum depth within its range); fmm_velocity_batched and fmm_velocity_adjoint return FMM_EINVAL while it is set.
  * Returns FMM_EINVAL for NULL or a negative capacity. */
 fmm_status fmm_set_adaptive(fmm_handle h, int leaf_capacity);
@@ -196,11 +200,15 @@ fmm_status fmm_advect(fmm_handle h, int64_t n, double *x, double *y, const doubl
 /* Waits for all work of the handle and returns the first device-side error since the last check. */
 fmm_status fmm_sync(fmm_handle h);
 
-/* Per-stage device times (ms) of the last evaluation when timing is on (fmm_set_timing(h, 1); not with
- * graphs): out[0] binning, [1] near field, [2] up sweep (P2M+M2M), [3] M2L, [4] L2L (and L2P in the
- * precision form, which evaluates the far field on the sweep stream), [5] the final sum and scatter to input
- * order (with L2P in the plain form), [6] whole evaluation, [7] near field and sweep overlapped (from the fork
- * to the join). Returns the number of values written (at most cap). */
+/* Per-stage device times (ms) of the last evaluation when timing is on (fmm_set_timing(h, 1)); with graphs
+ * (fmm_set_graph) the events are nodes of the graph, so every replay records them. Uniform tree: out[0]
+ * binning, [1] near field, [2] up sweep (P2M+M2M), [3] M2L, [4] L2L (and L2P in the precision form, which
+ * evaluates the far field on the sweep stream), [5] the final sum and scatter to input order (with L2P in the
+ * plain form), [6] whole evaluation, [7] from the fork to the join (near field and sweep overlapped; in a
+ * far-only evaluation the sweep alone). Adaptive tree: [0] binning, [1] from the fork to the end of the walk
+ * (U, W, L2P) that follows the sweep, [2] box lists + P2L + P2M + M2M, [3] the downward L2L + M2L levels,
+ * [5] the walk, [6] whole evaluation, [7] the sweep (fork to join). Stages an evaluation does not run read 0.
+ * Returns the number of values written (at most cap). */
 fmm_status fmm_set_timing(fmm_handle h, int enable);
 int fmm_stage_times(fmm_handle h, float *out, int cap);
 

@@ -40,10 +40,10 @@ class FMM:
     """One FMM configuration: tree depth L (4^L leaves), p expansion terms, blob core sigma.
 
     precision: "fp64" (plain form) or "mixed" (precision form). domain: (x0, y0, side) or None for the
-    bounding-box rule. graph: capture and replay the evaluation as a CUDA graph. m2l_engine: "tensor"
-    (tcgen05, default) or "cuda_cores" for the FP32 M2L levels of the precision form. leaf_capacity: 0 for the
+    bounding-box rule. graph: capture and replay the evaluation as a CUDA graph. m2l_engine: "cuda_cores"
+    (default) or "tensor" (tcgen05) for the FP32 M2L levels of the precision form. leaf_capacity: 0 for the
     uniform tree; B > 0 for the adaptive tree (depth is then its maximum depth; boxes holding more than B
-    particles are split; computed in FP64).
+    particles are split; both precision forms, FP32 expansions and near field in the precision form).
     """
 
     def __init__(self, depth: int, p: int, sigma: float, precision: str = "fp64", domain=None,

@@ -52,7 +52,7 @@ struct fmm_ctx {
     double dom[3] = {0, 0, 1};
     int mixed = 0;
     int coarse = -1;  // precision form: FP32 on every level (radius-scaled translations stay bounded)
-    int m2l_engine = FMM_M2L_TENSOR;
+    int m2l_engine = FMM_M2L_CUDA_CORES;  // the faster engine at the measured configurations; fmm_autotune re-times both
     int adaptive_cap = 0;  // > 0: adaptive tree (depth = maximum depth), split boxes holding more particles
     cudaStream_t stream = nullptr;  // caller's stream
     cudaStream_t exec = nullptr;    // internal stream used for graph capture / replay
@@ -485,15 +485,19 @@ static cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s)
                                                                                 : cudaEventRecordDefault);
 }
 
-// The adaptive tree: the same binning (Morton keys at the maximum depth), the multipole sweep on the side
-// stream concurrent with the near field over the U lists, then the final kernel (adaptive.cu).
+// The adaptive tree: the same binning (Morton keys at the maximum depth), the multipole sweep on the side stream
+// (box lists, P2L, P2M, M2M, then the downward L2L + M2L levels), then after the join one walk per target that
+// evaluates the U-list pairs, the W-list multipoles and the leaf's local and writes the sum in the caller's order
+// (adaptive.cu). Running the U-list pairs at the fork instead, concurrently with the sweep, with the W list and
+// L2P in a second walk on the sweep stream, was measured slower on GB300: both halves keep every SM's issue slots
+// busy, so they add up, and the second walk costs what it walks.
 static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const double *x, const double *y,
                                    const double *g, double *u, double *v)
 {
     Work &w = h->w;
-    bool far = mode != MODE_NEAR && w.maxdepth >= 1;
-    bool near = mode != MODE_FAR;
-    bool timed = h->timing != 0;
+    const bool near = mode != MODE_FAR;
+    const bool sweep = mode != MODE_NEAR && w.maxdepth >= 2;  // below depth 2 every pair is in a U list
+    const bool timed = h->timing != 0;
     int64_t nl = 0;
     (void)cudaGetLastError();
     if (timed)
@@ -506,22 +510,28 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     nl += launch_scan(w, s);
     nl += launch_scatter_sort(w, s);
     nl += launch_gather(w, x, y, g, nullptr, nullptr, s);
-    if (timed)
-        CU(record_timing(h->ev_t[1], s));
-    const bool sweep = far && w.maxdepth >= 2;
-    if (sweep) {
-        CU(cudaMemsetAsync(w.ad_cnt, 0, (FMM_MAXL + 2) * sizeof(int), s));
-        CU(cudaEventRecord(h->ev_fork, s));
-        CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        nl += launch_adaptive_up(w, h->t, h->side);
-        nl += launch_adaptive_down(w, h->t, h->side);
-        CU(cudaEventRecord(h->ev_join, h->side));
-    }
     const bool count = near && h->count_pairs;
     if (count)
         CU(cudaMemsetAsync(w.pair_count, 0, sizeof(unsigned long long), s));
-    if (sweep)  // the walk reads the W multipoles and the leaf's local expansion
+    if (sweep)
+        CU(cudaMemsetAsync(w.ad_cnt, 0, (FMM_MAXL + 2) * sizeof(int), s));
+    if (timed)
+        CU(record_timing(h->ev_t[1], s));
+    if (sweep) {
+        CU(cudaEventRecord(h->ev_fork, s));
+        CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        nl += launch_adaptive_up(w, h->t, h->side);
+        if (timed)
+            CU(record_timing(h->ev_t[2], h->side));
+        nl += launch_adaptive_down(w, h->t, h->side);
+        if (timed)
+            CU(record_timing(h->ev_t[3], h->side));
+        CU(cudaEventRecord(h->ev_join, h->side));
         CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+    }
+    if (timed)
+        CU(record_timing(h->ev_t[6], s));
+    // the walk reads the W multipoles and the leaf's local expansion
     nl += launch_adaptive_near(w, count ? w.pair_count : nullptr, near ? 1 : 0, sweep ? 1 : 0, u, v, s);
     if (timed)
         CU(record_timing(h->ev_t[5], s));
@@ -533,7 +543,8 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     CU(cudaGetLastError());
     h->launches += nl;
     h->last_timed = timed;
-    h->timed_mask = timed ? 0xa3u : 0u;  // binning, near-field walk (after the sweep when far), total
+    // recorded: binning (0-1), sweep (1-2 up, 2-3 down; 1-6 fork to join), the walk (6-5), total (0-7)
+    h->timed_mask = timed ? (sweep ? 0xefu : 0xe3u) : 0u;
     return FMM_OK;
 }
 

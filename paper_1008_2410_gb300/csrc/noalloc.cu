@@ -182,7 +182,7 @@ extern "C" fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, 
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return FMM_ECUDA;
     unsigned char *base;
-    bool fresh_tables;
+    Tables t{};
     {
         std::lock_guard<std::mutex> lk(g_mu);
         DeviceState &ds = g_dev[dev];
@@ -193,13 +193,16 @@ extern "C" fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, 
             ds.base = (unsigned char *)ptr;
         }
         base = ds.base;
-        fresh_tables = ds.tables_p != p;
-        ds.tables_p = p;
+        carve_tables(base, t);
+        if (ds.tables_p != p) {
+            // the tables are marked as holding p only once the upload has completed; a failed upload leaves
+            // them marked stale, so the next call uploads again
+            ds.tables_p = -1;
+            if (upload_tables(t, p, s) != FMM_OK)
+                return FMM_ECUDA;
+            ds.tables_p = p;
+        }
     }
-    Tables t{};
-    carve_tables(base, t);
-    if (fresh_tables && upload_tables(t, p, s) != FMM_OK)
-        return FMM_ECUDA;
     if (upload_m2l_constants(s) != 0)  // constant memory of the module, once per device (no allocation)
         return FMM_ECUDA;
     if (prepare_m2l_tc() != 0)  // kernel attributes, once per device
@@ -208,7 +211,7 @@ extern "C" fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, 
     unsigned char *h = base + tab;
     Work w{};
     carve_work(h + hdr, w, n, tree_depth, p, mixed);
-    w.m2l_tc = 1;  // the defaults of a handle
+    w.m2l_tc = 0;  // the default of a handle: FP32 M2L levels on the CUDA cores
     w.status = (unsigned int *)(h + hdr_status);
     w.pair_count = (unsigned long long *)(h + hdr_status + 32);
     w.minmax = (unsigned long long *)(h + hdr_minmax);

@@ -306,10 +306,95 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
     }
 }
 
+// The remainder of a pass: r targets spread over the warp's 64 slots (slot s = lane + 32 h, h = 0, 1, one half of
+// a packed pair each). Slot s takes target s mod r and the sources j0 + s / r + G k, k = 0, 1, ... (G = 64 / r
+// source groups), so a few leftover targets keep every lane busy for 1/G of the sources instead of all lanes
+// busy for all of them; slots s >= G r carry zero charge. One-float coordinates only (not the split form).
+// The slot geometry is recomputed per call (it is cheap) so that nothing of it stays live across the tile loop.
+struct RemSlots {
+    int e[2], g[2];  // per half: target position in leaf order, source group
+    bool a[2];       // per half: slot in use
+    int G;
+    __device__ __forceinline__ RemSlots(int rbase, int r)
+    {
+        const int lane = threadIdx.x & 31;
+        G = 64 / r;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int sl = lane + 32 * h;
+            a[h] = sl < G * r;
+            e[h] = rbase + (a[h] ? sl % r : 0);
+            g[h] = a[h] ? sl / r : 0;
+        }
+    }
+};
+
+template <bool SELF>
+__device__ __forceinline__ void p2p_segment_rem(const Work &w, const float4 *__restrict__ EH,
+                                                const float4 *__restrict__ EG, int j0, int j1, float sdx, float sdy,
+                                                int rbase, int r, f2 &PU, f2 &PV)
+{
+    const RemSlots R(rbase, r);
+    float hx[2], hy[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float4 th = w.eh[R.e[h]], tl = w.el[R.e[h]];
+        const float ax = th.x - sdx, ay = th.z - sdy;
+        hx[h] = ax + (tl.x + (th.x - (ax + sdx)));
+        hy[h] = ay + (tl.z + (th.z - (ay + sdy)));
+    }
+    const f2 AX = pk2(hx[0], hx[1]), AY = pk2(hy[0], hy[1]);
+    const int G = R.G;
+    for (int b = j0; b < j1; b += G) {
+        const int ja = b + R.g[0], jb = b + R.g[1];
+        const bool va = R.a[0] && ja < j1, vb = R.a[1] && jb < j1;
+        const float4 ha = EH[va ? ja : j0], hb = EH[vb ? jb : j0];
+        const float ga = va ? EG[ja].x : 0.f, gb = vb ? EG[jb].x : 0.f;
+        const f2 dx = sub2(AX, pk2(ha.x, hb.x)), dy = sub2(AY, pk2(ha.z, hb.z));
+        const f2 r2 = fma2(dx, dx, mul2(dy, dy));
+        float ra, rb;
+        up2(r2, ra, rb);
+        const float ea = ex2_approx(-ra), eb = ex2_approx(-rb);
+        f2 q;
+        float rmin;
+        if (SELF) {
+            q = pk2(rcp_approx(fmaxf(ra, 1e-30f)), rcp_approx(fmaxf(rb, 1e-30f)));
+            rmin = __uint_as_float(min(__float_as_uint(ra) - 1u, __float_as_uint(rb) - 1u));
+        } else {
+            q = pk2(rcp_approx(ra), rcp_approx(rb));
+            rmin = fminf(ra, rb);
+        }
+        f2 og = fma2(pk2(ea, eb), pk2(-ga, -gb), pk2(ga, gb));  // g (1 - e)
+        if (__any_sync(0xffffffffu, SELF ? (__float_as_uint(rmin) < __float_as_uint(P2P_THR)) : (rmin < P2P_THR))) {
+            float qa, qb, oa, ob;
+            up2(q, qa, qb);
+            up2(og, oa, ob);
+            if (ra < P2P_THR) {
+                qa = P2P_LN2 * small_y_factor10(P2P_LN2 * ra);
+                oa = ga;
+            }
+            if (rb < P2P_THR) {
+                qb = P2P_LN2 * small_y_factor10(P2P_LN2 * rb);
+                ob = gb;
+            }
+            q = pk2(qa, qb);
+            og = pk2(oa, ob);
+        }
+        const f2 gf = mul2(og, q);
+        PU = fma2(dy, gf, PU);  // u accumulates -dy g f: negated at the end
+        PV = fma2(dx, gf, PV);
+    }
+}
+
 // LPB leaves per block (1 or 2, one warp each; with 2 the leaves are the pair (2j, 2j+1) of one row and share
-// their 3 x 4 source neighbourhood). Each warp takes its leaf's targets in passes of at most 32 * ktmax, with
-// 2 or 4 targets per lane chosen by the pass size. Sources arrive by bulk copies into shared memory; each
-// target's sum over one tile (plain FP32) is added to its total with an error-free TwoSum.
+// their 3 x 4 source neighbourhood). Each warp takes its leaf's targets in passes of at most 32 * ktmax. With
+// ktmax = 4 (one-float coordinates) the passes hold 128 targets, four per lane, except the last: from 97 targets
+// on it is the same, otherwise a main group of up to 64 targets, two per lane, every lane meeting the same source,
+// plus the rest (r <= 32 after a full main group, or a whole pass of r <= 32) spread over the 64 slots with
+// G = 64 / r source groups (p2p_segment_rem); the G partial sums of each remainder target are added at the end.
+// With ktmax = 2, or in the split form, a pass holds at most 64 targets, two per lane. Sources arrive by bulk
+// copies into shared memory; each slot's sum over one tile (plain FP32) is added to its total with an error-free
+// TwoSum.
 template <int LPB>
 __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, int ktmax, int skip_plain)
 {
@@ -329,7 +414,8 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
     const bool split = d.s_unit > P2P_SPLIT_S;  // block-uniform; the split form runs 2 targets per lane
     if (skip_plain && !split)
         return;  // this system's near field is the symmetric kernel's
-    const int per_pass = 32 * (split ? 2 : ktmax);
+    const bool rem_form = !split && ktmax == 4;
+    const int per_pass = rem_form ? 128 : 64;
     int npass = (my_c + per_pass - 1) / per_pass;
     if (LPB == 2) {
         const int other = first + (warp ^ 1);
@@ -350,11 +436,21 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
     for (int pass = 0; pass < npass; ++pass) {
         int t_lo = 0, t_cnt = 0;
         if (pass < my_np) {
-            t_lo = (int)((int64_t)pass * my_c / my_np);
-            t_cnt = (int)((int64_t)(pass + 1) * my_c / my_np) - t_lo;
+            if (rem_form) {  // full passes of 128, the rest in the last
+                t_lo = 128 * pass;
+                t_cnt = min(128, my_c - t_lo);
+            } else {  // balanced passes
+                t_lo = (int)((int64_t)pass * my_c / my_np);
+                t_cnt = (int)((int64_t)(pass + 1) * my_c / my_np) - t_lo;
+            }
         }
-        const int kt = t_cnt == 0 ? 0 : (t_cnt <= 64 ? 2 : 4);
         const int tbase = my_s0 + t_lo;
+        // layout of the pass: more than 96 targets, four per lane (two packed pairs, broadcast sources); else a
+        // main group of up to 64, two per lane, and a remainder of at most 32 over the slots (source groups); a
+        // pass of 33..63 targets is all main group, one of at most 32 all remainder
+        const bool kt4 = rem_form && t_cnt > 96;
+        const int n_main = !rem_form || kt4 ? t_cnt : (t_cnt >= 64 ? 64 : (t_cnt > 32 ? t_cnt : 0));
+        const int r = t_cnt - n_main;
         f2 SU[2] = {0ull, 0ull}, CU[2] = {0ull, 0ull}, SV[2] = {0ull, 0ull}, CV[2] = {0ull, 0ull};
         for (int dyr = -1; dyr <= 1; ++dyr) {
             const int row = iy + dyr;
@@ -384,7 +480,7 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
                     return;
                 }
                 phase ^= 1;
-                if (kt == 0)
+                if (t_cnt == 0)
                     continue;
 #pragma unroll
                 for (int k3 = 0; k3 < 3; ++k3) {
@@ -397,26 +493,32 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
                         continue;
                     const float sdx = (float)(k3 - 1) * s, sdy = (float)dyr * s;
                     const bool self = k3 == 1 && dyr == 0;
-#define P2P_SEG(KT, SELF, SPLIT) p2p_segment<KT, SELF, SPLIT>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, t_cnt, PU, PV)
-                    if (split) {
+#define P2P_SEG(SELF, SPLIT) p2p_segment<2, SELF, SPLIT>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV)
+                    if (kt4) {
                         if (self)
-                            P2P_SEG(2, true, true);
+                            p2p_segment<4, true, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV);
                         else
-                            P2P_SEG(2, false, true);
-                    } else {
-                        if (kt == 2) {
+                            p2p_segment<4, false, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV);
+                    } else if (n_main > 0) {
+                        if (split) {
                             if (self)
-                                P2P_SEG(2, true, false);
+                                P2P_SEG(true, true);
                             else
-                                P2P_SEG(2, false, false);
+                                P2P_SEG(false, true);
                         } else {
                             if (self)
-                                P2P_SEG(4, true, false);
+                                P2P_SEG(true, false);
                             else
-                                P2P_SEG(4, false, false);
+                                P2P_SEG(false, false);
                         }
                     }
 #undef P2P_SEG
+                    if (r > 0) {
+                        if (self)
+                            p2p_segment_rem<true>(w, EH, EG, j0, j1, sdx, sdy, tbase + n_main, r, PU[1], PV[1]);
+                        else
+                            p2p_segment_rem<false>(w, EH, EG, j0, j1, sdx, sdy, tbase + n_main, r, PU[1], PV[1]);
+                    }
                 }
                 // compensated totals: plain FP32 sums cover at most one tile of sources
 #pragma unroll
@@ -429,8 +531,11 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
             }
         }
         const float snear = d.snear;
+        float2 *dst = w.p2p_rows ? w.nearp + (int64_t)blockIdx.y * w.n : w.near32;  // rows: one row's part
 #pragma unroll
-        for (int pr = 0; pr < 2; ++pr) {
+        for (int pr = 0; pr < 2; ++pr) {  // main group: targets lane + 32 (2 pr + h); pr = 1 only with kt4
+            if (pr == 1 && !kt4)
+                break;
             float su[2], cu[2], sv[2], cv[2];
             up2(SU[pr], su[0], su[1]);
             up2(CU[pr], cu[0], cu[1]);
@@ -439,15 +544,36 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int e = lane + 32 * (2 * pr + h);
-                if (e < t_cnt)
-                {
-                    const float2 r = make_float2(-(su[h] + cu[h]) * snear, (sv[h] + cv[h]) * snear);
-                    if (w.p2p_rows)  // one row's part, summed by the final kernel
-                        w.nearp[(int64_t)blockIdx.y * w.n + tbase + e] = r;
-                    else
-                        w.near32[tbase + e] = r;
+                if (e < n_main)
+                    dst[tbase + e] = make_float2(-(su[h] + cu[h]) * snear, (sv[h] + cv[h]) * snear);
+            }
+        }
+        // remainder: the G partial sums of each target (slots t, t + r, ..., t + (G - 1) r), added in FP64 through
+        // this warp's part of the (now idle) source tile
+        if (__syncthreads_or(r > 0)) {
+            float2 *red = reinterpret_cast<float2 *>(EH) + 64 * warp;
+            if (r > 0) {
+                float su[2], cu[2], sv[2], cv[2];
+                up2(SU[1], su[0], su[1]);
+                up2(CU[1], cu[0], cu[1]);
+                up2(SV[1], sv[0], sv[1]);
+                up2(CV[1], cv[0], cv[1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    red[lane + 32 * h] = make_float2(su[h] + cu[h], sv[h] + cv[h]);
+                __syncwarp();
+                const int G = 64 / r;
+                for (int t = lane; t < r; t += 32) {
+                    double au = 0.0, av = 0.0;
+                    for (int gq = 0; gq < G; ++gq) {
+                        const float2 part = red[t + gq * r];
+                        au += (double)part.x;
+                        av += (double)part.y;
+                    }
+                    dst[tbase + n_main + t] = make_float2(-(float)au * snear, (float)av * snear);
                 }
             }
+            __syncthreads();  // the tile is free again before the next pass copies into it
         }
     }
 }

@@ -4,7 +4,8 @@ T = a N/P + b log_4 P + c N/(B P) + d N B/P (the Greengard-Gropp form used in §
   a = 16t - 15,  b = (84 - 48t + 571t^2)/3,  c = (128 - 48t + 844t^2)/3,  d = 198      (Table 1)
   B_opt = sqrt(c/d)                                                                    (§4)
   full overlap of the root-tree bottleneck by near-field work:  B >= (b/d) P L_root / N (§4)
-Used to report algorithmic work next to measured times and to seed the autotuner's leaf occupancy.
+Used to report algorithmic work and the overlap bound next to measured times (the bench reports B_opt and the
+minimum leaf occupancy for overlap beside the occupancy it runs).
 """
 from __future__ import annotations
 

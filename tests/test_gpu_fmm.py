@@ -373,6 +373,33 @@ def test_stage_times_launch_count_and_autotune(lib):
     assert prm["m2l_engine"] in ("tensor", "cuda_cores")
 
 
+@pytest.mark.parametrize("leaf_capacity", [0, 24])
+def test_default_engine_and_stage_events_in_graph_replays(lib, leaf_capacity):
+    """A fresh handle runs the FP32 M2L levels on the CUDA cores; with graphs on, the stage events are graph nodes,
+    so a far-only replay reports its fork-to-join span (the sweep alone) and a near-only replay none of it."""
+    w = fi.clustered(30000, depth=6, p=12) if leaf_capacity else fi.uniform(50000, seed_index=48, depth=5, p=12)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain, graph=True, leaf_capacity=leaf_capacity)
+    assert f.params()["m2l_engine"] == "cuda_cores"
+    f.set_timing(True)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    u, v = torch.empty_like(x), torch.empty_like(x)
+    for _ in range(2):  # capture, then replay
+        f.velocity_far(x, y, g, u, v)
+    t = f.stage_times()
+    assert len(t) == 8 and t[7] > 0 and t[6] >= t[7]
+    if not leaf_capacity:  # uniform tree: no near-field kernel between the fork and the join's event nodes
+        assert t[1] < 0.5 * t[7]
+    for _ in range(2):
+        f.velocity_near(x, y, g, u, v)
+    t = f.stage_times()
+    assert len(t) == 8 and t[1] > 0 and t[2] == 0 and t[3] == 0
+    for _ in range(2):
+        f.velocity(x, y, g, u, v)
+    t = f.stage_times()
+    assert all(t[k] > 0 for k in ((0, 1, 2, 3, 6, 7) if leaf_capacity else (0, 1, 2, 3, 4, 6, 7)))
+    f.sync()
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("precision,graph", [("mixed", True), ("fp64", True)])
 def test_uniform_1m_sampled_parity(lib, oracle, precision, graph):

@@ -104,3 +104,15 @@ def test_suggested_depth_removes_the_far_field_tail(oracle):
         errs[depth] = float(np.linalg.norm(np.concatenate([u - ud, v - vd])) / np.linalg.norm(np.concatenate([ud, vd])))
     assert errs[4] > 1e-7  # tail-limited: 1.34e-7 whatever p (measured at p = 20 and 30)
     assert errs[d] < 1e-12
+
+
+def test_default_m2l_engine_is_the_cuda_core_kernel():
+    """Until the tensor-core M2L wins at the measured configurations, a handle that is not autotuned runs the FP32
+    M2L levels on the CUDA cores: the header documents it and the handle's initialiser sets it."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = open(os.path.join(root, "include", "fmm2d.h")).read()
+    assert "FMM_M2L_CUDA_CORES (default)" in hdr and "FMM_M2L_TENSOR (default)" not in hdr
+    src = open(os.path.join(root, "paper_1008_2410_gb300", "csrc", "capi.cu")).read()
+    assert "int m2l_engine = FMM_M2L_CUDA_CORES;" in src
+    na = open(os.path.join(root, "paper_1008_2410_gb300", "csrc", "noalloc.cu")).read()
+    assert "w.m2l_tc = 0;" in na

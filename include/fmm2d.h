@@ -200,6 +200,14 @@ fmm_status fmm_advect(fmm_handle h, int64_t n, double *x, double *y, const doubl
 /* Waits for all work of the handle and returns the first device-side error since the last check. */
 fmm_status fmm_sync(fmm_handle h);
 
+/* Test of the device-side timeout path (the paper has no counterpart; it checks this library's failure
+ * reporting). Launches, on the handle's stream, one thread that waits with the library's bounded mbarrier wait on
+ * a barrier that nothing arrives on and no copy targets, giving up after `polls` polls (1 .. 2^20; each poll may
+ * suspend the thread for a short hardware-defined time). The wait runs out, the status word gets the timeout bit,
+ * and the next fmm_sync (or call on the handle) returns FMM_ETIMEOUT; the handle stays usable afterwards.
+ * FMM_EINVAL for polls outside the range. */
+fmm_status fmm_selftest_timeout(fmm_handle h, int polls);
+
 /* Per-stage device times (ms) of the last evaluation when timing is on (fmm_set_timing(h, 1)); with graphs
  * (fmm_set_graph) the events are nodes of the graph, so every replay records them. Uniform tree: out[0]
  * binning, [1] near field, [2] up sweep (P2M+M2M), [3] M2L, [4] L2L (and L2P in the precision form, which
@@ -232,6 +240,17 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
                         double *u, double *v, int depth_lo, int depth_hi);
 fmm_status fmm_get_params(fmm_handle h, int *tree_depth, int *p, double *sigma, int *p2p_threads,
                           int *p2p_targets_per_thread);
+
+/* Picks the expansion order for an accuracy target (§3: the t-term expansions' truncation error falls
+ * geometrically with t): evaluates the given particles (device arrays, left unchanged) once in the plain FP64
+ * form at p = 32 as the reference, then in the handle's own form and tree at p = p_lo, p_lo + 1, ... and keeps
+ * the first p whose result is within rel_tol of the reference in relative L2 over all particles (in the
+ * precision form the FP32 rounding, a few 1e-7, is part of that error). Sets the handle's p (p_hi if no p in
+ * [p_lo, p_hi] meets rel_tol) and writes the error of the chosen p to *achieved (may be NULL). Allocates and
+ * frees 4 n doubles of device scratch; synchronises the handle's stream. FMM_EINVAL unless
+ * 1 <= p_lo <= p_hi <= 32 and rel_tol > 0. */
+fmm_status fmm_autotune_p(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                          double rel_tol, int p_lo, int p_hi, double *achieved);
 
 /* Measured throughput of the units the kernels are bound by, on the current device (a few hundred ms):
  * out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA TFLOP/s, out[2] SFU ex2+rcp results per second / 1e12,

@@ -49,12 +49,14 @@ SIGNATURES = {
     "fmm_velocity_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fmm_advect": (_I, [_P, _I64, _P, _P, _P, _D, _I, _I]),
     "fmm_sync": (_I, [_P]),
+    "fmm_selftest_timeout": (_I, [_P, _I]),
     "fmm_set_timing": (_I, [_P, _I]),
     "fmm_stage_times": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
     "fmm_set_count_pairs": (_I, [_P, _I]),
     "fmm_last_pair_count": (_I64, [_P]),
     "fmm_kernel_launches": (_I64, [_P]),
     "fmm_autotune": (_I, [_P, _I64, _P, _P, _P, _P, _P, _I, _I]),
+    "fmm_autotune_p": (_I, [_P, _I64, _P, _P, _P, _D, _I, _I, ctypes.POINTER(_D)]),
     "fmm_get_params": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I),
                             ctypes.POINTER(_I)]),
     "fmm_probe_peaks": (_I, [ctypes.POINTER(_D), _I]),

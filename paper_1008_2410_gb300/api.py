@@ -205,9 +205,24 @@ class FMM:
                                      _dev(u, "u"), _dev(v, "v"), int(depth_lo), int(depth_hi)), self.h)
         return self.params()
 
+    def autotune_p(self, x, y, gamma, rel_tol: float, p_lo: int = 1, p_hi: int = 32) -> tuple[int, float]:
+        """Smallest p in [p_lo, p_hi] within rel_tol (relative L2) of the FP64 form at p = 32; sets the handle's p
+        and returns (p, estimated error)."""
+        err = ctypes.c_double()
+        self._stream()
+        check(self._lib.fmm_autotune_p(self.h, x.numel(), _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"),
+                                       float(rel_tol), int(p_lo), int(p_hi), ctypes.byref(err)), self.h)
+        return self.params()["p"], err.value
+
     # -- diagnostics
     def sync(self) -> None:
         check(self._lib.fmm_sync(self.h), self.h)
+
+    def selftest_timeout(self, polls: int = 4096) -> None:
+        """Runs the library's bounded device wait on a barrier nothing completes (see fmm_selftest_timeout); the
+        next sync() raises FMMError with status FMM_ETIMEOUT."""
+        self._stream()
+        check(self._lib.fmm_selftest_timeout(self.h, int(polls)), self.h)
 
     def stage_times(self) -> list[float]:
         buf = (ctypes.c_float * 8)()

@@ -159,7 +159,7 @@ static fmm_status poll_status(fmm_handle h, bool block)
     unsigned int st = *h->h_status;
     if (st) {
         *h->h_status = 0;
-        CU(cudaMemsetAsync(h->w.status, 0, sizeof(unsigned int), h->stream));
+        CU(cudaMemsetAsync(h->hdr, 0, sizeof(unsigned int), h->stream));  // the status word heads the header
         fmm_status s = device_status_to_fmm(st);
         const char *what = s == FMM_EINVAL     ? "a particle lies outside the root square or is not finite"
                            : s == FMM_ETIMEOUT ? "a bounded wait for a shared-memory copy ran out"
@@ -798,6 +798,38 @@ static fmm_status autotune_adaptive(fmm_handle h, int64_t n, const double *x, co
     return FMM_OK;
 }
 
+// Sum of (u - ur)^2 + (v - vr)^2 and of ur^2 + vr^2 over all particles (FP64, one atomic per block and sum).
+__global__ void __launch_bounds__(256) k_rel_l2_parts(int64_t n, const double *__restrict__ u,
+                                                      const double *__restrict__ v, const double *__restrict__ ur,
+                                                      const double *__restrict__ vr, double *out)
+{
+    __shared__ double sd[8], sr[8];
+    double d = 0.0, r = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double du = u[i] - ur[i], dv = v[i] - vr[i];
+        d += du * du + dv * dv;
+        r += ur[i] * ur[i] + vr[i] * vr[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d += __shfl_xor_sync(0xffffffffu, d, o);
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sd[threadIdx.x >> 5] = d;
+        sr[threadIdx.x >> 5] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d = r = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            d += sd[k];
+            r += sr[k];
+        }
+        atomicAdd(out, d);
+        atomicAdd(out + 1, r);
+    }
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -1273,6 +1305,24 @@ fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const 
     return FMM_OK;
 }
 
+fmm_status fmm_selftest_timeout(fmm_handle h, int polls)
+{
+    if (!h || polls < 1 || polls > (1 << 20))
+        return h ? set_err(h, FMM_EINVAL, "polls must be in [1, 2^20]") : FMM_EINVAL;
+    fmm_status st;
+    if ((st = poll_status(h, false)) != FMM_OK)
+        return st;
+    // the status word lives in the fixed header, which exists from fmm_create on
+    Work w{};
+    w.status = (unsigned int *)h->hdr;
+    h->launches += launch_wait_timeout_selftest(w, polls, h->stream);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaEventRecord(h->ev_status, h->stream));
+    h->status_pending = 1;
+    return FMM_OK;
+}
+
 fmm_status fmm_sync(fmm_handle h)
 {
     if (!h)
@@ -1450,6 +1500,82 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
     if (best >= 1e30f)
         return set_err(h, FMM_ECUDA, "no candidate ran");
     return FMM_OK;
+}
+
+// Smallest p in [p_lo, p_hi] whose evaluation (the handle's form and tree) is within rel_tol of the FP64 form at
+// p = FMM_PMAX on the same tree, in relative L2 over all particles. The truncation error of the expansions falls
+// geometrically with p (§3's t-term expansions), so the first p that meets the target is the cheapest.
+fmm_status fmm_autotune_p(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                          double rel_tol, int p_lo, int p_hi, double *achieved)
+{
+    fmm_status st = check_common(h, n, x, y, gamma, x, y);
+    if (st != FMM_OK)
+        return st;
+    if (p_lo < 1 || p_hi > FMM_PMAX || p_lo > p_hi || !(rel_tol > 0.0))
+        return set_err(h, FMM_EINVAL, "autotune_p: 1 <= p_lo <= p_hi <= %d and rel_tol > 0", FMM_PMAX);
+    if (n == 0) {
+        h->p = p_lo;
+        if (achieved)
+            *achieved = 0.0;
+        return FMM_OK;
+    }
+    if ((st = poll_status(h, false)) != FMM_OK)
+        return st;
+    double *buf = nullptr, *sums = nullptr;
+    CU(cudaMalloc(&buf, (size_t)4 * n * sizeof(double)));
+    if (cudaMalloc(&sums, 2 * sizeof(double)) != cudaSuccess) {
+        cudaFree(buf);
+        return set_err(h, FMM_ENOMEM, "autotune_p: scratch");
+    }
+    double *ur = buf, *vr = buf + n, *u = buf + 2 * n, *v = buf + 3 * n;
+    const int save_p = h->p, save_mixed = h->mixed, save_timing = h->timing;
+    h->timing = 0;
+    auto done = [&](fmm_status s) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(buf);
+        cudaFree(sums);
+        h->mixed = save_mixed;
+        h->timing = save_timing;
+        return s;
+    };
+    // reference: the plain FP64 form at the largest p
+    h->mixed = 0;
+    h->p = FMM_PMAX;
+    if ((st = fmm_velocity(h, n, x, y, gamma, ur, vr)) != FMM_OK || (st = fmm_sync(h)) != FMM_OK) {
+        h->p = save_p;
+        return done(st);
+    }
+    h->mixed = save_mixed;
+    int best = p_hi;
+    double err = -1.0;
+    for (int p = p_lo; p <= p_hi; ++p) {
+        h->p = p;
+        if ((st = fmm_velocity(h, n, x, y, gamma, u, v)) != FMM_OK) {
+            h->p = save_p;
+            return done(st);
+        }
+        double hs[2] = {0.0, 0.0};
+        if (cudaMemsetAsync(sums, 0, 2 * sizeof(double), h->stream) != cudaSuccess) {
+            h->p = save_p;
+            return done(set_err(h, FMM_ECUDA, "autotune_p: memset"));
+        }
+        k_rel_l2_parts<<<152 * 4, 256, 0, h->stream>>>(n, u, v, ur, vr, sums);
+        ++h->launches;
+        if (cudaMemcpyAsync(hs, sums, sizeof hs, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            (st = fmm_sync(h)) != FMM_OK) {
+            h->p = save_p;
+            return done(st != FMM_OK ? st : set_err(h, FMM_ECUDA, "autotune_p: copy"));
+        }
+        err = hs[1] > 0.0 ? std::sqrt(hs[0] / hs[1]) : 0.0;
+        if (err <= rel_tol) {
+            best = p;
+            break;
+        }
+    }
+    h->p = best;
+    if (achieved)
+        *achieved = err;
+    return done(FMM_OK);
 }
 
 const char *fmm_status_string(fmm_status s)

@@ -199,6 +199,7 @@ int launch_p2m(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t
 int launch_m2m(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
 int launch_m2l(const Work &w, const Tables &t, int adjoint_charges, cudaStream_t s, int prio);
 int launch_l2l(const Work &w, const Tables &t, int level, int adjoint_charges, cudaStream_t s, int prio);
+int launch_wait_timeout_selftest(const Work &w, int polls, cudaStream_t s);  // one bounded wait that runs out
 int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);  // threads 32: 1 leaf per block, 64: 2,
                                                                      // 128: symmetric, 192: per source row
 int launch_rk_stage(int64_t n, double *x, double *y, double *tx, double *ty, const double *u, const double *v,

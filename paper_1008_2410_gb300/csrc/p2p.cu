@@ -121,15 +121,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Waits for the phase with the given parity; gives up after a bounded number of polls and reports a timeout
-// in the status word instead of hanging.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned int *status)
+// Waits for the phase with the given parity; gives up after a bounded number of polls (each try_wait may also
+// suspend the thread for a short, hardware-defined time) and reports a timeout in the status word instead of
+// hanging.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned int *status,
+                                                  int polls = 1 << 20)
 {
-    for (int it = 0; it < (1 << 20); ++it)
+    for (int it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity))
             return true;
     atomicOr(status, FMM_DEV_TIMEOUT);
     return false;
+}
+
+// Self-test of the timeout path: one thread initialises an mbarrier that expects one arrival, never arrives and
+// never starts a copy, then waits on it with the bounded wait above, so the wait runs out after `polls` polls and
+// the status word gets the timeout bit. Nothing is in flight when the kernel returns.
+__global__ void k_wait_timeout_selftest(unsigned int *status, int polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_proxy_async();
+    mbar_wait_bounded(&bar, 0, status, polls);
+}
+
+int launch_wait_timeout_selftest(const Work &w, int polls, cudaStream_t s)
+{
+    k_wait_timeout_selftest<<<1, 1, 0, s>>>(w.status, polls);
+    return 1;
 }
 
 // Packed FP32 pairs (one 64-bit register pair, two targets): sm_100-class f32x2 arithmetic.

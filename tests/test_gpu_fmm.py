@@ -373,6 +373,76 @@ def test_stage_times_launch_count_and_autotune(lib):
     assert prm["m2l_engine"] in ("tensor", "cuda_cores")
 
 
+@pytest.mark.slow
+def test_batched_64_systems_full_size_sampled_parity(lib, oracle):
+    """The full batched workload: 64 uniform systems of 4096 .. 262144 particles (4.5 M in all), each at its own
+    depth round(log4(N_k / 64)), p = 14, one graph launch per stage, in both forms; 128 sampled targets per system
+    against the oracle FMM of that system."""
+    b = fi.batched()
+    off = b.offsets
+    x = np.concatenate([s.x for s in b.systems])
+    y = np.concatenate([s.y for s in b.systems])
+    g = np.concatenate([s.gamma for s in b.systems])
+    kw = dict(depths=[s.depth for s in b.systems], sigmas=[s.sigma for s in b.systems],
+              domains=[s.domain for s in b.systems])
+    res = {}
+    for prec in ("fp64", "mixed"):
+        f = lib.FMM(b.systems[0].depth, b.p, b.systems[0].sigma, precision=prec, graph=True)
+        xd, yd, gd = dev(x), dev(y), dev(g)
+        u, v = f.velocity_batched(off, xd, yd, gd, **kw)
+        f.velocity_batched(off, xd, yd, gd, u=u, v=v, **kw)  # a replay of the captured graph
+        f.sync()
+        res[prec] = (u.cpu().numpy(), v.cpu().numpy())
+        f.close()
+    for k, sy in enumerate(b.systems):
+        t = fi.sample_targets(sy.n, 128, seed_index=100 + k)
+        uo, vo, _ = oracle.fmm(sy.x, sy.y, sy.gamma, sy.sigma, sy.depth, b.p, domain=sy.domain, targets=t)
+        for prec, tol in (("fp64", TOL64), ("mixed", TOL32)):
+            u, v = res[prec]
+            assert rel_l2((u[off[k]:off[k + 1]][t], v[off[k]:off[k + 1]][t]), (uo, vo)) < tol, (prec, k)
+
+
+@pytest.mark.slow
+def test_adjoint_full_size_config5_loss(lib, oracle):
+    """The adjoint at 2^20 uniform particles (depth 7, p = 17) for the loss L = 1/2 |u - u*|^2, u* the FMM velocity
+    of the perturbed circulations: dL/dgamma, dL/dx, dL/dy against the oracle's transposed stages."""
+    w = fi.uniform_1m()
+    gs = fi.adjoint_target_gamma(w)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="fp64", domain=w.domain)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    us, vs = f.velocity(x, y, dev(gs))
+    u, v = f.velocity(x, y, g)
+    gu, gv = u - us, v - vs
+    dg, dx, dy = f.adjoint(x, y, g, gu, gv)
+    f.sync()
+    og, ox, oy = oracle.fmm_adjoint(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, gu.cpu().numpy(), gv.cpu().numpy(),
+                                    domain=w.domain)
+    assert rel_l2((dg.cpu().numpy(),), (og,)) < 1e-11
+    assert rel_l2((dx.cpu().numpy(), dy.cpu().numpy()), (ox, oy)) < 1e-10
+
+
+def test_suggested_depth_reaches_eq7_on_the_gpu(lib, oracle):
+    """§2: the expansions carry the point-vortex kernel, so the FMM misses the Gaussian tail of pairs beyond adjacent
+    leaves. On the Lamb-Oseen lattice the GPU evaluation at fmm_suggest_depth's depth (3 for a tail tolerance of
+    1e-12: leaves 8 sigma wide) matches the direct sum of Eq. 7 to 1e-12 in the FP64 form (p = 30) and to 1e-6 in
+    the precision form, while at depth 4 (leaves 4 sigma wide) it stays tail-limited above 1e-7."""
+    w = fi.lattice_lamb_oseen()
+    d = lib.suggest_depth(w.n, w.sigma, w.domain[2], tail_tol=1e-12)
+    assert d == 3
+    t = fi.sample_targets(w.n, 512)
+    ud, vd = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=t)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    errs = {}
+    for depth, prec in ((d, "fp64"), (d, "mixed"), (4, "fp64")):
+        f = lib.FMM(depth, 30, w.sigma, precision=prec, domain=w.domain)
+        u, v = f.velocity(x, y, g)
+        f.sync()
+        errs[(depth, prec)] = rel_l2((u.cpu().numpy()[t], v.cpu().numpy()[t]), (ud, vd))
+    assert errs[(d, "fp64")] < 1e-12
+    assert errs[(d, "mixed")] < TOL32
+    assert errs[(4, "fp64")] > 1e-7
+
+
 @pytest.mark.parametrize("leaf_capacity", [0, 24])
 def test_default_engine_and_stage_events_in_graph_replays(lib, leaf_capacity):
     """A fresh handle runs the FP32 M2L levels on the CUDA cores; with graphs on, the stage events are graph nodes,
@@ -480,3 +550,54 @@ def test_advect_rejects_bad_arguments(lib):
             f.advect(x, y, g, *args)
     f.advect(x, y, g, 0.1, 0, 2)  # zero steps: nothing happens
     assert torch.equal(x, dev(w.x))
+
+
+# ---------------------------------------------------------------------------------------- failure reporting
+
+
+def test_bounded_wait_timeout_reaches_the_host_and_the_handle_recovers(lib):
+    """The bounded device wait (the one guarding every bulk copy of the near field) is made to run out on a
+    barrier that nothing completes: fmm_sync returns FMM_ETIMEOUT, and the same handle then evaluates correctly."""
+    from paper_1008_2410_gb300 import _lib
+
+    w = fi.uniform(4000, seed_index=49, depth=3, p=10)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    u0, v0 = f.velocity(x, y, g)
+    f.sync()
+    f.selftest_timeout(4096)
+    with pytest.raises(_lib.FMMError) as err:
+        f.sync()
+    assert err.value.status == _lib.FMM_ETIMEOUT
+    f.sync()  # reported once
+    u1, v1 = f.velocity(x, y, g)
+    f.sync()
+    assert torch.equal(u0, u1) and torch.equal(v0, v1)
+    # on a fresh handle that has not evaluated anything yet
+    f2 = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain)
+    f2.selftest_timeout(64)
+    with pytest.raises(_lib.FMMError) as err:
+        f2.sync()
+    assert err.value.status == _lib.FMM_ETIMEOUT
+    with pytest.raises(_lib.FMMError):
+        f2.selftest_timeout(0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+def test_autotune_p_meets_the_target_against_the_oracle(lib, oracle, precision, tol):
+    """fmm_autotune_p keeps the smallest p whose evaluation is within the target of the FP64 form at p = 32; the
+    chosen p's GPU result checked on a sample against the oracle's split sum (what the FMM converges to, §2) stays
+    within the target (the estimate is global, the check sampled: a factor 3 of slack), and p - 1 misses it."""
+    w = fi.uniform(60000, seed_index=50, depth=5, p=17)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    p, est = f.autotune_p(x, y, g, tol, 2, 30)
+    assert 2 < p <= 30 and est <= tol
+    u, v = f.velocity(x, y, g)
+    f.sync()
+    t = fi.sample_targets(w.n, 400)
+    us, vs = oracle.split_direct(w.x, w.y, w.gamma, w.sigma, w.depth, domain=w.domain, targets=t)
+    assert rel_l2((u.cpu().numpy()[t], v.cpu().numpy()[t]), (us, vs)) < 3 * tol
+    f2 = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain)
+    p2, est2 = f2.autotune_p(x, y, g, tol, p - 1, p - 1)
+    assert p2 == p - 1 and est2 > tol

@@ -177,6 +177,8 @@ static fmm_status ensure_tables(fmm_handle h)
         return set_err(h, FMM_ECUDA, "constant-table upload failed");
     if (prepare_m2l_tc() != 0)
         return set_err(h, FMM_ECUDA, "tensor-core M2L kernel attributes could not be set");
+    if (prepare_p2p() != 0)
+        return set_err(h, FMM_ECUDA, "near-field kernel attributes could not be set");
     if (h->tab_p == h->p)
         return FMM_OK;
     const int P = FMM_PMAX, RS = 2 * FMM_PMAX + 2;

@@ -228,6 +228,7 @@ void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *
 size_t m2l_tc_table_bytes(int p);
 void build_m2l_tc_table_host(int p, unsigned char *out);
 int prepare_m2l_tc();
+int prepare_p2p();  // near-field kernel attributes, once per device before any stream capture; 0 on success
 int launch_m2l_tc(const Work &w, const Tables &t, int l32, cudaStream_t s);
 int upload_m2l_constants(cudaStream_t s);  // once per device, before any stream capture; 0 on success
 

@@ -205,7 +205,7 @@ extern "C" fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, 
     }
     if (upload_m2l_constants(s) != 0)  // constant memory of the module, once per device (no allocation)
         return FMM_ECUDA;
-    if (prepare_m2l_tc() != 0)  // kernel attributes, once per device
+    if (prepare_m2l_tc() != 0 || prepare_p2p() != 0)  // kernel attributes, once per device
         return FMM_ECUDA;
 
     unsigned char *h = base + tab;

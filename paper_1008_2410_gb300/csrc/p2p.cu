@@ -186,9 +186,9 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 }
 
 // In units where r'^2 is the exponent of 2: exp(-r^2 / 2 sigma^2) = 2^-(r'^2), y = r'^2 ln 2. Below y = 1/2
-// the factor (1 - e^-y)/y comes from its Taylor series (10 terms, truncation < 3e-11): 1 - 2^-(r'^2) from the SFU
-// loses 2^-22.5 / y of its relative accuracy there. r' = 0 (a particle and itself, or coincident particles,
-// which always share a leaf) needs no series: with 1/r'^2 clamped, g (1 - e) / r'^2 = 0 exactly.
+// the factor (1 - e^-y)/y comes from the product form of small_q2 below: 1 - 2^-(r'^2) from the SFU loses
+// 2^-22.5 / y of its relative accuracy there. r' = 0 (a particle and itself, or coincident particles, which
+// always share a leaf) needs no special factor: with 1/r'^2 clamped, g (1 - e) / r'^2 = 0 exactly.
 #define P2P_THR 0.72134752044448170f
 #define P2P_LN2 0.69314718055994531f
 #ifndef P2P_UNROLL
@@ -197,22 +197,32 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 #ifndef P2P_MIN_BLOCKS
 #define P2P_MIN_BLOCKS 16  // minimum resident blocks per SM requested from the register allocator (64 registers)
 #endif
+#ifndef P2P_MIN_BLOCKS2
+#define P2P_MIN_BLOCKS2 24  // the same for the two-targets-per-lane instance (40 registers)
+#endif
+#ifndef P2P_TILE2
+#define P2P_TILE2 256  // sources per shared-memory tile of the two-per-lane instance (one-float coordinates)
+#endif
 constexpr int kP2PUnroll = P2P_UNROLL;
 
-__device__ __forceinline__ float small_y_factor10(float y)
+// (1 - 2^-a) / a for both halves of a packed pair a = r'^2 below the series threshold, written as
+// ln2 * 2^(-a/2) * sinh(t) / t with t = a ln2 / 2 <= 1/4 (the identity 1 - e^-y = 2 e^(-y/2) sinh(y/2)): the SFU's
+// 2^(-a/2) keeps its relative accuracy (no cancellation), and sinh(t)/t = sum_k t^(2k) / (2k+1)! to t^6 truncates
+// below 5e-11. Coefficients: ln2 (ln2/2)^(2k) / (2k+1)!, k = 0..3, a polynomial in a^2.
+#define P2P_SQ0 6.931471806e-01f
+#define P2P_SQ1 1.387602717e-02f
+#define P2P_SQ2 8.333473842e-05f
+#define P2P_SQ3 2.383239657e-07f
+__device__ __forceinline__ f2 small_q2(f2 r2)
 {
-    float s = 1.0f / 39916800.0f;
-    s = fmaf(s, -y, 1.0f / 3628800.0f);
-    s = fmaf(s, -y, 1.0f / 362880.0f);
-    s = fmaf(s, -y, 1.0f / 40320.0f);
-    s = fmaf(s, -y, 1.0f / 5040.0f);
-    s = fmaf(s, -y, 1.0f / 720.0f);
-    s = fmaf(s, -y, 1.0f / 120.0f);
-    s = fmaf(s, -y, 1.0f / 24.0f);
-    s = fmaf(s, -y, 1.0f / 6.0f);
-    s = fmaf(s, -y, 0.5f);
-    s = fmaf(s, -y, 1.0f);
-    return s;
+    float ra, rb;
+    up2(r2, ra, rb);
+    const f2 h = pk2(ex2_approx(-0.5f * ra), ex2_approx(-0.5f * rb));
+    const f2 v = mul2(r2, r2);
+    f2 t = fma2(v, pk2(P2P_SQ3, P2P_SQ3), pk2(P2P_SQ2, P2P_SQ2));
+    t = fma2(v, t, pk2(P2P_SQ1, P2P_SQ1));
+    t = fma2(v, t, pk2(P2P_SQ0, P2P_SQ0));
+    return mul2(h, t);
 }
 
 // Error-free packed sum: s + c += x (Knuth's TwoSum on both halves).
@@ -300,16 +310,17 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
         if (__any_sync(0xffffffffu, SELF ? (__float_as_uint(rmin) < __float_as_uint(P2P_THR)) : (rmin < P2P_THR))) {
 #pragma unroll
             for (int pr = 0; pr < NP; ++pr) {
-                float ra, rb, qa, qb, oa, ob;
+                float ra, rb, qa, qb, oa, ob, sa, sb;
                 up2(r2[pr], ra, rb);
                 up2(q[pr], qa, qb);
                 up2(og[pr], oa, ob);
+                up2(small_q2(r2[pr]), sa, sb);
                 if (ra < P2P_THR) {
-                    qa = P2P_LN2 * small_y_factor10(P2P_LN2 * ra);
+                    qa = sa;
                     oa = g.x;
                 }
                 if (rb < P2P_THR) {
-                    qb = P2P_LN2 * small_y_factor10(P2P_LN2 * rb);
+                    qb = sb;
                     ob = g.x;
                 }
                 q[pr] = pk2(qa, qb);
@@ -385,15 +396,16 @@ __device__ __forceinline__ void p2p_segment_rem(const Work &w, const float4 *__r
         }
         f2 og = fma2(pk2(ea, eb), pk2(-ga, -gb), pk2(ga, gb));  // g (1 - e)
         if (__any_sync(0xffffffffu, SELF ? (__float_as_uint(rmin) < __float_as_uint(P2P_THR)) : (rmin < P2P_THR))) {
-            float qa, qb, oa, ob;
+            float qa, qb, oa, ob, sa, sb;
             up2(q, qa, qb);
             up2(og, oa, ob);
+            up2(small_q2(r2), sa, sb);
             if (ra < P2P_THR) {
-                qa = P2P_LN2 * small_y_factor10(P2P_LN2 * ra);
+                qa = sa;
                 oa = ga;
             }
             if (rb < P2P_THR) {
-                qb = P2P_LN2 * small_y_factor10(P2P_LN2 * rb);
+                qb = sb;
                 ob = gb;
             }
             q = pk2(qa, qb);
@@ -411,15 +423,23 @@ __device__ __forceinline__ void p2p_segment_rem(const Work &w, const float4 *__r
 // on it is the same, otherwise a main group of up to 64 targets, two per lane, every lane meeting the same source,
 // plus the rest (r <= 32 after a full main group, or a whole pass of r <= 32) spread over the 64 slots with
 // G = 64 / r source groups (p2p_segment_rem); the G partial sums of each remainder target are added at the end.
-// With ktmax = 2, or in the split form, a pass holds at most 64 targets, two per lane. Sources arrive by bulk
-// copies into shared memory; each slot's sum over one tile (plain FP32) is added to its total with an error-free
-// TwoSum.
-template <int LPB>
-__global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, int ktmax, int skip_plain)
+// With ktmax = 2 (a second instance, KTM = 2, compiled for fewer registers and so more warps per SM) a pass holds
+// either a main group of up to 64 targets or a remainder of at most 32, never both, so one set of accumulators is
+// live; in the split form passes are balanced, at most 64 targets, two per lane. Sources arrive by bulk copies into
+// shared memory; each slot's sum over one tile (plain FP32) is added to its total with an error-free TwoSum.
+// Register budget of the two instances (minimum resident blocks per SM).
+template <int KTM>
+struct P2PBounds {
+    static constexpr int min_blocks = KTM == 4 ? P2P_MIN_BLOCKS : P2P_MIN_BLOCKS2;
+};
+
+template <int LPB, int KTM>
+__global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w, int tile, int ktmax, int skip_plain)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    float4 *EH = reinterpret_cast<float4 *>(smem_raw), *EL = EH + tile, *EG = EL + tile;
+    // EH, EG, then EL (only the split form reads EL, so one-float launches allocate 32 bytes per source)
+    float4 *EH = reinterpret_cast<float4 *>(smem_raw), *EG = EH + tile, *EL = EG + tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int first = blockIdx.x * LPB;
     if (first >= w.nleaf)
@@ -433,8 +453,12 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
     const bool split = d.s_unit > P2P_SPLIT_S;  // block-uniform; the split form runs 2 targets per lane
     if (skip_plain && !split)
         return;  // this system's near field is the symmetric kernel's
-    const bool rem_form = !split && ktmax == 4;
-    const int per_pass = rem_form ? 128 : 64;
+    (void)ktmax;
+    const bool rem_form = !split;
+    // passes: KTM = 4, 128 targets (the last one the rest); KTM = 2, 64 targets, then the rest as one pass
+    // (a main group of 33..63, or a remainder of at most 32); split form: balanced passes of at most 64
+    const int full_pass = KTM == 4 ? 128 : 64;
+    const int per_pass = rem_form ? full_pass : 64;
     int npass = (my_c + per_pass - 1) / per_pass;
     if (LPB == 2) {
         const int other = first + (warp ^ 1);
@@ -444,6 +468,9 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
     if (npass == 0)
         return;  // block-uniform: every leaf of the block is empty
     const int my_np = (my_c + per_pass - 1) / per_pass;
+    // the remainder's accumulators: a slot pair of their own where a pass holds both groups (KTM = 4), the main
+    // group's where a pass holds one or the other (KTM = 2: one accumulator set live)
+    constexpr int RI = KTM == 4 ? 1 : 0;
     const float s = d.s_unit;
     const int c_lo = ix0 - 1, ncol = LPB + 2;  // block columns c_lo .. c_lo + ncol - 1
     if (threadIdx.x == 0) {
@@ -455,9 +482,9 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
     for (int pass = 0; pass < npass; ++pass) {
         int t_lo = 0, t_cnt = 0;
         if (pass < my_np) {
-            if (rem_form) {  // full passes of 128, the rest in the last
-                t_lo = 128 * pass;
-                t_cnt = min(128, my_c - t_lo);
+            if (rem_form) {  // full passes, the rest in the last
+                t_lo = full_pass * pass;
+                t_cnt = min(full_pass, my_c - t_lo);
             } else {  // balanced passes
                 t_lo = (int)((int64_t)pass * my_c / my_np);
                 t_cnt = (int)((int64_t)(pass + 1) * my_c / my_np) - t_lo;
@@ -467,9 +494,9 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
         // layout of the pass: more than 96 targets, four per lane (two packed pairs, broadcast sources); else a
         // main group of up to 64, two per lane, and a remainder of at most 32 over the slots (source groups); a
         // pass of 33..63 targets is all main group, one of at most 32 all remainder
-        const bool kt4 = rem_form && t_cnt > 96;
+        const bool kt4 = KTM == 4 && rem_form && t_cnt > 96;
         const int n_main = !rem_form || kt4 ? t_cnt : (t_cnt >= 64 ? 64 : (t_cnt > 32 ? t_cnt : 0));
-        const int r = t_cnt - n_main;
+        const int r = t_cnt - n_main;  // KTM = 2: n_main and r are never both non-zero
         f2 SU[2] = {0ull, 0ull}, CU[2] = {0ull, 0ull}, SV[2] = {0ull, 0ull}, CV[2] = {0ull, 0ull};
         for (int dyr = -1; dyr <= 1; ++dyr) {
             const int row = iy + dyr;
@@ -513,11 +540,11 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
                     const float sdx = (float)(k3 - 1) * s, sdy = (float)dyr * s;
                     const bool self = k3 == 1 && dyr == 0;
 #define P2P_SEG(SELF, SPLIT) p2p_segment<2, SELF, SPLIT>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV)
-                    if (kt4) {
+                    if (KTM == 4 && kt4) {
                         if (self)
-                            p2p_segment<4, true, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV);
+                            p2p_segment<KTM, true, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV);
                         else
-                            p2p_segment<4, false, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV);
+                            p2p_segment<KTM, false, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV);
                     } else if (n_main > 0) {
                         if (split) {
                             if (self)
@@ -534,14 +561,14 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
 #undef P2P_SEG
                     if (r > 0) {
                         if (self)
-                            p2p_segment_rem<true>(w, EH, EG, j0, j1, sdx, sdy, tbase + n_main, r, PU[1], PV[1]);
+                            p2p_segment_rem<true>(w, EH, EG, j0, j1, sdx, sdy, tbase + n_main, r, PU[RI], PV[RI]);
                         else
-                            p2p_segment_rem<false>(w, EH, EG, j0, j1, sdx, sdy, tbase + n_main, r, PU[1], PV[1]);
+                            p2p_segment_rem<false>(w, EH, EG, j0, j1, sdx, sdy, tbase + n_main, r, PU[RI], PV[RI]);
                     }
                 }
                 // compensated totals: plain FP32 sums cover at most one tile of sources
 #pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
+                for (int pr = 0; pr < (KTM == 4 ? 2 : 1); ++pr) {
                     two_sum2(SU[pr], CU[pr], PU[pr]);
                     two_sum2(SV[pr], CV[pr], PV[pr]);
                     PU[pr] = 0ull;
@@ -554,6 +581,8 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {  // main group: targets lane + 32 (2 pr + h); pr = 1 only with kt4
             if (pr == 1 && !kt4)
+                break;
+            if (n_main == 0)
                 break;
             float su[2], cu[2], sv[2], cv[2];
             up2(SU[pr], su[0], su[1]);
@@ -573,10 +602,10 @@ __global__ void __launch_bounds__(64, P2P_MIN_BLOCKS) k_p2p32(Work w, int tile, 
             float2 *red = reinterpret_cast<float2 *>(EH) + 64 * warp;
             if (r > 0) {
                 float su[2], cu[2], sv[2], cv[2];
-                up2(SU[1], su[0], su[1]);
-                up2(CU[1], cu[0], cu[1]);
-                up2(SV[1], sv[0], sv[1]);
-                up2(CV[1], cv[0], cv[1]);
+                up2(SU[RI], su[0], su[1]);
+                up2(CU[RI], cu[0], cu[1]);
+                up2(SV[RI], sv[0], sv[1]);
+                up2(CV[RI], cv[0], cv[1]);
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
                     red[lane + 32 * h] = make_float2(su[h] + cu[h], sv[h] + cv[h]);
@@ -654,16 +683,17 @@ __device__ __forceinline__ void p2ps_chunk(const float4 *__restrict__ SH, const 
         if (__any_sync(0xffffffffu, SELF ? (__float_as_uint(rmin) < __float_as_uint(P2P_THR)) : (rmin < P2P_THR))) {
 #pragma unroll
             for (int pr = 0; pr < NP; ++pr) {
-                float ra, rb, qa, qb, ea, eb;
+                float ra, rb, qa, qb, ea, eb, sa, sb;
                 up2(r2[pr], ra, rb);
                 up2(q[pr], qa, qb);
                 up2(e[pr], ea, eb);
+                up2(small_q2(r2[pr]), sa, sb);
                 if (ra < P2P_THR) {
-                    qa = P2P_LN2 * small_y_factor10(P2P_LN2 * ra);
+                    qa = sa;
                     ea = 0.f;
                 }
                 if (rb < P2P_THR) {
-                    qb = P2P_LN2 * small_y_factor10(P2P_LN2 * rb);
+                    qb = sb;
                     eb = 0.f;
                 }
                 q[pr] = pk2(qa, qb);
@@ -865,6 +895,27 @@ __global__ void __launch_bounds__(32 * LW, P2PS_MIN_BLOCKS) k_p2p32s(Work w, int
     }
 }
 
+// Per-device kernel attributes of the near field (once, before any stream capture): the largest shared-memory
+// carveout, so that the two-per-lane instance reaches its register-limited 24 blocks per SM.
+static int g_p2p_ready[64];
+
+int prepare_p2p()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return -1;
+    if (g_p2p_ready[dev])
+        return 0;
+    const int c = cudaSharedmemCarveoutMaxShared;
+    if (cudaFuncSetAttribute(k_p2p32<1, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_p2p32<2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_p2p32<1, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
+        cudaFuncSetAttribute(k_p2p32<2, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess)
+        return -1;
+    g_p2p_ready[dev] = 1;
+    return 0;
+}
+
 int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
 {
     if (w.nleaf == 0)
@@ -881,32 +932,47 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
         k_p2p32s<LW><<<(w.nleaf + LW - 1) / LW, 32 * LW, 0, s>>>(w, ktmax);
         ++nl;
         if (!w.p2p_all_plain) {
-            const int tile = 256;
-            k_p2p32<1><<<w.nleaf, 32, (size_t)tile * 48, s>>>(w, tile, 2, 1);
+            const int tile = 192;
+            k_p2p32<1, 2><<<w.nleaf, 32, (size_t)tile * 48, s>>>(w, tile, 2, 1);
             ++nl;
         }
         return nl;
     }
+    // shared memory per block: 32 bytes per source when every system keeps one-float coordinates, else 48; the
+    // four-per-lane instance runs 16 blocks per SM (tile 256), the two-per-lane instance 24 (tile 256 or 192)
+    const int tile = ktmax == 4 ? 256 : (w.p2p_all_plain ? P2P_TILE2 : 192);
+    const size_t sm = (size_t)tile * (w.p2p_all_plain ? 32 : 48);
     if (threads == 192 && w.p2p_rows) {
         // the target-side kernel with each of the three source rows of a leaf pair in its own block: three
         // times the blocks at a third of the length, so the last wave leaves less of the GPU idle
         const bool pr2 = w.lv.nsys_at[1] == w.nsys;
-        const int tile = 256;
         const dim3 grid(pr2 ? (w.nleaf + 1) / 2 : w.nleaf, 3);
-        if (pr2)
-            k_p2p32<2><<<grid, 64, (size_t)tile * 48, s>>>(w, tile, ktmax, 0);
-        else
-            k_p2p32<1><<<grid, 32, (size_t)tile * 48, s>>>(w, tile, ktmax, 0);
+        if (pr2) {
+            if (ktmax == 4)
+                k_p2p32<2, 4><<<grid, 64, sm, s>>>(w, tile, ktmax, 0);
+            else
+                k_p2p32<2, 2><<<grid, 64, sm, s>>>(w, tile, ktmax, 0);
+        } else {
+            if (ktmax == 4)
+                k_p2p32<1, 4><<<grid, 32, sm, s>>>(w, tile, ktmax, 0);
+            else
+                k_p2p32<1, 2><<<grid, 32, sm, s>>>(w, tile, ktmax, 0);
+        }
         return 1;
     }
     // two leaves per block needs every system's leaves to pair up within rows (depth >= 1)
     bool pairs = threads == 64 && w.lv.nsys_at[1] == w.nsys;
-    int tile = 256;  // 16 blocks x 256 x 48 B of shared memory per SM
-    size_t sm = (size_t)tile * 48;
-    if (pairs)
-        k_p2p32<2><<<(w.nleaf + 1) / 2, 64, sm, s>>>(w, tile, ktmax, 0);
-    else
-        k_p2p32<1><<<w.nleaf, 32, sm, s>>>(w, tile, ktmax, 0);
+    if (pairs) {
+        if (ktmax == 4)
+            k_p2p32<2, 4><<<(w.nleaf + 1) / 2, 64, sm, s>>>(w, tile, ktmax, 0);
+        else
+            k_p2p32<2, 2><<<(w.nleaf + 1) / 2, 64, sm, s>>>(w, tile, ktmax, 0);
+    } else {
+        if (ktmax == 4)
+            k_p2p32<1, 4><<<w.nleaf, 32, sm, s>>>(w, tile, ktmax, 0);
+        else
+            k_p2p32<1, 2><<<w.nleaf, 32, sm, s>>>(w, tile, ktmax, 0);
+    }
     return 1;
 }
 

@@ -240,7 +240,7 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
         out["m2l"] = m2l_leg(api, w, x, y, g, args.steps, flush, stream)
     out["advect"] = advect_leg(api, w, x, y, g, tuned, args.precision, flush, stream)
     out["batched"] = batched_leg(api, args.precision, flush, stream)
-    out["adjoint"] = adjoint_leg(api, w, x, y, g, flush, stream)
+    out["adjoint"], adj_check = adjoint_leg(api, w, x, y, g, flush, stream)
     if args.workload == "patches_16m" or args.adaptive:
         f.velocity(x, y, g, u, v)
         out["adaptive"] = adaptive_leg(api, w, x, y, g, u, v, args.precision, flush, stream,
@@ -327,8 +327,22 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     except Exception as exc:  # the probe is a report, not part of the metric
         out["probed_peaks"] = {"error": str(exc)}
 
+    # the smallest p that keeps the precision form within 1e-6 of the FP64 form at p = 32 (fmm_autotune_p)
+    if args.precision == "mixed":
+        fp = api.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain, graph=True)
+        fp.set_p2p_tile(tuned["p2p_threads"], tuned["p2p_targets_per_thread"])
+        pt, est = fp.autotune_p(x, y, g, 1e-6, 4, 24)
+        up, vp = torch.empty_like(x), torch.empty_like(x)
+        for _ in range(3):
+            fp.velocity(x, y, g, up, vp)
+        msp, _ = timed_steps(lambda: fp.velocity(x, y, g, up, vp), 10, flush, stream)
+        fp.close()
+        out["tuned_p"] = {"target_rel_err": 1e-6, "p": pt, "estimated_rel_err": est,
+                          "value": n / (statistics.median(msp) / 1e3) / 1e6, "unit": "Mparticles/s",
+                          "note": "fmm_autotune_p against the FP64 form at p = 32; the headline keeps the workload's p"}
+
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, u.cpu().numpy(), v.cpu().numpy())
+        out["cpu_baseline"] = cpu_baseline(w, u.cpu().numpy(), v.cpu().numpy(), adj_check)
     f.close()
     return out
 
@@ -470,26 +484,61 @@ def batched_leg(api, precision, flush, stream) -> dict:
               domains=[list(s.domain) for s in bt.systems])
     u, v = f.velocity_batched(off, x, y, g, **kw)
     ms, _ = timed_steps(lambda: f.velocity_batched(off, x, y, g, u=u, v=v, **kw), 10, flush, stream)
+    # the batched autotuner: leaf occupancy (per-system depths) and near-field tile
+    tuned = f.autotune_batched(off, x, y, g, sigmas=kw["sigmas"], domains=kw["domains"])
+    kwt = dict(kw, depths=tuned["depths"])
+    f.velocity_batched(off, x, y, g, u=u, v=v, **kwt)
+    mst, _ = timed_steps(lambda: f.velocity_batched(off, x, y, g, u=u, v=v, **kwt), 10, flush, stream)
     f.close()
-    t = st_.median(ms)
+    t, tt = st_.median(ms), st_.median(mst)
+    occ = [float(s.n) / 4 ** d for s, d in zip(bt.systems, tuned["depths"])]
     return {"systems": len(bt.systems), "particles": int(off[-1]), "ms_per_step": t,
-            "value": int(off[-1]) / (t / 1e3) / 1e6, "unit": "Mparticles/s"}
+            "value": int(off[-1]) / (t / 1e3) / 1e6, "unit": "Mparticles/s",
+            "config": "depth_k = round(log4(N_k / 64)), default tile",
+            "autotuned": {"ms_per_step": tt, "value": int(off[-1]) / (tt / 1e3) / 1e6,
+                          "p2p_tile": [tuned["p2p_threads"], tuned["p2p_targets_per_thread"]],
+                          "depths": tuned["depths"], "mean_leaf_occupancy": sum(occ) / len(occ)}}
 
 
 def adjoint_leg(api, w, x, y, g, flush, stream) -> dict:
-    """Exact adjoint (dL/dgamma, dL/dx, dL/dy for L = sum(gu u + gv v)), FP64 form, on the same workload."""
+    """Exact adjoint (dL/dgamma, dL/dx, dL/dy) for the loss L = 1/2 |u - u*|^2, u* the FMM velocity of the perturbed
+    circulations gamma* = gamma + 0.01 N(0, 1)/N (the adjoint workload), FP64 form, on the same particles. Returns
+    the timing and, for the CPU leg's accuracy check, the seeds and the GPU gradients."""
     import statistics as st_
 
+    import numpy as np
     import torch
 
+    import fmm_inputs as fi
+
     f = api.FMM(w.depth, w.p, w.sigma, precision="fp64", domain=w.domain)
-    gu = torch.ones_like(x)
-    gv = torch.ones_like(x)
+    gs = torch.from_numpy(fi.adjoint_target_gamma(w)).cuda()
+    us, vs = f.velocity(x, y, gs)
+    u, v = f.velocity(x, y, g)
+    gu, gv = u - us, v - vs
     f.adjoint(x, y, g, gu, gv)
     ms, _ = timed_steps(lambda: f.adjoint(x, y, g, gu, gv), 3, flush, stream)
+    f.sync()
     f.close()
     t = st_.median(ms)
-    return {"form": "fp64", "ms_per_step": t, "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s"}
+    loss = float(0.5 * (gu * gu + gv * gv).sum())
+    out = {"form": "fp64", "loss": "1/2 |u - u*|^2, u* from gamma + 0.01 N(0,1)/N", "loss_value": loss,
+           "ms_per_step": t, "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s"}
+    # the same loss on a 2^16-particle case of the recipe (depth 5): the oracle's adjoint of all particles takes
+    # about 40 s at 2^20 (that size is checked by the GPU tests), a few seconds here
+    ws = fi.uniform(1 << 16, seed_index=1, depth=5, p=w.p)  # sigma = 0.5 / sqrt(N), as the recipe
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    xs, ys, gs_ = dev(ws.x), dev(ws.y), dev(ws.gamma)
+    f = api.FMM(ws.depth, ws.p, ws.sigma, precision="fp64", domain=ws.domain)
+    us, vs = f.velocity(xs, ys, dev(fi.adjoint_target_gamma(ws)))
+    u, v = f.velocity(xs, ys, gs_)
+    gu, gv = u - us, v - vs
+    dg, dx, dy = f.adjoint(xs, ys, gs_, gu, gv)
+    f.sync()
+    f.close()
+    check = {"workload": ws, **{k: a.cpu().numpy() for k, a in (("gu", gu), ("gv", gv), ("dg", dg), ("dx", dx),
+                                                                 ("dy", dy))}}
+    return out, check
 
 
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak on this machine)
@@ -624,10 +673,11 @@ def clustered_leg(api, precision, flush, stream, max_depth: int = 11, leaf_capac
             "rel_diff_adaptive_vs_uniform": float(torch.sqrt(((ua - uu) ** 2).sum() + ((va - vu) ** 2).sum()) / den)}
 
 
-def cpu_baseline(w, u_gpu, v_gpu) -> dict:
+def cpu_baseline(w, u_gpu, v_gpu, adj=None) -> dict:
     """The FP64 oracle as it stands, on all host cores: one full FMM evaluation of the same workload (or, above
     2^21 particles, its far field plus near field at 4096 sampled targets), plus accuracy figures of the GPU
-    result against it and against the direct sum at 256 sampled targets."""
+    result against it and against the direct sum at 256 sampled targets, and (adj) of the GPU adjoint against the
+    oracle's transposed stages for the same seeds."""
     import numpy as np
 
     import fmm_inputs as fi
@@ -646,10 +696,24 @@ def cpu_baseline(w, u_gpu, v_gpu) -> dict:
     ts = fi.sample_targets(w.n, 256, seed_index=8)
     ud, vd = oracle.direct(w.x, w.y, w.gamma, w.sigma, targets=ts)
     err_dir = float(np.sqrt(np.sum((u_gpu[ts] - ud) ** 2 + (v_gpu[ts] - vd) ** 2) / np.sum(ud**2 + vd**2)))
-    return {"value": count / dt / 1e6, "unit": "Mparticles/s", "cores": cores, "kind": "oracle",
-            "sample": ("full evaluation, all targets" if full else
-                       "far field of all particles + near field at 4096 sampled targets; rate = targets/s"),
-            "seconds": dt, "gpu_rel_err_vs_oracle_fmm": err_fmm, "gpu_rel_err_vs_direct_sum_256": err_dir}
+    res = {"value": count / dt / 1e6, "unit": "Mparticles/s", "cores": cores, "kind": "oracle",
+           "sample": ("full evaluation, all targets" if full else
+                      "far field of all particles + near field at 4096 sampled targets; rate = targets/s"),
+           "seconds": dt, "gpu_rel_err_vs_oracle_fmm": err_fmm, "gpu_rel_err_vs_direct_sum_256": err_dir}
+    if adj is not None:
+        rel = lambda a, b: float(np.linalg.norm(np.concatenate([np.ravel(t) for t in a]) -
+                                                np.concatenate([np.ravel(t) for t in b])) /
+                                 np.linalg.norm(np.concatenate([np.ravel(t) for t in b])))
+        wa = adj["workload"]
+        t0 = time.perf_counter()
+        og, ox, oy = oracle.fmm_adjoint(wa.x, wa.y, wa.gamma, wa.sigma, wa.depth, wa.p, adj["gu"], adj["gv"],
+                                        domain=wa.domain)
+        res["adjoint_check"] = {"gpu_rel_err_dgamma_vs_oracle": rel((adj["dg"],), (og,)),
+                                "gpu_rel_err_dxdy_vs_oracle": rel((adj["dx"], adj["dy"]), (ox, oy)),
+                                "oracle_seconds": time.perf_counter() - t0,
+                                "case": f"N = {wa.n} uniform, depth {wa.depth}, p {wa.p}, loss 1/2 |u - u*|^2, "
+                                        "all particles"}
+    return res
 
 
 def run_reference(args, rank: int, world: int) -> dict | None:

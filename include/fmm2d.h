@@ -241,6 +241,15 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
 fmm_status fmm_get_params(fmm_handle h, int *tree_depth, int *p, double *sigma, int *p2p_threads,
                           int *p2p_targets_per_thread);
 
+/* Autotuner of batched evaluations (fmm_velocity_batched's arguments, depths excepted): times the batch with each
+ * system's depth set for a leaf occupancy of 16, 32, 48, 64, 96 or 128 particles (depth = round(log4(N_k /
+ * occupancy)), clamped to [0, 12]) and, in the precision form, each near-field tile of fmm_set_p2p_tile; keeps
+ * the fastest. The tile is stored in the handle; the chosen depths are written to depths_out (HOST, nsys ints)
+ * for the caller's later fmm_velocity_batched calls. u, v are scratch outputs. */
+fmm_status fmm_autotune_batched(fmm_handle h, int nsys, const int64_t *offsets, const double *sigmas,
+                                const double *domains, const double *x, const double *y, const double *gamma,
+                                double *u, double *v, int *depths_out);
+
 /* Picks the expansion order for an accuracy target (§3: the t-term expansions' truncation error falls
  * geometrically with t): evaluates the given particles (device arrays, left unchanged) once in the plain FP64
  * form at p = 32 as the reference, then in the handle's own form and tree at p = p_lo, p_lo + 1, ... and keeps

@@ -57,6 +57,7 @@ SIGNATURES = {
     "fmm_kernel_launches": (_I64, [_P]),
     "fmm_autotune": (_I, [_P, _I64, _P, _P, _P, _P, _P, _I, _I]),
     "fmm_autotune_p": (_I, [_P, _I64, _P, _P, _P, _D, _I, _I, ctypes.POINTER(_D)]),
+    "fmm_autotune_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fmm_get_params": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I),
                             ctypes.POINTER(_I)]),
     "fmm_probe_peaks": (_I, [ctypes.POINTER(_D), _I]),

@@ -205,6 +205,26 @@ class FMM:
                                      _dev(u, "u"), _dev(v, "v"), int(depth_lo), int(depth_hi)), self.h)
         return self.params()
 
+    def autotune_batched(self, offsets, x, y, gamma, sigmas=None, domains=None) -> dict:
+        """Leaf occupancy (per-system depths) and near-field tile of the fastest batched evaluation; returns the
+        handle's parameters plus the chosen "depths"."""
+        import numpy as np
+
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        nsys = off.size - 1
+        sig = None if sigmas is None else np.ascontiguousarray(np.asarray(sigmas, dtype=np.float64))
+        dom = None if domains is None else np.ascontiguousarray(np.asarray(domains, dtype=np.float64).reshape(-1))
+        dep = np.zeros(nsys, dtype=np.int32)
+        u, v = torch.empty_like(x), torch.empty_like(x)
+        self._stream()
+        check(self._lib.fmm_autotune_batched(
+            self.h, nsys, off.ctypes.data, None if sig is None else sig.ctypes.data,
+            None if dom is None else dom.ctypes.data, _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"),
+            _dev(u, "u"), _dev(v, "v"), dep.ctypes.data), self.h)
+        prm = self.params()
+        prm["depths"] = [int(d) for d in dep]
+        return prm
+
     def autotune_p(self, x, y, gamma, rel_tol: float, p_lo: int = 1, p_hi: int = 32) -> tuple[int, float]:
         """Smallest p in [p_lo, p_hi] within rel_tol (relative L2) of the FP64 form at p = 32; sets the handle's p
         and returns (p, estimated error)."""

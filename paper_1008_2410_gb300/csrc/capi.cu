@@ -1504,6 +1504,74 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
     return FMM_OK;
 }
 
+// Batched systems (config 4): the leaf occupancy (each system's depth from its particle count) and the near-field
+// tile of the fastest fmm_velocity_batched, timed as the handle runs it (graph replays when it uses graphs).
+fmm_status fmm_autotune_batched(fmm_handle h, int nsys, const int64_t *offsets, const double *sigmas,
+                                const double *domains, const double *x, const double *y, const double *gamma,
+                                double *u, double *v, int *depths_out)
+{
+    if (!h)
+        return FMM_EINVAL;
+    if (nsys < 1 || nsys > FMM_MAXSYS || !offsets || !depths_out)
+        return set_err(h, FMM_EINVAL, "autotune_batched: nsys in [1, %d], offsets and depths_out given", FMM_MAXSYS);
+    static const double targets[] = {16.0, 32.0, 48.0, 64.0, 96.0, 128.0};
+    static const int tiles[][2] = {{64, 4}, {64, 2}, {128, 4}, {192, 4}, {192, 2}, {128, 2}, {32, 4}, {32, 2}};
+    const int ntile = h->mixed ? 8 : 1;
+    std::vector<int> depths(nsys), best_depths(nsys);
+    const int save_timing = h->timing;
+    h->timing = 0;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bth = h->p2p_threads, bkt = h->p2p_kt;
+    fmm_status st = FMM_OK;
+    for (double tgt : targets) {
+        for (int k = 0; k < nsys; ++k) {
+            const double nk = (double)(offsets[k + 1] - offsets[k]);
+            int d = nk > 0 ? (int)std::lround(std::log(nk / tgt) / std::log(4.0)) : 0;
+            depths[k] = std::max(0, std::min(d, FMM_MAXL));
+        }
+        for (int ti = 0; ti < ntile; ++ti) {
+            h->p2p_threads = tiles[ti][0];
+            h->p2p_kt = tiles[ti][1];
+            float ts[5];
+            bool ok = true;
+            for (int r = 0; r < 7 && ok; ++r) {
+                ok = cudaEventRecord(e0, h->stream) == cudaSuccess &&
+                     (st = fmm_velocity_batched(h, nsys, offsets, depths.data(), sigmas, domains, x, y, gamma, u, v)) ==
+                         FMM_OK &&
+                     cudaEventRecord(e1, h->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+                if (ok && r >= 2)
+                    cudaEventElapsedTime(&ts[r - 2], e0, e1);
+            }
+            if (!ok)
+                break;
+            std::sort(ts, ts + 5);
+            if (ts[2] < best) {
+                best = ts[2];
+                best_depths = depths;
+                bth = tiles[ti][0];
+                bkt = tiles[ti][1];
+            }
+        }
+        if (st != FMM_OK)
+            break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->timing = save_timing;
+    h->p2p_threads = bth;
+    h->p2p_kt = bkt;
+    if (st != FMM_OK)
+        return st;
+    if (best >= 1e30f)
+        return set_err(h, FMM_ECUDA, "autotune_batched: no candidate ran");
+    for (int k = 0; k < nsys; ++k)
+        depths_out[k] = best_depths[k];
+    return FMM_OK;
+}
+
 // Smallest p in [p_lo, p_hi] whose evaluation (the handle's form and tree) is within rel_tol of the FP64 form at
 // p = FMM_PMAX on the same tree, in relative L2 over all particles. The truncation error of the expansions falls
 // geometrically with p (§3's t-term expansions), so the first p that meets the target is the cheapest.

@@ -601,3 +601,29 @@ def test_autotune_p_meets_the_target_against_the_oracle(lib, oracle, precision, 
     f2 = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain)
     p2, est2 = f2.autotune_p(x, y, g, tol, p - 1, p - 1)
     assert p2 == p - 1 and est2 > tol
+
+
+def test_autotune_batched_picks_depths_and_tile(lib, oracle):
+    """fmm_autotune_batched times leaf occupancies and tiles; the chosen depths follow round(log4(N_k / B)) for one
+    of its occupancies B, and the batch evaluated with them matches the oracle per system."""
+    b = fi.batched(nsys=5, nmin=2000, nmax=30000, p=10, seed_index=44)
+    off = b.offsets
+    x = np.concatenate([s.x for s in b.systems])
+    y = np.concatenate([s.y for s in b.systems])
+    g = np.concatenate([s.gamma for s in b.systems])
+    sig = [s.sigma for s in b.systems]
+    doms = [s.domain for s in b.systems]
+    f = lib.FMM(3, b.p, 0.01, precision="mixed", graph=True)
+    xd, yd, gd = dev(x), dev(y), dev(g)
+    prm = f.autotune_batched(off, xd, yd, gd, sigmas=sig, domains=doms)
+    deps = prm["depths"]
+    assert len(deps) == len(b.systems)
+    assert any(all(d == max(0, min(12, round(math.log(s.n / occ, 4)))) for d, s in zip(deps, b.systems))
+               for occ in (16, 32, 48, 64, 96, 128))
+    assert prm["p2p_threads"] in (32, 64, 128, 192) and prm["p2p_targets_per_thread"] in (2, 4)
+    u, v = f.velocity_batched(off, xd, yd, gd, depths=deps, sigmas=sig, domains=doms)
+    f.sync()
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    for k, s in enumerate(b.systems):
+        uo, vo, _ = oracle.fmm(s.x, s.y, s.gamma, s.sigma, deps[k], b.p, domain=s.domain)
+        assert rel_l2((u[off[k]:off[k + 1]], v[off[k]:off[k + 1]]), (uo, vo)) < TOL32, k

@@ -25,6 +25,8 @@
 //   M2P        w(z) += (1/w_s) sum_m a~_m / t^(m+1),                   t = (z - c_s) / w_s
 // Two forms: FP64 throughout, or the precision form (FP32 expansions and FP32 near field on hi + lo split
 // coordinates, FP64 sums per source leaf and at the end).
+#include <type_traits>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -459,6 +461,132 @@ __global__ void __launch_bounds__(128) k_ad_down(Work w, Tables tb, int l)
     }
 }
 
+// Precision form: the same locals with the V list one source per lane. Lane q takes V source q (at most 27: the
+// 36 cells of the parent's 6 x 6 children block, compacted by ballot), forms x_m = (-1)^(m+1) rho^m a~_m, contracts
+// it with the binomials C(m + k, m) by prefix sums (sum_k y_k s^k = u X(u) with u = 1/(1 - s), and multiplying a
+// truncated series by u is a prefix sum of its coefficients: P (P - 1) packed additions, no table), scales by
+// rho^(k+1) and leaves its partial local in shared memory; lane k then adds the V sources' partials of coefficient
+// k, the parent's L2L and the X part. P >= p terms (zero padded).
+typedef unsigned long long ad_f2;
+__device__ __forceinline__ ad_f2 ad_pk2(float a, float b)
+{
+    ad_f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void ad_up2(ad_f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ ad_f2 ad_add2(ad_f2 a, ad_f2 b)
+{
+    ad_f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_ad_down32(Work w, Tables tb, int l)
+{
+    __shared__ float2 part[4][27][P + 1];
+    __shared__ float2 sp[4][FMM_PMAX];
+    __shared__ int vl[4][28];
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SysDev &d = w.sys[0];
+    const Tree t{w.start, d.depth, w.adapt_cap};
+    const int nbx = w.ad_cnt[l], p = w.p, PP = FMM_PMAX, nside = 1 << l;
+    for (int idx = blockIdx.x * 4 + wi; idx < nbx; idx += gridDim.x * 4) {
+        const unsigned m = (unsigned)w.ad_list[d.box0[l] + idx];
+        const int bx = (int)compact1(m), by = (int)compact1(m >> 1);
+        // V candidates: the 36 cells of the parent's 6 x 6 children block, one per lane, compacted by ballot
+        const int px = bx >> 1, py = by >> 1;
+        int nv = 0;
+        for (int base = 0; base < 36; base += 32) {
+            const int q = base + lane;
+            bool ok = false;
+            int ent = 0;
+            if (q < 36) {
+                const int sx = 2 * px - 2 + q % 6, sy = 2 * py - 2 + q / 6;
+                if (sx >= 0 && sy >= 0 && sx < nside && sy < nside && !(abs(sx - bx) <= 1 && abs(sy - by) <= 1) &&
+                    box_exists(t, l, sx, sy)) {
+                    const unsigned ms = morton2(sx, sy);
+                    ok = box_count(t, l, ms) > 0;
+                    ent = (((sy - by + 3) * 7 + (sx - bx + 3)) << 24) | (int)ms;
+                }
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, ok);
+            if (ok)
+                vl[wi][nv + __popc(mk & ((1u << lane) - 1))] = ent;
+            nv += __popc(mk);
+        }
+        // the parent's local for the L2L below
+        if (l >= 3 && lane < p)
+            sp[wi][lane] = loc_of<float>(w, l - 1, m >> 2)[lane];
+        __syncwarp();
+        if (lane < nv) {
+            const int e = vl[wi][lane];
+            const int off = e >> 24;
+            const int ox = off % 7 - 3, oy = off / 7 - 3;
+            const float den = (float)(ox * ox + oy * oy);
+            const float rr = (float)ox / den, ri = -(float)oy / den;  // rho = 1 / (dx + i dy)
+            const float2 *src = mp_of<float>(w, l, (unsigned)(e & 0xffffff));
+            ad_f2 X[P];
+            float pr = 1.f, pi = 0.f;
+#pragma unroll
+            for (int mm = 0; mm < P; ++mm) {
+                const float2 a = mm < p ? src[mm] : make_float2(0.f, 0.f);
+                const float sg = (mm & 1) ? 1.f : -1.f;  // (-1)^(m+1)
+                X[mm] = ad_pk2(sg * (pr * a.x - pi * a.y), sg * (pr * a.y + pi * a.x));
+                const float tt = pr * rr - pi * ri;
+                pi = pr * ri + pi * rr;
+                pr = tt;
+            }
+            ad_f2 T[P];
+            T[0] = X[P - 1];
+#pragma unroll
+            for (int k = 1; k < P; ++k)
+                T[k] = 0ull;
+#pragma unroll
+            for (int mm = P - 2; mm >= -1; --mm) {
+#pragma unroll
+                for (int k = 1; k < P; ++k)
+                    T[k] = ad_add2(T[k], T[k - 1]);
+                if (mm >= 0)
+                    T[0] = ad_add2(T[0], X[mm]);
+            }
+            float qr = rr, qi = ri;  // rho^(k+1)
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                float br, bi;
+                ad_up2(T[k], br, bi);
+                part[wi][lane][k] = make_float2(qr * br - qi * bi, qr * bi + qi * br);
+                const float tt = qr * rr - qi * ri;
+                qi = qr * ri + qi * rr;
+                qr = tt;
+            }
+        }
+        __syncwarp();
+        if (lane < p) {
+            float2 acc = loc_of<float>(w, l, m)[lane];  // the X-list part (k_ad_p2l)
+            if (l >= 3) {
+                const float2 *T = Store<float>::l2l(tb) + (((by & 1) << 1) | (bx & 1)) * PP * PP;  // [input j][output k]
+                for (int j = lane; j < p; ++j) {
+                    const float2 c = T[j * PP + lane], a = sp[wi][j];
+                    acc.x += c.x * a.x - c.y * a.y;
+                    acc.y += c.x * a.y + c.y * a.x;
+                }
+            }
+            float sr = 0.f, si = 0.f;
+            for (int q = 0; q < nv; ++q) {
+                const float2 v = part[wi][q][lane];
+                sr += v.x;
+                si += v.y;
+            }
+            acc.x += sr;
+            acc.y += si;
+            loc_of<float>(w, l, m)[lane] = acc;
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------ leaf of a sorted particle, U / W walk
 
 // The leaf is the first level whose box around the particle holds at most B particles (or level L); the count of
@@ -780,9 +908,13 @@ int sweep_levels(const Work &w, const Tables &t, int part, cudaStream_t s)
             k_ad_p2m<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, l);
         for (int l = L - 1; l >= 2; --l, ++nl)
             k_ad_m2m<R><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
-    } else {  // downward: L2L + M2L + P2L per level
-        for (int l = 2; l <= L; ++l, ++nl)
-            k_ad_down<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
+    } else {  // downward: L2L + M2L (V list) over the X part, per level
+        for (int l = 2; l <= L; ++l, ++nl) {
+            if constexpr (std::is_same<R, float>::value)
+                k_ad_down32<PM><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
+            else
+                k_ad_down<R, PM><<<kSweepBlocks, 128, 0, s>>>(w, t, l);
+        }
     }
     return nl;
 }

@@ -200,6 +200,29 @@ fmm_status fmm_advect(fmm_handle h, int64_t n, double *x, double *y, const doubl
 /* Waits for all work of the handle and returns the first device-side error since the last check. */
 fmm_status fmm_sync(fmm_handle h);
 
+/* Sharded evaluation (§3-§4: P processes each own the subtrees below a level k of the tree; the levels above k,
+ * the "root tree", are formed from every process's level-k multipoles; each process's near field needs the
+ * particles of the leaves next to its own). Both calls need the uniform tree, an explicit root square shared by
+ * all parts (fmm_set_domain) and 2 <= level <= the handle's depth; FMM_EINVAL otherwise.
+ *
+ * fmm_level_multipoles: bins the given particles (device arrays, as fmm_velocity) and forms their multipoles
+ * (P2M, then M2M up to `level`); writes the 4^level boxes of that level, row-major (box = iy 2^level + ix), p
+ * complex coefficients each in the library's radius-scaled form (a_m scaled by w_level^-m, charges -i gamma) as
+ * (re, im) doubles to M_out (DEVICE, 4^level * p * 2 doubles) and the boxes' particle counts to count_out (DEVICE,
+ * 4^level int64). Boxes without particles give zeros. Asynchronous on the handle's stream.
+ *
+ * fmm_velocity_level: fmm_velocity of the given particles in which, once the upward pass has reached `level`, that
+ * level's multipoles and counts are replaced by M_in and count_in (same layout, DEVICE): levels `level` and
+ * coarser then stand for every particle those arrays sum (e.g. the sum over all parts of fmm_level_multipoles),
+ * while finer levels and the near field use the given particles. A part that passes its own particles plus every
+ * particle in the level-`level` boxes adjacent to its own gets, at its own particles, the velocity of the whole
+ * system (the finer levels' interaction lists and the adjacent leaves of its boxes all lie in that neighbourhood);
+ * results at the other particles are not meaningful. */
+fmm_status fmm_level_multipoles(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                                int level, double *M_out, int64_t *count_out);
+fmm_status fmm_velocity_level(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                              int level, const double *M_in, const int64_t *count_in, double *u, double *v);
+
 /* Test of the device-side timeout path (the paper has no counterpart; it checks this library's failure
  * reporting). Launches, on the handle's stream, one thread that waits with the library's bounded mbarrier wait on
  * a barrier that nothing arrives on and no copy targets, giving up after `polls` polls (1 .. 2^20; each poll may

@@ -205,6 +205,31 @@ class FMM:
                                      _dev(u, "u"), _dev(v, "v"), int(depth_lo), int(depth_hi)), self.h)
         return self.params()
 
+    def level_multipoles(self, x, y, gamma, level: int):
+        """(M, counts) of the given particles at tree level `level`: M a (4^level, p) complex128 CUDA tensor in the
+        library's radius-scaled form, counts a (4^level,) int64 CUDA tensor (see fmm_level_multipoles)."""
+        nb = 1 << (2 * int(level))
+        p = self.params()["p"]
+        M = torch.empty((nb, p, 2), dtype=torch.float64, device=x.device)
+        cnt = torch.empty(nb, dtype=torch.int64, device=x.device)
+        self._stream()
+        check(self._lib.fmm_level_multipoles(self.h, x.numel(), _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"),
+                                             int(level), M.data_ptr(), cnt.data_ptr()), self.h)
+        return M, cnt
+
+    def velocity_level(self, x, y, gamma, level: int, M, counts, u=None, v=None):
+        """fmm_velocity with level `level`'s multipoles and counts taken from (M, counts) (fmm_velocity_level)."""
+        n = x.numel()
+        u = torch.empty_like(x) if u is None else u
+        v = torch.empty_like(x) if v is None else v
+        if not (M.is_cuda and M.dtype == torch.float64 and M.is_contiguous() and counts.is_cuda and
+                counts.dtype == torch.int64 and counts.is_contiguous()):
+            raise TypeError("M must be contiguous float64 and counts contiguous int64 CUDA tensors")
+        self._stream()
+        check(self._lib.fmm_velocity_level(self.h, n, _dev(x, "x"), _dev(y, "y"), _dev(gamma, "gamma"), int(level),
+                                           M.data_ptr(), counts.data_ptr(), _dev(u, "u"), _dev(v, "v")), self.h)
+        return u, v
+
     def autotune_batched(self, offsets, x, y, gamma, sigmas=None, domains=None) -> dict:
         """Leaf occupancy (per-system depths) and near-field tile of the fastest batched evaluation; returns the
         handle's parameters plus the chosen "depths"."""

@@ -54,6 +54,10 @@ struct fmm_ctx {
     int coarse = -1;  // precision form: FP32 on every level (radius-scaled translations stay bounded)
     int m2l_engine = FMM_M2L_CUDA_CORES;  // the faster engine at the measured configurations; fmm_autotune re-times both
     int adaptive_cap = 0;  // > 0: adaptive tree (depth = maximum depth), split boxes holding more particles
+    // sharded evaluations: level whose multipoles and counts come from outside (0: none), and the arrays
+    int ext_level = 0;
+    const double2 *ext_M = nullptr;
+    const long long *ext_cnt = nullptr;
     cudaStream_t stream = nullptr;  // caller's stream
     cudaStream_t exec = nullptr;    // internal stream used for graph capture / replay
     cudaStream_t side = nullptr;    // high-priority stream of the multipole sweep
@@ -94,9 +98,9 @@ struct fmm_ctx {
     uint64_t layout_version = 1;
     size_t layout_sig[6] = {};
     struct GKey {
-        int mode, n, nsys, mixed, coarse, m2l_engine, threads, kt, count_pairs, p, timing, adaptive;
+        int mode, n, nsys, mixed, coarse, m2l_engine, threads, kt, count_pairs, p, timing, adaptive, ext_level;
         uint64_t layout;
-        const void *ptr[5];
+        const void *ptr[7];
         uint64_t version;
         void *ws;
     } gkey{};
@@ -595,8 +599,13 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
         CU(cudaEventRecord(h->ev_fork, s));
         CU(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         nl += launch_p2m(w, h->t, 0, h->side);
-        for (int l = w.lv.maxdepth - 1; l >= 2; --l)
+        if (h->ext_level == w.lv.maxdepth)
+            nl += launch_level_import(w, h->ext_level, h->ext_M, h->ext_cnt, h->side);
+        for (int l = w.lv.maxdepth - 1; l >= 2; --l) {
             nl += launch_m2m(w, h->t, l, 0, h->side, 1);
+            if (l == h->ext_level)  // the coarse levels carry every particle the given level stands for
+                nl += launch_level_import(w, l, h->ext_M, h->ext_cnt, h->side);
+        }
         if (timed)
             CU(record_timing(h->ev_t[2], h->side));
         nl += launch_m2l(w, h->t, 0, h->side, 1);
@@ -688,6 +697,9 @@ static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x
     key.ptr[2] = g;
     key.ptr[3] = u;
     key.ptr[4] = v;
+    key.ext_level = h->ext_level;
+    key.ptr[5] = h->ext_M;
+    key.ptr[6] = h->ext_cnt;
     key.version = h->cfg_version;
     key.ws = h->ws;
     if (!h->gexec || memcmp(&key, &h->gkey, sizeof key) != 0) {
@@ -1305,6 +1317,81 @@ fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const 
     h->status_pending = 1;
     h->launches += nl;
     return FMM_OK;
+}
+
+static fmm_status check_level(fmm_handle h, int level)
+{
+    if (h->adaptive_cap)
+        return set_err(h, FMM_EINVAL, "level exchange needs the uniform tree (adaptive capacity is set)");
+    if (!h->has_domain)
+        return set_err(h, FMM_EINVAL, "level exchange needs an explicit root square shared by every part");
+    if (level < 2 || level > h->depth)
+        return set_err(h, FMM_EINVAL, "level must be in [2, depth = %d]", h->depth);
+    return FMM_OK;
+}
+
+fmm_status fmm_level_multipoles(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                                int level, double *M_out, int64_t *count_out)
+{
+    fmm_status st = check_common(h, n, x, y, gamma, x, y);
+    if (st != FMM_OK)
+        return st;
+    if ((st = check_level(h, level)) != FMM_OK)
+        return st;
+    if (!M_out || !count_out)
+        return set_err(h, FMM_EINVAL, "NULL output");
+    if ((st = poll_status(h, false)) != FMM_OK)
+        return st;
+    const size_t nb = (size_t)1 << (2 * level);
+    if (n == 0) {
+        CU(cudaMemsetAsync(M_out, 0, nb * h->p * 2 * sizeof(double), h->stream));
+        CU(cudaMemsetAsync(count_out, 0, nb * sizeof(int64_t), h->stream));
+        return FMM_OK;
+    }
+    set_single_system(h, n);
+    if ((st = ensure_tables(h)) != FMM_OK || (st = ensure_workspace(h, n, 0)) != FMM_OK ||
+        (st = upload_systems(h)) != FMM_OK)
+        return st;
+    Work &w = h->w;
+    cudaStream_t s = h->stream;
+    int64_t nl = 0;
+    (void)cudaGetLastError();
+    CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
+    nl += launch_domain_finalize(w, s);
+    nl += launch_keys(w, x, y, gamma, s);
+    nl += launch_scan(w, s);
+    nl += launch_scatter_sort(w, s);
+    nl += launch_gather(w, x, y, gamma, nullptr, nullptr, s);
+    nl += launch_p2m(w, h->t, 0, s);
+    for (int l = w.lv.maxdepth - 1; l >= level; --l)
+        nl += launch_m2m(w, h->t, l, 0, s, 1);
+    nl += launch_level_export(w, level, (double2 *)M_out, (long long *)count_out, s);
+    CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(h->ev_status, s));
+    CU(cudaGetLastError());
+    h->status_pending = 1;
+    h->launches += nl;
+    return FMM_OK;
+}
+
+fmm_status fmm_velocity_level(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
+                              int level, const double *M_in, const int64_t *count_in, double *u, double *v)
+{
+    fmm_status st = check_common(h, n, x, y, gamma, u, v);
+    if (st != FMM_OK)
+        return st;
+    if ((st = check_level(h, level)) != FMM_OK)
+        return st;
+    if (!M_in || !count_in)
+        return set_err(h, FMM_EINVAL, "NULL level arrays");
+    h->ext_level = level;
+    h->ext_M = (const double2 *)M_in;
+    h->ext_cnt = (const long long *)count_in;
+    st = velocity_mode(h, MODE_FULL, n, x, y, gamma, u, v);
+    h->ext_level = 0;
+    h->ext_M = nullptr;
+    h->ext_cnt = nullptr;
+    return st;
 }
 
 fmm_status fmm_selftest_timeout(fmm_handle h, int polls)

@@ -204,6 +204,10 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s);  // threads 
                                                                      // 128: symmetric, 192: per source row
 int launch_rk_stage(int64_t n, double *x, double *y, double *tx, double *ty, const double *u, const double *v,
                     double *au, double *av, double b, double c_next, double dt, int first, int last, cudaStream_t s);
+// Sharded evaluations: level l's multipoles (double2, 4^l * p, boxes row-major) and box counts of the first system
+// out of / into the tree.
+int launch_level_export(const Work &w, int l, double2 *dst, long long *cnt, cudaStream_t s);
+int launch_level_import(const Work &w, int l, const double2 *src, const long long *cnt, cudaStream_t s);
 int launch_l2p(const Work &w, cudaStream_t s);  // precision form with far32: far field into far32 (stage 8)
 int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
 int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far

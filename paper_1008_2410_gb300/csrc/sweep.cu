@@ -584,6 +584,66 @@ int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio
     return n;
 }
 
+// ------------------------------------------------------------------ level exchange of sharded evaluations
+
+// Level l's multipoles (radius-scaled, in the level's storage precision) and box particle counts of the first
+// system, to dst (4^l * p double2, boxes row-major) and cnt (4^l); boxes without particles give zeros (their
+// multipoles are never written by P2M / M2M).
+__global__ void k_level_export(Work w, int l, double2 *__restrict__ dst, long long *__restrict__ cnt)
+{
+    const SysDev &d = w.sys[0];
+    const int p = w.p;
+    const int64_t nb = (int64_t)1 << (2 * l), i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nb * p)
+        return;
+    const int64_t b = i / p, box = d.box0[l] + b;
+    const int c = w.bcount[box];
+    if (i - b * p == 0)
+        cnt[b] = c;
+    double2 v = make_double2(0.0, 0.0);
+    if (c != 0) {
+        if (level_fp64(w, l)) {
+            v = w.M64[box * p + (i - b * p)];
+        } else {
+            const float2 f = w.M32[box * p + (i - b * p)];
+            v = make_double2((double)f.x, (double)f.y);
+        }
+    }
+    dst[i] = v;
+}
+
+// The reverse: level l's multipoles and counts of the first system from src / cnt (same layout).
+__global__ void k_level_import(Work w, int l, const double2 *__restrict__ src, const long long *__restrict__ cnt)
+{
+    const SysDev &d = w.sys[0];
+    const int p = w.p;
+    const int64_t nb = (int64_t)1 << (2 * l), i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nb * p)
+        return;
+    const int64_t b = i / p, box = d.box0[l] + b;
+    if (i - b * p == 0)
+        w.bcount[box] = (int)cnt[b];
+    const double2 v = src[i];
+    if (level_fp64(w, l))
+        w.M64[box * p + (i - b * p)] = v;
+    else
+        w.M32[box * p + (i - b * p)] = make_float2((float)v.x, (float)v.y);
+}
+
+int launch_level_export(const Work &w, int l, double2 *dst, long long *cnt, cudaStream_t s)
+{
+    const int64_t items = ((int64_t)1 << (2 * l)) * w.p;
+    k_level_export<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(w, l, dst, cnt);
+    return 1;
+}
+
+int launch_level_import(const Work &w, int l, const double2 *src, const long long *cnt, cudaStream_t s)
+{
+    const int64_t items = ((int64_t)1 << (2 * l)) * w.p;
+    k_level_import<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(w, l, src, cnt);
+    return 1;
+}
+
 // ------------------------------------------------------------------ stage 7: L2L (block = the 4 children of a parent)
 
 // Four warps, one per child of one parent box at level l, lane k = coefficient; the parent's local expansion is

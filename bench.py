@@ -305,11 +305,15 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
     ke = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    each = []
     for _ in range(ke):
-        f.velocity_host(xh, yh, gh, uh, vh)
+        t1 = time.perf_counter()
+        f.velocity_host(xh, yh, gh, uh, vh)  # synchronous: returns once u, v are in host memory
+        each.append(time.perf_counter() - t1)
     te = (time.perf_counter() - t0) / ke
     out["e2e"] = {"value": n / te / 1e6, "unit": "Mparticles/s", "h2d_bytes_per_step": 3 * 8 * n,
-                  "d2h_bytes_per_step": 2 * 8 * n, "ms_per_step": te * 1e3}
+                  "d2h_bytes_per_step": 2 * 8 * n, "ms_per_step": te * 1e3, "calls": ke,
+                  "ms_min_median_max": [1e3 * min(each), 1e3 * statistics.median(each), 1e3 * max(each)]}
 
     # the paper's overlap bound (§4) with P = resident warps of this GPU
     from paper_1008_2410_gb300 import model
@@ -648,8 +652,11 @@ def clustered_leg(api, precision, flush, stream, max_depth: int = 11, leaf_capac
     fa.velocity_host(xh, yh, gh, uh, vh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    each = []
     for _ in range(3):
+        t1 = time.perf_counter()
         fa.velocity_host(xh, yh, gh, uh, vh)
+        each.append(time.perf_counter() - t1)
     te = (time.perf_counter() - t0) / 3
     fa.close()
     torch.cuda.synchronize()
@@ -666,7 +673,9 @@ def clustered_leg(api, precision, flush, stream, max_depth: int = 11, leaf_capac
                               "sweep": ov_a, "exposed_sweep_ms": ov_a["exposed_sweep_ms"],
                               "hidden_fraction": ov_a["hidden_fraction"],
                               "e2e": {"value": w.n / te / 1e6, "unit": "Mparticles/s", "ms_per_step": te * 1e3,
-                                      "h2d_bytes_per_step": 3 * 8 * w.n, "d2h_bytes_per_step": 2 * 8 * w.n},
+                                      "h2d_bytes_per_step": 3 * 8 * w.n, "d2h_bytes_per_step": 2 * 8 * w.n,
+                                      "ms_min_median_max": [1e3 * min(each), 1e3 * statistics.median(each),
+                                                            1e3 * max(each)]},
                               "autotuned": {"leaf_capacity": tuned_a["leaf_capacity"],
                                             "value": w.n / (statistics.median(mst) / 1e3) / 1e6,
                                             "ms_per_step": statistics.median(mst)}},

@@ -522,12 +522,23 @@ def adjoint_leg(api, w, x, y, g, flush, stream) -> dict:
     gu, gv = u - us, v - vs
     f.adjoint(x, y, g, gu, gv)
     ms, _ = timed_steps(lambda: f.adjoint(x, y, g, gu, gv), 3, flush, stream)
+    dg, dx, dy = f.adjoint(x, y, g, gu, gv)
+    # the near-field part in FP32 (fmm_set_adjoint_precision): time and distance from the FP64 adjoint
+    f.set_adjoint_precision("mixed")
+    f.adjoint(x, y, g, gu, gv)
+    ms32, _ = timed_steps(lambda: f.adjoint(x, y, g, gu, gv), 5, flush, stream)
+    dg32, dx32, dy32 = f.adjoint(x, y, g, gu, gv)
     f.sync()
     f.close()
     t = st_.median(ms)
+    t32 = st_.median(ms32)
+    rel = lambda a, b: float(torch.sqrt(sum(((p - q) ** 2).sum() for p, q in zip(a, b)) / sum((q**2).sum() for q in b)))
     loss = float(0.5 * (gu * gu + gv * gv).sum())
     out = {"form": "fp64", "loss": "1/2 |u - u*|^2, u* from gamma + 0.01 N(0,1)/N", "loss_value": loss,
-           "ms_per_step": t, "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s"}
+           "ms_per_step": t, "value": w.n / (t / 1e3) / 1e6, "unit": "Mparticles/s",
+           "fp32_near_field": {"ms_per_step": t32, "value": w.n / (t32 / 1e3) / 1e6, "unit": "Mparticles/s",
+                               "rel_diff_dgamma_vs_fp64": rel((dg32,), (dg,)),
+                               "rel_diff_dxdy_vs_fp64": rel((dx32, dy32), (dx, dy))}}
     # the same loss on a 2^16-particle case of the recipe (depth 5): the oracle's adjoint of all particles takes
     # about 40 s at 2^20 (that size is checked by the GPU tests), a few seconds here
     ws = fi.uniform(1 << 16, seed_index=1, depth=5, p=w.p)  # sigma = 0.5 / sqrt(N), as the recipe

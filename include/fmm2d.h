@@ -173,9 +173,18 @@ fmm_status fmm_velocity_far(fmm_handle h, int64_t n, const double *x, const doub
 /* Adjoint (reverse-mode derivative) of fmm_velocity for a loss L with dL/du = gu, dL/dv = gv (device FP64):
  * writes dL/dgamma, dL/dx, dL/dy (device FP64; any output may be NULL to skip it). The far field's
  * transpose is evaluated exactly (the truncated far-field operator of this tree is antisymmetric), so finite
- * differences of fmm_velocity agree to rounding as long as no particle changes leaf. Always FP64. */
+ * differences of fmm_velocity agree to rounding as long as no particle changes leaf. FP64 unless
+ * fmm_set_adjoint_precision chose FP32 for the near-field part. */
 fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,
                                 const double *gu, const double *gv, double *dgamma, double *dx, double *dy);
+
+/* Precision of the adjoint's near-field part (its dominant cost: every adjacent pair with K_sigma's Jacobian).
+ * FMM_FP64 (default): FP64 throughout, the exact transpose to rounding (finite differences of fmm_velocity agree
+ * to rounding). FMM_MIXED: that part in FP32 on leaf-relative coordinates (the forward precision form's units; the
+ * small-r factors of K_sigma and of its derivative from their series), FP64 sums across rows of leaves; systems
+ * whose leaves are wider than about 38 sigma keep FP64; the far-field part stays FP64. Agrees with the FP64 adjoint
+ * to about 1e-6 relative. */
+fmm_status fmm_set_adjoint_precision(fmm_handle h, fmm_precision mode);
 
 /* nsys independent systems in one evaluation (one launch per stage across all systems). offsets (HOST,
  * nsys + 1 entries, non-decreasing, offsets[0] = 0) delimit each system's particles in the device arrays.

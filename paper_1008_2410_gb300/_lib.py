@@ -50,6 +50,7 @@ SIGNATURES = {
     "fmm_advect": (_I, [_P, _I64, _P, _P, _P, _D, _I, _I]),
     "fmm_sync": (_I, [_P]),
     "fmm_selftest_timeout": (_I, [_P, _I]),
+    "fmm_set_adjoint_precision": (_I, [_P, _I]),
     "fmm_level_multipoles": (_I, [_P, _I64, _P, _P, _P, _I, _P, _P]),
     "fmm_velocity_level": (_I, [_P, _I64, _P, _P, _P, _I, _P, _P, _P, _P]),
     "fmm_set_timing": (_I, [_P, _I]),

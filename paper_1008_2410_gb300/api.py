@@ -88,6 +88,12 @@ class FMM:
         code = {"cuda_cores": 0, "tensor": 1}[engine]
         check(self._lib.fmm_set_m2l_engine(self.h, code), self.h)
 
+    def set_adjoint_precision(self, precision: str) -> None:
+        """Near-field part of the adjoint: "fp64" (default, exact to rounding) or "mixed" (FP32, ~1e-6)."""
+        mode = {"fp64": FMM_FP64, "mixed": FMM_MIXED}[precision]
+        check(self._lib.fmm_set_adjoint_precision(self.h, mode), self.h)
+        self.adjoint_precision = precision
+
     def set_adaptive(self, leaf_capacity: int) -> None:
         """0: uniform tree; B > 0: adaptive tree splitting boxes with more than B particles."""
         check(self._lib.fmm_set_adaptive(self.h, int(leaf_capacity)), self.h)

@@ -54,6 +54,7 @@ struct fmm_ctx {
     int coarse = -1;  // precision form: FP32 on every level (radius-scaled translations stay bounded)
     int m2l_engine = FMM_M2L_CUDA_CORES;  // the faster engine at the measured configurations; fmm_autotune re-times both
     int adaptive_cap = 0;  // > 0: adaptive tree (depth = maximum depth), split boxes holding more particles
+    int adj_fp32 = 0;      // near-field part of the adjoint in FP32 (fmm_set_adjoint_precision)
     // sharded evaluations: level whose multipoles and counts come from outside (0: none), and the arrays
     int ext_level = 0;
     const double2 *ext_M = nullptr;
@@ -1306,7 +1307,7 @@ fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const 
         CU(cudaEventRecord(h->ev_join, h->side));
     }
     // near field written to the outputs first; the far part is added after the join
-    nl += launch_adjoint_p2p(w, dgamma, dx, dy, s);
+    nl += launch_adjoint_p2p(w, dgamma, dx, dy, h->adj_fp32, s);
     if (far) {
         CU(cudaStreamWaitEvent(s, h->ev_join, 0));
         nl += launch_adjoint_combine(w, dgamma, dx, dy, s);
@@ -1409,6 +1410,14 @@ fmm_status fmm_selftest_timeout(fmm_handle h, int polls)
     CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaEventRecord(h->ev_status, h->stream));
     h->status_pending = 1;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_adjoint_precision(fmm_handle h, fmm_precision mode)
+{
+    if (!h || (mode != FMM_FP64 && mode != FMM_MIXED))
+        return FMM_EINVAL;
+    h->adj_fp32 = mode == FMM_MIXED;
     return FMM_OK;
 }
 

@@ -212,7 +212,7 @@ int launch_l2p(const Work &w, cudaStream_t s);  // precision form with far32: fa
 int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s);
 int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far
 int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);  // adds it
-int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);
+int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, int fp32, cudaStream_t s);
 
 // Adaptive tree (adaptive.cu, single system, keys in Morton order, sorted FP64 particles and, in the precision form,
 // the split records written by the leaf-order kernel). Side stream: the upward pass (box lists, P2L over X, P2M,

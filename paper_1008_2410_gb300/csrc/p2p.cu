@@ -984,7 +984,7 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
 //   dy_k     += (gamma_m gu_k - gamma_k gu_m) dKu/db + (gamma_m gv_k - gamma_k gv_m) dKv/db
 // (K is odd and its Jacobian even in z). Writes the near part in caller order (the far part is added later).
 __global__ void __launch_bounds__(64) k_adjoint_p2p64(Work w, double *__restrict__ odg, double *__restrict__ odx,
-                                                     double *__restrict__ ody)
+                                                     double *__restrict__ ody, int skip_plain)
 {
     __shared__ double shx[256], shy[256], shg[256], shu[256], shv[256];
     int leaf = blockIdx.x;
@@ -993,6 +993,8 @@ __global__ void __launch_bounds__(64) k_adjoint_p2p64(Work w, double *__restrict
         return;
     int k = w.nsys == 1 ? 0 : find_sys_by_leaf(w.sys, w.nsys, leaf);
     const SysDev &d = w.sys[k];
+    if (skip_plain && !(d.s_unit > P2P_SPLIT_S))
+        return;  // this system's near field is the FP32 kernel's
     int L = d.depth, ns = 1 << L, local = leaf - (int)d.leaf0;
     int ix = local & (ns - 1), iy = local >> L;
     double k2 = 1.0 / (2.0 * d.sigma * d.sigma);
@@ -1058,12 +1060,143 @@ __global__ void __launch_bounds__(64) k_adjoint_p2p64(Work w, double *__restrict
     }
 }
 
-int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s)
+// Precision form of the same near-field adjoint. Lengths in units r' = lambda r, lambda = s / w_L, with s the
+// system's s_unit, so that exp(-r^2 / 2 sigma^2) = 2^-(r'^2) (the forward's units); F(t) = (1 - 2^-t) / t and
+// F'(t) at t = r'^2 give, with C = lambda * snear (snear = lambda / 2 pi):
+//   Ku = -b' F snear,  Kv = a' F snear,
+//   dKu/da = -2 a'b' F' C,  dKu/db = -(F + 2 b'^2 F') C,  dKv/da = (F + 2 a'^2 F') C,  dKv/db = 2 a'b' F' C,
+// F' = (ln2 2^-t - F) / t. Below t = 1/(2 ln2) both come from series in y = t ln2 (g(y) = (1 - e^-y)/y and
+// g'(y), the terms of their Taylor series, F = ln2 g, F' = ln2^2 g'), behind a warp-uniform branch. Coordinates
+// relative to the target leaf's centre, formed in FP64 and rounded once to FP32 (|a'| <= 1.5 s); one target per
+// thread, sources staged per row of leaves in shared memory as FP32; FP32 sums per row, FP64 across rows.
+__device__ __forceinline__ void adj_small(float t, float &F, float &Fp)
+{
+    const float y = t * P2P_LN2;
+    // g(y) = sum_k (-y)^k / (k+1)!, g'(y) = sum_{k>=1} k (-y)^(k-1) (-1) / (k+1)!, to y^8
+    float g = 1.0f / 362880.0f;
+    g = fmaf(g, -y, 1.0f / 40320.0f);
+    g = fmaf(g, -y, 1.0f / 5040.0f);
+    g = fmaf(g, -y, 1.0f / 720.0f);
+    g = fmaf(g, -y, 1.0f / 120.0f);
+    g = fmaf(g, -y, 1.0f / 24.0f);
+    g = fmaf(g, -y, 1.0f / 6.0f);
+    g = fmaf(g, -y, 0.5f);
+    g = fmaf(g, -y, 1.0f);
+    float d = -9.0f / 3628800.0f;
+    d = fmaf(d, y, 8.0f / 362880.0f);
+    d = fmaf(d, y, -7.0f / 40320.0f);
+    d = fmaf(d, y, 6.0f / 5040.0f);
+    d = fmaf(d, y, -5.0f / 720.0f);
+    d = fmaf(d, y, 4.0f / 120.0f);
+    d = fmaf(d, y, -3.0f / 24.0f);
+    d = fmaf(d, y, 2.0f / 6.0f);
+    d = fmaf(d, y, -0.5f);
+    F = P2P_LN2 * g;
+    Fp = (P2P_LN2 * P2P_LN2) * d;
+}
+
+#define ADJ_TILE 256
+
+__global__ void __launch_bounds__(64) k_adjoint_p2p32(Work w, double *__restrict__ odg, double *__restrict__ odx,
+                                                      double *__restrict__ ody)
+{
+    __shared__ float shx[ADJ_TILE], shy[ADJ_TILE], shg[ADJ_TILE], shu[ADJ_TILE], shv[ADJ_TILE];
+    const int leaf = blockIdx.x;
+    const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
+    if (c == 0)
+        return;
+    const int k = w.nsys == 1 ? 0 : find_sys_by_leaf(w.sys, w.nsys, leaf);
+    const SysDev &d = w.sys[k];
+    if (d.s_unit > P2P_SPLIT_S)
+        return;  // leaves wider than the one-float bound: the FP64 kernel
+    const int L = d.depth, ns = 1 << L, local = leaf - (int)d.leaf0;
+    const int ix = local & (ns - 1), iy = local >> L;
+    const double lam = (double)d.s_unit / d.wl;
+    const double cx = d.x0 + (ix + 0.5) * d.wl, cy = d.y0 + (iy + 0.5) * d.wl;
+    const float snear = d.snear, C = (float)(lam * (double)d.snear);
+    const int jx0 = ix > 0 ? ix - 1 : 0, jx1 = ix < ns - 1 ? ix + 1 : ns - 1;
+    for (int t0 = 0; t0 < c; t0 += blockDim.x) {
+        const int tpos = s0 + t0 + threadIdx.x;
+        const bool valid = t0 + threadIdx.x < c;
+        float xt = 0.f, yt = 0.f, gt = 0.f, gut = 0.f, gvt = 0.f;
+        if (valid) {
+            xt = (float)((w.sx[tpos] - cx) * lam);
+            yt = (float)((w.sy[tpos] - cy) * lam);
+            gt = (float)w.sg[tpos];
+            gut = (float)w.sgu[tpos];
+            gvt = (float)w.sgv[tpos];
+        }
+        double ag = 0.0, ax = 0.0, ay = 0.0;
+        for (int dyr = -1; dyr <= 1; ++dyr) {
+            const int row = iy + dyr;
+            if (row < 0 || row >= ns)
+                continue;
+            const int r0 = w.start[d.leaf0 + row * ns + jx0], r1 = w.start[d.leaf0 + row * ns + jx1 + 1];
+            float pg = 0.f, px = 0.f, py = 0.f;
+            for (int q0 = r0; q0 < r1; q0 += ADJ_TILE) {
+                const int m = min(ADJ_TILE, r1 - q0);
+                __syncthreads();
+                for (int j = threadIdx.x; j < m; j += blockDim.x) {
+                    shx[j] = (float)((w.sx[q0 + j] - cx) * lam);
+                    shy[j] = (float)((w.sy[q0 + j] - cy) * lam);
+                    shg[j] = (float)w.sg[q0 + j];
+                    shu[j] = (float)w.sgu[q0 + j];
+                    shv[j] = (float)w.sgv[q0 + j];
+                }
+                __syncthreads();
+                for (int j = 0; j < m; ++j) {
+                    const float a = xt - shx[j], b = yt - shy[j];
+                    const float t = fmaf(a, a, b * b);
+                    const float e = ex2_approx(-t), q = rcp_approx(fmaxf(t, 1e-30f));
+                    float F = (1.0f - e) * q;
+                    float Fp = fmaf(P2P_LN2, e, -F) * q;
+                    if (__any_sync(0xffffffffu, t < P2P_THR)) {
+                        if (t < P2P_THR) {
+                            float Fs, Fps;
+                            adj_small(t, Fs, Fps);
+                            F = Fs;
+                            Fp = Fps;
+                        }
+                    }
+                    if (t > 0.f) {  // a particle and itself, or coincident particles: K = 0
+                        // dgamma_k -= gu_m Ku + gv_m Kv = F (gu_m b' - gv_m a') (times snear)
+                        pg = fmaf(F, fmaf(shu[j], b, -shv[j] * a), pg);
+                        const float cu = fmaf(shg[j], gut, -gt * shu[j]), cv = fmaf(shg[j], gvt, -gt * shv[j]);
+                        const float A = 2.0f * a * b * Fp;
+                        const float B1 = fmaf(2.0f * a * a, Fp, F), B2 = fmaf(2.0f * b * b, Fp, F);
+                        px = fmaf(cv, B1, fmaf(-cu, A, px));  // cu dKu/da + cv dKv/da (times C)
+                        py = fmaf(cv, A, fmaf(-cu, B2, py));  // cu dKu/db + cv dKv/db (times C)
+                    }
+                }
+            }
+            ag += (double)pg;
+            ax += (double)px;
+            ay += (double)py;
+        }
+        if (valid) {
+            const int i = w.perm[tpos];
+            if (odg)
+                odg[i] = ag * snear;
+            if (odx)
+                odx[i] = ax * C;
+            if (ody)
+                ody[i] = ay * C;
+        }
+    }
+}
+
+int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, int fp32, cudaStream_t s)
 {
     if (w.nleaf == 0)
         return 0;
-    k_adjoint_p2p64<<<w.nleaf, 64, 0, s>>>(w, dg, dx, dy);
-    return 1;
+    if (!fp32) {
+        k_adjoint_p2p64<<<w.nleaf, 64, 0, s>>>(w, dg, dx, dy, 0);
+        return 1;
+    }
+    // one-float systems in FP32, systems with wider leaves in FP64
+    k_adjoint_p2p32<<<w.nleaf, 64, 0, s>>>(w, dg, dx, dy);
+    k_adjoint_p2p64<<<w.nleaf, 64, 0, s>>>(w, dg, dx, dy, 1);
+    return 2;
 }
 
 }  // namespace fmm

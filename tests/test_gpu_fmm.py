@@ -298,6 +298,27 @@ def test_adjoint_matches_oracle(lib, oracle):
     assert rel_l2((dx.cpu().numpy(), dy.cpu().numpy()), (ox, oy)) < 1e-10
 
 
+@pytest.mark.parametrize("name,make,tol", [
+    ("uniform6000_d4_p12", lambda: fi.uniform(6000, seed_index=44, depth=4, p=12), 1e-6),
+    ("clustered20k_d5_p14", lambda: fi.clustered(20000, depth=5, p=14), 5e-6),
+    ("lattice_lamb_oseen", lambda: fi.lattice_lamb_oseen(), 1e-6),
+])
+def test_adjoint_fp32_near_field_matches_oracle(lib, oracle, name, make, tol):
+    """fmm_set_adjoint_precision(FMM_MIXED): the near-field part of the adjoint in FP32 (series for the small-r
+    factors of K_sigma and its derivative) against the oracle's transposed stages; dense leaves (the clustered case)
+    carry the largest FP32 coordinate rounding."""
+    w = make()
+    rs = np.random.default_rng(9)
+    gu, gv = rs.normal(size=w.n), rs.normal(size=w.n)
+    f = lib.FMM(w.depth, w.p, w.sigma, domain=w.domain)
+    f.set_adjoint_precision("mixed")
+    dg, dx, dy = f.adjoint(dev(w.x), dev(w.y), dev(w.gamma), dev(gu), dev(gv))
+    f.sync()
+    og, ox, oy = oracle.fmm_adjoint(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, gu, gv, domain=w.domain)
+    assert rel_l2((dg.cpu().numpy(),), (og,)) < tol
+    assert rel_l2((dx.cpu().numpy(), dy.cpu().numpy()), (ox, oy)) < 2 * tol
+
+
 def test_autograd_function_finite_differences(lib):
     w = fi.uniform(3000, seed_index=45, depth=3, p=14)
     f = lib.FMM(w.depth, w.p, w.sigma, domain=w.domain)

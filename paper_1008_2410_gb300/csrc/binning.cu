@@ -219,8 +219,15 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
         float hx, lx, hy, ly;
         frac_to_split(Fx, d.s_unit, &hx, &lx);
         frac_to_split(Fy, d.s_unit, &hy, &ly);
-        w.pos4u[i] = make_float4(hx, hy, lx, ly);
-        w.g32u[i] = __double2float_rn(g[i]);
+        w.pos4u[2 * (int64_t)i] = make_float4(hx, hy, lx, ly);
+        w.pos4u[2 * (int64_t)i + 1] = make_float4(__double2float_rn(g[i]), 0.f, 0.f, 0.f);
+    } else if (w.rec64) {
+        Rec64 r;
+        r.x = xi;
+        r.y = yi;
+        r.g = g[i];
+        r.pad = 0.0;
+        w.rec64[i] = r;
     }
 }
 
@@ -473,12 +480,13 @@ int launch_scan(const Work &w, cudaStream_t s)
 // ------------------------------------------------------------------ counting-sort scatter and in-leaf order
 
 __global__ void k_scatter(int n, const int *__restrict__ key, const int *__restrict__ slot,
-                          const int *__restrict__ start, int *tmp)
+                          const int *__restrict__ start, int2 *tmp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    tmp[start[key[i]] + slot[i]] = i;
+    const int k = key[i];
+    tmp[start[k] + slot[i]] = make_int2(i, k);  // caller index and leaf, at the leaf's arrival slot
 }
 
 int launch_scatter_sort(const Work &w, cudaStream_t s)
@@ -500,13 +508,23 @@ __device__ __forceinline__ void place_particle(const Work &w, int v, int pos, in
         w.iperm[v] = pos;
     w.sleaf[pos] = leaf;
     if (mixed) {
-        const float4 p = w.pos4u[v];
-        const float gg = w.g32u[v];
+        const float4 p = w.pos4u[2 * (int64_t)v];
+        const float gg = w.pos4u[2 * (int64_t)v + 1].x;
         w.eh[pos] = make_float4(p.x, p.x, p.y, p.y);
         w.el[pos] = make_float4(p.z, p.z, p.w, p.w);
         w.eg[pos] = make_float4(gg, gg, -gg, -gg);
     } else {
-        const double xv = x[v], yv = y[v], gv0 = g[v];
+        double xv, yv, gv0;
+        if (w.rec64) {
+            const Rec64 r = w.rec64[v];
+            xv = r.x;
+            yv = r.y;
+            gv0 = r.g;
+        } else {
+            xv = x[v];
+            yv = y[v];
+            gv0 = g[v];
+        }
         w.sx[pos] = xv;
         w.sy[pos] = yv;
         w.sg[pos] = gv0;
@@ -531,13 +549,13 @@ __device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, int *t
     const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
     for (int e0 = 0; e0 < c; e0 += blockDim.x) {
         const int e = e0 + threadIdx.x;
-        const int v = e < c ? w.tmp[s0 + e] : 0;
+        const int v = e < c ? w.tmp[s0 + e].x : 0;
         int rank = 0;
         for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
             const int m = min(SORT_TILE, c - f0);
             __syncthreads();
             for (int j = threadIdx.x; j < m; j += blockDim.x)
-                tile[j] = w.tmp[s0 + f0 + j];
+                tile[j] = w.tmp[s0 + f0 + j].x;
             __syncthreads();
             if (e < c)
                 for (int j = 0; j < m; ++j)
@@ -548,76 +566,66 @@ __device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, int *t
     }
 }
 
-// Leaf order. The uniform tree (and any tree up to 2^16 leaves): one block per leaf. The adaptive tree's depth-L
-// cells (millions, mostly empty, a few tens of particles at most): each block strides over chunks of 64 cells,
-// lists the chunk's non-empty ones, ranks those of at most 128 particles with one warp each (shuffles, no block
-// barrier) and the rest with the block.
-__global__ void __launch_bounds__(64) k_leaf_order(Work w, const double *__restrict__ x, const double *__restrict__ y,
+// Leaf order: each leaf's arrival order (atomic slots) is replaced by the caller's order, so that every run gives
+// bit-identical results. The adaptive tree's cells: one thread per sorted position: its entry (caller index v, leaf) says which leaf run it
+// is in; its rank is the number of entries of that run with a smaller caller index (the run's entries are read by
+// every thread of the run, so a warp's reads of one leaf coalesce). Leaves holding more than kSmallLeaf particles
+// are listed (by their first position) and ranked with a whole block each instead, through shared-memory tiles.
+constexpr int kSmallLeaf = 128;
+
+__global__ void __launch_bounds__(256) k_leaf_rank(Work w, const double *__restrict__ x, const double *__restrict__ y,
+                                                   const double *__restrict__ g, const double *__restrict__ gu,
+                                                   const double *__restrict__ gv, int mixed)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.n)
+        return;
+    const int2 e = w.tmp[p];
+    const int leaf = e.y, s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
+    if (c > kSmallLeaf) {
+        if (p == s0)
+            w.big[atomicAdd(w.big_cnt, 1)] = leaf;
+        return;
+    }
+    int rank = 0;
+    for (int q = s0; q < s0 + c; ++q)
+        rank += w.tmp[q].x < e.x;
+    place_particle(w, e.x, s0 + rank, leaf, x, y, g, gu, gv, mixed);
+}
+
+__global__ void __launch_bounds__(128) k_leaf_big(Work w, const double *__restrict__ x, const double *__restrict__ y,
+                                                  const double *__restrict__ g, const double *__restrict__ gu,
+                                                  const double *__restrict__ gv, int mixed)
+{
+    __shared__ int tile[SORT_TILE];
+    const int nb = *w.big_cnt;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x)  // block-uniform
+        order_leaf_block(w, w.big[b], tile, x, y, g, gu, gv, mixed);
+}
+
+// The uniform tree (tens of particles in each of at most millions of leaves): one block per leaf.
+__global__ void __launch_bounds__(64) k_leaf_block(Work w, const double *__restrict__ x, const double *__restrict__ y,
                                                    const double *__restrict__ g, const double *__restrict__ gu,
                                                    const double *__restrict__ gv, int mixed)
 {
     __shared__ int tile[SORT_TILE];
-    __shared__ int small[64], big[64];
-    __shared__ int nsmall, nbig;
-    if (gridDim.x >= w.nleaf) {
-        order_leaf_block(w, blockIdx.x, tile, x, y, g, gu, gv, mixed);
-        return;
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int base = blockIdx.x * 64; base < w.nleaf; base += gridDim.x * 64) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            nsmall = 0;
-            nbig = 0;
-        }
-        __syncthreads();
-        const int lf = base + (int)threadIdx.x;
-        if (lf < w.nleaf) {
-            const int c = w.start[lf + 1] - w.start[lf];
-            if (c > 128)
-                big[atomicAdd(&nbig, 1)] = lf;
-            else if (c > 0)
-                small[atomicAdd(&nsmall, 1)] = lf;
-        }
-        __syncthreads();
-        for (int ib = wid; ib < nsmall; ib += 2) {  // up to 4 particles per lane, ranked by shuffles
-            const int leaf = small[ib];
-            const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
-            const int rounds = (c + 31) >> 5;
-            int v[4], rank[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                v[q] = (q < rounds && lane + 32 * q < c) ? w.tmp[s0 + lane + 32 * q] : 0x7fffffff;  // pad ranks last
-                rank[q] = 0;
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (r >= rounds)
-                    break;
-                for (int j = 0; j < 32; ++j) {
-                    const int o = __shfl_sync(0xffffffffu, v[r], j);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        rank[q] += o < v[q];
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (lane + 32 * q < c)
-                    place_particle(w, v[q], s0 + rank[q], leaf, x, y, g, gu, gv, mixed);
-        }
-        const int nb = nbig;
-        for (int ib = 0; ib < nb; ++ib)
-            order_leaf_block(w, big[ib], tile, x, y, g, gu, gv, mixed);
-    }
+    order_leaf_block(w, blockIdx.x, tile, x, y, g, gu, gv, mixed);
 }
 
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,
                   const double *gv, cudaStream_t s)
 {
-    const int grid = (w.nleaf <= 65536 || !w.morton) ? w.nleaf : 152 * 32;
-    k_leaf_order<<<grid, 64, 0, s>>>(w, x, y, g, gu, gv, (w.mixed && !gu) ? 1 : 0);
-    return 1;
+    const int mixed = (w.mixed && !gu) ? 1 : 0;
+    if (!w.morton) {  // measured as fast as the per-position ranking there, in one launch
+        k_leaf_block<<<w.nleaf, 64, 0, s>>>(w, x, y, g, gu, gv, mixed);
+        return 1;
+    }
+    // the adaptive tree's depth-L cells (millions, mostly empty, a few tens of particles at most)
+    cudaMemsetAsync(w.big_cnt, 0, sizeof(int), s);
+    k_leaf_rank<<<(w.n + 255) / 256, 256, 0, s>>>(w, x, y, g, gu, gv, mixed);
+    const int most = w.n / (kSmallLeaf + 1) + 1;  // leaves that can hold more than kSmallLeaf particles
+    k_leaf_big<<<min(most, 152 * 8), 128, 0, s>>>(w, x, y, g, gu, gv, mixed);
+    return 2;
 }
 
 // ------------------------------------------------------------------ ordered near-field pair count

@@ -335,7 +335,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = (size_t)nleaf * 4 + 16;                      // 1 cnt
     sizes[i++] = (size_t)(nleaf + 1) * 4 + 16;                // 2 start
     sizes[i++] = (size_t)((nleaf + 1023) / 1024 + 2) * 4;     // 3 scan_tmp
-    sizes[i++] = np * 4;                                      // 4 tmp
+    sizes[i++] = np * 8;                                      // 4 tmp (caller index, leaf)
     sizes[i++] = np * 4;                                      // 5 perm
     sizes[i++] = np * 4;                                      // 6 sleaf
     sizes[i++] = f64 ? np * 8 : 0;                            // 7 sx
@@ -355,13 +355,14 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 21 AM64
     sizes[i++] = adjoint ? (size_t)nbox * p * 16 : 0;         // 22 AL64
     sizes[i++] = mixed ? np * 32 : 0;                         // 23 nearp [4][n]
-    sizes[i++] = mixed ? np * 16 : 0;                         // 24 pos4u
-    sizes[i++] = mixed ? np * 4 : 0;                          // 25 g32u
+    sizes[i++] = mixed ? np * 32 : 0;                         // 24 pos4u (two float4 per particle)
+    sizes[i++] = mixed ? 0 : np * 32;                         // 25 rec64
     sizes[i++] = np * 4;                                      // 26 slot
     sizes[i++] = np * 4;                                      // 27 iperm
     sizes[i++] = adjoint ? np * 24 : 0;                       // 28 adj_far
     sizes[i++] = h->adaptive_cap ? (size_t)nbox * 4 + 16 : 0;   // 29 ad_list
     sizes[i++] = h->adaptive_cap ? (FMM_MAXL + 2) * 4 : 0;      // 30 ad_cnt
+    sizes[i++] = (size_t)(n / 129 + 2) * 4;                    // 31 big (leaves of more than 128 particles)
     int count = i;
     Layout lay;
     size_t total = 0;
@@ -406,7 +407,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.cnt = (int *)(b + lay.off[1]);
     w.start = (int *)(b + lay.off[2]);
     w.scan_tmp = (int *)(b + lay.off[3]);
-    w.tmp = (int *)(b + lay.off[4]);
+    w.tmp = (int2 *)(b + lay.off[4]);
     w.perm = (int *)(b + lay.off[5]);
     w.sleaf = (int *)(b + lay.off[6]);
     w.sx = sizes[7] ? (double *)(b + lay.off[7]) : nullptr;
@@ -436,16 +437,18 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
         (void)cudaGetLastError();
     }
     w.pos4u = sizes[24] ? (float4 *)(b + lay.off[24]) : nullptr;
-    w.g32u = sizes[25] ? (float *)(b + lay.off[25]) : nullptr;
+    w.rec64 = sizes[25] ? (Rec64 *)(b + lay.off[25]) : nullptr;
     char *hd = (char *)h->hdr;
     w.status = (unsigned int *)hd;
     w.pair_count = (unsigned long long *)(hd + 32);
+    w.big_cnt = (int *)(hd + 64);
     w.minmax = (unsigned long long *)(hd + HDR_MINMAX);
     w.sys = (SysDev *)(hd + HDR_SYS);
     w.sys_list = (int *)(hd + HDR_LIST);
     w.adj_far = sizes[28] ? (double *)(b + lay.off[28]) : nullptr;
     w.ad_list = sizes[29] ? (int *)(b + lay.off[29]) : nullptr;
     w.ad_cnt = sizes[30] ? (int *)(b + lay.off[30]) : nullptr;
+    w.big = (int *)(b + lay.off[31]);
     w.lv = h->lv;
     return FMM_OK;
 }

@@ -81,6 +81,12 @@ struct Tables {
     unsigned char *m2l_tc;    // tensor-core M2L operand B (m2l_tc.cu)
 };
 
+// One particle's FP64 inputs in the caller's order, written by the key kernel so that the leaf-order kernel's
+// random gather reads one 32-byte sector per particle instead of three.
+struct __align__(32) Rec64 {
+    double x, y, g, pad;
+};
+
 struct Work {
     int n;
     int nleaf;
@@ -105,11 +111,14 @@ struct Work {
     int *ad_list;             // adaptive tree: Morton indices of the existing boxes of level l at [box0[l], ...)
     int *ad_cnt;              // [FMM_MAXL + 2] adaptive tree: number of existing boxes per level
     // arrays
-    int *key, *slot, *cnt, *start, *scan_tmp, *tmp, *perm, *sleaf;
+    int *key, *slot, *cnt, *start, *scan_tmp, *perm, *sleaf;
+    int2 *tmp;                // [n] leaf order before the in-leaf ranking: (caller index, leaf) at the arrival slot
+    int *big, *big_cnt;       // leaves too large for the per-position ranking, and their number
     double *sx, *sy, *sg;
     float4 *eh, *el, *eg;     // precision form, leaf order: (xh, xh, yh, yh), (xl, xl, yl, yl), (g, g, -g, -g)
-    float4 *pos4u;            // precision form, caller order (made while binning): (xh, yh, xl, yl)
-    float *g32u;
+    float4 *pos4u;            // precision form, caller order (made while binning), two float4 per particle in one
+                              // 32-byte sector: (xh, yh, xl, yl), (gamma, 0, 0, 0)
+    Rec64 *rec64;             // FP64 form and adaptive tree, caller order: (x, y, gamma)
     double2 *near64;
     float2 *near32;
     int *bcount;

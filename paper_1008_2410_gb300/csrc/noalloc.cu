@@ -120,7 +120,8 @@ size_t carve_work(unsigned char *b, Work &w, int64_t n, int depth, int p, bool m
     w.cnt = (int *)take((size_t)nleaf * 4 + 16);
     w.start = (int *)take((size_t)(nleaf + 1) * 4 + 16);
     w.scan_tmp = (int *)take((size_t)((nleaf + 1023) / 1024 + 2) * 4);
-    w.tmp = (int *)take(np * 4);
+    w.tmp = (int2 *)take(np * 8);
+    w.big = (int *)take((size_t)(n / 129 + 2) * 4);
     w.perm = (int *)take(np * 4);
     w.iperm = (int *)take(np * 4);
     w.sleaf = (int *)take(np * 4);
@@ -138,8 +139,8 @@ size_t carve_work(unsigned char *b, Work &w, int64_t n, int depth, int p, bool m
     w.L64 = (double2 *)take((size_t)nbox * p * 16);
     w.M32 = (float2 *)take(mixed ? (size_t)nbox * p * 8 : 0);
     w.L32 = (float2 *)take(mixed ? (size_t)nbox * p * 8 : 0);
-    w.pos4u = (float4 *)take(mixed ? np * 16 : 0);
-    w.g32u = (float *)take(mixed ? np * 4 : 0);
+    w.pos4u = (float4 *)take(mixed ? np * 32 : 0);
+    w.rec64 = (Rec64 *)take(mixed ? 0 : np * 32);
     w.n = (int)n;
     w.nleaf = (int)nleaf;
     w.nbox = nbox;
@@ -214,6 +215,7 @@ extern "C" fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, 
     w.m2l_tc = 0;  // the default of a handle: FP32 M2L levels on the CUDA cores
     w.status = (unsigned int *)(h + hdr_status);
     w.pair_count = (unsigned long long *)(h + hdr_status + 32);
+    w.big_cnt = (int *)(h + hdr_status + 64);
     w.minmax = (unsigned long long *)(h + hdr_minmax);
     w.sys = (SysDev *)(h + hdr_sys);
     w.sys_list = (int *)(h + hdr_list);

@@ -199,6 +199,46 @@ int64_t enum_threads(int L)
 
 constexpr int kSweepBlocks = 152 * 16;  // grid of the list-driven sweep kernels (4 warps per block)
 
+// Sum over a warp's lanes of PM complex partial sums per lane (lanes >= used hold zeros): in the precision form
+// through shared memory, one row per lane and lane k adding column k (PM stores and `used` loads per lane, against
+// a butterfly of 2 PM log2(32) shuffles); in the FP64 form by the butterfly. Lane k < PM returns coefficient k.
+template <typename R, int PM>
+__device__ __forceinline__ cpx<R> warp_coeff_sum(cpx<R> *acc, int lane, int used)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        __shared__ float2 red[4][32][PM + 1];
+        float2(*row)[PM + 1] = red[threadIdx.x >> 5];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            row[lane][k] = make_float2(acc[k].re, acc[k].im);
+        __syncwarp();
+        cpx<R> s = {0.f, 0.f};
+        if (lane < PM)
+            for (int r = 0; r < used; ++r) {
+                const float2 v = row[r][lane];
+                s.re += v.x;
+                s.im += v.y;
+            }
+        __syncwarp();
+        return s;
+    } else {
+        (void)used;
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[k].re += __shfl_xor_sync(0xffffffffu, acc[k].re, o);
+                acc[k].im += __shfl_xor_sync(0xffffffffu, acc[k].im, o);
+            }
+        cpx<R> s = acc[0];
+#pragma unroll
+        for (int k = 1; k < PM; ++k)
+            if (lane == k)
+                s = acc[k];
+        return s;
+    }
+}
+
 // ------------------------------------------------------------------ stage 4: P2M at the leaves of level l
 
 // One warp per leaf; lane = particle (32 at a time), each lane accumulating the PM coefficients of its particles
@@ -234,17 +274,9 @@ __global__ void __launch_bounds__(128) k_ad_p2m(Work w, int l)
                 pw = cmul(pw, z);
             }
         }
-#pragma unroll
-        for (int k = 0; k < PM; ++k)
-            for (int o = 16; o > 0; o >>= 1) {
-                acc[k].re += __shfl_xor_sync(0xffffffffu, acc[k].re, o);
-                acc[k].im += __shfl_xor_sync(0xffffffffu, acc[k].im, o);
-            }
-        auto *dst = mp_of<R>(w, l, m);
-#pragma unroll
-        for (int k = 0; k < PM; ++k)
-            if (lane == k && k < p)
-                st(dst + k, acc[k]);
+        const cpx<R> sum = warp_coeff_sum<R, PM>(acc, lane, min(cnt, 32));
+        if (lane < p)
+            st(mp_of<R>(w, l, m) + lane, sum);
     }
 }
 
@@ -326,6 +358,7 @@ __global__ void __launch_bounds__(128) k_ad_p2l(Work w, int l)
         for (int k = 0; k < PM; ++k)
             acc[k] = {(R)0, (R)0};
         const double2 c = centre(d, l, bx, by);
+        int used = 0;  // lanes that took a particle
         while (xm) {
             const int src = __ffs(xm) - 1;
             xm &= xm - 1;
@@ -333,6 +366,7 @@ __global__ void __launch_bounds__(128) k_ad_p2l(Work w, int l)
             const int lq = id >> 26, qx = (id >> 13) & 0x1fff, qy = id & 0x1fff;
             const unsigned mq = morton2(qx, qy);
             const int j0 = box_first(t, lq, mq), cnt = box_count(t, lq, mq);
+            used = max(used, min(cnt, 32));
             for (int e = lane; e < cnt; e += 32) {
                 const int j = j0 + e;
                 const double ax = (w.sx[j] - c.x) * iw, ay = (w.sy[j] - c.y) * iw;
@@ -347,16 +381,9 @@ __global__ void __launch_bounds__(128) k_ad_p2l(Work w, int l)
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < PM; ++k)
-            for (int o = 16; o > 0; o >>= 1) {
-                acc[k].re += __shfl_xor_sync(0xffffffffu, acc[k].re, o);
-                acc[k].im += __shfl_xor_sync(0xffffffffu, acc[k].im, o);
-            }
-#pragma unroll
-        for (int k = 0; k < PM; ++k)
-            if (lane == k && k < p)
-                st(dst + k, acc[k]);
+        const cpx<R> sum = warp_coeff_sum<R, PM>(acc, lane, used);
+        if (lane < p)
+            st(dst + lane, sum);
     }
 }
 

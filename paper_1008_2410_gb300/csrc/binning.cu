@@ -4,7 +4,9 @@
 // The root square and leaf rule are this library's reading of the paper (which leaves them open): an
 // explicit square, or the particles' bounding box centred with side extent * (1 + 2^-20); the leaf column
 // is floor((x - x0) * (2^L / S)) in IEEE double without FMA contraction, clamped to [0, 2^L - 1].
-// Within a leaf, particles keep the caller's order, so every run gives bit-identical results.
+// Within a leaf, particles keep the caller's order, so every run gives bit-identical results; the uniform tree's
+// precision form orders each leaf by boundary class first (the band of width sigma along each side that the
+// near field of the adjacent leaves must test for small r, see k_keys) and by caller index within a class.
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -70,6 +72,11 @@ __device__ void derive_constants(SysDev &d)
     d.inv_s = 1.0f / s;
     d.snear = (float)((double)s * d.far_scale);
     d.iu = sqrt(1.4426950408889634074 / (2.0 * d.sigma * d.sigma));
+    // band width delta = sigma (1 + 2^-8) in leaf widths; the margin keeps every pair the near field computes
+    // at r' ^ 2 < its series threshold (r < sigma, up to FP32 rounding) inside the tested bands
+    const double om = d.sigma * (1.0 + 0x1p-8) / d.wl;
+    d.bnd_ok = om < 0.5 ? 1 : 0;
+    d.fbnd = d.bnd_ok ? (long long)floor((0.5 - om) * 0x1p52) : 0;
 }
 
 __global__ void k_domain_finalize(SysDev *sys, int nsys, const unsigned long long *minmax)
@@ -220,7 +227,17 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
         frac_to_split(Fx, d.s_unit, &hx, &lx);
         frac_to_split(Fy, d.s_unit, &hy, &ly);
         w.pos4u[2 * (int64_t)i] = make_float4(hx, hy, lx, ly);
-        w.pos4u[2 * (int64_t)i + 1] = make_float4(__double2float_rn(g[i]), 0.f, 0.f, 0.f);
+        // boundary class: band (left, middle, right) x (bottom, middle, top) of the leaf, from the exact fraction
+        // F = zeta 2^52 (a point on the square's upper edge has F = 2^51: right or top band). Numbered around the
+        // leaf so that the band facing each of the 8 neighbours is a run of classes: 0 LB, 1 LM, 2 LT, 3 MT,
+        // 4 RT, 5 RM, 6 RB, 7 MB, 8 MM (the interior, last); everything is class 8 where the bands would overlap.
+        int cls = 8;
+        if (w.cls_off && d.bnd_ok) {
+            const int cx = Fx < -d.fbnd ? 0 : (Fx > d.fbnd ? 2 : 1);
+            const int cy = Fy < -d.fbnd ? 0 : (Fy > d.fbnd ? 2 : 1);
+            cls = (int)((0x432581670ull >> (4 * (3 * cy + cx))) & 15ull);
+        }
+        w.pos4u[2 * (int64_t)i + 1] = make_float4(__double2float_rn(g[i]), __int_as_float(cls), 0.f, 0.f);
     } else if (w.rec64) {
         Rec64 r;
         r.x = xi;
@@ -480,18 +497,19 @@ int launch_scan(const Work &w, cudaStream_t s)
 // ------------------------------------------------------------------ counting-sort scatter and in-leaf order
 
 __global__ void k_scatter(int n, const int *__restrict__ key, const int *__restrict__ slot,
-                          const int *__restrict__ start, int2 *tmp)
+                          const int *__restrict__ start, const float4 *__restrict__ pos4u, int2 *tmp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
     const int k = key[i];
-    tmp[start[k] + slot[i]] = make_int2(i, k);  // caller index and leaf, at the leaf's arrival slot
+    // caller index and leaf (or boundary class), at the leaf's arrival slot
+    tmp[start[k] + slot[i]] = make_int2(i, pos4u ? __float_as_int(pos4u[2 * (int64_t)i + 1].y) : k);
 }
 
 int launch_scatter_sort(const Work &w, cudaStream_t s)
 {
-    k_scatter<<<(w.n + 255) / 256, 256, 0, s>>>(w.n, w.key, w.slot, w.start, w.tmp);
+    k_scatter<<<(w.n + 255) / 256, 256, 0, s>>>(w.n, w.key, w.slot, w.start, w.cls_off ? w.pos4u : nullptr, w.tmp);
     return 1;
 }
 
@@ -542,27 +560,50 @@ __device__ __forceinline__ void place_particle(const Work &w, int v, int pos, in
     }
 }
 
-// Ranks one leaf's caller indices (all distinct) with the whole block so that the leaf keeps the caller's order.
-__device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, int *tile, const double *x, const double *y,
-                                                 const double *g, const double *gu, const double *gv, int mixed)
+// Ranks one leaf's entries (keys all distinct) with the whole block: by caller index, or with `cls` (tmp holds the
+// boundary class in .y) by (class, caller index); then writes the first position of classes 1..8 of the leaf.
+__device__ __forceinline__ unsigned long long rank_key(int2 e, bool cls)
+{
+    return ((cls ? (unsigned long long)(unsigned)e.y : 0ull) << 32) | (unsigned)e.x;
+}
+
+__device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, unsigned long long *tile, int *ccount,
+                                                 bool cls, const double *x, const double *y, const double *g,
+                                                 const double *gu, const double *gv, int mixed)
 {
     const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
+    if (cls && threadIdx.x < 9)
+        ccount[threadIdx.x] = 0;
     for (int e0 = 0; e0 < c; e0 += blockDim.x) {
         const int e = e0 + threadIdx.x;
-        const int v = e < c ? w.tmp[s0 + e].x : 0;
+        const int2 me = e < c ? w.tmp[s0 + e] : make_int2(0, 0);
+        const unsigned long long v = rank_key(me, cls);
         int rank = 0;
         for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
             const int m = min(SORT_TILE, c - f0);
             __syncthreads();
             for (int j = threadIdx.x; j < m; j += blockDim.x)
-                tile[j] = w.tmp[s0 + f0 + j].x;
+                tile[j] = rank_key(w.tmp[s0 + f0 + j], cls);
             __syncthreads();
             if (e < c)
                 for (int j = 0; j < m; ++j)
                     rank += tile[j] < v;
         }
-        if (e < c)
-            place_particle(w, v, s0 + rank, leaf, x, y, g, gu, gv, mixed);
+        if (e < c) {
+            place_particle(w, me.x, s0 + rank, leaf, x, y, g, gu, gv, mixed);
+            if (cls)
+                atomicAdd(&ccount[me.y], 1);
+        }
+    }
+    if (cls) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int pos = s0;
+            for (int k = 0; k < 8; ++k) {
+                pos += ccount[k];
+                w.cls_off[(int64_t)leaf * 8 + k] = pos;  // first position of class k + 1
+            }
+        }
     }
 }
 
@@ -597,10 +638,10 @@ __global__ void __launch_bounds__(128) k_leaf_big(Work w, const double *__restri
                                                   const double *__restrict__ g, const double *__restrict__ gu,
                                                   const double *__restrict__ gv, int mixed)
 {
-    __shared__ int tile[SORT_TILE];
+    __shared__ unsigned long long tile[SORT_TILE];
     const int nb = *w.big_cnt;
     for (int b = blockIdx.x; b < nb; b += gridDim.x)  // block-uniform
-        order_leaf_block(w, w.big[b], tile, x, y, g, gu, gv, mixed);
+        order_leaf_block(w, w.big[b], tile, nullptr, false, x, y, g, gu, gv, mixed);
 }
 
 // The uniform tree (tens of particles in each of at most millions of leaves): one block per leaf.
@@ -608,8 +649,9 @@ __global__ void __launch_bounds__(64) k_leaf_block(Work w, const double *__restr
                                                    const double *__restrict__ g, const double *__restrict__ gu,
                                                    const double *__restrict__ gv, int mixed)
 {
-    __shared__ int tile[SORT_TILE];
-    order_leaf_block(w, blockIdx.x, tile, x, y, g, gu, gv, mixed);
+    __shared__ unsigned long long tile[SORT_TILE];
+    __shared__ int ccount[9];
+    order_leaf_block(w, blockIdx.x, tile, ccount, w.cls_off != nullptr, x, y, g, gu, gv, mixed);
 }
 
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,

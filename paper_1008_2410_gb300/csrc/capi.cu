@@ -363,6 +363,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = h->adaptive_cap ? (size_t)nbox * 4 + 16 : 0;   // 29 ad_list
     sizes[i++] = h->adaptive_cap ? (FMM_MAXL + 2) * 4 : 0;      // 30 ad_cnt
     sizes[i++] = (size_t)(n / 129 + 2) * 4;                    // 31 big (leaves of more than 128 particles)
+    sizes[i++] = mixed ? (size_t)nleaf * 32 + 16 : 0;          // 32 cls_off (boundary classes of each leaf)
     int count = i;
     Layout lay;
     size_t total = 0;
@@ -449,6 +450,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.ad_list = sizes[29] ? (int *)(b + lay.off[29]) : nullptr;
     w.ad_cnt = sizes[30] ? (int *)(b + lay.off[30]) : nullptr;
     w.big = (int *)(b + lay.off[31]);
+    w.cls_off = sizes[32] ? (int *)(b + lay.off[32]) : nullptr;
     w.lv = h->lv;
     return FMM_OK;
 }

@@ -58,6 +58,12 @@ struct SysDev {
     float snear;                    // s / (2 pi w_L): scale of the near-field sum in these units
     float pad_f;
     double iu;                      // adaptive tree's precision form: 1 / u, u = sigma sqrt(2 / log2 e)
+    // boundary bands of the precision form's near field: a particle whose leaf-relative position zeta (in leaf
+    // widths, |zeta| <= 1/2) has |zeta_x| * 2^52 > fbnd lies within delta = sigma (1 + 2^-8) of its leaf's left or
+    // right side (likewise y); bnd_ok = 0 when the bands would overlap (leaf narrower than 2 delta)
+    long long fbnd;
+    int bnd_ok;
+    int pad_b;
 };
 
 // Per-level work lists for the tree sweeps, computed on the host and passed by value. The systems that have
@@ -112,7 +118,10 @@ struct Work {
     int *ad_cnt;              // [FMM_MAXL + 2] adaptive tree: number of existing boxes per level
     // arrays
     int *key, *slot, *cnt, *start, *scan_tmp, *perm, *sleaf;
-    int2 *tmp;                // [n] leaf order before the in-leaf ranking: (caller index, leaf) at the arrival slot
+    int2 *tmp;                // [n] leaf order before the in-leaf ranking: (caller index, leaf) at the arrival slot;
+                              // the uniform precision form stores (caller index, boundary class) instead
+    int *cls_off;             // uniform precision form: [nleaf][8] first sorted position of boundary classes 1..8
+                              // of each leaf (class 0 starts at start[leaf]), or null
     int *big, *big_cnt;       // leaves too large for the per-position ranking, and their number
     double *sx, *sy, *sg;
     float4 *eh, *el, *eg;     // precision form, leaf order: (xh, xh, yh, yh), (xl, xl, yl, yl), (g, g, -g, -g)

@@ -141,6 +141,7 @@ size_t carve_work(unsigned char *b, Work &w, int64_t n, int depth, int p, bool m
     w.L32 = (float2 *)take(mixed ? (size_t)nbox * p * 8 : 0);
     w.pos4u = (float4 *)take(mixed ? np * 32 : 0);
     w.rec64 = (Rec64 *)take(mixed ? 0 : np * 32);
+    w.cls_off = (int *)take(mixed ? (size_t)nleaf * 32 + 16 : 0);
     w.n = (int)n;
     w.nleaf = (int)nleaf;
     w.nbox = nbox;

@@ -16,6 +16,8 @@
 // memory, completed on an mbarrier with a bounded wait.
 #include "fmm_internal.cuh"
 
+#include <type_traits>
+
 namespace fmm {
 
 #define TWO_PI 6.283185307179586476925
@@ -190,6 +192,7 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 // 2^-22.5 / y of its relative accuracy there. r' = 0 (a particle and itself, or coincident particles, which
 // always share a leaf) needs no special factor: with 1/r'^2 clamped, g (1 - e) / r'^2 = 0 exactly.
 #define P2P_THR 0.72134752044448170f
+#define P2P_RMIN2 0x1p-16f  // floor of r'^2 in the plain factor of tested pairs (the series replaces it below P2P_THR)
 #define P2P_LN2 0.69314718055994531f
 #ifndef P2P_UNROLL
 #define P2P_UNROLL 1  // source loop unroll of the near-field kernel
@@ -201,7 +204,7 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 #define P2P_MIN_BLOCKS2 24  // the same for the two-targets-per-lane instance (40 registers)
 #endif
 #ifndef P2P_TILE2
-#define P2P_TILE2 256  // sources per shared-memory tile of the two-per-lane instance (one-float coordinates)
+#define P2P_TILE2 288  // sources per shared-memory tile of the two-per-lane instance (one-float coordinates)
 #endif
 constexpr int kP2PUnroll = P2P_UNROLL;
 
@@ -236,14 +239,19 @@ __device__ __forceinline__ void two_sum2(f2 &s, f2 &c, f2 x)
 }
 
 // Sources j0..j1 of one source leaf against KT targets per lane (KT/2 packed pairs), accumulated into PU, PV.
-// The lane's targets (leaf order index `tbase + lane + 32 q`, q < KT, only those < tcnt) are re-read and
-// re-expressed relative to the source leaf's centre: hi - dc s by Fast2Sum (|dc s| >= |hi|), error into lo.
+// The lane's targets (entries lane + 32 q, q < KT, only those < tcnt, of the pass's staged targets TT: x hi, x lo,
+// y hi, y lo) are re-expressed relative to the source leaf's centre: hi - dc s by Fast2Sum (|dc s| >= |hi|), error
+// into lo.
 // SPLIT keeps the sources' lo parts (differences at FP64-level resolution); otherwise each coordinate is one
 // float (the target's rounded once from its exact shifted hi + lo) and a difference costs one instruction.
+// Only sources ja..jb are tested for small r (the targets' own leaf: all of them); the others lie at least sigma
+// from every target (outside the band of their leaf that faces the targets' leaf), where the plain factor is
+// accurate, and run without the test: [j0, ja) and [jb, j1) first, then the band.
 template <int KT, bool SELF, bool SPLIT>
 __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restrict__ EH,
                                             const float4 *__restrict__ EL, const float4 *__restrict__ EG, int j0,
-                                            int j1, float sdx, float sdy, int tbase, int tcnt, f2 *PU, f2 *PV)
+                                            int j1, int ja, int jb, float sdx, float sdy,
+                                            const float4 *__restrict__ TT, int tcnt, f2 *PU, f2 *PV)
 {
     constexpr int NP = KT / 2;
     const int lane = threadIdx.x & 31;
@@ -254,15 +262,11 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int e = lane + 32 * (2 * pr + h);
-            float4 th = make_float4(0.f, 0.f, 0.f, 0.f), tl = th;
-            if (e < tcnt) {
-                th = w.eh[tbase + e];
-                tl = w.el[tbase + e];
-            }
-            hx[h] = th.x - sdx;
-            lx[h] = tl.x + (th.x - (hx[h] + sdx));
-            hy[h] = th.z - sdy;
-            ly[h] = tl.z + (th.z - (hy[h] + sdy));
+            const float4 t = e < tcnt ? TT[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            hx[h] = t.x - sdx;
+            lx[h] = t.y + (t.x - (hx[h] + sdx));
+            hy[h] = t.z - sdy;
+            ly[h] = t.w + (t.z - (hy[h] + sdy));
             if (!SPLIT) {
                 hx[h] += lx[h];
                 hy[h] += ly[h];
@@ -275,13 +279,16 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
             ALY[pr] = pk2(ly[0], ly[1]);
         }
     }
-#pragma unroll(kP2PUnroll)
-    for (int j = j0; j < j1; ++j) {
+    // One source against the lane's targets; `tst` (a std::bool_constant) selects the small-r test. Every pair
+    // first takes the plain factor g (1 - e) / r'^2, with r'^2 clamped below at P2P_RMIN2 where it is tested (so
+    // that it stays bounded: (1 - e) / r'^2 <= ln 2 + 2^-22 / P2P_RMIN2); for the rare warp with a pair at
+    // 0 < r < sigma the source is re-read, the plain factor recomputed bit for bit and replaced by the series
+    // through the difference, so none of the series' registers are live on the common path.
+    auto plain = [&](int j, auto tst, f2 *dx, f2 *dy, f2 *r2, f2 *gf) {
+        constexpr bool TEST = decltype(tst)::value;
         const float4 h = EH[j], g = EG[j], l = SPLIT ? EL[j] : h;
         const f2 sxh = pk2(h.x, h.y), syh = pk2(h.z, h.w);
         const f2 gp = pk2(g.x, g.y), gn = pk2(g.z, g.w);
-        f2 dx[NP], dy[NP], r2[NP], q[NP], og[NP];
-        float rmin = 3.0e38f;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
             if (SPLIT) {
@@ -295,45 +302,61 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
             float ra, rb;
             up2(r2[pr], ra, rb);
             const float ea = ex2_approx(-ra), eb = ex2_approx(-rb);
-            if (SELF) {
-                // own leaf: r' = 0 occurs; clamp 1/r'^2 and keep zeros out of the series test
-                q[pr] = pk2(rcp_approx(fmaxf(ra, 1e-30f)), rcp_approx(fmaxf(rb, 1e-30f)));
-                rmin = __uint_as_float(min(__float_as_uint(rmin), min(__float_as_uint(ra) - 1u, __float_as_uint(rb) - 1u)));
-            } else {
-                q[pr] = pk2(rcp_approx(ra), rcp_approx(rb));
-                rmin = fminf(rmin, fminf(ra, rb));
-            }
-            og[pr] = fma2(pk2(ea, eb), gn, gp);  // g (1 - e)
+            const f2 q = TEST ? pk2(rcp_approx(fmaxf(ra, P2P_RMIN2)), rcp_approx(fmaxf(rb, P2P_RMIN2)))
+                              : pk2(rcp_approx(ra), rcp_approx(rb));
+            gf[pr] = mul2(fma2(pk2(ea, eb), gn, gp), q);  // g (1 - e) / r'^2
         }
-        // rare (0 < r < sigma): warp-uniform branch to the series, off the common path. With SELF, rmin holds
-        // the bit pattern minus one (as unsigned), so r' = 0 maps to the largest value and never triggers it.
-        if (__any_sync(0xffffffffu, SELF ? (__float_as_uint(rmin) < __float_as_uint(P2P_THR)) : (rmin < P2P_THR))) {
-#pragma unroll
-            for (int pr = 0; pr < NP; ++pr) {
-                float ra, rb, qa, qb, oa, ob, sa, sb;
-                up2(r2[pr], ra, rb);
-                up2(q[pr], qa, qb);
-                up2(og[pr], oa, ob);
-                up2(small_q2(r2[pr]), sa, sb);
-                if (ra < P2P_THR) {
-                    qa = sa;
-                    oa = g.x;
-                }
-                if (rb < P2P_THR) {
-                    qb = sb;
-                    ob = g.x;
-                }
-                q[pr] = pk2(qa, qb);
-                og[pr] = pk2(oa, ob);
-            }
-        }
+    };
+    auto source = [&](int j, auto tst) {
+        constexpr bool TEST = decltype(tst)::value;
+        f2 dx[NP], dy[NP], r2[NP], gf[NP];
+        plain(j, tst, dx, dy, r2, gf);
+        bool close = false;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
-            const f2 gf = mul2(og[pr], q[pr]);
-            PU[pr] = fma2(dy[pr], gf, PU[pr]);  // u accumulates -dy g f: negated at the end
-            PV[pr] = fma2(dx[pr], gf, PV[pr]);
+            float ra, rb;
+            up2(r2[pr], ra, rb);
+            if (SELF)  // r' = 0 (a particle and itself) needs nothing: (1 - e) = 0 exactly; as unsigned, the bit
+                       // pattern minus one maps it to the largest value
+                close |= (__float_as_uint(ra) - 1u < __float_as_uint(P2P_THR)) |
+                         (__float_as_uint(rb) - 1u < __float_as_uint(P2P_THR));
+            else if (TEST)
+                close |= (ra < P2P_THR) | (rb < P2P_THR);
+            PU[pr] = fma2(dy[pr], gf[pr], PU[pr]);  // u accumulates -dy g f: negated at the end
+            PV[pr] = fma2(dx[pr], gf[pr], PV[pr]);
+        }
+        // rare (0 < r < sigma): warp-uniform branch to the series, off the common path
+        if (TEST && __any_sync(0xffffffffu, close)) {
+            plain(j, tst, dx, dy, r2, gf);
+            const float gs = EG[j].x;
+#pragma unroll
+            for (int pr = 0; pr < NP; ++pr) {
+                float ra, rb, fa, fb, sa, sb;
+                up2(r2[pr], ra, rb);
+                up2(gf[pr], fa, fb);
+                up2(small_q2(r2[pr]), sa, sb);
+                const float da = ra < P2P_THR ? fmaf(gs, sa, -fa) : 0.f;
+                const float db = rb < P2P_THR ? fmaf(gs, sb, -fb) : 0.f;
+                const f2 dd = pk2(da, db);  // series minus plain (zero where r' = 0: dx = dy = 0)
+                PU[pr] = fma2(dy[pr], dd, PU[pr]);
+                PV[pr] = fma2(dx[pr], dd, PV[pr]);
+            }
+        }
+    };
+    if (!SELF) {
+        int lo = j0, hi = ja;
+#pragma unroll 1
+        for (int ph = 0; ph < 2; ++ph) {
+#pragma unroll(kP2PUnroll)
+            for (int j = lo; j < hi; ++j)
+                source(j, std::false_type{});
+            lo = jb;
+            hi = j1;
         }
     }
+#pragma unroll(kP2PUnroll)
+    for (int j = ja; j < jb; ++j)
+        source(j, std::true_type{});
 }
 
 // The remainder of a pass: r targets spread over the warp's 64 slots (slot s = lane + 32 h, h = 0, 1, one half of
@@ -345,7 +368,7 @@ struct RemSlots {
     int e[2], g[2];  // per half: target position in leaf order, source group
     bool a[2];       // per half: slot in use
     int G;
-    __device__ __forceinline__ RemSlots(int rbase, int r)
+    __device__ __forceinline__ RemSlots(int rbase, int r)  // rbase: first remainder target in the staged copy
     {
         const int lane = threadIdx.x & 31;
         G = 64 / r;
@@ -360,18 +383,18 @@ struct RemSlots {
 };
 
 template <bool SELF>
-__device__ __forceinline__ void p2p_segment_rem(const Work &w, const float4 *__restrict__ EH,
-                                                const float4 *__restrict__ EG, int j0, int j1, float sdx, float sdy,
-                                                int rbase, int r, f2 &PU, f2 &PV)
+__device__ __forceinline__ void p2p_segment_rem(const float4 *__restrict__ EH, const float4 *__restrict__ EG,
+                                                int j0, int j1, float sdx, float sdy,
+                                                const float4 *__restrict__ TT, int rbase, int r, f2 &PU, f2 &PV)
 {
     const RemSlots R(rbase, r);
     float hx[2], hy[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const float4 th = w.eh[R.e[h]], tl = w.el[R.e[h]];
-        const float ax = th.x - sdx, ay = th.z - sdy;
-        hx[h] = ax + (tl.x + (th.x - (ax + sdx)));
-        hy[h] = ay + (tl.z + (th.z - (ay + sdy)));
+        const float4 t = TT[R.e[h]];
+        const float ax = t.x - sdx, ay = t.z - sdy;
+        hx[h] = ax + (t.y + (t.x - (ax + sdx)));
+        hy[h] = ay + (t.w + (t.z - (ay + sdy)));
     }
     const f2 AX = pk2(hx[0], hx[1]), AY = pk2(hy[0], hy[1]);
     const int G = R.G;
@@ -438,9 +461,12 @@ __global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    // EH, EG, then EL (only the split form reads EL, so one-float launches allocate 32 bytes per source)
+    __shared__ int4 segtab[LPB][3];  // per warp, per source column of the current row: first, end, band first, end
+    // EH, EG, then EL (only the split form reads EL, so one-float launches allocate 32 bytes per source), then
+    // each warp's targets of the current pass (p2p_smem_bytes)
     float4 *EH = reinterpret_cast<float4 *>(smem_raw), *EG = EH + tile, *EL = EG + tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *TT = EH + (size_t)tile * (w.p2p_all_plain ? 2 : 3) + warp * (KTM == 4 ? 128 : 64);
     const int first = blockIdx.x * LPB;
     if (first >= w.nleaf)
         return;
@@ -455,6 +481,7 @@ __global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w
         return;  // this system's near field is the symmetric kernel's
     (void)ktmax;
     const bool rem_form = !split;
+    const bool bands = w.cls_off != nullptr && d.bnd_ok;  // leaves ordered by boundary class (block-uniform)
     // passes: KTM = 4, 128 targets (the last one the rest); KTM = 2, 64 targets, then the rest as one pass
     // (a main group of 33..63, or a remainder of at most 32); split form: balanced passes of at most 64
     const int full_pass = KTM == 4 ? 128 : 64;
@@ -491,6 +518,17 @@ __global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w
             }
         }
         const int tbase = my_s0 + t_lo;
+        // the pass's targets, staged once (x hi, x lo, y hi, y lo): every segment re-reads them
+        __syncwarp();
+        for (int e = lane; e < full_pass; e += 32) {
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < t_cnt) {
+                const float4 th = w.eh[tbase + e], tl = w.el[tbase + e];
+                t = make_float4(th.x, tl.x, th.z, tl.z);
+            }
+            TT[e] = t;
+        }
+        __syncwarp();
         // layout of the pass: more than 96 targets, four per lane (two packed pairs, broadcast sources); else a
         // main group of up to 64, two per lane, and a remainder of at most 32 over the slots (source groups); a
         // pass of 33..63 targets is all main group, one of at most 32 all remainder
@@ -507,6 +545,31 @@ __global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w
             const int r0 = w.start[rowleaf + ca], r1 = w.start[rowleaf + cz + 1];
             if (r1 <= r0)
                 continue;
+            // this warp's three source leaves of the row (columns ix-1, ix, ix+1): their sorted ranges and the part
+            // tested for small r, the band facing the targets' leaf (a run of its boundary classes: a corner, a
+            // side with its two corners, or for the leaf above the whole boundary ring); the targets' own leaf, and
+            // systems without bands, are tested throughout
+            __syncwarp();
+            if (lane < 3) {
+                const int col = ix0 + warp - 1 + lane;
+                int4 t = make_int4(0, 0, 0, 0);
+                if (col >= 0 && col < ns) {
+                    t.x = w.start[rowleaf + col];
+                    t.y = w.start[rowleaf + col + 1];
+                    t.z = t.x;
+                    t.w = t.y;
+                    if (bands && !(lane == 1 && dyr == 0)) {
+                        const int *o = w.cls_off + (int64_t)(rowleaf + col) * 8;  // o[k - 1]: first of class k
+                        const int dir = (dyr + 1) * 3 + lane;  // source leaf at (lane - 1, dyr) from the targets'
+                        const int ka = (int)((0x006004224ull >> (4 * dir)) & 15ull);
+                        const int kb = (int)((0x187307355ull >> (4 * dir)) & 15ull);
+                        t.z = ka == 0 ? t.x : o[ka - 1];
+                        t.w = o[kb - 1];
+                    }
+                }
+                segtab[warp][lane] = t;
+            }
+            __syncwarp();
             f2 PU[2] = {0ull, 0ull}, PV[2] = {0ull, 0ull};
             for (int q0 = r0; q0 < r1; q0 += tile) {
                 const int m = min(tile, r1 - q0);
@@ -530,21 +593,20 @@ __global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w
                     continue;
 #pragma unroll
                 for (int k3 = 0; k3 < 3; ++k3) {
-                    const int col = ix0 + warp - 1 + k3;  // this warp's columns ix-1, ix, ix+1
-                    if (col < 0 || col >= ns)
-                        continue;
-                    const int b0 = w.start[rowleaf + col], b1 = w.start[rowleaf + col + 1];
-                    const int j0 = max(q0, b0) - q0, j1 = min(q0 + m, b1) - q0;
+                    const int4 sg = segtab[warp][k3];  // columns ix-1, ix, ix+1 (empty outside the grid)
+                    const int j0 = max(q0, sg.x) - q0, j1 = min(q0 + m, sg.y) - q0;
                     if (j0 >= j1)
                         continue;
                     const float sdx = (float)(k3 - 1) * s, sdy = (float)dyr * s;
                     const bool self = k3 == 1 && dyr == 0;
-#define P2P_SEG(SELF, SPLIT) p2p_segment<2, SELF, SPLIT>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV)
+                    const int ja = min(max(sg.z - q0, j0), j1), jb = max(min(sg.w - q0, j1), ja);  // tested
+#define P2P_SEG(SELF, SPLIT) \
+    p2p_segment<2, SELF, SPLIT>(w, EH, EL, EG, j0, j1, ja, jb, sdx, sdy, TT, n_main, PU, PV)
                     if (KTM == 4 && kt4) {
                         if (self)
-                            p2p_segment<KTM, true, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV);
+                            p2p_segment<KTM, true, false>(w, EH, EL, EG, j0, j1, ja, jb, sdx, sdy, TT, n_main, PU, PV);
                         else
-                            p2p_segment<KTM, false, false>(w, EH, EL, EG, j0, j1, sdx, sdy, tbase, n_main, PU, PV);
+                            p2p_segment<KTM, false, false>(w, EH, EL, EG, j0, j1, ja, jb, sdx, sdy, TT, n_main, PU, PV);
                     } else if (n_main > 0) {
                         if (split) {
                             if (self)
@@ -561,9 +623,9 @@ __global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w
 #undef P2P_SEG
                     if (r > 0) {
                         if (self)
-                            p2p_segment_rem<true>(w, EH, EG, j0, j1, sdx, sdy, tbase + n_main, r, PU[RI], PV[RI]);
+                            p2p_segment_rem<true>(EH, EG, j0, j1, sdx, sdy, TT, n_main, r, PU[RI], PV[RI]);
                         else
-                            p2p_segment_rem<false>(w, EH, EG, j0, j1, sdx, sdy, tbase + n_main, r, PU[RI], PV[RI]);
+                            p2p_segment_rem<false>(EH, EG, j0, j1, sdx, sdy, TT, n_main, r, PU[RI], PV[RI]);
                     }
                 }
                 // compensated totals: plain FP32 sums cover at most one tile of sources
@@ -933,15 +995,17 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
         ++nl;
         if (!w.p2p_all_plain) {
             const int tile = 192;
-            k_p2p32<1, 2><<<w.nleaf, 32, (size_t)tile * 48, s>>>(w, tile, 2, 1);
+            k_p2p32<1, 2><<<w.nleaf, 32, (size_t)tile * 48 + 64 * 16, s>>>(w, tile, 2, 1);
             ++nl;
         }
         return nl;
     }
     // shared memory per block: 32 bytes per source when every system keeps one-float coordinates, else 48; the
-    // four-per-lane instance runs 16 blocks per SM (tile 256), the two-per-lane instance 24 (tile 256 or 192)
+    // four-per-lane instance runs up to 16 blocks per SM (tile 256), the two-per-lane instance up to 20 (tile 288,
+    // or 192 with split coordinates), where a larger tile (fewer block-wide waits) measured faster than more blocks
     const int tile = ktmax == 4 ? 256 : (w.p2p_all_plain ? P2P_TILE2 : 192);
-    const size_t sm = (size_t)tile * (w.p2p_all_plain ? 32 : 48);
+    // plus the staged targets of a pass, 16 bytes each for up to 2 x 32 ktmax targets (two warps)
+    const size_t sm = (size_t)tile * (w.p2p_all_plain ? 32 : 48) + (size_t)2 * 32 * ktmax * 16;
     if (threads == 192 && w.p2p_rows) {
         // the target-side kernel with each of the three source rows of a leaf pair in its own block: three
         // times the blocks at a third of the length, so the last wave leaves less of the GPU idle

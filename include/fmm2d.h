@@ -140,7 +140,8 @@ fmm_status fmm_set_stream(fmm_handle h, void *cuda_stream);
 fmm_status fmm_set_graph(fmm_handle h, int enable);
 
 /* Near-field tile shape of the precision form: threads 32 (one leaf per thread block), 64 (two
- * horizontally adjacent leaves per block, sharing their source tiles) or 128 (symmetric: each pair of
+ * horizontally adjacent leaves per block, sharing their source tiles), 256 (four such leaves, 128-thread
+ * blocks; trees of depth >= 2, else as 64) or 128 (symmetric: each pair of
  * particles in adjacent leaves evaluated once and applied to both, one warp per leaf, four warps per block;
  * leaves wider than about 38 sigma still take the target-side kernel) or 192 (the 64-thread kernel with each
  * of the three source rows in its own block, summed at the end); targets_per_thread 2 or 4 (the most

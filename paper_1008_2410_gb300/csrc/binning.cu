@@ -56,14 +56,20 @@ __global__ void k_bbox(const SysDev *__restrict__ sys, int nsys, int n, const do
     }
 }
 
-// Root square of every system without an explicit one: centre of the box, side = extent * (1 + 2^-20),
-// at least 1e-300. Explicit IEEE operations keep the result identical to a plain C evaluation.
-__device__ void derive_constants(SysDev &d)
+// Constants every kernel reads, from the root square, depth and sigma; the host computes them for an explicit
+// square, the domain kernel for a bounding-box square. Only IEEE operations without a multiply-add (so no
+// contraction into an FMA on either side), so host and device give the same bits.
+__host__ __device__ void derive_constants(SysDev &d)
 {
     int L = d.depth;
     d.scale = ldexp(1.0, L) / d.S;
+#ifdef __CUDA_ARCH__
     d.xe = __dadd_rn(d.x0, d.S);
     d.ye = __dadd_rn(d.y0, d.S);
+#else
+    d.xe = d.x0 + d.S;
+    d.ye = d.y0 + d.S;
+#endif
     d.wl = ldexp(d.S, -L);
     d.far_scale = 1.0 / (6.283185307179586476925 * d.wl);
     double kap = d.wl * d.wl / (2.0 * d.sigma * d.sigma);
@@ -220,24 +226,34 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
             iy = 0;
     }
     const int kk = (int)(d.leaf0 + (w.morton ? (int64_t)morton2(ix, iy) : (int64_t)iy * nside + ix));
+    // boundary class (precision form, uniform tree): band (left, middle, right) x (bottom, middle, top) of the
+    // leaf, from the exact fraction F = zeta 2^52 (a point on the square's upper edge has F = 2^51: right or top
+    // band). Numbered around the leaf so that the band facing each of the 8 neighbours is a run of classes: 0 LB,
+    // 1 LM, 2 LT, 3 MT, 4 RT, 5 RM, 6 RB, 7 MB, 8 MM (the interior, last); everything is class 8 where the bands
+    // would overlap.
+    int cls = 8;
+    if (w.cls_off && d.bnd_ok) {
+        const int cx = Fx < -d.fbnd ? 0 : (Fx > d.fbnd ? 2 : 1);
+        const int cy = Fy < -d.fbnd ? 0 : (Fy > d.fbnd ? 2 : 1);
+        cls = (int)((0x432581670ull >> (4 * (3 * cy + cx))) & 15ull);
+    }
     w.key[i] = kk;
-    w.slot[i] = atomicAdd(&w.cnt[kk], 1);  // arrival slot inside the leaf (the in-leaf order is fixed later)
+    const int sl = atomicAdd(&w.cnt[kk], 1);  // arrival slot inside the leaf (the in-leaf order is fixed later)
+    w.slot[i] = sl;
+    if (w.bkt) {  // the entry straight into its leaf's bucket; a full bucket sends the evaluation to the scatter
+        if (sl < w.bkt_cap)
+            w.bkt[(int64_t)kk * w.bkt_cap + sl] = make_int2(i, cls);
+        else
+            w.cnt[w.nleaf] = 1;
+    }
     if (w.mixed) {
         float hx, lx, hy, ly;
         frac_to_split(Fx, d.s_unit, &hx, &lx);
         frac_to_split(Fy, d.s_unit, &hy, &ly);
         w.pos4u[2 * (int64_t)i] = make_float4(hx, hy, lx, ly);
-        // boundary class: band (left, middle, right) x (bottom, middle, top) of the leaf, from the exact fraction
-        // F = zeta 2^52 (a point on the square's upper edge has F = 2^51: right or top band). Numbered around the
-        // leaf so that the band facing each of the 8 neighbours is a run of classes: 0 LB, 1 LM, 2 LT, 3 MT,
-        // 4 RT, 5 RM, 6 RB, 7 MB, 8 MM (the interior, last); everything is class 8 where the bands would overlap.
-        int cls = 8;
-        if (w.cls_off && d.bnd_ok) {
-            const int cx = Fx < -d.fbnd ? 0 : (Fx > d.fbnd ? 2 : 1);
-            const int cy = Fy < -d.fbnd ? 0 : (Fy > d.fbnd ? 2 : 1);
-            cls = (int)((0x432581670ull >> (4 * (3 * cy + cx))) & 15ull);
-        }
-        w.pos4u[2 * (int64_t)i + 1] = make_float4(__double2float_rn(g[i]), __int_as_float(cls), 0.f, 0.f);
+        if (w.cls_off)
+            w.cls8[i] = (unsigned char)cls;
+        w.pos4u[2 * (int64_t)i + 1] = make_float4(__double2float_rn(g[i]), 0.f, 0.f, 0.f);
     } else if (w.rec64) {
         Rec64 r;
         r.x = xi;
@@ -496,20 +512,23 @@ int launch_scan(const Work &w, cudaStream_t s)
 
 // ------------------------------------------------------------------ counting-sort scatter and in-leaf order
 
-__global__ void k_scatter(int n, const int *__restrict__ key, const int *__restrict__ slot,
-                          const int *__restrict__ start, const float4 *__restrict__ pos4u, int2 *tmp)
+__global__ void k_scatter(Work w, const unsigned char *__restrict__ cls8, const int *__restrict__ overflow)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
-        return;
-    const int k = key[i];
-    // caller index and leaf (or boundary class), at the leaf's arrival slot
-    tmp[start[k] + slot[i]] = make_int2(i, pos4u ? __float_as_int(pos4u[2 * (int64_t)i + 1].y) : k);
+    if (overflow && *overflow == 0)
+        return;  // with leaf buckets the scatter runs only after one overflowed
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += gridDim.x * blockDim.x) {
+        const int k = w.key[i];
+        // caller index and leaf (or boundary class), at the leaf's arrival slot
+        w.tmp[w.start[k] + w.slot[i]] = make_int2(i, cls8 ? (int)cls8[i] : k);
+    }
 }
 
 int launch_scatter_sort(const Work &w, cudaStream_t s)
 {
-    k_scatter<<<(w.n + 255) / 256, 256, 0, s>>>(w.n, w.key, w.slot, w.start, w.cls_off ? w.pos4u : nullptr, w.tmp);
+    // with leaf buckets usually nothing to do: a grid of a few blocks per SM, which checks the flag and returns
+    const unsigned nb = (unsigned)((w.n + 255) / 256);
+    k_scatter<<<w.bkt ? (nb < 152u * 4u ? nb : 152u * 4u) : nb, 256, 0, s>>>(
+        w, w.cls_off ? w.cls8 : nullptr, w.bkt ? w.cnt + w.nleaf : nullptr);
     return 1;
 }
 
@@ -560,34 +579,53 @@ __device__ __forceinline__ void place_particle(const Work &w, int v, int pos, in
     }
 }
 
-// Ranks one leaf's entries (keys all distinct) with the whole block: by caller index, or with `cls` (tmp holds the
-// boundary class in .y) by (class, caller index); then writes the first position of classes 1..8 of the leaf.
-__device__ __forceinline__ unsigned long long rank_key(int2 e, bool cls)
+// Ranks one leaf's entries ent[0..c) (keys all distinct) with the whole block: by caller index, or with `cls`
+// (.y holds the boundary class) by (class, caller index); then writes the first position of classes 1..8 of the
+// leaf. K = unsigned packs (class, index) into 32 bits, for caller indices below 2^28.
+template <typename K>
+__device__ __forceinline__ K rank_key(int2 e, bool cls)
 {
-    return ((cls ? (unsigned long long)(unsigned)e.y : 0ull) << 32) | (unsigned)e.x;
+    if (sizeof(K) == 4)
+        return (K)(((cls ? (unsigned)e.y : 0u) << 28) | (unsigned)e.x);
+    return (K)(((cls ? (unsigned long long)(unsigned)e.y : 0ull) << 32) | (unsigned)e.x);
 }
 
-__device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, unsigned long long *tile, int *ccount,
-                                                 bool cls, const double *x, const double *y, const double *g,
-                                                 const double *gu, const double *gv, int mixed)
+template <typename K>
+__device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, const int2 *__restrict__ ent, K *tile,
+                                                 int *ccount, bool cls, const double *x, const double *y,
+                                                 const double *g, const double *gu, const double *gv, int mixed)
 {
     const int s0 = w.start[leaf], c = w.start[leaf + 1] - s0;
     if (cls && threadIdx.x < 9)
         ccount[threadIdx.x] = 0;
     for (int e0 = 0; e0 < c; e0 += blockDim.x) {
         const int e = e0 + threadIdx.x;
-        const int2 me = e < c ? w.tmp[s0 + e] : make_int2(0, 0);
-        const unsigned long long v = rank_key(me, cls);
+        const int2 me = e < c ? ent[e] : make_int2(0, 0);
+        const K v = rank_key<K>(me, cls);
         int rank = 0;
         for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
             const int m = min(SORT_TILE, c - f0);
+            constexpr int V = 16 / sizeof(K);  // keys per 16-byte shared-memory read
+            const int mv = (m + V - 1) / V;    // the tile padded with the largest key, which no entry reaches
             __syncthreads();
-            for (int j = threadIdx.x; j < m; j += blockDim.x)
-                tile[j] = rank_key(w.tmp[s0 + f0 + j], cls);
+            for (int j = threadIdx.x; j < mv * V; j += blockDim.x)
+                tile[j] = j < m ? rank_key<K>(ent[f0 + j], cls) : ~K(0);
             __syncthreads();
-            if (e < c)
-                for (int j = 0; j < m; ++j)
-                    rank += tile[j] < v;
+            if (e < c) {
+                if constexpr (sizeof(K) == 4) {
+                    const uint4 *t4 = reinterpret_cast<const uint4 *>(tile);
+                    for (int j = 0; j < mv; ++j) {
+                        const uint4 q = t4[j];
+                        rank += (q.x < v) + (q.y < v) + (q.z < v) + (q.w < v);
+                    }
+                } else {
+                    const ulonglong2 *t2 = reinterpret_cast<const ulonglong2 *>(tile);
+                    for (int j = 0; j < mv; ++j) {
+                        const ulonglong2 q = t2[j];
+                        rank += (q.x < v) + (q.y < v);
+                    }
+                }
+            }
         }
         if (e < c) {
             place_particle(w, me.x, s0 + rank, leaf, x, y, g, gu, gv, mixed);
@@ -638,10 +676,13 @@ __global__ void __launch_bounds__(128) k_leaf_big(Work w, const double *__restri
                                                   const double *__restrict__ g, const double *__restrict__ gu,
                                                   const double *__restrict__ gv, int mixed)
 {
-    __shared__ unsigned long long tile[SORT_TILE];
+    __shared__ __align__(16) unsigned long long tile[SORT_TILE];
     const int nb = *w.big_cnt;
-    for (int b = blockIdx.x; b < nb; b += gridDim.x)  // block-uniform
-        order_leaf_block(w, w.big[b], tile, nullptr, false, x, y, g, gu, gv, mixed);
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {  // block-uniform
+        const int leaf = w.big[b];
+        order_leaf_block<unsigned long long>(w, leaf, w.tmp + w.start[leaf], tile, nullptr, false, x, y, g, gu, gv,
+                                             mixed);
+    }
 }
 
 // The uniform tree (tens of particles in each of at most millions of leaves): one block per leaf.
@@ -649,9 +690,17 @@ __global__ void __launch_bounds__(64) k_leaf_block(Work w, const double *__restr
                                                    const double *__restrict__ g, const double *__restrict__ gu,
                                                    const double *__restrict__ gv, int mixed)
 {
-    __shared__ unsigned long long tile[SORT_TILE];
+    __shared__ __align__(16) unsigned long long tile[SORT_TILE];
     __shared__ int ccount[9];
-    order_leaf_block(w, blockIdx.x, tile, ccount, w.cls_off != nullptr, x, y, g, gu, gv, mixed);
+    const int leaf = blockIdx.x;
+    // no bucket overflowed: the leaf's bucket, else its run of the scattered list
+    const int2 *ent = w.bkt && w.cnt[w.nleaf] == 0 ? w.bkt + (int64_t)leaf * w.bkt_cap : w.tmp + w.start[leaf];
+    if (w.n <= (1 << 28))  // (class, caller index) in 32 bits
+        order_leaf_block<unsigned>(w, leaf, ent, reinterpret_cast<unsigned *>(tile), ccount, w.cls_off != nullptr,
+                                   x, y, g, gu, gv, mixed);
+    else
+        order_leaf_block<unsigned long long>(w, leaf, ent, tile, ccount, w.cls_off != nullptr, x, y, g, gu, gv,
+                                             mixed);
 }
 
 int launch_gather(const Work &w, const double *x, const double *y, const double *g, const double *gu,

@@ -269,6 +269,8 @@ static void build_system_layout(fmm_handle h, int64_t *nleaf_out, int64_t *nbox_
         leaf += (int64_t)1 << (2 * c.depth);
         for (int l = 0; l <= FMM_MAXL; ++l)
             d.box0[l] = -1;
+        if (c.explicit_domain)
+            derive_constants(d);  // else the domain kernel derives them from the bounding box
         if (c.depth > maxd)
             maxd = c.depth;
     }
@@ -332,7 +334,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     size_t sizes[40];
     int i = 0;
     sizes[i++] = np * 4;                                      // 0 key
-    sizes[i++] = (size_t)nleaf * 4 + 16;                      // 1 cnt
+    sizes[i++] = (size_t)nleaf * 4 + 16;                      // 1 cnt and the overflow flag
     sizes[i++] = (size_t)(nleaf + 1) * 4 + 16;                // 2 start
     sizes[i++] = (size_t)((nleaf + 1023) / 1024 + 2) * 4;     // 3 scan_tmp
     sizes[i++] = np * 8;                                      // 4 tmp (caller index, leaf)
@@ -364,6 +366,13 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = h->adaptive_cap ? (FMM_MAXL + 2) * 4 : 0;      // 30 ad_cnt
     sizes[i++] = (size_t)(n / 129 + 2) * 4;                    // 31 big (leaves of more than 128 particles)
     sizes[i++] = mixed ? (size_t)nleaf * 32 + 16 : 0;          // 32 cls_off (boundary classes of each leaf)
+    sizes[i++] = mixed ? np : 0;                              // 33 cls8 (boundary class of each particle)
+    // 34 leaf buckets of the uniform tree: four times the mean occupancy (at least 32) per leaf, so that only
+    // strongly clustered inputs overflow into the scatter; none where that would take more than 64 B a particle
+    int64_t bcap = 4 * ((n + nleaf - 1) / (nleaf > 0 ? nleaf : 1));
+    bcap = bcap < 32 ? 32 : (bcap + 31) / 32 * 32;
+    const bool use_bkt = !h->adaptive_cap && nleaf > 0 && (size_t)nleaf * (size_t)bcap * 8 <= 64 * np;
+    sizes[i++] = use_bkt ? (size_t)nleaf * (size_t)bcap * 8 : 0;
     int count = i;
     Layout lay;
     size_t total = 0;
@@ -451,6 +460,9 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.ad_cnt = sizes[30] ? (int *)(b + lay.off[30]) : nullptr;
     w.big = (int *)(b + lay.off[31]);
     w.cls_off = sizes[32] ? (int *)(b + lay.off[32]) : nullptr;
+    w.cls8 = sizes[33] ? (unsigned char *)(b + lay.off[33]) : nullptr;
+    w.bkt = sizes[34] ? (int2 *)(b + lay.off[34]) : nullptr;
+    w.bkt_cap = sizes[34] ? (int)bcap : 0;
     w.lv = h->lv;
     return FMM_OK;
 }
@@ -514,10 +526,11 @@ static fmm_status enqueue_adaptive(fmm_handle h, cudaStream_t s, int mode, const
     (void)cudaGetLastError();
     if (timed)
         CU(record_timing(h->ev_t[0], s));
-    CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
-    if (!h->has_domain)
+    CU(cudaMemsetAsync(w.cnt, 0, (size_t)(w.nleaf + 1) * sizeof(int), s));  // counts and overflow flag
+    if (!h->has_domain) {
         nl += launch_bbox(w, x, y, s);
-    nl += launch_domain_finalize(w, s);
+        nl += launch_domain_finalize(w, s);
+    }
     nl += launch_keys(w, x, y, g, s);
     nl += launch_scan(w, s);
     nl += launch_scatter_sort(w, s);
@@ -588,13 +601,14 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
     (void)cudaGetLastError();  // drop a stale, non-sticky error left by an unrelated runtime call
     if (timed)
         CU(record_timing(h->ev_t[0], s));
-    CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
+    CU(cudaMemsetAsync(w.cnt, 0, (size_t)(w.nleaf + 1) * sizeof(int), s));  // counts and overflow flag
     bool any_bbox = false;
     for (auto &c : h->sys_cfg)
         any_bbox |= !c.explicit_domain;
-    if (any_bbox)
+    if (any_bbox) {  // explicit squares: the host derived the constants
         nl += launch_bbox(w, x, y, s);
-    nl += launch_domain_finalize(w, s);
+        nl += launch_domain_finalize(w, s);
+    }
     nl += launch_keys(w, x, y, g, s);
     nl += launch_scan(w, s);
     nl += launch_scatter_sort(w, s);
@@ -1048,11 +1062,11 @@ fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread)
         threads = 64;
     if (targets_per_thread == 0)
         targets_per_thread = 4;
-    if ((threads != 32 && threads != 64 && threads != 128 && threads != 192) ||
+    if ((threads != 32 && threads != 64 && threads != 128 && threads != 192 && threads != 256) ||
         (targets_per_thread != 2 && targets_per_thread != 4))
         return set_err(h, FMM_EINVAL,
-                       "tile: threads 32 (one leaf per block), 64 (two), 128 (symmetric) or 192 (per source row), "
-                       "targets per thread 2 or 4");
+                       "tile: threads 32 (one leaf per block), 64 (two), 256 (four), 128 (symmetric) or 192 (per "
+                       "source row), targets per thread 2 or 4");
     h->p2p_threads = threads;
     h->p2p_kt = targets_per_thread;
     return FMM_OK;
@@ -1289,10 +1303,11 @@ fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const 
     cudaStream_t s = h->stream;
     int64_t nl = 0;
     bool far = w.lv.maxdepth >= 2;
-    CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
-    if (!h->has_domain)
+    CU(cudaMemsetAsync(w.cnt, 0, (size_t)(w.nleaf + 1) * sizeof(int), s));  // counts and overflow flag
+    if (!h->has_domain) {
         nl += launch_bbox(w, x, y, s);
-    nl += launch_domain_finalize(w, s);
+        nl += launch_domain_finalize(w, s);
+    }
     nl += launch_keys(w, x, y, gamma, s);
     nl += launch_scan(w, s);
     nl += launch_scatter_sort(w, s);
@@ -1362,9 +1377,8 @@ fmm_status fmm_level_multipoles(fmm_handle h, int64_t n, const double *x, const 
     cudaStream_t s = h->stream;
     int64_t nl = 0;
     (void)cudaGetLastError();
-    CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
-    nl += launch_domain_finalize(w, s);
-    nl += launch_keys(w, x, y, gamma, s);
+    CU(cudaMemsetAsync(w.cnt, 0, (size_t)(w.nleaf + 1) * sizeof(int), s));  // counts and overflow flag
+    nl += launch_keys(w, x, y, gamma, s);  // an explicit square: the host derived the constants
     nl += launch_scan(w, s);
     nl += launch_scatter_sort(w, s);
     nl += launch_gather(w, x, y, gamma, nullptr, nullptr, s);
@@ -1547,8 +1561,8 @@ fmm_status fmm_autotune(fmm_handle h, int64_t n, const double *x, const double *
             fclose(f);
         }
     }
-    int tiles[][2] = {{64, 4}, {128, 4}, {192, 4}, {128, 2}, {192, 2}, {64, 2}, {32, 4}, {32, 2}};
-    int ntile = h->mixed ? 8 : 1;
+    int tiles[][2] = {{64, 4}, {128, 4}, {192, 4}, {128, 2}, {192, 2}, {64, 2}, {256, 2}, {256, 4}, {32, 4}, {32, 2}};
+    int ntile = h->mixed ? 10 : 1;
     // candidates are timed the way the handle will run them: replayed graphs when the handle uses graphs (the
     // overlap of the near field with the sweep differs between eager launches and a graph)
     int save_timing = h->timing;
@@ -1616,8 +1630,9 @@ fmm_status fmm_autotune_batched(fmm_handle h, int nsys, const int64_t *offsets, 
     if (nsys < 1 || nsys > FMM_MAXSYS || !offsets || !depths_out)
         return set_err(h, FMM_EINVAL, "autotune_batched: nsys in [1, %d], offsets and depths_out given", FMM_MAXSYS);
     static const double targets[] = {16.0, 32.0, 48.0, 64.0, 96.0, 128.0};
-    static const int tiles[][2] = {{64, 4}, {64, 2}, {128, 4}, {192, 4}, {192, 2}, {128, 2}, {32, 4}, {32, 2}};
-    const int ntile = h->mixed ? 8 : 1;
+    static const int tiles[][2] = {{64, 4}, {64, 2}, {256, 2}, {256, 4}, {128, 4}, {192, 4}, {192, 2}, {128, 2},
+                                   {32, 4}, {32, 2}};
+    const int ntile = h->mixed ? 10 : 1;
     std::vector<int> depths(nsys), best_depths(nsys);
     const int save_timing = h->timing;
     h->timing = 0;

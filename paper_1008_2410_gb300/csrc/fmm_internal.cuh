@@ -122,6 +122,11 @@ struct Work {
                               // the uniform precision form stores (caller index, boundary class) instead
     int *cls_off;             // uniform precision form: [nleaf][8] first sorted position of boundary classes 1..8
                               // of each leaf (class 0 starts at start[leaf]), or null
+    unsigned char *cls8;      // with cls_off: [n] caller order, boundary class of each particle (key kernel)
+    int2 *bkt;                // uniform tree: [nleaf][bkt_cap] each leaf's entries (caller index, class) at their
+                              // arrival slots, written by the key kernel; cnt[nleaf] != 0 marks a leaf that
+                              // overflowed, and the evaluation then takes the scatter into tmp instead; or null
+    int bkt_cap;
     int *big, *big_cnt;       // leaves too large for the per-position ranking, and their number
     double *sx, *sy, *sg;
     float4 *eh, *el, *eg;     // precision form, leaf order: (xh, xh, yh, yh), (xl, xl, yl, yl), (g, g, -g, -g)
@@ -207,6 +212,7 @@ __device__ inline int find_sys_by_leaf(const SysDev *sys, int nsys, int64_t leaf
 // ---- launchers (each returns the number of kernels launched) ----
 int launch_bbox(const Work &w, const double *x, const double *y, cudaStream_t s);
 int launch_domain_finalize(const Work &w, cudaStream_t s);
+__host__ __device__ void derive_constants(SysDev &d);  // binning.cu: per-system constants from square, depth, sigma
 int launch_keys(const Work &w, const double *x, const double *y, const double *g, cudaStream_t s);
 int launch_scan(const Work &w, cudaStream_t s);  // cnt -> start
 int launch_scatter_sort(const Work &w, cudaStream_t s);

@@ -142,6 +142,7 @@ size_t carve_work(unsigned char *b, Work &w, int64_t n, int depth, int p, bool m
     w.pos4u = (float4 *)take(mixed ? np * 32 : 0);
     w.rec64 = (Rec64 *)take(mixed ? 0 : np * 32);
     w.cls_off = (int *)take(mixed ? (size_t)nleaf * 32 + 16 : 0);
+    w.cls8 = (unsigned char *)take(mixed ? np : 0);
     w.n = (int)n;
     w.nleaf = (int)nleaf;
     w.nbox = nbox;
@@ -264,7 +265,7 @@ extern "C" fmm_status fmm_velocity_noalloc(int tree_depth, int p, double sigma, 
     NA_CU(cudaMemcpyAsync(w.sys, &sd, sizeof sd, cudaMemcpyHostToDevice, s));
     NA_CU(cudaMemcpyAsync(w.sys_list, list, sizeof list, cudaMemcpyHostToDevice, s));
     NA_CU(cudaMemsetAsync(w.status, 0, 64, s));
-    NA_CU(cudaMemsetAsync(w.cnt, 0, (size_t)w.nleaf * sizeof(int), s));
+    NA_CU(cudaMemsetAsync(w.cnt, 0, (size_t)(w.nleaf + 1) * sizeof(int), s));
     // the same stages as fmm_velocity, in order on the caller's stream (no second stream, no events)
     if (!domain)
         launch_bbox(w, x, y, s);

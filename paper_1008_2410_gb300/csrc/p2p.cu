@@ -206,6 +206,9 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 #ifndef P2P_TILE2
 #define P2P_TILE2 288  // sources per shared-memory tile of the two-per-lane instance (one-float coordinates)
 #endif
+#ifndef P2P_TILE4
+#define P2P_TILE4 448  // the same with four leaves per block (a row of six source leaves)
+#endif
 constexpr int kP2PUnroll = P2P_UNROLL;
 
 // (1 - 2^-a) / a for both halves of a packed pair a = r'^2 below the series threshold, written as
@@ -440,8 +443,8 @@ __device__ __forceinline__ void p2p_segment_rem(const float4 *__restrict__ EH, c
     }
 }
 
-// LPB leaves per block (1 or 2, one warp each; with 2 the leaves are the pair (2j, 2j+1) of one row and share
-// their 3 x 4 source neighbourhood). Each warp takes its leaf's targets in passes of at most 32 * ktmax. With
+// LPB leaves per block (1, 2 or 4, one warp each; with 2 or 4 the leaves are consecutive in one row and share
+// their 3 x (LPB + 2) source neighbourhood). Each warp takes its leaf's targets in passes of at most 32 * ktmax. With
 // ktmax = 4 (one-float coordinates) the passes hold 128 targets, four per lane, except the last: from 97 targets
 // on it is the same, otherwise a main group of up to 64 targets, two per lane, every lane meeting the same source,
 // plus the rest (r <= 32 after a full main group, or a whole pass of r <= 32) spread over the 64 slots with
@@ -450,14 +453,16 @@ __device__ __forceinline__ void p2p_segment_rem(const float4 *__restrict__ EH, c
 // either a main group of up to 64 targets or a remainder of at most 32, never both, so one set of accumulators is
 // live; in the split form passes are balanced, at most 64 targets, two per lane. Sources arrive by bulk copies into
 // shared memory; each slot's sum over one tile (plain FP32) is added to its total with an error-free TwoSum.
-// Register budget of the two instances (minimum resident blocks per SM).
-template <int KTM>
+// Register budget of the two instances (minimum resident blocks per SM, of 64 threads; of 128 with four leaves).
+template <int LPB, int KTM>
 struct P2PBounds {
-    static constexpr int min_blocks = KTM == 4 ? P2P_MIN_BLOCKS : P2P_MIN_BLOCKS2;
+    static constexpr int threads = LPB == 4 ? 128 : 64;
+    static constexpr int min_blocks = (KTM == 4 ? P2P_MIN_BLOCKS : P2P_MIN_BLOCKS2) / (LPB == 4 ? 2 : 1);
 };
 
 template <int LPB, int KTM>
-__global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w, int tile, int ktmax, int skip_plain)
+__global__ void __launch_bounds__(P2PBounds<LPB, KTM>::threads, P2PBounds<LPB, KTM>::min_blocks)
+    k_p2p32(Work w, int tile, int ktmax, int skip_plain)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -487,8 +492,9 @@ __global__ void __launch_bounds__(64, P2PBounds<KTM>::min_blocks) k_p2p32(Work w
     const int full_pass = KTM == 4 ? 128 : 64;
     const int per_pass = rem_form ? full_pass : 64;
     int npass = (my_c + per_pass - 1) / per_pass;
-    if (LPB == 2) {
-        const int other = first + (warp ^ 1);
+#pragma unroll
+    for (int q = 1; q < LPB; ++q) {  // the block runs as many passes as its fullest leaf needs
+        const int other = first + (warp ^ q);
         const int oc = w.start[other + 1] - w.start[other];
         npass = max(npass, (oc + per_pass - 1) / per_pass);
     }
@@ -1004,8 +1010,19 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
     // four-per-lane instance runs up to 16 blocks per SM (tile 256), the two-per-lane instance up to 20 (tile 288,
     // or 192 with split coordinates), where a larger tile (fewer block-wide waits) measured faster than more blocks
     const int tile = ktmax == 4 ? 256 : (w.p2p_all_plain ? P2P_TILE2 : 192);
-    // plus the staged targets of a pass, 16 bytes each for up to 2 x 32 ktmax targets (two warps)
+    // plus the staged targets of a pass, 16 bytes each for up to 32 ktmax targets per warp (two warps)
     const size_t sm = (size_t)tile * (w.p2p_all_plain ? 32 : 48) + (size_t)2 * 32 * ktmax * 16;
+    if (threads == 256 && w.lv.nsys_at[2] == w.nsys) {
+        // four leaves per block (every system at least 4 leaves wide): a 3 x 6 source neighbourhood for four
+        // target leaves, twice the warps per block at the same per-warp register budget
+        const int tile4 = w.p2p_all_plain ? P2P_TILE4 : 288;
+        const size_t sm4 = (size_t)tile4 * (w.p2p_all_plain ? 32 : 48) + (size_t)4 * 32 * ktmax * 16;
+        if (ktmax == 4)
+            k_p2p32<4, 4><<<(w.nleaf + 3) / 4, 128, sm4, s>>>(w, tile4, ktmax, 0);
+        else
+            k_p2p32<4, 2><<<(w.nleaf + 3) / 4, 128, sm4, s>>>(w, tile4, ktmax, 0);
+        return 1;
+    }
     if (threads == 192 && w.p2p_rows) {
         // the target-side kernel with each of the three source rows of a leaf pair in its own block: three
         // times the blocks at a third of the length, so the last wave leaves less of the GPU idle
@@ -1025,7 +1042,7 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
         return 1;
     }
     // two leaves per block needs every system's leaves to pair up within rows (depth >= 1)
-    bool pairs = threads == 64 && w.lv.nsys_at[1] == w.nsys;
+    bool pairs = (threads == 64 || threads == 256) && w.lv.nsys_at[1] == w.nsys;
     if (pairs) {
         if (ktmax == 4)
             k_p2p32<2, 4><<<(w.nleaf + 1) / 2, 64, sm, s>>>(w, tile, ktmax, 0);

@@ -793,7 +793,8 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
     const SysDev &d = w.sys[k];
     int L = d.depth;
     bool far = use_far && L >= 2;
-    int64_t base = far ? (d.box0[L] + (int)(w.sleaf[pos] - d.leaf0)) * (int64_t)w.p : 0;
+    // first local coefficient of the particle's leaf (read only where the far field is evaluated here)
+    auto leaf_base = [&]() { return (d.box0[L] + (int)(w.sleaf[pos] - d.leaf0)) * (int64_t)w.p; };
     if (w.mixed && !level_fp64(w, L)) {
         // precision form: FP32 far field and sum, one conversion to FP64 at the end
         float fu = 0.f, fv = 0.f;
@@ -804,7 +805,7 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
         } else if (far) {
             float4 hh = w.eh[pos], ll = w.el[pos];
             cx<float> z = {(hh.x + ll.x) * d.inv_s, (hh.z + ll.z) * d.inv_s};
-            cx<float> s = horner_u<PM, float>(w.L32, base, w.p, z);
+            cx<float> s = horner_u<PM, float>(w.L32, leaf_base(), w.p, z);
             float fs = (float)d.far_scale;
             fu = s.re * fs;
             fv = -s.im * fs;
@@ -853,7 +854,7 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
             int ix = local & ((1 << L) - 1), iy = local >> L;
             z = {(w.sx[pos] - d.x0) * d.scale - (ix + 0.5), (w.sy[pos] - d.y0) * d.scale - (iy + 0.5)};
         }
-        cx<double> s = horner<double>(w.L64, base, w.p, z);
+        cx<double> s = horner<double>(w.L64, leaf_base(), w.p, z);
         fu = s.re * d.far_scale;
         fv = -s.im * d.far_scale;
     }
@@ -873,9 +874,42 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
     v[i] = nv + fv;
 }
 
+// The common precision-form case of stage 10 (the near field from the target-side kernel, the far field from
+// k_l2p32, every leaf level FP32): the same sums as k_combine in a kernel small enough to keep every warp slot
+// of an SM resident, two particles per thread, so that the dependent gathers through iperm overlap.
+__global__ void __launch_bounds__(256) k_combine32(Work w, int use_near, int use_far, double *__restrict__ u,
+                                                   double *__restrict__ v)
+{
+    const int i0 = blockIdx.x * 512 + threadIdx.x;
+    if (i0 == 0 && w.status_host)
+        *w.status_host = *w.status;  // every earlier stage has finished: hand the status word to the host
+    int pos[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        pos[h] = i0 + 256 * h < w.n ? w.iperm[i0 + 256 * h] : -1;
+    float2 t[2], f[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        t[h] = use_near && pos[h] >= 0 ? w.near32[pos[h]] : make_float2(0.f, 0.f);
+        f[h] = use_far && pos[h] >= 0 ? w.far32[pos[h]] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (pos[h] >= 0) {
+            u[i0 + 256 * h] = (double)(t[h].x + f[h].x);
+            v[i0 + 256 * h] = (double)(t[h].y + f[h].y);
+        }
+}
+
 int launch_combine(const Work &w, int use_near, int use_far, double *u, double *v, cudaStream_t s)
 {
     const unsigned nb = (unsigned)((w.n + 255) / 256);
+    const int lmin = w.coarse_level + 1 > 2 ? w.coarse_level + 1 : 2;  // every system this deep: all leaves FP32
+    if (w.mixed && !w.p2p_rows && !w.p2p_sym && (!use_far || w.far32) && lmin <= FMM_MAXL &&
+        w.lv.nsys_at[lmin] == w.nsys) {
+        k_combine32<<<(unsigned)((w.n + 511) / 512), 256, 0, s>>>(w, use_near, use_far, u, v);
+        return 1;
+    }
     if (w.p <= 8)
         k_combine<8><<<nb, 256, 0, s>>>(w, use_near, use_far, u, v);
     else if (w.p <= 16)

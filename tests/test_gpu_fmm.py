@@ -102,7 +102,8 @@ def test_mixed_symmetric_near_field_matches_oracle(lib, oracle, name, make, doma
     assert rel_l2((u.cpu().numpy(), v.cpu().numpy()), (uo, vo)) < TOL32
 
 
-@pytest.mark.parametrize("tile", [(64, 4), (64, 2), (32, 4), (32, 2), (128, 4), (128, 2), (192, 4), (192, 2)])
+@pytest.mark.parametrize("tile", [(64, 4), (64, 2), (256, 4), (256, 2), (32, 4), (32, 2), (128, 4), (128, 2), (192, 4),
+                                  (192, 2)])
 def test_mixed_tile_shapes(lib, oracle, tile):
     w = fi.clustered(30000, depth=4, p=12)  # dense leaves: several target chunks and source tiles per leaf
     uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)

@@ -265,7 +265,9 @@ def run_ours(args, rank: int, world: int, local_rank: int) -> dict | None:
             rec = dict(line.split(": ", 1) for line in open(tr_path).read().splitlines() if ": " in line)
             src = open(os.path.join(ROOT, "paper_1008_2410_gb300", "csrc", "p2p.cu"), "rb").read()
             if rec.get("p2p_cu_sha1", "").strip() == hashlib.sha1(src).hexdigest():
-                traffic = float(rec["dram_bytes_per_launch"])
+                # per-tile capture if the summary has one for the tile the autotuner picked
+                tile_key = f"dram_bytes_per_launch_{tuned['p2p_threads']}x{tuned['p2p_targets_per_thread']}"
+                traffic = float(rec.get(tile_key, rec["dram_bytes_per_launch"]))
         except Exception:
             traffic = None
     out["roofline"] = {"bound": "alu", "kernel": (f"{kname} (near field, stage 9, tile {tuned['p2p_threads']}x"

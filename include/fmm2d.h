@@ -242,7 +242,9 @@ fmm_status fmm_velocity_level(fmm_handle h, int64_t n, const double *x, const do
 fmm_status fmm_selftest_timeout(fmm_handle h, int polls);
 
 /* Per-stage device times (ms) of the last evaluation when timing is on (fmm_set_timing(h, 1)); with graphs
- * (fmm_set_graph) the events are nodes of the graph, so every replay records them. Uniform tree: out[0]
+ * (fmm_set_graph) the events are nodes of the graph, so every replay records them (each event node costs a few
+ * microseconds of the evaluation). fmm_set_timing(h, 2), uniform tree: only the near field's two events, out[1]
+ * (every other stage reads 0). Uniform tree: out[0]
  * binning, [1] near field, [2] up sweep (P2M+M2M), [3] M2L, [4] L2L (and L2P in the precision form, which
  * evaluates the far field on the sweep stream), [5] the final sum and scatter to input order (with L2P in the
  * plain form), [6] whole evaluation, [7] from the fork to the join (near field and sweep overlapped; in a

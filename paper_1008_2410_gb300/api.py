@@ -113,8 +113,9 @@ class FMM:
     def set_p2p_tile(self, threads: int, targets_per_thread: int) -> None:
         check(self._lib.fmm_set_p2p_tile(self.h, int(threads), int(targets_per_thread)), self.h)
 
-    def set_timing(self, enable: bool) -> None:
-        check(self._lib.fmm_set_timing(self.h, int(bool(enable))), self.h)
+    def set_timing(self, enable) -> None:
+        """True: every stage event; "near": only the near field's two events (uniform tree; fewer graph nodes)."""
+        check(self._lib.fmm_set_timing(self.h, 2 if enable == "near" else int(bool(enable))), self.h)
 
     def set_count_pairs(self, enable: bool) -> None:
         check(self._lib.fmm_set_count_pairs(self.h, int(bool(enable))), self.h)

@@ -582,6 +582,7 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
     bool far = mode != MODE_NEAR && w.lv.maxdepth >= 2;
     bool near = mode != MODE_FAR;
     bool timed = h->timing != 0;  // in a graph the event records become event-record nodes
+    const bool all_ev = h->timing == 1;  // timing 2: the near field's two events only (each node costs ~3 us)
     int64_t nl = 0;
     // symmetric near field (tile 128): reactions land in nearp and the final sum adds them. The host knows a
     // system takes one-float coordinates only for an explicit square (s is computed here as the device does,
@@ -599,7 +600,7 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
             w.p2p_all_plain = 0;
     }
     (void)cudaGetLastError();  // drop a stale, non-sticky error left by an unrelated runtime call
-    if (timed)
+    if (timed && all_ev)
         CU(record_timing(h->ev_t[0], s));
     CU(cudaMemsetAsync(w.cnt, 0, (size_t)(w.nleaf + 1) * sizeof(int), s));  // counts and overflow flag
     bool any_bbox = false;
@@ -626,15 +627,15 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
             if (l == h->ext_level)  // the coarse levels carry every particle the given level stands for
                 nl += launch_level_import(w, l, h->ext_M, h->ext_cnt, h->side);
         }
-        if (timed)
+        if (timed && all_ev)
             CU(record_timing(h->ev_t[2], h->side));
         nl += launch_m2l(w, h->t, 0, h->side, 1);
-        if (timed)
+        if (timed && all_ev)
             CU(record_timing(h->ev_t[3], h->side));
         for (int l = 2; l < w.lv.maxdepth; ++l)
             nl += launch_l2l(w, h->t, l, 0, h->side, 1);
         nl += launch_l2p(w, h->side);  // precision form: the far field before the join
-        if (timed)
+        if (timed && all_ev)
             CU(record_timing(h->ev_t[4], h->side));
         CU(cudaEventRecord(h->ev_join, h->side));
     }
@@ -644,7 +645,7 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
         CU(record_timing(h->ev_t[5], s));
     if (far)
         CU(cudaStreamWaitEvent(s, h->ev_join, 0));
-    if (timed)
+    if (timed && all_ev)
         CU(record_timing(h->ev_t[6], s));
     nl += launch_combine(w, near ? 1 : 0, far ? 1 : 0, u, v, s);
     if (h->count_pairs) {
@@ -654,12 +655,12 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
     }
     if (!w.status_host)  // the final sum kernel writes it otherwise
         CU(cudaMemcpyAsync(h->h_status, w.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
-    if (timed)
+    if (timed && all_ev)
         CU(record_timing(h->ev_t[7], s));
     CU(cudaGetLastError());
     h->launches += nl;
     h->last_timed = timed;
-    h->timed_mask = timed ? (far ? 0xffu : 0xe3u) : 0u;
+    h->timed_mask = timed ? (all_ev ? (far ? 0xffu : 0xe3u) : 0x22u) : 0u;
     return FMM_OK;
 }
 
@@ -1454,7 +1455,7 @@ fmm_status fmm_set_timing(fmm_handle h, int enable)
 {
     if (!h)
         return FMM_EINVAL;
-    h->timing = enable ? 1 : 0;
+    h->timing = enable == 2 ? 2 : (enable ? 1 : 0);
     return FMM_OK;
 }
 
@@ -1462,9 +1463,9 @@ int fmm_stage_times(fmm_handle h, float *out, int cap)
 {
     if (!h || !out || cap <= 0 || !h->last_timed)
         return 0;
-    if (cudaEventSynchronize(h->ev_t[7]) != cudaSuccess)
-        return 0;
     const unsigned m = h->timed_mask;
+    if (cudaEventSynchronize(h->ev_t[(m >> 7) & 1u ? 7 : 5]) != cudaSuccess)  // the last event recorded
+        return 0;
     auto el = [&](int a, int b) {
         float ms = 0.f;
         if (((m >> a) & 1u) && ((m >> b) & 1u) && cudaEventElapsedTime(&ms, h->ev_t[a], h->ev_t[b]) != cudaSuccess) {

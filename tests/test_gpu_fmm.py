@@ -492,6 +492,23 @@ def test_default_engine_and_stage_events_in_graph_replays(lib, leaf_capacity):
     f.sync()
 
 
+def test_near_field_only_stage_events(lib):
+    """Timing mode "near" (the bench's timed steps): only the near field's two events are graph nodes, so stage 1
+    reads the near field and every other stage reads 0; the results equal an untimed evaluation's bit for bit."""
+    w = fi.uniform(50000, seed_index=48, depth=5, p=12)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="mixed", domain=w.domain, graph=True)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    u0, v0 = f.velocity(x, y, g)
+    f.set_timing("near")
+    u, v = torch.empty_like(x), torch.empty_like(x)
+    for _ in range(2):  # capture, then replay
+        f.velocity(x, y, g, u, v)
+    t = f.stage_times()
+    assert len(t) == 8 and t[1] > 0 and all(t[k] == 0 for k in (0, 2, 3, 4, 5, 6, 7))
+    assert torch.equal(u, u0) and torch.equal(v, v0)
+    f.sync()
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("precision,graph", [("mixed", True), ("fp64", True)])
 def test_uniform_1m_sampled_parity(lib, oracle, precision, graph):

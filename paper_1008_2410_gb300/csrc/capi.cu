@@ -344,9 +344,9 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     sizes[i++] = f64 ? np * 8 : 0;                            // 8 sy
     sizes[i++] = f64 ? np * 8 : 0;                            // 9 sg
     sizes[i++] = (mixed || ad_mixed) ? np * 48 : 0;           // 10 eh, el, eg
-    sizes[i++] = mixed ? np * 8 : 0;                          // 11 far32
+    sizes[i++] = 0;                                           // 11 (far32 lives in near32's records)
     sizes[i++] = (mixed || h->adaptive_cap) ? 0 : np * 16;    // 12 near64 (the adaptive walk writes u, v itself)
-    sizes[i++] = mixed ? np * 8 : 0;                          // 13 near32
+    sizes[i++] = mixed ? np * 16 : 0;                         // 13 near32 + far32, interleaved
     sizes[i++] = (size_t)nbox * 4 + 16;                       // 14 bcount
     sizes[i++] = ad_mixed ? 0 : (size_t)nbox * p * 16;        // 15 M64 (the adaptive precision form keeps FP32 only)
     sizes[i++] = ad_mixed ? 0 : (size_t)nbox * p * 16;        // 16 L64
@@ -427,8 +427,10 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.el = sizes[10] ? w.eh + np : nullptr;
     w.eg = sizes[10] ? w.el + np : nullptr;
     w.near64 = sizes[12] ? (double2 *)(b + lay.off[12]) : nullptr;
+    // precision form: near and far field of each particle side by side in one 16-byte record
     w.near32 = sizes[13] ? (float2 *)(b + lay.off[13]) : nullptr;
-    w.far32 = sizes[11] ? (float2 *)(b + lay.off[11]) : nullptr;
+    w.far32 = sizes[13] ? w.near32 + 1 : nullptr;
+    w.nf_stride = sizes[13] ? 2 : 1;
     w.nearp = sizes[23] ? (float2 *)(b + lay.off[23]) : nullptr;
     w.bcount = (int *)(b + lay.off[14]);
     w.M64 = sizes[15] ? (double2 *)(b + lay.off[15]) : nullptr;

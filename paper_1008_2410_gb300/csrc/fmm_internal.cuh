@@ -102,6 +102,8 @@ struct Work {
     int coarse_level;         // levels <= this run in FP64 in the precision form
     int m2l_tc;               // FP32 M2L levels on the tensor cores (1) or on the CUDA cores (0)
     float2 *far32;            // [n] leaf order: FP32 far field (L2P) of the precision form, or null (fused)
+    int nf_stride;            // float2 stride of near32 / far32: 2 where they interleave (near, far) per particle so
+                              // that the final sum gathers one 16-byte record, else 1
     int *iperm;               // [n] caller index -> leaf-order position (inverse of perm)
     unsigned int *status_host;  // page-locked copy of *status written by the final sum kernel, or null
     float2 *nearp;            // [4][n] leaf order: symmetric near field, reactions from the leaf at -P2P

@@ -134,6 +134,7 @@ size_t carve_work(unsigned char *b, Work &w, int64_t n, int depth, int p, bool m
     w.eg = e ? w.el + np : nullptr;
     w.near64 = (double2 *)take(mixed ? 0 : np * 16);
     w.near32 = (float2 *)take(mixed ? np * 8 : 0);
+    w.nf_stride = 1;
     w.bcount = (int *)take((size_t)nbox * 4 + 16);
     w.M64 = (double2 *)take((size_t)nbox * p * 16);
     w.L64 = (double2 *)take((size_t)nbox * p * 16);

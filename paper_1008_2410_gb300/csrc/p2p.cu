@@ -646,6 +646,7 @@ __global__ void __launch_bounds__(P2PBounds<LPB, KTM>::threads, P2PBounds<LPB, K
         }
         const float snear = d.snear;
         float2 *dst = w.p2p_rows ? w.nearp + (int64_t)blockIdx.y * w.n : w.near32;  // rows: one row's part
+        const int dstride = w.p2p_rows ? 1 : w.nf_stride;
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {  // main group: targets lane + 32 (2 pr + h); pr = 1 only with kt4
             if (pr == 1 && !kt4)
@@ -661,7 +662,7 @@ __global__ void __launch_bounds__(P2PBounds<LPB, KTM>::threads, P2PBounds<LPB, K
             for (int h = 0; h < 2; ++h) {
                 const int e = lane + 32 * (2 * pr + h);
                 if (e < n_main)
-                    dst[tbase + e] = make_float2(-(su[h] + cu[h]) * snear, (sv[h] + cv[h]) * snear);
+                    dst[(int64_t)(tbase + e) * dstride] = make_float2(-(su[h] + cu[h]) * snear, (sv[h] + cv[h]) * snear);
             }
         }
         // remainder: the G partial sums of each target (slots t, t + r, ..., t + (G - 1) r), added in FP64 through
@@ -686,7 +687,7 @@ __global__ void __launch_bounds__(P2PBounds<LPB, KTM>::threads, P2PBounds<LPB, K
                         au += (double)part.x;
                         av += (double)part.y;
                     }
-                    dst[tbase + n_main + t] = make_float2(-(float)au * snear, (float)av * snear);
+                    dst[(int64_t)(tbase + n_main + t) * dstride] = make_float2(-(float)au * snear, (float)av * snear);
                 }
             }
             __syncthreads();  // the tile is free again before the next pass copies into it
@@ -957,7 +958,8 @@ __global__ void __launch_bounds__(32 * LW, P2PS_MIN_BLOCKS) k_p2p32s(Work w, int
             for (int hh = 0; hh < 2; ++hh) {
                 const int e = lane + 32 * (2 * pr + hh);
                 if (e < t_cnt)
-                    w.near32[tbase + e] = make_float2(-(su[hh] + cu[hh]) * snear, (svv[hh] + cv[hh]) * snear);
+                    w.near32[(int64_t)(tbase + e) * w.nf_stride] =
+                        make_float2(-(su[hh] + cu[hh]) * snear, (svv[hh] + cv[hh]) * snear);
             }
         }
     }

@@ -757,7 +757,7 @@ __global__ void k_l2p32(Work w)
     cx<float> z = {(hh.x + ll.x) * d.inv_s, (hh.z + ll.z) * d.inv_s};
     cx<float> s = horner_u<PM, float>(w.L32, base, w.p, z);
     float fs = (float)d.far_scale;
-    w.far32[pos] = make_float2(s.re * fs, -s.im * fs);
+    w.far32[(int64_t)pos * w.nf_stride] = make_float2(s.re * fs, -s.im * fs);
 }
 
 int launch_l2p(const Work &w, cudaStream_t s)
@@ -799,7 +799,7 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
         // precision form: FP32 far field and sum, one conversion to FP64 at the end
         float fu = 0.f, fv = 0.f;
         if (far && w.far32) {
-            const float2 f = w.far32[pos];  // k_l2p32
+            const float2 f = w.far32[(int64_t)pos * w.nf_stride];  // k_l2p32
             fu = f.x;
             fv = f.y;
         } else if (far) {
@@ -819,7 +819,7 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
                 t.y += q.y;
             }
         } else if (use_near) {
-            t = w.near32[pos];
+            t = w.near32[(int64_t)pos * w.nf_stride];
         }
         if (use_near && w.p2p_sym && d.s_unit <= P2P_SPLIT_S) {
             // symmetric near field: add the reactions from the four backward neighbour leaves, fixed order
@@ -861,7 +861,7 @@ __global__ void k_combine(Work w, int use_near, int use_far, double *__restrict_
     double nu = 0.0, nv = 0.0;
     if (use_near) {
         if (w.mixed) {
-            float2 t = w.near32[pos];
+            float2 t = w.near32[(int64_t)pos * w.nf_stride];
             nu = t.x;
             nv = t.y;
         } else {
@@ -890,8 +890,14 @@ __global__ void __launch_bounds__(256) k_combine32(Work w, int use_near, int use
     float2 t[2], f[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        t[h] = use_near && pos[h] >= 0 ? w.near32[pos[h]] : make_float2(0.f, 0.f);
-        f[h] = use_far && pos[h] >= 0 ? w.far32[pos[h]] : make_float2(0.f, 0.f);
+        if (w.nf_stride == 2 && pos[h] >= 0) {  // near and far side by side: one 16-byte gather
+            const float4 q = reinterpret_cast<const float4 *>(w.near32)[pos[h]];
+            t[h] = use_near ? make_float2(q.x, q.y) : make_float2(0.f, 0.f);
+            f[h] = use_far ? make_float2(q.z, q.w) : make_float2(0.f, 0.f);
+        } else {
+            t[h] = use_near && pos[h] >= 0 ? w.near32[(int64_t)pos[h] * w.nf_stride] : make_float2(0.f, 0.f);
+            f[h] = use_far && pos[h] >= 0 ? w.far32[(int64_t)pos[h] * w.nf_stride] : make_float2(0.f, 0.f);
+        }
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h)

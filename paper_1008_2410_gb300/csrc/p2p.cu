@@ -198,7 +198,7 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 #define P2P_UNROLL 1  // source loop unroll of the near-field kernel
 #endif
 #ifndef P2P_MIN_BLOCKS
-#define P2P_MIN_BLOCKS 16  // minimum resident blocks per SM requested from the register allocator (64 registers)
+#define P2P_MIN_BLOCKS 18  // minimum resident blocks per SM requested from the register allocator (56 registers)
 #endif
 #ifndef P2P_MIN_BLOCKS2
 #define P2P_MIN_BLOCKS2 24  // the same for the two-targets-per-lane instance (40 registers)
@@ -1009,7 +1009,7 @@ int launch_p2p(const Work &w, int threads, int kt, cudaStream_t s)
         return nl;
     }
     // shared memory per block: 32 bytes per source when every system keeps one-float coordinates, else 48; the
-    // four-per-lane instance runs up to 16 blocks per SM (tile 256), the two-per-lane instance up to 20 (tile 288,
+    // four-per-lane instance runs up to 17 blocks per SM (tile 256, 56 registers), the two-per-lane instance up to 20 (tile 288,
     // or 192 with split coordinates), where a larger tile (fewer block-wide waits) measured faster than more blocks
     const int tile = ktmax == 4 ? 256 : (w.p2p_all_plain ? P2P_TILE2 : 192);
     // plus the staged targets of a pass, 16 bytes each for up to 32 ktmax targets per warp (two warps)

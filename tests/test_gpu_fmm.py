@@ -62,6 +62,10 @@ CASES = [
     ("p1_d3", lambda: fi.uniform(2000, seed_index=37, depth=3, p=1)),
     ("p32_d3", lambda: fi.uniform(2000, seed_index=38, depth=3, p=32)),
     ("patches64k_d6_p20", lambda: fi.patches(1 << 16, seed_index=39, depth=6, p=20)),
+    # leaves 3 sigma wide: most particles sit in a boundary band, so the near field tests most neighbour sources
+    ("wide_bands_d5", lambda: fi.uniform(20000, seed_index=41, depth=5, p=14, sigma=0.0105)),
+    # leaves narrower than two band widths: no band order, every source tested
+    ("no_bands_d6", lambda: fi.uniform(20000, seed_index=42, depth=6, p=14, sigma=0.01)),
 ]
 
 
@@ -391,7 +395,7 @@ def test_stage_times_launch_count_and_autotune(lib):
     assert f.kernel_launches() > n0 + 8
     prm = f.autotune(x, y, g, 4, 6)
     assert 4 <= prm["depth"] <= 6
-    assert prm["p2p_threads"] in (32, 64, 128, 192) and prm["p2p_targets_per_thread"] in (2, 4)
+    assert prm["p2p_threads"] in (32, 64, 128, 192, 256) and prm["p2p_targets_per_thread"] in (2, 4)
     assert prm["m2l_engine"] in ("tensor", "cuda_cores")
 
 
@@ -659,7 +663,7 @@ def test_autotune_batched_picks_depths_and_tile(lib, oracle):
     assert len(deps) == len(b.systems)
     assert any(all(d == max(0, min(12, round(math.log(s.n / occ, 4)))) for d, s in zip(deps, b.systems))
                for occ in (16, 32, 48, 64, 96, 128))
-    assert prm["p2p_threads"] in (32, 64, 128, 192) and prm["p2p_targets_per_thread"] in (2, 4)
+    assert prm["p2p_threads"] in (32, 64, 128, 192, 256) and prm["p2p_targets_per_thread"] in (2, 4)
     u, v = f.velocity_batched(off, xd, yd, gd, depths=deps, sigmas=sig, domains=doms)
     f.sync()
     u, v = u.cpu().numpy(), v.cpu().numpy()

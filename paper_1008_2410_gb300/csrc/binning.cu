@@ -78,9 +78,10 @@ __host__ __device__ void derive_constants(SysDev &d)
     d.inv_s = 1.0f / s;
     d.snear = (float)((double)s * d.far_scale);
     d.iu = sqrt(1.4426950408889634074 / (2.0 * d.sigma * d.sigma));
-    // band width delta = sigma (1 + 2^-8) in leaf widths; the margin keeps every pair the near field computes
-    // at r' ^ 2 < its series threshold (r < sigma, up to FP32 rounding) inside the tested bands
-    const double om = d.sigma * (1.0 + 0x1p-8) / d.wl;
+    // band width delta = 6 sigma (1 + 2^-8) in leaf widths: a pair farther apart has exp(-r^2 / 2 sigma^2) <
+    // 2^-25, so 1 - exp rounds to 1 in FP32 and the near field skips the exponential outside the bands; the
+    // bands also hold every pair below the series threshold (r < sigma), with room for FP32 rounding
+    const double om = 6.0 * d.sigma * (1.0 + 0x1p-8) / d.wl;
     d.bnd_ok = om < 0.5 ? 1 : 0;
     d.fbnd = d.bnd_ok ? (long long)floor((0.5 - om) * 0x1p52) : 0;
 }

@@ -247,13 +247,14 @@ __device__ __forceinline__ void two_sum2(f2 &s, f2 &c, f2 x)
 // into lo.
 // SPLIT keeps the sources' lo parts (differences at FP64-level resolution); otherwise each coordinate is one
 // float (the target's rounded once from its exact shifted hi + lo) and a difference costs one instruction.
-// Only sources ja..jb are tested for small r (the targets' own leaf: all of them); the others lie at least sigma
-// from every target (outside the band of their leaf that faces the targets' leaf), where the plain factor is
-// accurate, and run without the test: [j0, ja) and [jb, j1) first, then the band.
+// Only sources j0..t1 and ja..jb are tested for small r and take the exponential (the targets' own leaf: all of
+// them); the others lie more than 6 sigma from every target (outside the band of their leaf that faces the
+// targets' leaf), where 1 - exp(-r^2 / 2 sigma^2) is 1 in FP32, and run without either: [t1, ja) and [jb, j1)
+// first, then the band.
 template <int KT, bool SELF, bool SPLIT>
 __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restrict__ EH,
                                             const float4 *__restrict__ EL, const float4 *__restrict__ EG, int j0,
-                                            int j1, int ja, int jb, float sdx, float sdy,
+                                            int j1, int t1, int ja, int jb, float sdx, float sdy,
                                             const float4 *__restrict__ TT, int tcnt, f2 *PU, f2 *PV)
 {
     constexpr int NP = KT / 2;
@@ -304,10 +305,14 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
             r2[pr] = fma2(dx[pr], dx[pr], mul2(dy[pr], dy[pr]));
             float ra, rb;
             up2(r2[pr], ra, rb);
-            const float ea = ex2_approx(-ra), eb = ex2_approx(-rb);
-            const f2 q = TEST ? pk2(rcp_approx(fmaxf(ra, P2P_RMIN2)), rcp_approx(fmaxf(rb, P2P_RMIN2)))
-                              : pk2(rcp_approx(ra), rcp_approx(rb));
-            gf[pr] = mul2(fma2(pk2(ea, eb), gn, gp), q);  // g (1 - e) / r'^2
+            if (TEST) {
+                const float ea = ex2_approx(-ra), eb = ex2_approx(-rb);
+                const f2 q = pk2(rcp_approx(fmaxf(ra, P2P_RMIN2)), rcp_approx(fmaxf(rb, P2P_RMIN2)));
+                gf[pr] = mul2(fma2(pk2(ea, eb), gn, gp), q);  // g (1 - e) / r'^2
+            } else {
+                // outside the bands r > 6 sigma: e < 2^-25, and 1 - e is 1 in FP32
+                gf[pr] = mul2(gp, pk2(rcp_approx(ra), rcp_approx(rb)));  // g / r'^2
+            }
         }
     };
     auto source = [&](int j, auto tst) {
@@ -347,7 +352,7 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
         }
     };
     if (!SELF) {
-        int lo = j0, hi = ja;
+        int lo = t1, hi = ja;
 #pragma unroll 1
         for (int ph = 0; ph < 2; ++ph) {
 #pragma unroll(kP2PUnroll)
@@ -357,9 +362,15 @@ __device__ __forceinline__ void p2p_segment(const Work &w, const float4 *__restr
             hi = j1;
         }
     }
+    int lo = j0, hi = t1;
+#pragma unroll 1
+    for (int ph = 0; ph < 2; ++ph) {
 #pragma unroll(kP2PUnroll)
-    for (int j = ja; j < jb; ++j)
-        source(j, std::true_type{});
+        for (int j = lo; j < hi; ++j)
+            source(j, std::true_type{});
+        lo = ja;
+        hi = jb;
+    }
 }
 
 // The remainder of a pass: r targets spread over the warp's 64 slots (slot s = lane + 32 h, h = 0, 1, one half of
@@ -467,6 +478,7 @@ __global__ void __launch_bounds__(P2PBounds<LPB, KTM>::threads, P2PBounds<LPB, K
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int4 segtab[LPB][3];  // per warp, per source column of the current row: first, end, band first, end
+    __shared__ int segt1[LPB][3];    // the same: end of a second band run at the leaf's front (empty but above)
     // EH, EG, then EL (only the split form reads EL, so one-float launches allocate 32 bytes per source), then
     // each warp's targets of the current pass (p2p_smem_bytes)
     float4 *EH = reinterpret_cast<float4 *>(smem_raw), *EG = EH + tile, *EL = EG + tile;
@@ -552,28 +564,34 @@ __global__ void __launch_bounds__(P2PBounds<LPB, KTM>::threads, P2PBounds<LPB, K
             if (r1 <= r0)
                 continue;
             // this warp's three source leaves of the row (columns ix-1, ix, ix+1): their sorted ranges and the part
-            // tested for small r, the band facing the targets' leaf (a run of its boundary classes: a corner, a
-            // side with its two corners, or for the leaf above the whole boundary ring); the targets' own leaf, and
-            // systems without bands, are tested throughout
+            // tested for small r, the band facing the targets' leaf (a run of its boundary classes: a corner or a
+            // side with its two corners; for the leaf above, whose facing side is cut by the cyclic class order,
+            // classes 6-7 and class 0 at the front); the targets' own leaf, and systems without bands, are tested
+            // throughout
             __syncwarp();
             if (lane < 3) {
                 const int col = ix0 + warp - 1 + lane;
                 int4 t = make_int4(0, 0, 0, 0);
+                int t1 = 0;
                 if (col >= 0 && col < ns) {
                     t.x = w.start[rowleaf + col];
                     t.y = w.start[rowleaf + col + 1];
                     t.z = t.x;
                     t.w = t.y;
+                    t1 = t.x;
                     if (bands && !(lane == 1 && dyr == 0)) {
                         const int *o = w.cls_off + (int64_t)(rowleaf + col) * 8;  // o[k - 1]: first of class k
                         const int dir = (dyr + 1) * 3 + lane;  // source leaf at (lane - 1, dyr) from the targets'
-                        const int ka = (int)((0x006004224ull >> (4 * dir)) & 15ull);
+                        const int ka = (int)((0x066004224ull >> (4 * dir)) & 15ull);
                         const int kb = (int)((0x187307355ull >> (4 * dir)) & 15ull);
                         t.z = ka == 0 ? t.x : o[ka - 1];
                         t.w = o[kb - 1];
+                        if (dir == 7)
+                            t1 = o[0];  // class 0 (bottom-left corner) also faces the targets' leaf below
                     }
                 }
                 segtab[warp][lane] = t;
+                segt1[warp][lane] = t1;
             }
             __syncwarp();
             f2 PU[2] = {0ull, 0ull}, PV[2] = {0ull, 0ull};
@@ -605,14 +623,18 @@ __global__ void __launch_bounds__(P2PBounds<LPB, KTM>::threads, P2PBounds<LPB, K
                         continue;
                     const float sdx = (float)(k3 - 1) * s, sdy = (float)dyr * s;
                     const bool self = k3 == 1 && dyr == 0;
-                    const int ja = min(max(sg.z - q0, j0), j1), jb = max(min(sg.w - q0, j1), ja);  // tested
+                    // tested: [j0, t1) and [ja, jb)
+                    const int t1 = min(max(segt1[warp][k3] - q0, j0), j1);
+                    const int ja = min(max(sg.z - q0, t1), j1), jb = max(min(sg.w - q0, j1), ja);
 #define P2P_SEG(SELF, SPLIT) \
-    p2p_segment<2, SELF, SPLIT>(w, EH, EL, EG, j0, j1, ja, jb, sdx, sdy, TT, n_main, PU, PV)
+    p2p_segment<2, SELF, SPLIT>(w, EH, EL, EG, j0, j1, t1, ja, jb, sdx, sdy, TT, n_main, PU, PV)
                     if (KTM == 4 && kt4) {
                         if (self)
-                            p2p_segment<KTM, true, false>(w, EH, EL, EG, j0, j1, ja, jb, sdx, sdy, TT, n_main, PU, PV);
+                            p2p_segment<KTM, true, false>(w, EH, EL, EG, j0, j1, t1, ja, jb, sdx, sdy, TT, n_main, PU,
+                                                          PV);
                         else
-                            p2p_segment<KTM, false, false>(w, EH, EL, EG, j0, j1, ja, jb, sdx, sdy, TT, n_main, PU, PV);
+                            p2p_segment<KTM, false, false>(w, EH, EL, EG, j0, j1, t1, ja, jb, sdx, sdy, TT, n_main,
+                                                           PU, PV);
                     } else if (n_main > 0) {
                         if (split) {
                             if (self)

@@ -12,6 +12,8 @@ compiles it with gcc and exposes thin numpy wrappers. Every function follows the
 * ``direct``          -- Eq. 7, the O(N^2) velocity sum (optionally at a subset of targets)
 * ``split_direct``    -- the sum the FMM converges to (§2, last paragraph): K_sigma for particles in equal or
                          adjacent leaves, the point-vortex kernel for all other pairs
+* ``far_tail``        -- the regularised far-field correction: (K_sigma - K_point) over the pairs whose leaves are
+                         2 .. 1 + rings leaves apart
 * ``fmm``             -- the serial FMM of Fig. 1, stages 1-10, with the §3 multipole coefficients
 * ``fmm_adjoint``     -- gradient of sum(gu*u + gv*v) by the transposed stages in reverse order
 * ``advect``          -- Eq. 3: particles moved with the FMM or direct-sum velocity, Runge-Kutta order 2 or 4
@@ -82,6 +84,9 @@ def _load():
         lib.oracle_split_direct.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D,
                                             ctypes.c_int64, _I64, _D, _D]
         lib.oracle_split_direct.restype = ctypes.c_int
+        lib.oracle_far_tail.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                        _D, ctypes.c_int64, _I64, _D, _D]
+        lib.oracle_far_tail.restype = ctypes.c_int
         lib.oracle_fmm_adjoint.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, _D, _D, _D, _D, _D, _D]
         lib.oracle_fmm_adjoint.restype = ctypes.c_int
@@ -237,6 +242,20 @@ def fmm(x, y, gamma, sigma: float, depth: int, p: int, domain=None, targets=None
     if rc != 0:
         raise MemoryError("oracle_fmm failed")
     return u, v, npairs.value
+
+
+def far_tail(x, y, gamma, sigma: float, depth: int, rings: int, domain=None, targets=None):
+    """Regularised far-field correction: (K_sigma - K_point) summed over the pairs whose leaves are 2 .. 1 + rings
+    leaves apart (Chebyshev distance). Returns (u, v) at ``targets`` (all particles if None)."""
+    x, y, g = _f64(x), _f64(y), _f64(gamma)
+    n = x.size
+    nt, t = _targets(n, targets)
+    u, v = np.zeros(nt), np.zeros(nt)
+    rc = _load().oracle_far_tail(n, _ptr(x), _ptr(y), _ptr(g), float(sigma), int(depth), int(rings),
+                                 _ptr(_dom(domain)), nt, _ptr(t, _I64), _ptr(u), _ptr(v))
+    if rc != 0:
+        raise ValueError("oracle_far_tail failed")
+    return u, v
 
 
 def split_direct(x, y, gamma, sigma: float, depth: int, domain=None, targets=None):

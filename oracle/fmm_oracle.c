@@ -583,6 +583,45 @@ int oracle_split_direct(int64_t n, const double *x, const double *y, const doubl
     return 0;
 }
 
+/* The regularised far-field correction (reading of §2, last paragraph, for leaves not much wider than sigma):
+ * sum_j gamma_j (K_sigma - K_point)(z_i - z_j) over the particles j whose leaves are `rings` or fewer leaves
+ * beyond the adjacent ones (Chebyshev leaf distance 2 .. 1 + rings), written out as the difference of the two
+ * kernels. Added to the FMM, those pairs take the exact Eq. 6 kernel; the pairs still left to the point-vortex
+ * kernel are at least (1 + rings) leaf widths w apart, so they miss at most exp(-(1 + rings)^2 w^2 / 2 sigma^2)
+ * of theirs. Same target convention as oracle_split_direct. */
+int oracle_far_tail(int64_t n, const double *x, const double *y, const double *g, double sigma, int L, int rings,
+                    const double *dom, int64_t nt, const int64_t *tidx, double *u, double *v)
+{
+    if (n <= 0 || nt <= 0)
+        return 0;
+    tree_t t;
+    int rc = tree_build(&t, n, x, y, L, 1, dom);
+    if (rc != 0) {
+        tree_free(&t);
+        return rc;
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < nt; ++k) {
+        int64_t i = tidx ? tidx[k] : k;
+        double su = 0.0, sv = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            int dx = abs(t.ix[i] - t.ix[j]), dy = abs(t.iy[i] - t.iy[j]);
+            int dist = dx > dy ? dx : dy;
+            if (dist < 2 || dist > 1 + rings)
+                continue;
+            double ku, kv, pu, pv;
+            oracle_kernel(x[i] - x[j], y[i] - y[j], sigma, &ku, &kv);
+            point_vortex_kernel(x[i] - x[j], y[i] - y[j], &pu, &pv);
+            su += g[j] * (ku - pu);
+            sv += g[j] * (kv - pv);
+        }
+        u[k] = su;
+        v[k] = sv;
+    }
+    tree_free(&t);
+    return 0;
+}
+
 /* ---------------------------------------------------------------- the adjoint of the FMM */
 
 /* Derivatives of K_sigma at (a, b): J = [[dku/da, dku/db], [dkv/da, dkv/db]], with

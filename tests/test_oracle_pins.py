@@ -347,6 +347,27 @@ def test_fmm_lattice_against_direct_sum(oracle):
     assert rel_l2((u, v), (ud, vd)) < 1e-4
 
 
+def test_far_tail_closes_the_gap_to_eq7(oracle):
+    """The regularised far-field correction (§2, last paragraph): the split sum plus (K_sigma - K_point) over the
+    pairs whose leaves are two leaves apart is Eq. 7 up to the tail of the pairs at least two leaf widths apart,
+    exp(-(2 w)^2 / 2 sigma^2) = exp(-32) on the lattice (w = 4 sigma); without it the gap is the exp(-10) tail of
+    the nearest far pairs. With no rings the correction is zero, and a wrong sign, a missing or doubled ring would
+    leave a gap of the size of the uncorrected one."""
+    w = fi.lattice_lamb_oseen()
+    ud, vd = oracle.direct(w.x, w.y, w.gamma, w.sigma)
+    us, vs = oracle.split_direct(w.x, w.y, w.gamma, w.sigma, w.depth, domain=w.domain)
+    ut, vt = oracle.far_tail(w.x, w.y, w.gamma, w.sigma, w.depth, 1, domain=w.domain)
+    gap = rel_l2((us, vs), (ud, vd))
+    assert gap > 1e-8
+    assert rel_l2((us + ut, vs + vt), (ud, vd)) < 1e-12
+    u0, v0 = oracle.far_tail(w.x, w.y, w.gamma, w.sigma, w.depth, 0, domain=w.domain)
+    assert not np.any(u0) and not np.any(v0)
+    # two rings add only the exp(-32) pairs: the same sum to 1e-12
+    u2, v2 = oracle.far_tail(w.x, w.y, w.gamma, w.sigma, w.depth, 2, domain=w.domain)
+    assert rel_l2((us + u2, vs + v2), (ud, vd)) < 1e-12
+    assert rel_l2((u2, v2), (ut, vt)) < 1e-6
+
+
 def test_fmm_empty_and_outside(oracle):
     u, v, npairs = oracle.fmm(np.zeros(0), np.zeros(0), np.zeros(0), 0.1, 3, 5, domain=(0, 0, 1))
     assert u.size == 0 and npairs == 0

@@ -149,6 +149,17 @@ fmm_status fmm_set_graph(fmm_handle h, int enable);
  * Set by fmm_autotune; exposed for experiments. */
 fmm_status fmm_set_p2p_tile(fmm_handle h, int threads, int targets_per_thread);
 
+/* Regularised far-field correction (§2, last paragraph: the FMM's far field uses the point-vortex kernel, which
+ * misses the Gaussian tail of K_sigma for far pairs when the leaves are only a few sigma wide): adds
+ * gamma_j (K_sigma - K_point)(z_i - z_j) = gamma_j (dy, -dx) exp(-r^2 / 2 sigma^2) / (2 pi r^2) over the sources
+ * j whose leaves are 2 .. 1 + rings leaves from target i's leaf (Chebyshev leaf distance), after the near field;
+ * the pairs still left to the point-vortex kernel are then at least (1 + rings) leaf widths w apart and miss at
+ * most exp(-(1 + rings)^2 w^2 / 2 sigma^2) of their term. rings in [0, 8]; 0 (the default) turns it off. Uniform
+ * tree only: an evaluation with it on an adaptive handle, the adjoint and the level exchange return FMM_EINVAL.
+ * FP64 form in FP64 (exp), precision form in FP32 on the split coordinates. No counterpart in the paper's
+ * kernels; the reading is the paper's kernel split made exact up to the stated tail. */
+fmm_status fmm_set_far_tail(fmm_handle h, int rings);
+
 /* Velocity of n particles (x, y, gamma device FP64 arrays) written to u, v (device FP64). Fig. 1 stages
  * 1-10 as described at the top of this file. */
 fmm_status fmm_velocity(fmm_handle h, int64_t n, const double *x, const double *y, const double *gamma,

@@ -41,6 +41,7 @@ SIGNATURES = {
     "fmm_set_stream": (_I, [_P, _P]),
     "fmm_set_graph": (_I, [_P, _I]),
     "fmm_set_p2p_tile": (_I, [_P, _I, _I]),
+    "fmm_set_far_tail": (_I, [_P, _I]),
     "fmm_velocity": (_I, [_P, _I64, _P, _P, _P, _P, _P]),
     "fmm_velocity_host": (_I, [_P, _I64, _P, _P, _P, _P, _P]),
     "fmm_velocity_near": (_I, [_P, _I64, _P, _P, _P, _P, _P]),

@@ -113,6 +113,10 @@ class FMM:
     def set_p2p_tile(self, threads: int, targets_per_thread: int) -> None:
         check(self._lib.fmm_set_p2p_tile(self.h, int(threads), int(targets_per_thread)), self.h)
 
+    def set_far_tail(self, rings: int) -> None:
+        """Regularised far-field correction over the leaves 2 .. 1 + rings leaves away (0: off; uniform tree)."""
+        check(self._lib.fmm_set_far_tail(self.h, int(rings)), self.h)
+
     def set_timing(self, enable) -> None:
         """True: every stage event; "near": only the near field's two events (uniform tree; fewer graph nodes)."""
         check(self._lib.fmm_set_timing(self.h, 2 if enable == "near" else int(bool(enable))), self.h)

@@ -52,6 +52,7 @@ struct fmm_ctx {
     double dom[3] = {0, 0, 1};
     int mixed = 0;
     int coarse = -1;  // precision form: FP32 on every level (radius-scaled translations stay bounded)
+    int tail_rings = 0;  // uniform tree: rings of leaves beyond the adjacent ones that get the far-field correction
     int m2l_engine = FMM_M2L_CUDA_CORES;  // the faster engine at the measured configurations; fmm_autotune re-times both
     int adaptive_cap = 0;  // > 0: adaptive tree (depth = maximum depth), split boxes holding more particles
     int adj_fp32 = 0;      // near-field part of the adjoint in FP32 (fmm_set_adjoint_precision)
@@ -99,7 +100,7 @@ struct fmm_ctx {
     uint64_t layout_version = 1;
     size_t layout_sig[6] = {};
     struct GKey {
-        int mode, n, nsys, mixed, coarse, m2l_engine, threads, kt, count_pairs, p, timing, adaptive, ext_level;
+        int mode, n, nsys, mixed, coarse, m2l_engine, threads, kt, count_pairs, p, timing, adaptive, ext_level, tail;
         uint64_t layout;
         const void *ptr[7];
         uint64_t version;
@@ -641,8 +642,10 @@ static fmm_status enqueue_forward(fmm_handle h, cudaStream_t s, int mode, const 
             CU(record_timing(h->ev_t[4], h->side));
         CU(cudaEventRecord(h->ev_join, h->side));
     }
-    if (near)
+    if (near) {
         nl += launch_p2p(w, h->p2p_threads, h->p2p_kt, s);
+        nl += launch_far_tail(w, h->tail_rings, s);
+    }
     if (timed)
         CU(record_timing(h->ev_t[5], s));
     if (far)
@@ -686,6 +689,8 @@ static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x
                               const double *g, double *u, double *v)
 {
     fmm_status st;
+    if (h->tail_rings && h->adaptive_cap)
+        return set_err(h, FMM_EINVAL, "the far-field tail correction needs the uniform tree (fmm_set_far_tail(h, 0))");
     if ((st = ensure_tables(h)) != FMM_OK)
         return st;
     if ((st = ensure_workspace(h, n, 0)) != FMM_OK)
@@ -713,6 +718,7 @@ static fmm_status run_forward(fmm_handle h, int mode, int64_t n, const double *x
     key.count_pairs = h->count_pairs;
     key.p = h->p;
     key.timing = h->timing;
+    key.tail = h->tail_rings;
     key.adaptive = h->adaptive_cap;
     key.layout = h->layout_version;
     key.ptr[0] = x;
@@ -988,6 +994,14 @@ fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level)
     if (!h || coarse_level < -1 || coarse_level > FMM_MAXL)
         return FMM_EINVAL;
     h->coarse = coarse_level;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_far_tail(fmm_handle h, int rings)
+{
+    if (!h || rings < 0 || rings > 8)
+        return FMM_EINVAL;
+    h->tail_rings = rings;
     return FMM_OK;
 }
 
@@ -1291,6 +1305,8 @@ fmm_status fmm_velocity_adjoint(fmm_handle h, int64_t n, const double *x, const 
         return st;
     if (h->adaptive_cap)
         return set_err(h, FMM_EINVAL, "the adjoint uses the uniform tree (adaptive capacity is set)");
+    if (h->tail_rings)
+        return set_err(h, FMM_EINVAL, "the adjoint has no far-field tail correction (fmm_set_far_tail(h, 0))");
     if ((st = poll_status(h, false)) != FMM_OK)
         return st;
     if (n == 0)
@@ -1347,6 +1363,8 @@ static fmm_status check_level(fmm_handle h, int level)
 {
     if (h->adaptive_cap)
         return set_err(h, FMM_EINVAL, "level exchange needs the uniform tree (adaptive capacity is set)");
+    if (h->tail_rings)
+        return set_err(h, FMM_EINVAL, "level exchange has no far-field tail correction (fmm_set_far_tail(h, 0))");
     if (!h->has_domain)
         return set_err(h, FMM_EINVAL, "level exchange needs an explicit root square shared by every part");
     if (level < 2 || level > h->depth)

@@ -496,6 +496,66 @@ def test_default_engine_and_stage_events_in_graph_replays(lib, leaf_capacity):
     f.sync()
 
 
+@pytest.mark.parametrize("precision,tol,case", [("fp64", TOL64, "lattice"), ("fp64", TOL64, "narrow"),
+                                                ("mixed", TOL32, "narrow")])
+def test_far_tail_matches_oracle(lib, oracle, precision, tol, case):
+    """The regularised far-field correction: the GPU evaluation with it equals the oracle FMM plus the oracle's
+    brute-force correction, and the correction alone (with minus without) equals the oracle's. On the lattice
+    (leaves 4 sigma wide, one ring) the correction is 1.6e-7 of the velocity and at p = 20 it takes the FMM from
+    that gap to Eq. 7 down to truncation; on leaves 1.5 sigma wide (three rings) it is 2.5 per cent of the velocity,
+    large enough to check the precision form's FP32 correction (and the FMM then meets Eq. 7 to 3.5e-7 instead of
+    2.5e-2)."""
+    if case == "lattice":
+        w, rings = fi.lattice_lamb_oseen(), 1
+    else:
+        w, rings = fi.uniform(20000, seed_index=44, depth=5, p=14, sigma=1.0 / 32 / 1.5), 3
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    f = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain)
+    u0, v0 = f.velocity(x, y, g)
+    f.set_far_tail(rings)
+    u1, v1 = f.velocity(x, y, g)
+    f.sync()
+    uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain)
+    ut, vt = oracle.far_tail(w.x, w.y, w.gamma, w.sigma, w.depth, rings, domain=w.domain)
+    got = (u1.cpu().numpy(), v1.cpu().numpy())
+    assert rel_l2(got, (uo + ut, vo + vt)) < tol
+    dcorr = (got[0] - u0.cpu().numpy(), got[1] - v0.cpu().numpy())
+    assert rel_l2(dcorr, (ut, vt)) < (1e-9 if precision == "fp64" else 1e-4)
+    if case == "lattice":
+        ud, vd = oracle.direct(w.x, w.y, w.gamma, w.sigma)
+        f20 = lib.FMM(w.depth, 20, w.sigma, precision="fp64", domain=w.domain)
+        a0 = f20.velocity(x, y, g)
+        f20.set_far_tail(1)
+        a1 = f20.velocity(x, y, g)
+        f20.sync()
+        e0 = rel_l2((a0[0].cpu().numpy(), a0[1].cpu().numpy()), (ud, vd))
+        e1 = rel_l2((a1[0].cpu().numpy(), a1[1].cpu().numpy()), (ud, vd))
+        assert e1 < e0 / 10
+
+
+def test_far_tail_rejected_where_not_built(lib):
+    """The correction runs on the uniform tree's forward evaluation only: the adaptive tree, the adjoint and the
+    level exchange refuse a handle with it on, and the handle works again once it is off."""
+    w = fi.uniform(3000, seed_index=43, depth=3, p=10)
+    x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
+    fa = lib.FMM(6, w.p, w.sigma, precision="mixed", domain=w.domain, leaf_capacity=32)
+    fa.set_far_tail(1)
+    with pytest.raises(RuntimeError):
+        fa.velocity(x, y, g)
+    fa.set_far_tail(0)
+    fa.velocity(x, y, g)
+    fa.sync()
+    f = lib.FMM(w.depth, w.p, w.sigma, precision="fp64", domain=w.domain)
+    f.set_far_tail(1)
+    with pytest.raises(RuntimeError):
+        f.adjoint(x, y, g, torch.ones_like(x), torch.ones_like(x))
+    with pytest.raises(RuntimeError):
+        f.level_multipoles(x, y, g, 2)
+    f.set_far_tail(0)
+    f.adjoint(x, y, g, torch.ones_like(x), torch.ones_like(x))
+    f.sync()
+
+
 def test_near_field_only_stage_events(lib):
     """Timing mode "near" (the bench's timed steps): only the near field's two events are graph nodes, so stage 1
     reads the near field and every other stage reads 0; the results equal an untimed evaluation's bit for bit."""

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfmm2d.so")
-SOURCES = ["capi.cu", "binning.cu", "sweep.cu", "m2l_tc.cu", "p2p.cu", "advect.cu", "adaptive.cu", "probe.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "binning.cu", "sweep.cu", "m2l_tc.cu", "p2p.cu", "far_tail.cu", "advect.cu", "adaptive.cu", "probe.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -239,7 +239,7 @@ int launch_combine(const Work &w, int use_near, int use_far, double *u, double *
 int launch_adjoint_far(const Work &w, cudaStream_t s);  // far part of (dgamma, dx, dy) into adj_far
 int launch_adjoint_combine(const Work &w, double *dg, double *dx, double *dy, cudaStream_t s);  // adds it
 int launch_adjoint_p2p(const Work &w, double *dg, double *dx, double *dy, int fp32, cudaStream_t s);
-// Regularised far-field correction of the uniform tree (p2p.cu): adds (K_sigma - K_point) over the sources whose
+// Regularised far-field correction of the uniform tree (far_tail.cu): adds (K_sigma - K_point) over the sources whose
 // leaves are 2 .. 1 + rings leaves from each target's leaf to the near field (after the near-field kernel).
 int launch_far_tail(const Work &w, int rings, cudaStream_t s);
 

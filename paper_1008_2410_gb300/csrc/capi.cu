@@ -374,6 +374,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     bcap = bcap < 32 ? 32 : (bcap + 31) / 32 * 32;
     const bool use_bkt = !h->adaptive_cap && nleaf > 0 && (size_t)nleaf * (size_t)bcap * 8 <= 64 * np;
     sizes[i++] = use_bkt ? (size_t)nleaf * (size_t)bcap * 8 : 0;
+    sizes[i++] = mixed ? m2l_tc_layout_bytes(h->lv, p) : 0;     // 35 mtc (tensor-core M2L windows)
     int count = i;
     Layout lay;
     size_t total = 0;
@@ -438,6 +439,7 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.L64 = sizes[16] ? (double2 *)(b + lay.off[16]) : nullptr;
     w.M32 = sizes[17] ? (float2 *)(b + lay.off[17]) : nullptr;
     w.L32 = sizes[18] ? (float2 *)(b + lay.off[18]) : nullptr;
+    w.mtc = sizes[35] ? (float4 *)(b + lay.off[35]) : nullptr;
     w.sgu = sizes[19] ? (double *)(b + lay.off[19]) : nullptr;
     w.sgv = sizes[20] ? (double *)(b + lay.off[20]) : nullptr;
     w.AM64 = sizes[21] ? (double2 *)(b + lay.off[21]) : nullptr;

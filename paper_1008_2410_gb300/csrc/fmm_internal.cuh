@@ -84,7 +84,7 @@ struct Tables {
     float2 *rho32;
     double *binom64;          // [PMAX][PMAX]  C(m + l, m)
     float *binom32;
-    unsigned char *m2l_tc;    // tensor-core M2L operand B (m2l_tc.cu)
+    unsigned char *m2l_tc;    // tensor-core M2L operands B_delta (m2l_tc.cu)
 };
 
 // One particle's FP64 inputs in the caller's order, written by the key kernel so that the leaf-order kernel's
@@ -140,6 +140,8 @@ struct Work {
     int *bcount;
     double2 *M64, *L64;
     float2 *M32, *L32;
+    float4 *mtc;              // precision form, levels 2 .. 7: the tensor-core M2L's window source layout (TF32 hi and
+                              // lo planes of the multipoles per class, m2l_tc.cu), or null
     // adjoint extras
     double *sgu, *sgv;
     double2 *AM64, *AL64;     // expansions of the adjoint charges G = gu + i gv
@@ -255,14 +257,17 @@ int launch_adaptive_near(const Work &w, unsigned long long *pairs, int use_near,
 
 void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *binom);
 
-// Tensor-core M2L (m2l_tc.cu): its operand table for p (the signed binomial matrix, TF32 hi and lo), the
-// table's size, the per-device kernel attributes (before any stream capture; 0 on success) and the launch
-// over levels l32 .. maxdepth.
+// Tensor-core M2L (m2l_tc.cu): its operand table for p (the 40 offsets' translation matrices, TF32 hi and lo),
+// the table's size, the p and levels it covers, the per-device kernel attributes (before any stream capture;
+// 0 on success) and the launch over levels l_lo .. l_hi (<= m2l_tc_max_level()); returns the launches made.
 size_t m2l_tc_table_bytes(int p);
+size_t m2l_tc_layout_bytes(const LevelInfo &lv, int p);  // Work::mtc for these levels and p (0: not used)
 void build_m2l_tc_table_host(int p, unsigned char *out);
+bool m2l_tc_supported(int p);
+int m2l_tc_max_level();
 int prepare_m2l_tc();
 int prepare_p2p();  // near-field kernel attributes, once per device before any stream capture; 0 on success
-int launch_m2l_tc(const Work &w, const Tables &t, int l32, cudaStream_t s);
+int launch_m2l_tc(const Work &w, const Tables &t, int l_lo, int l_hi, cudaStream_t s);
 int upload_m2l_constants(cudaStream_t s);  // once per device, before any stream capture; 0 on success
 
 }  // namespace fmm

@@ -1,28 +1,36 @@
 // m2l_tc.cu -- Fig. 1 stage 6 (M2L, §3) of the precision form on the tensor cores (tcgen05, TMEM).
 //
 // With radius-scaled coefficients the translation from a source box at offset delta = (dx, dy) box widths
-// (a Gaussian integer, max(|dx|, |dy|) in {2, 3}) is the same at every level and factors as
-//     b^_l += rho^(l+1) sum_m B[l][m] (rho^m a~_m),   B[l][m] = (-1)^(m+1) C(m+l, m),   rho = 1/delta,
-// so the only dense contraction is with the real matrix B, shared by every offset and level. A CTA owns up to
-// 128 target boxes of one level, one system and one child position (cx, cy) -- boxes that share their 27
-// interaction offsets (children of the parent's neighbours that are not adjacent) -- and walks those offsets.
-// Per offset it gathers the 128 source multipoles (zero for sources outside the domain or empty), scales them
-// by rho^m (CUDA cores), splits the real and the imaginary parts into two TF32 values each (hi, lo) and issues
-//     D_re = A_re B^T,  D_im = A_im B^T   as hi*hi + hi*lo + lo*hi (3xTF32)
-// with tcgen05.mma, accumulators in tensor memory. B (hi and lo, built on the host in FP64) is loaded once.
-// Each offset gets fresh accumulators (two stages alternate); they are read back with tcgen05.ld, multiplied by
-// rho^(l+1) and summed over the 27 offsets in FP32 registers. A single accumulator over all offsets measured
-// 7.7e-6 relative error against 3.8e-7 with the per-offset read-back: long accumulation chains inside the
-// tensor core lose accuracy.
+// (a Gaussian integer, max(|dx|, |dy|) in {2, 3}) is the same matrix at every level:
+//     b^_l += sum_m T[l][m] a~_m,   T[l][m] = (-1)^(m+1) C(m + l, m) rho^(m+l+1),   rho = 1 / delta.
+// Over the reals, with real and imaginary parts interleaved (input k = 2m + {0, 1}, output n = 2l + {0, 1}),
+// each of the 40 offsets is one 2p x 2p real matrix B_delta; the host builds them in FP64 and stores every
+// entry as a TF32 pair (hi, lo). A translation is a row of A (a source box's 2p numbers, split hi + lo as well)
+// times B_delta^T, evaluated as hi*hi + hi*lo + lo*hi (3xTF32) by tcgen05.mma into tensor memory.
 //
-// Each target row is shared by KP / 8 threads, 8 coefficients each, so that the per-offset CUDA-core work
-// (gather, scaling, split, read-back) is spread over 4 KP / 8 warps per CTA.
+// The boxes of a level fall into four classes by child position c = (cx, cy). A box of class c at class
+// coordinates (i, j) (its parent's coordinates) takes its 27 interaction-list sources from the children of the
+// parent's 3 x 3 neighbours: boxes of class c' at class coordinates (i + ox, j + oy), ox, oy in {-1, 0, 1}.
+// On a class grid whose rows carry one zero column at either end (row length Lc = 2^(l-1) + 2), the sources
+// of 128 consecutive target positions q0 .. q0 + 127 at one offset are 128 consecutive positions, starting at
+// (1 + oy) Lc + 1 + ox in the window [q0 - Lc - 1, q0 + Lc + 129) of class c'. A first kernel writes every
+// level's multipoles in that form once per evaluation (per class, TF32 hi and lo planes of 16-byte K chunks, one
+// position per chunk, zeros for padding and empty boxes); a CTA (128 target positions of one class) then takes
+// each source class's window by bulk asynchronous copies (one contiguous run per plane), and every offset's A
+// operand is a shared-memory descriptor into it (8-row core matrices 128 bytes apart, K planes one window
+// apart). Per offset no CUDA-core work remains but reading the accumulator back.
 //
-// Pipeline (two shared-memory stages s = q & 1 for offset q): the loads of offset q + 1 are issued first;
-// then wait for the MMAs of offset q - 2 (stage s), read their accumulators, stage A(q) into s; after a
-// barrier one thread issues the MMAs of offset q and commits them to mma_bar[s]. Every wait is bounded: on a
-// timeout the CTA sets FMM_DEV_TIMEOUT, lets its MMAs in flight finish (bounded), frees its tensor memory and
+// Per offset: the B pair arrives by a bulk copy into a ring of slots; one thread issues the 3 KP / 8 MMAs into
+// one of two accumulators and commits them to an mbarrier; then the 128 threads (one per target position and
+// tensor-memory lane) read the previous offset's accumulator and add it to their 2p registers, so the tensor
+// core never accumulates over more than one offset. Two window buffers alternate: the copies of the source
+// class after next start as soon as the MMAs of a class have completed. Every wait is bounded: on a timeout the
+// CTA sets FMM_DEV_TIMEOUT, lets its MMAs and copies in flight land (bounded), frees its tensor memory and
 // returns without writing.
+//
+// Levels whose class grid is wider than 64 boxes (their windows do not fit twice) and p > 20 take the CUDA-core
+// kernel (sweep.cu).
+#include <complex>
 #include <cstring>
 #include <vector>
 
@@ -32,32 +40,40 @@ namespace fmm {
 
 namespace {
 
-constexpr int kRows = 128;  // MMA M: target boxes per CTA
-constexpr int kNOff = 27;   // interaction offsets per child position
+constexpr int kRows = 128;        // MMA M: target positions per CTA
+constexpr int kNOff = 27;         // interaction offsets per class
+constexpr int kMaxClassWidth = 64;  // widest class grid (level 7) whose two windows fit in shared memory
+constexpr int kPMaxTc = 20;
+constexpr int kNDelta = 49;       // offset table index (dy + 3) * 7 + (dx + 3)
+constexpr int kReplicas = 8;      // copies of the B table, CTA i reading copy i % 8: every CTA of a class streams the
+                                  // same 27 matrices, and one copy would concentrate those reads on a few L2 slices
 
 template <int PB>
 struct TcShape {
-    static constexpr int KP = PB;                    // K: coefficient index m (PB a multiple of 8)
-    static constexpr int NP = (PB + 15) / 16 * 16;   // N: output index l, padded to the M = 128 rule
-    static constexpr int A_PART = kRows * KP * 4;    // one of re-hi, re-lo, im-hi, im-lo
-    static constexpr int B_PART = NP * KP * 4;       // one TF32 part of B
-    static constexpr int STAGE_A = 4 * A_PART;
-    static constexpr int B_BYTES = 2 * B_PART;
-    static constexpr int RHO_BYTES = kNOff * (PB + 1) * 8;  // rho^k, k = 0 .. PB, of the CTA's 27 offsets
-    static constexpr int SMEM = 2 * STAGE_A + B_BYTES + RHO_BYTES;
-    // accumulators: stage s, part (re 0, im 1) at column (2 s + part) NP; 4 NP columns (a power of two), at
-    // most 512 per SM for any number of CTAs that fit in shared memory
-    static constexpr int COLS = 4 * NP;
-    // G = KP / 8 threads per target row, each owning 8 coefficients (m on input, l on output); warp w holds
-    // rows 32 (w % 4) .. + 31 (the tensor-memory lanes it may read) and coefficients 8 (w / 4) .. + 7
-    static constexpr int G = KP / 8;
-    static constexpr int THREADS = kRows * G;
-    static constexpr int MIN_BLOCKS = PB <= 16 ? 3 : PB <= 24 ? 2 : 1;  // as many as shared memory admits
+    static constexpr int KP = (2 * PB + 7) / 8 * 8;     // K: 2p real inputs, padded to the MMA's K step
+    static constexpr int NP = (2 * PB + 15) / 16 * 16;  // N: 2p real outputs, padded to the M = 128 rule
+    static constexpr int KC = KP / 4;                   // 16-byte K chunks (window planes)
+    static constexpr int NG = KP / 8;                   // 8-row groups of B that may hold nonzero rows
+    static constexpr int B_PART = NP * KP * 4;          // one TF32 part of B_delta in the operand layout
+    static constexpr int B_LOAD = NG * KC * 128;        // bytes of a part that are copied (the rest is zero)
+    static constexpr int B_SLOT = 2 * B_PART;
+    static constexpr int NSLOT = 3;
+    static constexpr int RD = KP / 8;                   // 8-column read-backs per offset
 };
 
-// Byte offset of element (row, k) in the K-major, non-swizzled operand layout: 8-row x 16-byte core matrices,
-// K-adjacent core matrices 128 bytes apart (leading-dimension offset), 8-row groups KP/4 * 128 bytes apart
-// (stride-dimension offset).
+// Window length: the 2 Lc + 130 positions a tile reads.
+__host__ __device__ inline int window_len(int Lc) { return 2 * Lc + 130; }
+
+template <int PB>
+constexpr size_t smem_bytes(int ws)
+{
+    using S = TcShape<PB>;
+    return 2 * (size_t)(2 * S::KC * ws * 16) + (size_t)S::NSLOT * S::B_SLOT;
+}
+
+// Byte offset of element (row, k) in the K-major, non-swizzled operand layout of B: 8-row x 16-byte core
+// matrices, K-adjacent core matrices 128 bytes apart (leading-dimension offset), 8-row groups KP/4 * 128 bytes
+// apart (stride-dimension offset).
 __host__ __device__ inline int core_off(int row, int k, int KP)
 {
     return ((row >> 3) * (KP >> 2) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
@@ -90,6 +106,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
             return true;
     return false;
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// plain (non-multicast) bulk copy from this GPU's global memory into this CTA's shared memory
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
 __device__ __forceinline__ float tf32_rn(float x)
 {
     uint32_t r;
@@ -108,254 +137,374 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r)
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
 }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Adds rho^(l+1) (D_re[l] + i D_im[l]) for this thread's 8 output coefficients l = l0 + j (those < p) of its
-// row into (ar, ai); taddr_* point at column l0 of the stage's two accumulators.
-__device__ __forceinline__ void accumulate_tmem(uint32_t taddr_re, uint32_t taddr_im, const float2 *rho, int l0,
-                                                int p, float *ar, float *ai)
+// Window source layout, built per evaluation by k_m2l_tc_layout: for every level l <= 7 (from level 2), system
+// at l and class c', 2 (hi, lo) x KC planes of NPOS(l) 16-byte chunks; chunk P of plane kc holds coefficients
+// m = 2 kc, 2 kc + 1 (re, im each) of the box at padded position qq = P - Lc - 1 (row qq / Lc, column qq % Lc - 1)
+// of the class grid, or zeros (outside the grid, padding column, empty box, m >= p). A tile's window is then one
+// contiguous run of 2 Lc + 130 chunks per plane, starting at P = q0.
+__host__ __device__ inline int npos_of(int l)
 {
-    uint32_t re[8], im[8];
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    tmem_ld8(taddr_re, re);
-    tmem_ld8(taddr_im, im);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        if (l0 + j < p) {
-            const float2 r = rho[l0 + j + 1];
-            const float dr = __uint_as_float(re[j]), di = __uint_as_float(im[j]);
-            ar[j] = fmaf(r.x, dr, fmaf(-r.y, di, ar[j]));
-            ai[j] = fmaf(r.x, di, fmaf(r.y, dr, ai[j]));
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const int nc = 1 << (l - 1), Lc = nc + 2;
+    return (nc + 2) * Lc + 130;
+}
+// float4 offset of the planes of (level l, system index sidx at l, class c)
+__host__ __device__ inline int64_t layout_base(const LevelInfo &lv, int KC, int l, int sidx, int c)
+{
+    int64_t b = 0;
+    for (int k = 2; k < l; ++k)
+        b += (int64_t)lv.nsys_at[k] * 8 * KC * npos_of(k);
+    return b + (int64_t)(sidx * 4 + c) * 2 * KC * npos_of(l);
 }
 
+// Block (plane (level, system, class, K chunk), run of 256 positions), nch runs per plane; a thread writes
+// position P's hi and lo chunks.
 template <int PB>
-__global__ void __launch_bounds__(TcShape<PB>::THREADS, TcShape<PB>::MIN_BLOCKS) k_m2l_tc(Work w, const unsigned char *__restrict__ btab,
-                                                    const float2 *__restrict__ rho32, int l32)
+__global__ void __launch_bounds__(256) k_m2l_tc_layout(Work w, int l_lo, int l_hi, int nch)
 {
     using S = TcShape<PB>;
-    constexpr int RS = 2 * FMM_PMAX + 2;  // row length of the rho^k table
+    int64_t g = blockIdx.x / nch;
+    const int run = (int)(blockIdx.x % nch);
+    int l = l_lo;
+    for (; l <= l_hi; ++l) {
+        const int64_t cnt = (int64_t)w.lv.nsys_at[l] * 4 * S::KC;
+        if (g < cnt)
+            break;
+        g -= cnt;
+    }
+    if (l > l_hi)
+        return;  // block-uniform
+    const int kc = (int)(g % S::KC), r = (int)(g / S::KC), c = r & 3, sidx = r >> 2;
+    const SysDev &d = w.sys[sys_at_level(w, l, sidx)];
+    const int p = w.p, ns = 1 << l, nc = ns >> 1, Lc = nc + 2, np_ = npos_of(l);
+    const int m0 = 2 * kc, m1 = 2 * kc + 1;
+    const int64_t lev0 = d.box0[l];
+    float4 *dst = w.mtc + layout_base(w.lv, S::KC, l, sidx, c) + (int64_t)kc * np_;
+    const int P = run * blockDim.x + threadIdx.x;
+    if (P < np_) {
+        const int qq = P - Lc - 1;
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        if (qq >= 0 && qq < nc * Lc) {
+            const int row = qq / Lc, colp = qq - row * Lc;
+            if (colp >= 1 && colp <= nc) {
+                const int64_t box = lev0 + (int64_t)(2 * row + (c >> 1)) * ns + 2 * (colp - 1) + (c & 1);
+                if (w.bcount[box] != 0) {
+                    const float2 *src = w.M32 + box * p;
+                    if (m0 < p)
+                        a0 = src[m0];
+                    if (m1 < p)
+                        a1 = src[m1];
+                }
+            }
+        }
+        const float4 hi = make_float4(tf32_rn(a0.x), tf32_rn(a0.y), tf32_rn(a1.x), tf32_rn(a1.y));
+        const float4 lo = make_float4(tf32_rn(a0.x - hi.x), tf32_rn(a0.y - hi.y), tf32_rn(a1.x - hi.z),
+                                      tf32_rn(a1.y - hi.w));
+        dst[P] = hi;
+        dst[(int64_t)S::KC * np_ + P] = lo;
+    }
+}
+
+// Waits for the phase of the given parity, or gives up when another role of the CTA has failed (*bad) or after
+// a bounded number of polls (then sets *bad).
+__device__ __forceinline__ bool wait_or_bad(uint64_t *bar, uint32_t parity, volatile int *bad)
+{
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (mbar_try(bar, parity))
+            return true;
+        if ((it & 15) == 15 && *bad)
+            return false;
+    }
+    *bad = 1;
+    return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Roles: warps 0-3 read the accumulators back (warp w owns tensor-memory lanes 32 w .. 32 w + 31, i.e. target
+// positions), one thread of warp 4 issues the MMAs, one thread of warp 5 issues the bulk copies. Hand-offs go
+// through mbarriers: B slots (full / empty), window buffers (full / empty) and NS accumulator stages
+// (full / empty); the MMA thread frees a B slot, a window buffer or signals a stage by tcgen05.commit.
+constexpr int kThreads = 192;
+constexpr int kStages = 3;  // accumulator stages; each holds three accumulators (hi*hi, hi*lo, lo*hi) of NP columns
+constexpr int kParts = 3;
+__host__ __device__ constexpr int tmem_cols(int np) { return kStages * kParts * np <= 256 ? 256 : 512; }
+
+template <int PB>
+__global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(Work w, const unsigned char *__restrict__ btab, int l_lo,
+                                                        int l_hi, int ws)
+{
+    using S = TcShape<PB>;
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ __align__(8) uint64_t bfull[S::NSLOT], bempty[S::NSLOT], wfull[2], wempty[2], tfull[kStages],
+        tempty[kStages];
     __shared__ uint32_t tmem_base;
     __shared__ int s_bad;
-    __shared__ int2 s_off[kNOff];
-    unsigned char *sB = sm + 2 * S::STAGE_A;
-    float2 *s_rho = reinterpret_cast<float2 *>(sB + S::B_BYTES);  // [kNOff][PB + 1]
+    __shared__ int s_gq[5];         // first offset of each source class in the CTA's list; s_gq[4] = 27
+    __shared__ int s_delta[kNOff];  // B table index of each offset
+    __shared__ int s_a0[kNOff];     // window position of each offset's first A row
+    const int WB = 2 * S::KC * ws * 16;  // one window buffer: hi planes, then lo planes
+    unsigned char *const sB = sm + 2 * WB;
+    volatile int *bad = &s_bad;
 
-    // work item -> (level l, system, child position, tile of 128 boxes of that position)
-    int64_t g = blockIdx.x, tiles = 1;
-    int l = l32;
-    for (; l <= w.lv.maxdepth; ++l) {
-        tiles = l >= 5 ? ((int64_t)1 << (2 * l - 9)) : 1;  // 4^(l-1) boxes per position, 128 per tile
+    // block -> (level, system, class, tile of 128 positions); finest level first
+    int64_t g = blockIdx.x;
+    int l = l_hi, tiles = 1;
+    for (; l >= l_lo; --l) {
+        const int ncl = 1 << (l - 1);
+        tiles = (ncl * (ncl + 2) + kRows - 1) / kRows;
         const int64_t cnt = (int64_t)w.lv.nsys_at[l] * 4 * tiles;
         if (g < cnt)
             break;
         g -= cnt;
     }
-    if (l > w.lv.maxdepth)
+    if (l < l_lo)
         return;  // block-uniform
     const int sidx = (int)(g / (4 * tiles));
-    const int64_t rem = g - (int64_t)sidx * 4 * tiles;
-    const int cls = (int)(rem / tiles);
-    const int64_t tile = rem - (int64_t)cls * tiles;
+    const int rem = (int)(g - (int64_t)sidx * 4 * tiles);
+    const int cls = rem / tiles, tile = rem - cls * tiles;
     const SysDev &d = w.sys[sys_at_level(w, l, sidx)];
-    const int tid = threadIdx.x, warp = tid >> 5, p = w.p;
-    const int row = 32 * (warp & 3) + (tid & 31), m0 = 8 * (warp >> 2);  // this thread's row and coefficients
-    const int cx = cls & 1, cy = cls >> 1, ns = 1 << l, nh = ns >> 1;
-    const int64_t ib = tile * kRows + row;  // this row's index among the boxes of the child position
-    const bool row_ok = ib < (int64_t)nh * nh;
-    const int bx = 2 * (int)(ib & (nh - 1)) + cx, by = 2 * (int)(ib >> (l - 1)) + cy;
-    const int64_t lev0 = d.box0[l];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, p = w.p;
+    const int cx = cls & 1, cy = cls >> 1, ns = 1 << l, nc = ns >> 1, Lc = nc + 2;
+    const int q0 = tile * kRows;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(S::COLS));
+                     "r"(tmem_cols(S::NP)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         int q = 0;
-        for (int ry = -2 - cy; ry <= 3 - cy; ++ry)
-            for (int rx = -2 - cx; rx <= 3 - cx; ++rx)
-                if (rx < -1 || rx > 1 || ry < -1 || ry > 1)
-                    s_off[q++] = make_int2(rx, ry);
+        for (int gs = 0; gs < 4; ++gs) {
+            s_gq[gs] = q;
+            for (int ry = -2 - cy; ry <= 3 - cy; ++ry)
+                for (int rx = -2 - cx; rx <= 3 - cx; ++rx) {
+                    if (rx >= -1 && rx <= 1 && ry >= -1 && ry <= 1)
+                        continue;  // adjacent: near field
+                    const int ux = cx + rx + 4, uy = cy + ry + 4;  // source box = 2 (i, j) + (ux, uy) - 4
+                    if ((ux & 1) + 2 * (uy & 1) != gs)
+                        continue;
+                    s_delta[q] = (ry + 3) * 7 + (rx + 3);
+                    s_a0[q] = (1 + (uy >> 1) - 2) * Lc + 1 + (ux >> 1) - 2;
+                    ++q;
+                }
+        }
+        s_gq[4] = q;
         s_bad = 0;
-        for (int i = 0; i < 2; ++i)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[i])));
+        for (int i = 0; i < S::NSLOT; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bempty[i])));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wempty[i])));
+        }
+        for (int i = 0; i < kStages; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&tempty[i])));  // one per warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // B (hi, lo) once; 16-byte pieces
-    for (int i = tid; i < S::B_BYTES / 16; i += blockDim.x)
-        reinterpret_cast<float4 *>(sB)[i] = reinterpret_cast<const float4 *>(btab)[i];
-    __syncthreads();  // s_off ready
-    for (int i = tid; i < kNOff * (PB + 1); i += blockDim.x) {
-        const int q = i / (PB + 1), k = i - q * (PB + 1);
-        const int2 o = s_off[q];
-        s_rho[i] = rho32[((o.y + 3) * 7 + (o.x + 3)) * RS + k];
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B visible to the tensor core
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base;
-    const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + m0;  // this warp's lanes, column m0
-    // instruction descriptor: D f32, A and B tf32, both K-major, N = NP, M = 128
-    const uint32_t idesc =
-        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(S::NP >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-
-    auto gather = [&](int q, float2 *r) {
-        const int2 o = s_off[q];
-        const int jx = bx + o.x, jy = by + o.y;
-        bool v = row_ok && jx >= 0 && jy >= 0 && jx < ns && jy < ns;
-        const int64_t sb = lev0 + (int64_t)jy * ns + jx;
-        v = v && w.bcount[sb] != 0;
-        const float2 *src = w.M32 + sb * p + m0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            r[j] = (v && m0 + j < p) ? src[j] : make_float2(0.f, 0.f);
-    };
-
-    float ar[8], ai[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        ar[j] = 0.f;
-        ai[j] = 0.f;
-    }
-    float2 nxt[8];
-    gather(0, nxt);
-    int committed = -1;  // (thread 0) last offset whose MMAs were committed
-    for (int q = 0; q < kNOff; ++q) {
-        const int s = q & 1;
-        float2 cur[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            cur[j] = nxt[j];
-        if (q + 1 < kNOff)
-            gather(q + 1, nxt);  // loads in flight while this offset is staged
-        if (q >= 2) {
-            if (!__all_sync(0xffffffffu, mbar_wait(&mma_bar[s], ((q - 2) >> 1) & 1)))
-                s_bad = 1;
-            else
-                accumulate_tmem(tlane + (2 * s) * S::NP, tlane + (2 * s + 1) * S::NP, s_rho + (q - 2) * (PB + 1),
-                                m0, p, ar, ai);
-        }
-        // A(q): rho^m a~_m, real and imaginary parts, each split hi + lo
-        unsigned char *sa = sm + s * S::STAGE_A;
-        const float2 *rq = s_rho + q * (PB + 1);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {  // the thread's two 4-coefficient chunks
-            float re[4], im[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float2 a = cur[4 * c + j], r = rq[m0 + 4 * c + j];
-                re[j] = fmaf(r.x, a.x, -r.y * a.y);
-                im[j] = fmaf(r.x, a.y, r.y * a.x);
+    // zeros that no copy overwrites: B rows >= 8 NG of every slot
+    {
+        constexpr int zb = (S::B_PART - S::B_LOAD) / 16;
+        if constexpr (zb > 0) {
+            for (int i = tid; i < S::NSLOT * 2 * zb; i += kThreads) {
+                const int part = i / zb, j = i - part * zb;
+                reinterpret_cast<float4 *>(sB + part * S::B_PART + S::B_LOAD)[j] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            const float4 rh = make_float4(tf32_rn(re[0]), tf32_rn(re[1]), tf32_rn(re[2]), tf32_rn(re[3]));
-            const float4 rl = make_float4(tf32_rn(re[0] - rh.x), tf32_rn(re[1] - rh.y), tf32_rn(re[2] - rh.z),
-                                          tf32_rn(re[3] - rh.w));
-            const float4 ih = make_float4(tf32_rn(im[0]), tf32_rn(im[1]), tf32_rn(im[2]), tf32_rn(im[3]));
-            const float4 il = make_float4(tf32_rn(im[0] - ih.x), tf32_rn(im[1] - ih.y), tf32_rn(im[2] - ih.z),
-                                          tf32_rn(im[3] - ih.w));
-            const int off = core_off(row, m0 + 4 * c, S::KP);
-            *reinterpret_cast<float4 *>(sa + off) = rh;
-            *reinterpret_cast<float4 *>(sa + S::A_PART + off) = rl;
-            *reinterpret_cast<float4 *>(sa + 2 * S::A_PART + off) = ih;
-            *reinterpret_cast<float4 *>(sa + 3 * S::A_PART + off) = il;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (s_bad)
-            break;  // block-uniform: read after the barrier
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sB);
-            const uint32_t lbo = 128, sbo = (S::KP / 4) * 128;
+    }
+    fence_async_smem();  // those zeros, visible to the tensor core
+    tc_before_sync();
+    __syncthreads();     // offset lists, barriers and tensor memory ready
+    tc_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    float acc[S::KP];
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                const uint32_t d_acc = tmem + (2 * s + part) * S::NP;
-                const uint32_t ap = a0 + 2 * part * S::A_PART;
+    for (int k = 0; k < S::KP; ++k)
+        acc[k] = 0.f;
+
+    // The copy and MMA warps run their loops with all 32 lanes (waits by every lane, so each warp stays
+    // converged); lane 0 alone issues the copies, MMAs and commits.
+    auto warp_wait = [&](uint64_t *bar, uint32_t parity) {
+        return __all_sync(0xffffffffu, wait_or_bad(bar, parity, bad));
+    };
+    if (warp == 5) {
+        // ---------------- copies: windows (source classes) and B_delta, in the order the MMAs use them
+        const int np_ = npos_of(l);
+        const uint32_t wrun = (uint32_t)(2 * Lc + 130) * 16u;  // bytes of one plane's window
+        int nb = 0, nw = 0;  // copies of B and of windows issued
+        auto load_window = [&](int gs) {
+            if (lane == 0) {
+                uint64_t *bar = &wfull[gs & 1];
+                const float4 *src = w.mtc + layout_base(w.lv, S::KC, l, sidx, gs) + q0;
+                unsigned char *dst = sm + (gs & 1) * WB;
+                mbar_expect_tx(bar, 2u * S::KC * wrun);
+                for (int pl = 0; pl < 2 * S::KC; ++pl)
+                    bulk_g2s(dst + (size_t)pl * ws * 16, src + (int64_t)pl * np_, wrun, bar);
+            }
+            __syncwarp();
+            nw = gs + 1;
+        };
+        load_window(0);
+        load_window(1);
+        int gs = 0;
+        for (int q = 0; q < kNOff; ++q) {
+            const int slot = q % S::NSLOT;
+            if (q >= S::NSLOT && !warp_wait(&bempty[slot], (uint32_t)(q / S::NSLOT - 1) & 1u))
+                break;
+            if (lane == 0) {
+                const unsigned char *src =
+                    btab + ((size_t)(blockIdx.x % kReplicas) * kNDelta + s_delta[q]) * S::B_SLOT;
+                mbar_expect_tx(&bfull[slot], 2 * S::B_LOAD);
+                bulk_g2s(sB + slot * S::B_SLOT, src, S::B_LOAD, &bfull[slot]);
+                bulk_g2s(sB + slot * S::B_SLOT + S::B_PART, src + S::B_PART, S::B_LOAD, &bfull[slot]);
+            }
+            __syncwarp();
+            nb = q + 1;
+            // three B of class gs + 1 are on their way: wait for class gs's MMAs, then its buffer takes gs + 2
+            if (gs + 2 < 4 && q == s_gq[gs + 1] + 2) {
+                if (!warp_wait(&wempty[gs & 1], (uint32_t)(gs >> 1) & 1u))
+                    break;
+                load_window(gs + 2);
+                ++gs;
+            }
+        }
+        // every copy lands before the CTA may exit (bounded): the last one issued into each slot and buffer
+        for (int q = nb - S::NSLOT < 0 ? 0 : nb - S::NSLOT; q < nb; ++q)
+            mbar_wait(&bfull[q % S::NSLOT], (uint32_t)(q / S::NSLOT) & 1u);
+        for (int gs = nw - 2 < 0 ? 0 : nw - 2; gs < nw; ++gs)
+            mbar_wait(&wfull[gs & 1], (uint32_t)(gs >> 1) & 1u);
+    } else if (warp == 4) {
+        // ---------------- MMAs
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(S::NP >> 3) << 17) |
+                               ((uint32_t)(kRows >> 4) << 24);  // D f32, A, B tf32 K-major, N = NP, M = 128
+        const uint32_t lbo_a = (uint32_t)ws * 16u, plane2 = 2u * (uint32_t)ws * 16u;
+        int committed = -1;
+        int gs = 0;
+        for (int q = 0; q < kNOff; ++q) {
+            if (q == s_gq[gs] && !warp_wait(&wfull[gs & 1], (uint32_t)(gs >> 1) & 1u))
+                break;
+            const int slot = q % S::NSLOT, st = q % kStages;
+            if (!warp_wait(&bfull[slot], (uint32_t)(q / S::NSLOT) & 1u))
+                break;
+            if (q >= kStages && !warp_wait(&tempty[st], (uint32_t)(q / kStages - 1) & 1u))
+                break;
+            const bool last_of_class = q + 1 == s_gq[gs + 1];
+            if (lane == 0) {
+                tc_after_sync();
+                const uint32_t ah0 = smem_u32(sm + (gs & 1) * WB) + (uint32_t)s_a0[q] * 16u;
+                const uint32_t al0 = ah0 + (uint32_t)(S::KC * ws * 16);
+                const uint32_t bh0 = smem_u32(sB + slot * S::B_SLOT), bl0 = bh0 + S::B_PART;
+                // three independent accumulation chains (hi*hi, hi*lo, lo*hi) so that consecutive MMAs do not wait
+                // for each other's accumulator
+                const uint32_t d_acc = tmem + (uint32_t)(st * kParts * S::NP);
 #pragma unroll
                 for (int ks = 0; ks < S::KP / 8; ++ks) {
-                    const uint32_t ko = ks * 256;  // 8 TF32 of K = two core matrices
-                    const uint64_t ah = sdesc(ap + ko, lbo, sbo), al = sdesc(ap + S::A_PART + ko, lbo, sbo);
-                    const uint64_t bh = sdesc(b0 + ko, lbo, sbo), bl = sdesc(b0 + S::B_PART + ko, lbo, sbo);
-                    mma_tf32(d_acc, ah, bh, idesc, ks > 0 ? 1u : 0u);
-                    mma_tf32(d_acc, ah, bl, idesc, 1u);
-                    mma_tf32(d_acc, al, bh, idesc, 1u);
+                    const uint64_t ah = sdesc(ah0 + ks * plane2, lbo_a, 128), al = sdesc(al0 + ks * plane2, lbo_a, 128);
+                    const uint64_t bh = sdesc(bh0 + ks * 256, 128, S::KC * 128),
+                                   bl = sdesc(bl0 + ks * 256, 128, S::KC * 128);
+                    const uint32_t acc_on = ks > 0 ? 1u : 0u;
+                    mma_tf32(d_acc, ah, bh, idesc, acc_on);
+                    mma_tf32(d_acc + S::NP, ah, bl, idesc, acc_on);
+                    mma_tf32(d_acc + 2 * S::NP, al, bh, idesc, acc_on);
                 }
+                tc_commit(&tfull[st]);
+                tc_commit(&bempty[slot]);
+                if (last_of_class)
+                    tc_commit(&wempty[gs & 1]);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&mma_bar[s]))
-                         : "memory");
+            __syncwarp();
+            if (last_of_class)
+                ++gs;
             committed = q;
         }
-    }
-    __syncthreads();
-    bool ok = !s_bad;
-    if (ok) {
-        // offsets kNOff - 2 and kNOff - 1 are still in their accumulators
+        if (committed >= 0)  // the last MMAs land before shared and tensor memory are released (bounded)
+            mbar_wait(&tfull[committed % kStages], (uint32_t)(committed / kStages) & 1u);
+    } else {
+        // ---------------- read-back: warps 0-3, one target position per thread
+        const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int q = 0; q < kNOff; ++q) {
+            const int st = q % kStages;
+            if (!__all_sync(0xffffffffu, wait_or_bad(&tfull[st], (uint32_t)(q / kStages) & 1u, bad)))
+                break;
+            tc_after_sync();
+            uint32_t r[kParts][S::RD][8];
 #pragma unroll
-        for (int q = kNOff - 2; q < kNOff; ++q) {
-            const int s = q & 1;
-            const bool okq = __all_sync(0xffffffffu, mbar_wait(&mma_bar[s], (q >> 1) & 1));
-            if (okq)
-                accumulate_tmem(tlane + (2 * s) * S::NP, tlane + (2 * s + 1) * S::NP, s_rho + q * (PB + 1), m0, p,
-                                ar, ai);
-            ok = ok && okq;
+            for (int pt = 0; pt < kParts; ++pt)
+#pragma unroll
+                for (int j = 0; j < S::RD; ++j)
+                    tmem_ld8(tlane + (uint32_t)((st * kParts + pt) * S::NP + 8 * j), r[pt][j]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&tempty[st]);
+#pragma unroll
+            for (int j = 0; j < S::RD; ++j)
+#pragma unroll
+                for (int i = 0; i < 8; ++i)  // the small products first
+                    acc[8 * j + i] += (__uint_as_float(r[1][j][i]) + __uint_as_float(r[2][j][i])) +
+                                      __uint_as_float(r[0][j][i]);
         }
     }
-    if (ok && row_ok) {
-        float2 *dst = w.L32 + (lev0 + (int64_t)by * ns + bx) * p + m0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (m0 + j < p)
-                dst[j] = make_float2(ar[j], ai[j]);
-    }
-    if (!ok && tid == 0) {
-        atomicOr(w.status, FMM_DEV_TIMEOUT);
-        if (committed >= 0)  // let the last MMAs land before the shared and tensor memory are released
-            mbar_wait(&mma_bar[committed & 1], (committed >> 1) & 1);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_before_sync();
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::COLS));
+    const bool ok = !s_bad;
+    if (ok && warp < 4) {
+        const int tq = q0 + tid, row = tq / Lc, colp = tq - row * Lc;
+        if (row < nc && colp >= 1 && colp <= nc) {
+            const int64_t box = d.box0[l] + (int64_t)(2 * row + cy) * ns + 2 * (colp - 1) + cx;
+            if (w.bcount[box] != 0) {
+                float2 *dst = w.L32 + box * p;
+#pragma unroll
+                for (int m = 0; m < PB; ++m)
+                    if (m < p)
+                        dst[m] = make_float2(acc[2 * m], acc[2 * m + 1]);
+            }
+        }
+    }
+    if (!ok && tid == 0)
+        atomicOr(w.status, FMM_DEV_TIMEOUT);
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols(S::NP)));
+    }
 }
 
 template <int PB>
 int set_smem_attr()
 {
-    return cudaFuncSetAttribute(k_m2l_tc<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<PB>::SMEM) ==
-                   cudaSuccess
+    return cudaFuncSetAttribute(k_m2l_tc<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<PB>(window_len(kMaxClassWidth + 2))) == cudaSuccess
                ? 0
                : -1;
 }
 
-int bucket_of(int p) { return p <= 8 ? 8 : p <= 16 ? 16 : p <= 24 ? 24 : 32; }
+int bucket_of(int p) { return p <= 8 ? 8 : p <= 12 ? 12 : p <= 16 ? 16 : 20; }
+
+template <int PB>
+constexpr size_t table_bytes()
+{
+    return (size_t)kReplicas * kNDelta * TcShape<PB>::B_SLOT;
+}
 
 bool g_tc_ready[64] = {};
 
-}  // namespace
-
-size_t m2l_tc_table_bytes(int p)
-{
-    switch (bucket_of(p)) {
-    case 8:
-        return TcShape<8>::B_BYTES;
-    case 16:
-        return TcShape<16>::B_BYTES;
-    case 24:
-        return TcShape<24>::B_BYTES;
-    default:
-        return TcShape<32>::B_BYTES;
-    }
-}
-
 // TF32 value nearest to x (ties away from zero), the rounding of cvt.rna.tf32.f32.
-static float tf32_round_host(double x)
+float tf32_round_host(double x)
 {
     float f = (float)x;
     uint32_t u;
@@ -365,24 +514,98 @@ static float tf32_round_host(double x)
     return f;
 }
 
-// B[l][m] = (-1)^(m+1) C(m+l, m) for l, m < p (zero padding elsewhere), hi part then lo part, each [NP rows l]
-// [KP columns m] in the operand layout.
+template <int PB>
+void build_table(int p, unsigned char *out)
+{
+    using S = TcShape<PB>;
+    memset(out, 0, table_bytes<PB>());
+    std::vector<std::complex<double>> pw(2 * PB + 1);
+    const size_t one = (size_t)kNDelta * S::B_SLOT;
+    for (int dy = -3; dy <= 3; ++dy)
+        for (int dx = -3; dx <= 3; ++dx) {
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1)
+                continue;
+            const std::complex<double> rho = 1.0 / std::complex<double>(dx, dy);
+            pw[0] = 1.0;
+            for (int k = 1; k <= 2 * p; ++k)
+                pw[k] = pw[k - 1] * rho;
+            unsigned char *hi = out + (size_t)((dy + 3) * 7 + (dx + 3)) * S::B_SLOT, *lo = hi + S::B_PART;
+            for (int l = 0; l < p; ++l)
+                for (int m = 0; m < p; ++m) {
+                    double c = 1.0;
+                    for (int i = 1; i <= m; ++i)
+                        c = c * (double)(l + i) / (double)i;  // C(m + l, m)
+                    const std::complex<double> t = ((m & 1) ? c : -c) * pw[m + l + 1];
+                    // rows n = 2l (real part of b_l), 2l + 1 (imaginary); columns k = 2m (Re a_m), 2m + 1 (Im a_m)
+                    const double e[2][2] = {{t.real(), -t.imag()}, {t.imag(), t.real()}};
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b) {
+                            const float h = tf32_round_host(e[a][b]), r = tf32_round_host(e[a][b] - (double)h);
+                            const int off = core_off(2 * l + a, 2 * m + b, S::KP);
+                            memcpy(hi + off, &h, 4);
+                            memcpy(lo + off, &r, 4);
+                        }
+                }
+        }
+    for (int rep = 1; rep < kReplicas; ++rep)
+        memcpy(out + rep * one, out, one);
+}
+
+template <int PB>
+int launch_bucket(const Work &w, const Tables &t, int l_lo, int l_hi, int64_t items, cudaStream_t s)
+{
+    int64_t planes = 0;
+    for (int l = l_lo; l <= l_hi; ++l)
+        planes += (int64_t)w.lv.nsys_at[l] * 4 * TcShape<PB>::KC;
+    const int nch = (npos_of(l_hi) + 255) / 256;
+    k_m2l_tc_layout<PB><<<(unsigned)(planes * nch), 256, 0, s>>>(w, l_lo, l_hi, nch);
+    const int ws = window_len((1 << (l_hi - 1)) + 2);
+    k_m2l_tc<PB><<<(unsigned)items, kThreads, smem_bytes<PB>(ws), s>>>(w, t.m2l_tc, l_lo, l_hi, ws);
+    return 2;
+}
+
+}  // namespace
+
+bool m2l_tc_supported(int p) { return p >= 1 && p <= kPMaxTc; }
+
+int m2l_tc_max_level() { return 7; }  // the finest level whose class grid (2^(l-1) boxes wide) is <= kMaxClassWidth
+
+size_t m2l_tc_table_bytes(int p)
+{
+    switch (bucket_of(p < kPMaxTc ? p : kPMaxTc)) {
+    case 8:
+        return table_bytes<8>();
+    case 12:
+        return table_bytes<12>();
+    case 16:
+        return table_bytes<16>();
+    default:
+        return table_bytes<20>();
+    }
+}
+
+// B_delta (hi, lo) of the 40 offsets for p (zeros for p > 20, which never runs here), in the layout above,
+// indexed (dy + 3) * 7 + (dx + 3), the 9 near offsets zero; the whole table kReplicas times.
 void build_m2l_tc_table_host(int p, unsigned char *out)
 {
-    const int pb = bucket_of(p), KP = pb, NP = (pb + 15) / 16 * 16;
-    const size_t part = (size_t)NP * KP * 4;
-    memset(out, 0, 2 * part);
-    for (int l = 0; l < p; ++l)
-        for (int m = 0; m < p; ++m) {
-            double c = 1.0;
-            for (int i = 1; i <= m; ++i)
-                c = c * (double)(l + i) / (double)i;  // C(m + l, m)
-            const double v = (m & 1) ? c : -c;
-            const float hi = tf32_round_host(v), lo = tf32_round_host(v - (double)hi);
-            const int off = core_off(l, m, KP);
-            memcpy(out + off, &hi, 4);
-            memcpy(out + part + off, &lo, 4);
-        }
+    if (!m2l_tc_supported(p)) {
+        memset(out, 0, m2l_tc_table_bytes(p));
+        return;
+    }
+    switch (bucket_of(p)) {
+    case 8:
+        build_table<8>(p, out);
+        break;
+    case 12:
+        build_table<12>(p, out);
+        break;
+    case 16:
+        build_table<16>(p, out);
+        break;
+    default:
+        build_table<20>(p, out);
+        break;
+    }
 }
 
 int prepare_m2l_tc()
@@ -392,43 +615,44 @@ int prepare_m2l_tc()
         return -1;
     if (g_tc_ready[dev])
         return 0;
-    if (set_smem_attr<8>() || set_smem_attr<16>() || set_smem_attr<24>() || set_smem_attr<32>())
+    if (set_smem_attr<8>() || set_smem_attr<12>() || set_smem_attr<16>() || set_smem_attr<20>())
         return -1;
     g_tc_ready[dev] = 1;
     return 0;
 }
 
-int64_t m2l_tc_items(const Work &w, int l32)
+size_t m2l_tc_layout_bytes(const LevelInfo &lv, int p)
 {
-    int64_t n = 0;
-    for (int l = l32; l <= w.lv.maxdepth; ++l) {
-        const int64_t tiles = l >= 5 ? ((int64_t)1 << (2 * l - 9)) : 1;
-        n += (int64_t)w.lv.nsys_at[l] * 4 * tiles;
-    }
-    return n;
+    if (!m2l_tc_supported(p))
+        return 0;
+    const int kc = bucket_of(p) == 8 ? TcShape<8>::KC : bucket_of(p) == 12 ? TcShape<12>::KC
+                                                       : bucket_of(p) == 16 ? TcShape<16>::KC
+                                                                            : TcShape<20>::KC;
+    const int lt = lv.maxdepth < m2l_tc_max_level() ? lv.maxdepth : m2l_tc_max_level();
+    return lt < 2 ? 0 : (size_t)layout_base(lv, kc, lt + 1, 0, 0) * 16;
 }
 
-int launch_m2l_tc(const Work &w, const Tables &t, int l32, cudaStream_t s)
+int launch_m2l_tc(const Work &w, const Tables &t, int l_lo, int l_hi, cudaStream_t s)
 {
-    const int64_t items = m2l_tc_items(w, l32);
+    if (!m2l_tc_supported(w.p) || !w.mtc || l_hi > m2l_tc_max_level() || l_lo < 2 || l_hi < l_lo)
+        return 0;
+    int64_t items = 0;
+    for (int l = l_lo; l <= l_hi; ++l) {
+        const int nc = 1 << (l - 1);
+        items += (int64_t)w.lv.nsys_at[l] * 4 * ((nc * (nc + 2) + kRows - 1) / kRows);
+    }
     if (items == 0)
         return 0;
-    const unsigned blocks = (unsigned)items;
     switch (bucket_of(w.p)) {
     case 8:
-        k_m2l_tc<8><<<blocks, TcShape<8>::THREADS, TcShape<8>::SMEM, s>>>(w, t.m2l_tc, t.rho32, l32);
-        break;
+        return launch_bucket<8>(w, t, l_lo, l_hi, items, s);
+    case 12:
+        return launch_bucket<12>(w, t, l_lo, l_hi, items, s);
     case 16:
-        k_m2l_tc<16><<<blocks, TcShape<16>::THREADS, TcShape<16>::SMEM, s>>>(w, t.m2l_tc, t.rho32, l32);
-        break;
-    case 24:
-        k_m2l_tc<24><<<blocks, TcShape<24>::THREADS, TcShape<24>::SMEM, s>>>(w, t.m2l_tc, t.rho32, l32);
-        break;
+        return launch_bucket<16>(w, t, l_lo, l_hi, items, s);
     default:
-        k_m2l_tc<32><<<blocks, TcShape<32>::THREADS, TcShape<32>::SMEM, s>>>(w, t.m2l_tc, t.rho32, l32);
-        break;
+        return launch_bucket<20>(w, t, l_lo, l_hi, items, s);
     }
-    return 1;
 }
 
 }  // namespace fmm

@@ -48,7 +48,7 @@ size_t tables_bytes()
     size_t t = 0;
     for (size_t s : kTabSizes)
         t += up256(s);
-    return t + up256(m2l_tc_table_bytes(FMM_PMAX));  // tensor-core M2L operands, largest p bucket
+    return t;  // no tensor-core M2L operands: this entry runs the FP32 M2L levels on the CUDA cores
 }
 
 void carve_tables(unsigned char *b, Tables &t)
@@ -67,7 +67,7 @@ void carve_tables(unsigned char *b, Tables &t)
     t.rho32 = (float2 *)p[5];
     t.binom64 = (double *)p[6];
     t.binom32 = (float *)p[7];
-    t.m2l_tc = b + off;
+    t.m2l_tc = nullptr;
 }
 
 // Host copies of the tables for one p; the copy into the device array is ordered on the caller's stream.
@@ -92,11 +92,6 @@ fmm_status upload_tables(const Tables &t, int p, cudaStream_t s)
     for (int i = 0; i < 8; ++i)
         if (cudaMemcpyAsync(dst[i], src[i], kTabSizes[i], cudaMemcpyHostToDevice, s) != cudaSuccess)
             return FMM_ECUDA;
-    static std::vector<unsigned char> tc;
-    tc.assign(m2l_tc_table_bytes(p), 0);
-    build_m2l_tc_table_host(p, tc.data());
-    if (cudaMemcpyAsync(t.m2l_tc, tc.data(), tc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return FMM_ECUDA;
     // pageable sources: make sure the copies have read them before the static buffers are reused
     return cudaStreamSynchronize(s) == cudaSuccess ? FMM_OK : FMM_ECUDA;
 }

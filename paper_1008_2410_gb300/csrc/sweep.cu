@@ -560,25 +560,32 @@ int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio
             m2l_box_launch<32>(w, t, adj, 0, split, s);
         ++n;
     }
-    if (split < total && w.m2l_tc && t.m2l_tc) {
-        n += launch_m2l_tc(w, t, l32, s);
-    } else if (split < total) {
+    // FP32 levels: the tensor cores take l32 .. the finest level they cover, the CUDA cores the rest
+    int64_t src0 = split;
+    if (split < total && w.m2l_tc && t.m2l_tc && m2l_tc_supported(w.p)) {
+        const int lt = min(w.lv.maxdepth, m2l_tc_max_level());
+        if (lt >= l32) {
+            n += launch_m2l_tc(w, t, l32, lt, s);
+            src0 = w.lv.m2l_item0[lt + 1];
+        }
+    }
+    if (src0 < total) {
         if (w.p <= 8)
-            m2l_src_launch<8>(w, split, total, s);
+            m2l_src_launch<8>(w, src0, total, s);
         else if (w.p <= 12)
-            m2l_src_launch<12>(w, split, total, s);
+            m2l_src_launch<12>(w, src0, total, s);
         else if (w.p <= 14)
-            m2l_src_launch<14>(w, split, total, s);
+            m2l_src_launch<14>(w, src0, total, s);
         else if (w.p <= 16)
-            m2l_src_launch<16>(w, split, total, s);
+            m2l_src_launch<16>(w, src0, total, s);
         else if (w.p <= 17)
-            m2l_src_launch<17>(w, split, total, s);
+            m2l_src_launch<17>(w, src0, total, s);
         else if (w.p <= 20)
-            m2l_src_launch<20>(w, split, total, s);
+            m2l_src_launch<20>(w, src0, total, s);
         else if (w.p <= 24)
-            m2l_src_launch<24>(w, split, total, s);
+            m2l_src_launch<24>(w, src0, total, s);
         else
-            m2l_src_launch<32>(w, split, total, s);
+            m2l_src_launch<32>(w, src0, total, s);
         ++n;
     }
     return n;

@@ -144,6 +144,7 @@ M2L_CASES = [
     ("p32_d3", lambda: fi.uniform(2000, seed_index=38, depth=3, p=32)),
     ("clustered20k_d5_p14", lambda: fi.clustered(20000, depth=5, p=14)),  # empty boxes: zero source rows
     ("patches64k_d6_p20", lambda: fi.patches(1 << 16, seed_index=39, depth=6, p=20)),  # several tiles a level
+    ("d8_p6", lambda: fi.uniform(200000, seed_index=42, depth=8, p=6)),  # levels <= 7 and level 8 split by engine
 ]
 
 

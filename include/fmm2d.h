@@ -309,7 +309,9 @@ fmm_status fmm_autotune_p(fmm_handle h, int64_t n, const double *x, const double
 
 /* Measured throughput of the units the kernels are bound by, on the current device (a few hundred ms):
  * out[0] FP32 FMA TFLOP/s, out[1] FP64 FMA TFLOP/s, out[2] SFU ex2+rcp results per second / 1e12,
- * out[3] SM count. cap >= 4. Allocates and frees 1 MiB of device memory. */
+ * out[3] SM count; with cap >= 6 also out[4], out[5] clock cycles per tcgen05.mma kind::tf32 (M = 128, K = 8)
+ * at N = 48 and N = 256, issued back to back by one thread per SM. cap >= 4. Allocates and frees 1 MiB of
+ * device memory. */
 fmm_status fmm_probe_peaks(double *out, int cap);
 
 /* Allocation-free evaluation, for callers that cannot let a library allocate device memory (code running under

@@ -95,13 +95,14 @@ def load() -> ctypes.CDLL:
 
 
 def probe_peaks() -> dict:
-    """Measured FP32 / FP64 FMA TFLOP/s and SFU (ex2 + rcp) rate of the current device."""
+    """Measured FP32 / FP64 FMA TFLOP/s, SFU (ex2 + rcp) rate and TF32 MMA issue cycles of the current device."""
     lib = load()
-    buf = (_D * 4)()
-    st = lib.fmm_probe_peaks(buf, 4)
+    buf = (_D * 6)()
+    st = lib.fmm_probe_peaks(buf, 6)
     if st != FMM_OK:
         raise FMMError(st, lib.fmm_status_string(st).decode())
-    return {"fp32_tflops": buf[0], "fp64_tflops": buf[1], "sfu_tops": buf[2], "sms": int(buf[3])}
+    return {"fp32_tflops": buf[0], "fp64_tflops": buf[1], "sfu_tops": buf[2], "sms": int(buf[3]),
+            "tf32_mma_cycles_n48": buf[4], "tf32_mma_cycles_n256": buf[5]}
 
 
 class FMMError(RuntimeError):

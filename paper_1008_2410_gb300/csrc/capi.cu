@@ -375,6 +375,8 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     const bool use_bkt = !h->adaptive_cap && nleaf > 0 && (size_t)nleaf * (size_t)bcap * 8 <= 64 * np;
     sizes[i++] = use_bkt ? (size_t)nleaf * (size_t)bcap * 8 : 0;
     sizes[i++] = mixed ? m2l_tc_layout_bytes(h->lv, p) : 0;     // 35 mtc (tensor-core M2L windows)
+    sizes[i++] = mixed ? m2l_tc_part_bytes(h->lv, p) : 0;       // 36 m2l_part (its partial locals)
+    sizes[i++] = mixed ? m2l_tc_count_bytes(h->lv, p) : 0;      // 37 m2l_cnt (its tile counters)
     int count = i;
     Layout lay;
     size_t total = 0;
@@ -440,6 +442,8 @@ static fmm_status ensure_workspace(fmm_handle h, int64_t n, int adjoint)
     w.M32 = sizes[17] ? (float2 *)(b + lay.off[17]) : nullptr;
     w.L32 = sizes[18] ? (float2 *)(b + lay.off[18]) : nullptr;
     w.mtc = sizes[35] ? (float4 *)(b + lay.off[35]) : nullptr;
+    w.m2l_part = sizes[36] ? (float2 *)(b + lay.off[36]) : nullptr;
+    w.m2l_cnt = sizes[37] ? (int *)(b + lay.off[37]) : nullptr;
     w.sgu = sizes[19] ? (double *)(b + lay.off[19]) : nullptr;
     w.sgv = sizes[20] ? (double *)(b + lay.off[20]) : nullptr;
     w.AM64 = sizes[21] ? (double2 *)(b + lay.off[21]) : nullptr;

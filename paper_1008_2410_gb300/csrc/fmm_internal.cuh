@@ -142,6 +142,8 @@ struct Work {
     float2 *M32, *L32;
     float4 *mtc;              // precision form, levels 2 .. 7: the tensor-core M2L's window source layout (TF32 hi and
                               // lo planes of the multipoles per class, m2l_tc.cu), or null
+    float2 *m2l_part;         // with mtc: the tensor-core M2L's partial locals, four per box (one per source class)
+    int *m2l_cnt;             // with mtc: completion counters of its tiles
     // adjoint extras
     double *sgu, *sgv;
     double2 *AM64, *AL64;     // expansions of the adjoint charges G = gu + i gv
@@ -262,6 +264,8 @@ void build_tables_host(int p, double2 *m2m, double2 *l2l, double2 *rho, double *
 // 0 on success) and the launch over levels l_lo .. l_hi (<= m2l_tc_max_level()); returns the launches made.
 size_t m2l_tc_table_bytes(int p);
 size_t m2l_tc_layout_bytes(const LevelInfo &lv, int p);  // Work::mtc for these levels and p (0: not used)
+size_t m2l_tc_part_bytes(const LevelInfo &lv, int p);    // Work::m2l_part
+size_t m2l_tc_count_bytes(const LevelInfo &lv, int p);   // Work::m2l_cnt
 void build_m2l_tc_table_host(int p, unsigned char *out);
 bool m2l_tc_supported(int p);
 int m2l_tc_max_level();

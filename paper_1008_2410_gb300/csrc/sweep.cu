@@ -564,8 +564,9 @@ int launch_m2l(const Work &w, const Tables &t, int adj, cudaStream_t s, int prio
     int64_t src0 = split;
     if (split < total && w.m2l_tc && t.m2l_tc && m2l_tc_supported(w.p)) {
         const int lt = min(w.lv.maxdepth, m2l_tc_max_level());
-        if (lt >= l32) {
-            n += launch_m2l_tc(w, t, l32, lt, s);
+        const int k = lt >= l32 ? launch_m2l_tc(w, t, l32, lt, s) : 0;
+        if (k > 0) {
+            n += k;
             src0 = w.lv.m2l_item0[lt + 1];
         }
     }

@@ -731,3 +731,14 @@ def test_autotune_batched_picks_depths_and_tile(lib, oracle):
     for k, s in enumerate(b.systems):
         uo, vo, _ = oracle.fmm(s.x, s.y, s.gamma, s.sigma, deps[k], b.p, domain=s.domain)
         assert rel_l2((u[off[k]:off[k + 1]], v[off[k]:off[k + 1]]), (uo, vo)) < TOL32, k
+
+
+def test_probe_peaks_reports_every_unit(lib):
+    """The throughput probe returns finite, positive rates for the FP32, FP64 and SFU pipes, the SM count, and the
+    cycles per TF32 tensor-core MMA at N = 48 and N = 256 (the figures the M2L engine choice rests on)."""
+    from paper_1008_2410_gb300 import _lib
+
+    pk = _lib.probe_peaks()
+    for k in ("fp32_tflops", "fp64_tflops", "sfu_tops", "tf32_mma_cycles_n48", "tf32_mma_cycles_n256"):
+        assert np.isfinite(pk[k]) and pk[k] > 0, k
+    assert pk["sms"] > 0

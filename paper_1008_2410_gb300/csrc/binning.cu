@@ -192,12 +192,11 @@ __device__ __forceinline__ long long ordered(double v)
     return b < 0 ? (long long)(0x8000000000000000ull - (unsigned long long)b) : b;
 }
 
-__global__ void k_keys(Work w, const double *__restrict__ x, const double *__restrict__ y,
-                       const double *__restrict__ g)
+// Key, boundary class and the caller-order records of particle i (everything but its arrival slot); returns the
+// global leaf.
+__device__ __forceinline__ int key_of(const Work &w, const double *__restrict__ x, const double *__restrict__ y,
+                                      const double *__restrict__ g, int i, int &cls)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.n)
-        return;
     int k = w.nsys == 1 ? 0 : find_sys_by_particle(w.sys, w.nsys, i);
     const SysDev &d = w.sys[k];
     const double xi = x[i], yi = y[i];
@@ -232,21 +231,13 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
     // band). Numbered around the leaf so that the band facing each of the 8 neighbours is a run of classes: 0 LB,
     // 1 LM, 2 LT, 3 MT, 4 RT, 5 RM, 6 RB, 7 MB, 8 MM (the interior, last); everything is class 8 where the bands
     // would overlap.
-    int cls = 8;
+    cls = 8;
     if (w.cls_off && d.bnd_ok) {
         const int cx = Fx < -d.fbnd ? 0 : (Fx > d.fbnd ? 2 : 1);
         const int cy = Fy < -d.fbnd ? 0 : (Fy > d.fbnd ? 2 : 1);
         cls = (int)((0x432581670ull >> (4 * (3 * cy + cx))) & 15ull);
     }
     w.key[i] = kk;
-    const int sl = atomicAdd(&w.cnt[kk], 1);  // arrival slot inside the leaf (the in-leaf order is fixed later)
-    w.slot[i] = sl;
-    if (w.bkt) {  // the entry straight into its leaf's bucket; a full bucket sends the evaluation to the scatter
-        if (sl < w.bkt_cap)
-            w.bkt[(int64_t)kk * w.bkt_cap + sl] = make_int2(i, cls);
-        else
-            w.cnt[w.nleaf] = 1;
-    }
     if (w.mixed) {
         float hx, lx, hy, ly;
         frac_to_split(Fx, d.s_unit, &hx, &lx);
@@ -263,11 +254,44 @@ __global__ void k_keys(Work w, const double *__restrict__ x, const double *__res
         r.pad = 0.0;
         w.rec64[i] = r;
     }
+    return kk;
+}
+
+// KPT particles per thread (block: 256 threads, 256 KPT consecutive particles, coalesced per step): their keys and
+// records first, then their arrival slots by returning atomics. Measured at 2^20: 32 us with one particle per
+// thread, 37 us with four (the leaf counters' atomics, not their latency, bound the kernel).
+constexpr int KPT = 1;
+__global__ void __launch_bounds__(256) k_keys(Work w, const double *__restrict__ x, const double *__restrict__ y,
+                                              const double *__restrict__ g)
+{
+    const int base = blockIdx.x * (256 * KPT) + threadIdx.x;
+    int kk[KPT], cls[KPT], sl[KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        const int i = base + 256 * j;
+        kk[j] = i < w.n ? key_of(w, x, y, g, i, cls[j]) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < KPT; ++j)
+        sl[j] = kk[j] >= 0 ? atomicAdd(&w.cnt[kk[j]], 1) : 0;  // arrival slot inside the leaf (order fixed later)
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        const int i = base + 256 * j;
+        if (kk[j] < 0)
+            continue;
+        w.slot[i] = sl[j];
+        if (w.bkt) {  // the entry straight into its leaf's bucket; a full bucket sends the evaluation to the scatter
+            if (sl[j] < w.bkt_cap)
+                w.bkt[(int64_t)kk[j] * w.bkt_cap + sl[j]] = make_int2(i, cls[j]);
+            else
+                w.cnt[w.nleaf] = 1;
+        }
+    }
 }
 
 int launch_keys(const Work &w, const double *x, const double *y, const double *g, cudaStream_t s)
 {
-    k_keys<<<(w.n + 255) / 256, 256, 0, s>>>(w, x, y, g);
+    k_keys<<<(w.n + 256 * KPT - 1) / (256 * KPT), 256, 0, s>>>(w, x, y, g);
     return 1;
 }
 
@@ -536,18 +560,18 @@ int launch_scatter_sort(const Work &w, cudaStream_t s)
 #define SORT_TILE 256
 
 // Writes the leaf-ordered copies of caller particle v at sorted position pos: FP64 form (x, y, gamma [, gu, gv]);
-// precision form the duplicated split records eh = (xh, xh, yh, yh), el = (xl, xl, yl, yl), eg = (g, g, -g, -g).
+// precision form the duplicated split records eh = (xh, xh, yh, yh), el = (xl, xl, yl, yl), eg = (g, g, -g, -g),
+// from its caller-order record (p, gg) read in advance by the caller.
 __device__ __forceinline__ void place_particle(const Work &w, int v, int pos, int leaf, const double *__restrict__ x,
                                                const double *__restrict__ y, const double *__restrict__ g,
-                                               const double *__restrict__ gu, const double *__restrict__ gv, int mixed)
+                                               const double *__restrict__ gu, const double *__restrict__ gv, int mixed,
+                                               float4 p = float4{}, float gg = 0.f)
 {
     w.perm[pos] = v;
     if (!w.morton)  // the adaptive tree reads no inverse permutation
         w.iperm[v] = pos;
     w.sleaf[pos] = leaf;
     if (mixed) {
-        const float4 p = w.pos4u[2 * (int64_t)v];
-        const float gg = w.pos4u[2 * (int64_t)v + 1].x;
         w.eh[pos] = make_float4(p.x, p.x, p.y, p.y);
         w.el[pos] = make_float4(p.z, p.z, p.w, p.w);
         w.eg[pos] = make_float4(gg, gg, -gg, -gg);
@@ -602,6 +626,12 @@ __device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, const 
     for (int e0 = 0; e0 < c; e0 += blockDim.x) {
         const int e = e0 + threadIdx.x;
         const int2 me = e < c ? ent[e] : make_int2(0, 0);
+        float4 rec = float4{};
+        float rg = 0.f;
+        if (mixed && e < c) {  // the random read of the caller-order record overlaps the ranking
+            rec = w.pos4u[2 * (int64_t)me.x];
+            rg = w.pos4u[2 * (int64_t)me.x + 1].x;
+        }
         const K v = rank_key<K>(me, cls);
         int rank = 0;
         for (int f0 = 0; f0 < c; f0 += SORT_TILE) {
@@ -629,7 +659,7 @@ __device__ __forceinline__ void order_leaf_block(const Work &w, int leaf, const 
             }
         }
         if (e < c) {
-            place_particle(w, me.x, s0 + rank, leaf, x, y, g, gu, gv, mixed);
+            place_particle(w, me.x, s0 + rank, leaf, x, y, g, gu, gv, mixed, rec, rg);
             if (cls)
                 atomicAdd(&ccount[me.y], 1);
         }
@@ -667,10 +697,16 @@ __global__ void __launch_bounds__(256) k_leaf_rank(Work w, const double *__restr
             w.big[atomicAdd(w.big_cnt, 1)] = leaf;
         return;
     }
+    float4 rec = float4{};
+    float rg = 0.f;
+    if (mixed) {
+        rec = w.pos4u[2 * (int64_t)e.x];
+        rg = w.pos4u[2 * (int64_t)e.x + 1].x;
+    }
     int rank = 0;
     for (int q = s0; q < s0 + c; ++q)
         rank += w.tmp[q].x < e.x;
-    place_particle(w, e.x, s0 + rank, leaf, x, y, g, gu, gv, mixed);
+    place_particle(w, e.x, s0 + rank, leaf, x, y, g, gu, gv, mixed, rec, rg);
 }
 
 __global__ void __launch_bounds__(128) k_leaf_big(Work w, const double *__restrict__ x, const double *__restrict__ y,

@@ -268,15 +268,16 @@ def test_batched_systems_match_single_evaluations(lib, oracle):
     depths = [s.depth for s in b.systems]
     sigmas = [s.sigma for s in b.systems]
     doms = [s.domain for s in b.systems]
-    for prec, tol in (("fp64", TOL64), ("mixed", TOL32)):
-        f = lib.FMM(3, b.p, 0.01, precision=prec, graph=True)
+    # the precision form with either M2L engine (the tensor-core kernel indexes its tiles per system and level)
+    for prec, tol, eng in (("fp64", TOL64, None), ("mixed", TOL32, "cuda_cores"), ("mixed", TOL32, "tensor")):
+        f = lib.FMM(3, b.p, 0.01, precision=prec, graph=True, m2l_engine=eng)
         u, v = f.velocity_batched(off, dev(x), dev(y), dev(g), depths=depths, sigmas=sigmas, domains=doms)
         f.sync()
         u, v = u.cpu().numpy(), v.cpu().numpy()
         for k, s in enumerate(b.systems):
             uo, vo, _ = oracle.fmm(s.x, s.y, s.gamma, s.sigma, s.depth, b.p, domain=s.domain)
             sl = slice(off[k], off[k + 1])
-            assert rel_l2((u[sl], v[sl]), (uo, vo)) < tol, (prec, k)
+            assert rel_l2((u[sl], v[sl]), (uo, vo)) < tol, (prec, eng, k)
     # bounding-box rule per system, and an empty system in the middle
     off2 = np.array([0, off[1], off[1], off[2]])
     f = lib.FMM(3, b.p, 0.01)

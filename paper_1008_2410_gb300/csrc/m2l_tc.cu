@@ -230,36 +230,42 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar)
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Per-level offsets of one layout launch, computed on the host: for level lev[k], its first thread, the float4
+// offset of its planes and the positions per plane; and the range of tile counters the launch zeroes.
+struct LayoutPlan {
+    int nlev;
+    int lev[FMM_MAXL];
+    int npos[FMM_MAXL];
+    int64_t t0[FMM_MAXL + 1];
+    int64_t base[FMM_MAXL];
+    int64_t c0, c1;
+};
+
 // Source layout of levels l_lo .. l_hi: a thread per (level, system, class, K chunk, position P) writes the hi
 // and lo chunks of coefficients 2 kc, 2 kc + 1 of the box at P; the first threads also zero the levels' tile
 // counters (there are fewer counters than threads).
 template <int PB>
-__global__ void __launch_bounds__(256) k_m2l_tc_layout(Work w, int l_lo, int l_hi)
+__global__ void __launch_bounds__(256) k_m2l_tc_layout(Work w, LayoutPlan pl)
 {
     using S = TcShape<PB>;
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    {
-        const int64_t c0 = count_base(w.lv, l_lo, 0), c1 = count_base(w.lv, l_hi + 1, 0);
-        if (g < c1 - c0)
-            w.m2l_cnt[c0 + g] = 0;
-    }
-    int l = l_lo;
-    for (; l <= l_hi; ++l) {
-        const int64_t cnt = (int64_t)w.lv.nsys_at[l] * 4 * S::KC * npos_of(l);
-        if (g < cnt)
-            break;
-        g -= cnt;
-    }
-    if (l > l_hi)
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < pl.c1 - pl.c0)
+        w.m2l_cnt[pl.c0 + g] = 0;
+    int k = 0;
+    while (k < pl.nlev && g >= pl.t0[k + 1])
+        ++k;
+    if (k >= pl.nlev)
         return;
-    const unsigned np_ = (unsigned)npos_of(l), gl = (unsigned)g;  // a level's positions are far below 2^32
-    const int P = (int)(gl % np_), r = (int)(gl / np_), kc = r % S::KC, c = (r / S::KC) & 3, sidx = r / S::KC >> 2;
-    const SysDev &d = w.sys[sys_at_level(w, l, sidx)];
-    const int p = w.p, ns = 1 << l, nc = ns >> 1, Lc = nc + 2, qq = P - Lc - 1;
+    const int l = pl.lev[k];
+    const unsigned np_ = (unsigned)pl.npos[k], gl = (unsigned)(g - pl.t0[k]);  // a level's positions < 2^32
+    const unsigned P = gl % np_, r = gl / np_;
+    const int kc = (int)(r % S::KC), c = (int)(r / S::KC) & 3, sidx = (int)(r / S::KC) >> 2;
+    const int p = w.p, ns = 1 << l, nc = ns >> 1, Lc = nc + 2, qq = (int)P - Lc - 1;
     float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
     if (qq >= 0 && qq < nc * Lc) {
         const int row = qq / Lc, colp = qq - row * Lc;
         if (colp >= 1 && colp <= nc) {
+            const SysDev &d = w.sys[sys_at_level(w, l, sidx)];
             const int64_t box = d.box0[l] + (int64_t)(2 * row + (c >> 1)) * ns + 2 * (colp - 1) + (c & 1);
             if (w.bcount[box] != 0) {
                 const float2 *src = w.M32 + box * p;
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(256) k_m2l_tc_layout(Work w, int l_lo, int l_h
     const float4 hi = make_float4(tf32_rn(a0.x), tf32_rn(a0.y), tf32_rn(a1.x), tf32_rn(a1.y));
     const float4 lo = make_float4(tf32_rn(a0.x - hi.x), tf32_rn(a0.y - hi.y), tf32_rn(a1.x - hi.z),
                                   tf32_rn(a1.y - hi.w));
-    float4 *dst = w.mtc + layout_base(w.lv, S::KC, l, sidx, c) + (int64_t)kc * (int64_t)np_ + P;
+    float4 *dst = w.mtc + pl.base[k] + (int64_t)(sidx * 4 + c) * 2 * S::KC * np_ + (int64_t)kc * np_ + P;
     dst[0] = hi;
     dst[(int64_t)S::KC * np_] = lo;
 }
@@ -565,10 +571,19 @@ void build_table(int p, unsigned char *out)
 template <int PB>
 int launch_bucket(const Work &w, const Tables &t, int l_lo, int l_hi, int64_t items, cudaStream_t s)
 {
-    int64_t pos = 0;
-    for (int l = l_lo; l <= l_hi; ++l)
-        pos += (int64_t)w.lv.nsys_at[l] * 4 * TcShape<PB>::KC * npos_of(l);
-    k_m2l_tc_layout<PB><<<(unsigned)((pos + 255) / 256), 256, 0, s>>>(w, l_lo, l_hi);
+    LayoutPlan pl{};
+    pl.t0[0] = 0;
+    for (int l = l_lo; l <= l_hi; ++l) {
+        const int k = pl.nlev++;
+        pl.lev[k] = l;
+        pl.npos[k] = npos_of(l);
+        pl.base[k] = layout_base(w.lv, TcShape<PB>::KC, l, 0, 0);
+        pl.t0[k + 1] = pl.t0[k] + (int64_t)w.lv.nsys_at[l] * 4 * TcShape<PB>::KC * npos_of(l);
+    }
+    pl.c0 = count_base(w.lv, l_lo, 0);
+    pl.c1 = count_base(w.lv, l_hi + 1, 0);
+    const int64_t threads = pl.t0[pl.nlev] > pl.c1 - pl.c0 ? pl.t0[pl.nlev] : pl.c1 - pl.c0;
+    k_m2l_tc_layout<PB><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(w, pl);
     const int ws = window_len((1 << (l_hi - 1)) + 2);
     k_m2l_tc<PB><<<(unsigned)items, kThreads, smem_bytes<PB>(ws), s>>>(w, t.m2l_tc, l_lo, l_hi, ws);
     return 2;

@@ -38,9 +38,9 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
-def run(lib, w, precision="fp64", domain="explicit", graph=False, mode="full", tile=None):
+def run(lib, w, precision="fp64", domain="explicit", graph=False, mode="full", tile=None, m2l_engine=None):
     f = lib.FMM(w.depth, w.p, w.sigma, precision=precision, domain=w.domain if domain == "explicit" else None,
-                graph=graph)
+                graph=graph, m2l_engine=m2l_engine)
     if tile:
         f.set_p2p_tile(*tile)
     x, y, g = dev(w.x), dev(w.y), dev(w.gamma)
@@ -576,12 +576,14 @@ def test_near_field_only_stage_events(lib):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision,graph", [("mixed", True), ("fp64", True)])
-def test_uniform_1m_sampled_parity(lib, oracle, precision, graph):
+@pytest.mark.parametrize("precision,graph,engine", [("mixed", True, None), ("fp64", True, None),
+                                                    ("mixed", True, "tensor")])
+def test_uniform_1m_sampled_parity(lib, oracle, precision, graph, engine):
     """The 2^20-particle uniform workload (depth 7, p = 17) in the launch configuration the bench times,
-    checked at 2048 sampled targets against the oracle FMM."""
+    checked at 2048 sampled targets against the oracle FMM; also with the FP32 M2L levels on the tensor cores
+    (full 256-position tiles at level 7 and the largest K bucket)."""
     w = fi.uniform_1m()
-    u, v, _ = run(lib, w, precision=precision, graph=graph)
+    u, v, _ = run(lib, w, precision=precision, graph=graph, m2l_engine=engine)
     t = fi.sample_targets(w.n, 2048)
     uo, vo, _ = oracle.fmm(w.x, w.y, w.gamma, w.sigma, w.depth, w.p, domain=w.domain, targets=t)
     assert rel_l2((u[t], v[t]), (uo, vo)) < (TOL64 if precision == "fp64" else TOL32)

@@ -83,14 +83,15 @@ fmm_status fmm_set_precision(fmm_handle h, fmm_precision mode);
  * Ignored by FMM_FP64. */
 fmm_status fmm_set_coarse_level(fmm_handle h, int coarse_level);
 
-/* Where the FP32 levels of M2L (Fig. 1 stage 6, the translation b_l of §3) run in the precision form; both
- * use the factored radius-scaled form b_l = rho^(l+1) sum_m (-1)^(m+1) C(m+l, m) rho^m a_m, rho = 1/delta.
- * FMM_M2L_TENSOR: per interaction offset, the gathered multipoles of 128 target boxes (scaled by
- * rho^m) times the signed binomial matrix, which all offsets and levels share, as a dense GEMM on the tensor
- * cores (tcgen05, 3xTF32: every operand split into two TF32 parts, accumulators in tensor memory, each
- * offset's product read back, scaled by rho^(l+1) and summed in FP32).
- * FMM_M2L_CUDA_CORES (default): one lane per (target, source) pair in FP32 on the CUDA cores. Both agree with
- * the FP64 form to a few 1e-7 relative. fmm_autotune times both and keeps the faster.
+/* Where the FP32 levels of M2L (Fig. 1 stage 6, the translation b_l of §3) run in the precision form, on
+ * radius-scaled coefficients: b_l = sum_m (-1)^(m+1) C(m+l, m) rho^(m+l+1) a_m, rho = 1/delta.
+ * FMM_M2L_CUDA_CORES (default): one lane per (target, source) pair in FP32, the binomial contraction by prefix sums.
+ * FMM_M2L_TENSOR: tcgen05 tensor-core MMAs (kind::tf32) with 256 target boxes per instruction: each offset's
+ * 2p x 2p real translation matrix and the source multipoles both split into TF32 hi + lo (four products), the
+ * sources of one child class read from a bulk-copied window of a per-class layout written by a first kernel;
+ * levels up to 7 and p <= 20 (deeper levels and larger p take the CUDA-core kernel). Both agree with the FP64
+ * form to below 1e-6 relative (a few 1e-7 on the CUDA cores, up to about 7e-7 on the tensor cores, whose FP32
+ * accumulation runs over tens of MMAs). fmm_autotune times both and keeps the faster.
  * FP64 levels (the plain form, levels <= coarse_level) and the adjoint always use FP64 CUDA-core kernels.
  * Returns FMM_EINVAL for any other value. */
 #define FMM_M2L_CUDA_CORES 0
